@@ -1,0 +1,92 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module only defines workloads: the physical parameters the paper uses
+(arXiv:1206.1779 Sec. 2.1 and Sec. 3), the quadrature sizes of each workload,
+a smooth starting guess with a seeded perturbation, and seeded Euclidean times
+for the Schwinger function.  It holds none of the residual, kernel or Jacobian
+arithmetic; both the CUDA path and the CPU oracle receive its outputs as inputs.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Paper values: alpha(mu^2) = 1 with N_c = 3 gives g^2 N_c = 4 pi * 3 (Sec. 2.1);
+# Z(x_Z) = 0.256 at x_Z = Lambda^2, x_G = 0 and G(x_G)^{-1} = 0 for the scaling
+# solution (Sec. 2.1); delta = -9/44 (Sec. 2); kappa = (93 - sqrt(1201))/98,
+# the closed form of the printed 0.595353 (Sec. 2).
+KAPPA = (93.0 - math.sqrt(1201.0)) / 98.0
+DELTA = -9.0 / 44.0
+G2NC = 12.0 * math.pi
+
+WORKLOADS = {
+    # one FP64 Newton step: N = 16 per function, 64 radial x 32 angular nodes
+    "newton_step_n16": dict(n_cheb=16, n_radial=64, n_angular=32),
+    # FP64 full solve + Schwinger function: N = 64, 256 x 128 nodes
+    "full_solve_n64": dict(n_cheb=64, n_radial=256, n_angular=128),
+    # N = 128 with 512 x 256 nodes
+    "matrix_n128": dict(n_cheb=128, n_radial=512, n_angular=256),
+}
+
+
+def problem(n_cheb: int, n_radial: int, n_angular: int, eps2: float = 1e-6, lambda2: float = 1e6,
+            g2nc: float = G2NC, x_G: float = 0.0, ginv_G: float = 0.0, x_Z: float | None = None,
+            zinv_Z: float = 1.0 / 0.256, kappa: float = KAPPA, delta: float = DELTA,
+            radial_mode: int = 0, extrap_mode: int = 0, precision: int = 0) -> dict:
+    """Problem parameters as a plain dict (field names of dse_problem)."""
+    return dict(n_cheb=int(n_cheb), n_radial=int(n_radial), n_angular=int(n_angular),
+                eps2=float(eps2), lambda2=float(lambda2), g2nc=float(g2nc), x_G=float(x_G),
+                ginv_G=float(ginv_G), x_Z=float(lambda2 if x_Z is None else x_Z), zinv_Z=float(zinv_Z),
+                kappa=float(kappa), delta=float(delta), radial_mode=int(radial_mode),
+                extrap_mode=int(extrap_mode), precision=int(precision))
+
+
+def workload_problem(name: str, **over) -> dict:
+    kw = dict(WORKLOADS[name])
+    kw.update(over)
+    return problem(**kw)
+
+
+def starting_guess(params: dict, seed: int = 0, noise: float = 0.01) -> np.ndarray:
+    """Coefficients (a; b) of a smooth IR-power-law / UV-logarithm guess plus
+    noise * N(0,1)/(j+1) drawn from numpy's default_rng(seed).
+
+    The guess functions are  ln G0 = -kappa ln(x/(1+x)) + delta ln(1 + w ln(1+x))
+    and ln Z0 = 2 kappa ln(x/(1+x)) + gamma ln(1 + w ln(1+x)) + const with
+    w = 11 g^2 N_c / (48 pi^2) and const fixing Z0(lambda2) = 1/zinv_Z; they are
+    interpolated by numpy's Chebyshev routine in the variable
+    s = ln(x / sqrt(eps2 lambda2)) / (ln(lambda2/eps2)/2) and converted to the
+    b_0/2, a_0/2 convention of the expansion.
+    """
+    N = params["n_cheb"]
+    kappa, delta = params["kappa"], params["delta"]
+    gamma = -1.0 - 2.0 * delta
+    w = 11.0 * params["g2nc"] / (48.0 * math.pi ** 2)
+    l0 = 0.5 * math.log(params["eps2"] * params["lambda2"])
+    l1 = 0.5 * math.log(params["lambda2"] / params["eps2"])
+
+    def lnG0(s):
+        x = np.exp(l0 + l1 * s)
+        return -kappa * np.log(x / (1 + x)) + delta * np.log1p(w * np.log1p(x))
+
+    def lnZ0_raw(s):
+        x = np.exp(l0 + l1 * s)
+        return 2 * kappa * np.log(x / (1 + x)) + gamma * np.log1p(w * np.log1p(x))
+
+    zs = -math.log(params["zinv_Z"]) - float(lnZ0_raw(np.array([1.0]))[0])
+    cb = np.polynomial.chebyshev.chebinterpolate(lnG0, N - 1)
+    ca = np.polynomial.chebyshev.chebinterpolate(lambda s: lnZ0_raw(s) + zs, N - 1)
+    cb = np.asarray(cb, dtype=np.float64); ca = np.asarray(ca, dtype=np.float64)
+    cb[0] *= 2.0
+    ca[0] *= 2.0
+    rng = np.random.default_rng(seed)
+    j = np.arange(N)
+    ca = ca + noise * rng.standard_normal(N) / (j + 1)
+    cb = cb + noise * rng.standard_normal(N) / (j + 1)
+    return np.concatenate([ca, cb]).astype(np.float64)
+
+
+def schwinger_times(n_t: int = 4096, seed: int = 0, lo: float = 0.1, hi: float = 50.0) -> np.ndarray:
+    """Euclidean times t ~ U[lo, hi] from numpy's default_rng(seed)."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=int(n_t)).astype(np.float64)
