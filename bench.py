@@ -1,0 +1,348 @@
+"""Benchmark: full FP64 Newton solve of the ghost-gluon DSE system plus the gluon
+Schwinger function (arXiv:1206.1779 Sec. 3 Newton iteration, Sec. 2.2 / 5
+Schwinger function) on GB300, through the C ABI of include/dse.h.
+
+One step = one solve from the seeded starting guess to a dimensionless residual
+below 1e-10 (N = 64 coefficients per dressing function, 256 radial x 128 angular
+Gauss-Legendre nodes, every Newton matrix assembled on the device, LU on the
+device) followed by Delta(t) at 4096 seeded times with 8192 nodes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+
+Under torchrun each rank runs an independent replica (the path does not shard):
+rank 0 prints one JSON line with the whole-job throughput.  --impl reference
+times the FP64 CPU oracle on this host's cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1206_1779_gb300 import inputs  # noqa: E402
+
+METRIC = "Newton-matrix entries*quad-nodes/s and Newton solves/s at 1e-8 accuracy, % FP64 peak"
+UNIT = "entries*nodes/s"
+WORKLOAD = "full_solve_n64"
+N_T = 4096
+N_NODES = 8192
+TOL = 1e-10
+L2_FLUSH_BYTES = 256 << 20
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes per
+# clock per SM (1.25 TFLOP/s nominal) at the sampled SM clock under load.
+N_SM = 152
+FP64_FLOP_PER_CLK_SM = 4.0
+
+
+def flops_per_triple(N: int) -> float:
+    # algorithmic work of the hot kernel per (x, y, theta) triple: the T_j
+    # recurrence (N FMA), two series ln G(z), ln Z(z) (2N FMA) and three
+    # derivative sums weight * phi_j(z) (3N FMA) -> 12 N flops, plus ~50 flops
+    # of geometry, kernels and integrands (log/exp/division counted separately)
+    return 12.0 * N + 50.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_record(kernel_src: str):
+    """DRAM bytes per hot-kernel launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "triple_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if rec.get("kernel_sha256") != h:
+        return None
+    return rec.get("dram_bytes_per_launch_full_size")
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local, dist
+
+
+def max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def run_gb300(args):
+    import torch
+
+    import paper_1206_1779_gb300 as dse
+
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    dse.load()
+    p = inputs.workload_problem(WORKLOAD)
+    N, nr, na = p["n_cheb"], p["n_radial"], p["n_angular"]
+    c0 = inputs.starting_guess(p, seed=0)
+    tt = inputs.schwinger_times(N_T, seed=0)
+    stream = torch.cuda.current_stream()
+
+    t_plan0 = time.perf_counter()
+    plan = dse.Plan(p)
+    t_plan = time.perf_counter() - t_plan0
+    c0_dev = torch.from_numpy(c0).cuda()
+    t_dev = torch.from_numpy(tt).cuda()
+    coef = torch.empty_like(c0_dev)
+    delta = torch.empty_like(t_dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        coef.copy_(c0_dev)
+        it, st = plan.solve(coef, tol=TOL, max_iter=50)
+        plan.schwinger(coef, t_dev, N_NODES, out=delta)
+        return it, st
+
+    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: each step bracketed by CUDA events, L2 flushed between steps
+    clocks = ClockSampler(local)
+    plan.profile(True)
+    launches0 = plan.counters()[0]
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    iters = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, st = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append(it)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches1, n_timed, timed_ms = plan.counters()
+    plan.profile(False)
+    barrier(dist)
+    total_ms = max_over_ranks(dist, float(np.sum(times)))
+
+    matrices_per_step = float(np.mean(iters))
+    entries_nodes = 4.0 * N * N * nr * na
+    units = world * args.steps * matrices_per_step * entries_nodes
+    value = units / (total_ms * 1e-3)
+    solves_per_s = world * args.steps / (total_ms * 1e-3)
+
+    # roofline of the hot kernel: algorithmic FP64 flops per launch / event time
+    Rt = N + 1 + (1 if p["x_G"] > 0 else 0)
+    triples = Rt * nr * na
+    flops_launch = triples * flops_per_triple(N)
+    avg_launch_ms = timed_ms / max(n_timed, 1)
+    achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    traffic = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    c0_host = torch.from_numpy(c0).pin_memory()
+    t_host = torch.from_numpy(tt).pin_memory()
+    out_c = torch.empty_like(c0_host).pin_memory()
+    out_d = torch.empty_like(t_host).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    barrier(dist)
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        coef.copy_(c0_host, non_blocking=True)
+        t_dev.copy_(t_host, non_blocking=True)
+        plan.solve(coef, tol=TOL, max_iter=50)
+        plan.schwinger(coef, t_dev, N_NODES, out=delta)
+        out_c.copy_(coef, non_blocking=True)
+        out_d.copy_(delta, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - w0)
+    e2e_value = world * e2e_steps * matrices_per_step * entries_nodes / e2e_s
+    plan.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(p, c0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_cheb": N, "n_radial": nr, "n_angular": na,
+                       "newton_tol_scaled": TOL, "schwinger": {"n_t": N_T, "n_nodes": N_NODES},
+                       "newton_matrices_per_step": matrices_per_step, "parallelism": "replicas%d" % world,
+                       "l2": "flushed between steps (256 MiB write); working set < 2 MiB"},
+            "solves_per_s": solves_per_s,
+            "plan_create_s": t_plan,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_triple (FP64 radial x angular quadrature)",
+                         "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM at the sampled SM clock",
+                         "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(c0.nbytes + tt.nbytes),
+                    "d2h_bytes_per_step": int(c0.nbytes + tt.nbytes)},
+            "gpu_launches": int(launches1 - launches0),
+            "clocks": clk,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_sample(p, c0, budget_s: float = 12.0):
+    """The oracle as it stands, on this host's cores: Newton matrices of the
+    same workload until about budget_s seconds of CPU work."""
+    from oracle import oracle as O
+    O.build()
+    N, nr, na = p["n_cheb"], p["n_radial"], p["n_angular"]
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        O.newton_matrix(p, c0)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * 4.0 * N * N * nr * na / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d Newton matrices (residual + analytic Jacobian) of %s, N=%d, %dx%d nodes, %.1f s"
+                      % (n, WORKLOAD, N, nr, na, dt)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    p = inputs.workload_problem(WORKLOAD)
+    N, nr, na = p["n_cheb"], p["n_radial"], p["n_angular"]
+    c0 = inputs.starting_guess(p, seed=0)
+    tt = inputs.schwinger_times(N_T, seed=0)
+
+    def step():
+        c, it, _ = O.solve(p, c0, tol=TOL, max_iter=50)
+        O.schwinger(p, c, tt, N_NODES)
+        return it + 1
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    mats = 0
+    for _ in range(args.steps):
+        mats += step()
+    dt = time.perf_counter() - t0
+    value = mats * 4.0 * N * N * nr * na / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n_cheb": N, "n_radial": nr, "n_angular": na,
+                       "newton_tol_scaled": TOL, "schwinger": {"n_t": N_T, "n_nodes": N_NODES}},
+            "solves_per_s": args.steps / dt,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "%d full solves + Schwinger of %s on host cores" % (args.steps, WORKLOAD)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

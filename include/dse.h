@@ -1,0 +1,155 @@
+/*
+ * dse.h -- C ABI of the GB300 (sm_103a) solver for the Landau-gauge ghost-gluon
+ * Dyson-Schwinger system of Hopfer, Alkofer and Haase, "Solving the Ghost-Gluon
+ * System of Yang-Mills Theory on GPUs" (arXiv:1206.1779).
+ *
+ * The ghost and gluon dressing functions G(x), Z(x) are expanded as
+ *   ln G(x) = b_0/2 + sum_{j>=1} b_j T_j(s(x)),   ln Z(x) = a_0/2 + sum_{j>=1} a_j T_j(s(x))
+ * in the mapped variable s(x) = log(x/(Lambda eps)) / log(Lambda/eps)  (Sec. 3).
+ * The unknown vector is  c = (a_0 .. a_{N-1}, b_0 .. b_{N-1})  (2N doubles).
+ * The residual F has the rows  z(x_0..x_{N-1}), g(x_0..x_{N-1})  at the mapped
+ * Chebyshev roots x_i (Sec. 3, residual equations), with
+ *   z(x) = Z(x)^{-1} - Z(x_Z)^{-1} - Pi_Z(x) + Pi_Z(x_Z)
+ *   g(x) = G(x)^{-1} - G(x_G)^{-1} - Pi_G(x) + Pi_G(x_G)
+ * and the self-energies of the ghost and gluon equations of Sec. 2 (bare
+ * ghost-gluon vertex, three-gluon vertex model with a = b = 3 delta, kernels M and
+ * Q including the +15/4 term, O(4) reduction with a sharp cutoff).  Every
+ * integral is a radial Gauss-Legendre rule in ln y over [eps2, lambda2] times an
+ * angular Gauss-Legendre rule in theta over [0, pi]; outside [eps2, lambda2] the
+ * dressing functions follow the IR power laws and UV logarithms of Sec. 2.
+ *
+ * Conventions for every entry point
+ *  - Pointers prefixed d_ are CUDA device pointers (FP64, contiguous), owned by
+ *    the caller, that must stay valid until the work queued on the plan's stream
+ *    has finished.  Pointers prefixed h_ are host pointers.
+ *  - All work is queued on the plan's CUDA stream.  dse_residual,
+ *    dse_newton_matrix, dse_dressing, dse_quadrature and dse_schwinger return
+ *    without waiting; dse_newton_step, dse_solve and dse_plan_status wait for the
+ *    stream.
+ *  - Every call returns DSE_OK (0) or a negative status (below); nothing is
+ *    printed and no C++ exception crosses the ABI.  Argument errors are detected
+ *    before any work is queued.  A non-finite value produced on the device sets a
+ *    sticky flag that the next synchronising call reports (DSE_ERR_NONFINITE).
+ *  - The plan owns its device workspace (allocated once in dse_plan_create) and
+ *    is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef DSE_H
+#define DSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSE_OK 0
+#define DSE_ERR_ARG (-1)           /* bad size, null pointer or parameter       */
+#define DSE_ERR_NONFINITE (-2)     /* NaN/Inf in F, J or the Newton update      */
+#define DSE_ERR_SINGULAR (-3)      /* LU pivot below 1e-300 or not finite       */
+#define DSE_ERR_CUDA (-4)          /* a CUDA runtime call failed                */
+#define DSE_ERR_UNSUPPORTED (-5)   /* mode not implemented in this library      */
+#define DSE_ERR_NOT_CONVERGED (-6) /* dse_solve reached max_iter                */
+
+/* Limits of this build. */
+#define DSE_MAX_CHEB 256           /* N per dressing function                   */
+#define DSE_MAX_NODES 65536        /* n_radial, n_angular                       */
+#define DSE_MAX_SCHWINGER_NODES (1 << 20)
+
+/* Problem definition (Sec. 2.1 and Sec. 3 of the paper give the values used
+ * there: g2nc = 12 pi (alpha(mu^2) = 1, N_c = 3), x_Z = lambda2, Z(x_Z) = 0.256,
+ * x_G = 0, ginv_G = 0 for the scaling solution, delta = -9/44, kappa ~ 0.595353). */
+typedef struct {
+    int n_cheb;       /* N Chebyshev coefficients per dressing function, 1..DSE_MAX_CHEB   */
+    int n_radial;     /* radial Gauss-Legendre nodes in ln y                             */
+    int n_angular;    /* angular Gauss-Legendre nodes in theta                           */
+    double eps2;      /* IR matching point epsilon^2 (> 0)                               */
+    double lambda2;   /* UV cutoff Lambda^2 (> eps2)                                     */
+    double g2nc;      /* g^2 N_c; the equations carry K = g2nc/(2 pi)^3                  */
+    double x_G;       /* ghost subtraction point (>= 0)                                  */
+    double ginv_G;    /* G(x_G)^{-1}                                                     */
+    double x_Z;       /* gluon subtraction point (> 0)                                   */
+    double zinv_Z;    /* Z(x_Z)^{-1}                                                     */
+    double kappa;     /* IR exponent: Z ~ x^{2 kappa}, G ~ x^{-kappa} below eps2         */
+    double delta;     /* ghost anomalous dimension; gamma = -1 - 2 delta                 */
+    int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2]         */
+    int extrap_mode;  /* 0: IR power laws and UV logarithms; 1: constant continuation    */
+    int precision;    /* 0: FP64 throughout                                              */
+} dse_problem;
+
+typedef struct dse_plan dse_plan;
+
+/* Create a plan: validates the problem, allocates the device workspace and runs
+ * the set-up kernels (Gauss-Legendre nodes and weights by Newton iteration on the
+ * Legendre recurrence, mapped radial/angular rules, collocation points; Sec. 2,
+ * Sec. 3, Sec. 4.2).  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  Waits for the set-up kernels.  On failure *out is NULL. */
+int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** out);
+
+/* Release the plan and its workspace (waits for its stream).  NULL is accepted. */
+int dse_plan_destroy(dse_plan* plan);
+
+/* Queue later calls on another stream. */
+int dse_plan_set_stream(dse_plan* plan, void* cuda_stream);
+
+/* Wait for the plan's stream and report the sticky device status
+ * (DSE_OK, DSE_ERR_NONFINITE or DSE_ERR_SINGULAR); the flag is cleared. */
+int dse_plan_status(dse_plan* plan);
+
+/* Copy the plan's rules: d_y, d_W (n_radial; int_{eps2}^{lambda2} dy f ~ sum W_k f(y_k)),
+ * d_theta, d_wt (n_angular; int_0^pi dtheta g ~ sum w_l g(theta_l)), d_x
+ * (n_cheb collocation points, ascending).  Any pointer may be NULL. */
+int dse_quadrature(dse_plan* plan, double* d_y, double* d_W, double* d_theta, double* d_wt,
+                   double* d_x);
+
+/* ln G(x_m), ln Z(x_m) for m < n (Sec. 3 expansion; Sec. 2 IR/UV forms outside
+ * [eps2, lambda2]).  d_coeffs: 2N; d_x: n positive momenta; outputs n each. */
+int dse_dressing(dse_plan* plan, const double* d_coeffs, int n, const double* d_x,
+                 double* d_lnG, double* d_lnZ);
+
+/* Residual F (2N): z(x_0..x_{N-1}) then g(x_0..x_{N-1})  (Sec. 3, residual equations). */
+int dse_residual(dse_plan* plan, const double* d_coeffs, double* d_F);
+
+/* Newton matrix J (2N x 2N, row-major; rows z then g, columns a then b, the
+ * layout of Sec. 3) with every entry dF_i/dc_j an analytic radial x angular
+ * quadrature, and the residual F (d_F may be NULL). */
+int dse_newton_matrix(dse_plan* plan, const double* d_coeffs, double* d_J, double* d_F);
+
+/* One Newton-Raphson step (Sec. 3): J Delta = F by LU with partial pivoting on
+ * the device, then c <- c - rho Delta in place.  h_stats (host, 3 doubles,
+ * nullable): ||F||_inf, ||diag(Z(x_i), G(x_i)) F||_inf (the dimensionless residual
+ * used as the stopping test), ||Delta||_inf, all for the coefficients on entry.
+ * Waits for the stream.  On DSE_ERR_SINGULAR / DSE_ERR_NONFINITE the
+ * coefficients are left unchanged. */
+int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stats);
+
+/* Newton iteration from d_coeffs until the dimensionless residual (h_stats[1]
+ * of dse_newton_step) drops below tol: the first n_relax steps use rho_relax,
+ * the rest rho = 1 (under-relaxation of Sec. 3).  *h_iters receives the number
+ * of steps taken, h_stats (nullable) the stats of the last step.  Returns
+ * DSE_ERR_NOT_CONVERGED after max_iter steps. */
+int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double rho_relax,
+              int n_relax, int* h_iters, double* h_stats);
+
+/* Gluon Schwinger function (Sec. 2.2):
+ *   Delta(t_m) = (1/pi) int_0^inf d|p| cos(t_m |p|) Z(p^2)/p^2,
+ * with n_nodes Gauss-Legendre nodes in u = ln p^2 over [ln eps2, ln lambda2]
+ * (tails outside the range are left out).  The nodes for a given n_nodes are
+ * generated on the device on first use and kept in the plan. */
+int dse_schwinger(dse_plan* plan, const double* d_coeffs, const double* d_t, int n_t,
+                  int n_nodes, double* d_delta);
+
+/* Instrumentation.  dse_plan_profile(plan, 1) makes every later assembly record
+ * CUDA events around its quadrature kernel (the hot kernel) on the plan's
+ * stream; dse_plan_counters waits for the stream and reports the number of
+ * kernels this plan has launched since creation (h_launches), the number of
+ * timed quadrature-kernel launches and their summed device time in ms since
+ * profiling was enabled.  At most 4096 launches are timed per enable; any
+ * pointer may be NULL. */
+int dse_plan_profile(dse_plan* plan, int enable);
+int dse_plan_counters(dse_plan* plan, long long* h_launches, int* h_timed, double* h_timed_ms);
+
+/* Human-readable name of a status code (static storage). */
+const char* dse_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSE_H */

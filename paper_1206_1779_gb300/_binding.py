@@ -1,0 +1,238 @@
+"""ctypes binding of include/dse.h (argument marshalling only).
+
+Device buffers are torch tensors (CUDA, float64, contiguous); the plan follows
+torch's current CUDA stream.  There is no CPU fallback: if the CUDA library is
+missing the import of the binding's entry points fails with an error."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+DSE_OK = 0
+DSE_ERR_ARG = -1
+DSE_ERR_NONFINITE = -2
+DSE_ERR_SINGULAR = -3
+DSE_ERR_CUDA = -4
+DSE_ERR_UNSUPPORTED = -5
+DSE_ERR_NOT_CONVERGED = -6
+DSE_MAX_CHEB = 256
+
+EXPORTS = ["dse_plan_create", "dse_plan_destroy", "dse_plan_set_stream", "dse_plan_status", "dse_quadrature",
+           "dse_dressing", "dse_residual", "dse_newton_matrix", "dse_newton_step", "dse_solve", "dse_schwinger",
+           "dse_plan_profile", "dse_plan_counters", "dse_status_string"]
+
+
+class DseError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (what, status_string(code), code))
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("n_cheb", ctypes.c_int), ("n_radial", ctypes.c_int), ("n_angular", ctypes.c_int),
+        ("eps2", ctypes.c_double), ("lambda2", ctypes.c_double), ("g2nc", ctypes.c_double),
+        ("x_G", ctypes.c_double), ("ginv_G", ctypes.c_double),
+        ("x_Z", ctypes.c_double), ("zinv_Z", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("delta", ctypes.c_double),
+        ("radial_mode", ctypes.c_int), ("extrap_mode", ctypes.c_int), ("precision", ctypes.c_int),
+    ]
+
+    @classmethod
+    def from_params(cls, params: dict) -> "Problem":
+        p = cls()
+        for name, _ in cls._fields_:
+            setattr(p, name, params[name])
+        return p
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the CUDA library (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("dse CUDA library not built (%s); run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    PP = ctypes.POINTER(Problem)
+    sig = {
+        "dse_plan_create": [PP, _VP, ctypes.POINTER(_VP)],
+        "dse_plan_destroy": [_VP],
+        "dse_plan_set_stream": [_VP, _VP],
+        "dse_plan_status": [_VP],
+        "dse_quadrature": [_VP, _VP, _VP, _VP, _VP, _VP],
+        "dse_dressing": [_VP, _VP, ctypes.c_int, _VP, _VP, _VP],
+        "dse_residual": [_VP, _VP, _VP],
+        "dse_newton_matrix": [_VP, _VP, _VP, _VP],
+        "dse_newton_step": [_VP, _VP, ctypes.c_double, _D],
+        "dse_solve": [_VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                      ctypes.POINTER(ctypes.c_int), _D],
+        "dse_schwinger": [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
+        "dse_plan_profile": [_VP, ctypes.c_int],
+        "dse_plan_counters": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_double)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.dse_status_string.argtypes = [ctypes.c_int]
+    L.dse_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().dse_status_string(int(code)).decode()
+    except Exception:  # library not loadable: plain code
+        return "status %d" % code
+
+
+def _check(code: int, what: str) -> None:
+    if code != DSE_OK:
+        raise DseError(code, what)
+
+
+def _dev_ptr(t, n: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if t.device.type != "cuda" or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    if t.numel() < n:
+        raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """A dse_plan for one problem (workspace and quadrature rules on the current device)."""
+
+    def __init__(self, params: dict):
+        import torch
+        self._L = load()
+        self.params = dict(params)
+        self.N = int(params["n_cheb"])
+        self.n_radial = int(params["n_radial"])
+        self.n_angular = int(params["n_angular"])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        prob = Problem.from_params(self.params)
+        h = _VP()
+        _check(self._L.dse_plan_create(ctypes.byref(prob), _stream_ptr(), ctypes.byref(h)), "dse_plan_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.dse_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _sync_stream(self) -> None:
+        self._L.dse_plan_set_stream(self._h, _stream_ptr())
+
+    def _new(self, *shape):
+        import torch
+        return torch.empty(*shape, dtype=torch.float64, device=self.device)
+
+    def quadrature(self):
+        y, W, th, wt, x = (self._new(self.n_radial), self._new(self.n_radial), self._new(self.n_angular),
+                           self._new(self.n_angular), self._new(self.N))
+        self._sync_stream()
+        _check(self._L.dse_quadrature(self._h, *[ctypes.c_void_p(t.data_ptr()) for t in (y, W, th, wt, x)]),
+               "dse_quadrature")
+        return y, W, th, wt, x
+
+    def dressing(self, coeffs, x):
+        n = x.numel()
+        lG, lZ = self._new(n), self._new(n)
+        self._sync_stream()
+        _check(self._L.dse_dressing(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), n, _dev_ptr(x, n, "x"),
+                                    ctypes.c_void_p(lG.data_ptr()), ctypes.c_void_p(lZ.data_ptr())), "dse_dressing")
+        return lG, lZ
+
+    def residual(self, coeffs, out=None):
+        F = out if out is not None else self._new(2 * self.N)
+        self._sync_stream()
+        _check(self._L.dse_residual(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), _dev_ptr(F, 2 * self.N, "F")),
+               "dse_residual")
+        return F
+
+    def newton_matrix(self, coeffs, J=None, F=None):
+        n = 2 * self.N
+        J = J if J is not None else self._new(n, n)
+        F = F if F is not None else self._new(n)
+        self._sync_stream()
+        _check(self._L.dse_newton_matrix(self._h, _dev_ptr(coeffs, n, "coeffs"), _dev_ptr(J, n * n, "J"),
+                                         _dev_ptr(F, n, "F")), "dse_newton_matrix")
+        return J, F
+
+    def newton_step(self, coeffs, rho: float = 1.0):
+        """In-place Newton step; returns (||F||inf, scaled ||F||inf, ||Delta||inf) on entry."""
+        st = (ctypes.c_double * 3)()
+        self._sync_stream()
+        _check(self._L.dse_newton_step(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), float(rho),
+                                       ctypes.cast(st, _D)), "dse_newton_step")
+        return tuple(st)
+
+    def solve(self, coeffs, tol: float = 1e-10, max_iter: int = 50, rho_relax: float = 1.0, n_relax: int = 0):
+        """In-place Newton iteration; returns (iterations, stats of the last step)."""
+        st = (ctypes.c_double * 3)()
+        it = ctypes.c_int(0)
+        self._sync_stream()
+        _check(self._L.dse_solve(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), float(tol), int(max_iter),
+                                 float(rho_relax), int(n_relax), ctypes.byref(it), ctypes.cast(st, _D)), "dse_solve")
+        return it.value, tuple(st)
+
+    def schwinger(self, coeffs, t, n_nodes: int, out=None):
+        n_t = t.numel()
+        out = out if out is not None else self._new(n_t)
+        self._sync_stream()
+        _check(self._L.dse_schwinger(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), _dev_ptr(t, n_t, "t"), n_t,
+                                     int(n_nodes), _dev_ptr(out, n_t, "delta")), "dse_schwinger")
+        return out
+
+    def status(self) -> int:
+        return self._L.dse_plan_status(self._h)
+
+    def profile(self, enable: bool = True) -> None:
+        _check(self._L.dse_plan_profile(self._h, int(bool(enable))), "dse_plan_profile")
+
+    def counters(self):
+        """(kernel launches since creation, timed hot-kernel launches, their device ms)."""
+        n = ctypes.c_longlong(0)
+        k = ctypes.c_int(0)
+        ms = ctypes.c_double(0.0)
+        _check(self._L.dse_plan_counters(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
+               "dse_plan_counters")
+        return n.value, k.value, ms.value

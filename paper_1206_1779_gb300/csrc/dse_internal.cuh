@@ -1,0 +1,83 @@
+// dse_internal.cuh -- internal types and launchers of the sm_103a solver for the
+// ghost-gluon Dyson-Schwinger system (arXiv:1206.1779).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dse.h"
+
+namespace dse {
+
+// Device status bits (sticky until read by a synchronising call).
+enum : int { kStatusNonfinite = 1, kStatusSingular = 2 };
+
+// Derived constants of Sec. 2 / Sec. 3, passed by value to every kernel.
+struct Consts {
+    int N, nr, na, extrap;
+    double eps2, lam2, ln_eps2, ln_lam2;
+    double L0, L1, invL1;          // ln x = L0 + L1 s
+    double K;                      // g^2 Nc / (2 pi)^3
+    double kappa, delta, gam;      // IR exponent, anomalous dimensions
+    double pG, qZ;                 // vertex-model exponents on G and Z
+    double omega;                  // UV log coefficient 11 g^2 Nc / (48 pi^2)
+    double x_G, x_Z, ginv_G, zinv_Z;
+};
+
+// Per radial node: y_k, quadrature weight W_k (Jacobian y_k included), sqrt(y_k).
+struct Rad { double y, W, sy, pad; };
+// Per angular node: weight w_l, sigma_l = sin^2(theta_l/2), sin^2 theta_l, sin^4 theta_l.
+struct Ang { double w, sig, s2, s4; };
+// Per triple-kernel row (external momentum): x, sqrt(x), K/(3x), flags.
+struct Row { double x, sx, pre; int flags, pad; };
+enum : int { kRowGluon = 1, kRowGhost = 2 };
+// Per radial node, per coefficient vector: ln G(y), ln Z(y), G(y), Z(y),
+// p ln G(y) + q ln Z(y), y G(y).
+struct YTab { double lG, lZ, G, Z, pq, yG, pad0, pad1; };
+// Per collocation point: ln G, ln Z, G, Z, 1/G, 1/Z.
+struct XTab { double lG, lZ, G, Z, Ginv, Zinv, pad0, pad1; };
+
+struct TripleArgs {
+    Consts c;
+    int Rt;         // rows handled by the triple kernel
+    int KB;         // radial nodes per block
+    int KS;         // radial splits (gridDim.x)
+    int nch;        // angular chunks of 32 per radial node
+    const Rad* rad;
+    const Ang* ang;
+    const Row* rows;
+    const YTab* ytab;
+    const double* coef;   // 2N: a then b
+    double* Upart;        // [Rt][nr][nch][3]   angular sums per radial node
+    double* Vpart;        // [Rt][KS][3][N]     z-derivative sums per split
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_gauss_legendre(int n, double* inv, double* x, double* w, cudaStream_t s);
+cudaError_t launch_setup_rules(const Consts& c, const double* gl_r, const double* gw_r,
+                               const double* gl_a, const double* gw_a, Rad* rad, Ang* ang, double* theta,
+                               double* xcol, Row* rows, int Rt, cudaStream_t s);
+cudaError_t launch_tables(const Consts& c, const double* coef, const Rad* rad, const double* xcol,
+                          YTab* ytab, double* phiy, XTab* xtab, double* phix, cudaStream_t s);
+cudaError_t launch_triple(bool full, const TripleArgs& a, cudaStream_t s);
+size_t triple_smem_bytes(bool full, int N);
+int triple_block_threads(int N);
+int triple_max_blocks_per_sm(bool full, int N);
+cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch, const Rad* rad,
+                             const Ang* ang, const Row* rows, const YTab* ytab, const double* phiy,
+                             const double* Upart, const double* Vpart, double* D, cudaStream_t s);
+cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix,
+                            const double* D, double* J, double* F, int* status, cudaStream_t s);
+cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab,
+                             double* coef, double rho, double* work, double* stats, int* status,
+                             cudaStream_t s);
+cudaError_t launch_dressing(const Consts& c, const double* coef, int n, const double* x, double* lG,
+                            double* lZ, int* status, cudaStream_t s);
+cudaError_t launch_schwinger_map(const Consts& c, int n, const double* gx, const double* gw, double* pn,
+                                 double* wn, cudaStream_t s);
+cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, const double* pn,
+                             const double* wn, double* sigw, const double* t, int n_t, double* partial,
+                             int nsplit, double* delta, int* status, cudaStream_t s);
+int schwinger_splits(int n_t, int n_nodes);
+
+}  // namespace dse

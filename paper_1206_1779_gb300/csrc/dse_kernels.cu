@@ -1,0 +1,689 @@
+// dse_kernels.cu -- set-up, table, contraction, assembly, Newton-step and
+// Schwinger-function kernels of the sm_103a solver (arXiv:1206.1779).
+#include "dse_internal.cuh"
+#include "dse_series.cuh"
+
+namespace dse {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// ------------------------------------------------------------------------
+// Gauss-Legendre rule (Sec. 2 radial/angular rules; Sec. 5 node generation
+// in parallel): one thread per root pair, Newton iteration on the three-term
+// Legendre recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}, starting from
+// cos(pi (i + 3/4)/(n + 1/2)); the weight 2 / ((1 - x^2) P_n'(x)^2) is taken
+// from one more recurrence pass at the converged root.
+__device__ __forceinline__ void legendre_pair(int n, double r, const double* __restrict__ inv, double& pn,
+                                              double& pnm1) {
+    double p0 = 1.0, p1 = r;
+    for (int k = 1; k < n; ++k) {
+        const double rp1 = r * p1;
+        // p2 = ((2k+1) r p1 - k p0) / (k+1) = r p1 + (r p1 - p0) k/(k+1)
+        const double p2 = fma(rp1 - p0, (double)k * inv[k + 1], rp1);
+        p0 = p1;
+        p1 = p2;
+    }
+    pn = p1;
+    pnm1 = p0;
+}
+
+__global__ void k_inverse_table(int n, double* inv) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= n) inv[k] = k > 0 ? 1.0 / (double)k : 0.0;
+}
+
+__global__ void k_gauss_legendre(int n, const double* __restrict__ inv, double* __restrict__ x,
+                                 double* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int half = (n + 1) / 2;
+    if (i >= half) return;
+    double r = cos(kPi * ((double)i + 0.75) / ((double)n + 0.5));
+    double pn, pm;
+    for (int it = 0; it < 100; ++it) {
+        legendre_pair(n, r, inv, pn, pm);
+        const double dp = (double)n * (r * pn - pm) / (r * r - 1.0);
+        const double dr = pn / dp;
+        r -= dr;
+        if (fabs(dr) <= 1e-16 * (1.0 + fabs(r))) break;
+    }
+    legendre_pair(n, r, inv, pn, pm);
+    const double dp = (double)n * (r * pn - pm) / (r * r - 1.0);
+    const double wt = 2.0 / ((1.0 - r * r) * dp * dp);
+    const int hi = n - 1 - i;
+    x[hi] = r;
+    w[hi] = wt;
+    if (i != hi) {
+        x[i] = -r;
+        w[i] = wt;
+    }
+}
+
+// Mapped rules: radial t = ln y = L0 + L1 tau (weight L1 omega y), angular
+// theta = pi/2 (1 + tau) (weight pi/2 omega), collocation points x_i at the
+// mapped roots s_i = -cos(pi (2i+1)/(2N)) of T_N (Sec. 3), triple-kernel rows.
+__global__ void k_setup_rules(const Consts c, const double* __restrict__ gr, const double* __restrict__ wr,
+                              const double* __restrict__ ga, const double* __restrict__ wa, Rad* __restrict__ rad,
+                              Ang* __restrict__ ang, double* __restrict__ theta, double* __restrict__ xcol,
+                              Row* __restrict__ rows, int Rt) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < c.nr) {
+        const double y = exp(c.L0 + c.L1 * gr[m]);
+        Rad r;
+        r.y = y;
+        r.W = c.L1 * wr[m] * y;
+        r.sy = sqrt(y);
+        r.pad = 0.0;
+        rad[m] = r;
+        return;
+    }
+    int q = m - c.nr;
+    if (q < c.na) {
+        const double th = 0.5 * kPi * (1.0 + ga[q]);
+        const double sh = sin(0.5 * th);
+        const double sn = sin(th);
+        Ang a;
+        a.w = 0.5 * kPi * wa[q];
+        a.sig = sh * sh;
+        a.s2 = sn * sn;
+        a.s4 = a.s2 * a.s2;
+        ang[q] = a;
+        theta[q] = th;
+        return;
+    }
+    q -= c.na;
+    if (q < c.N) {
+        const double s = -cos(kPi * (2.0 * q + 1.0) / (2.0 * c.N));
+        xcol[q] = exp(c.L0 + c.L1 * s);
+        return;
+    }
+    q -= c.N;
+    if (q < Rt) {
+        double x;
+        int flags;
+        if (q < c.N) {
+            const double s = -cos(kPi * (2.0 * q + 1.0) / (2.0 * c.N));
+            x = exp(c.L0 + c.L1 * s);
+            flags = kRowGluon | kRowGhost;
+        } else if (q == c.N) {
+            x = c.x_Z;
+            flags = kRowGluon;
+        } else {
+            x = c.x_G;
+            flags = kRowGhost;
+        }
+        Row r;
+        r.x = x;
+        r.sx = sqrt(x);
+        r.pre = x > 0.0 ? c.K / (3.0 * x) : 0.0;
+        r.flags = flags;
+        r.pad = 0;
+        rows[q] = r;
+    }
+}
+
+// Dressing functions at the radial nodes and collocation points for the
+// current coefficients, with the basis tables phi_j(y_k), phi_j(x_i).
+__global__ void k_tables(const Consts c, const double* __restrict__ coef, const Rad* __restrict__ rad,
+                         const double* __restrict__ xcol, YTab* __restrict__ ytab, double* __restrict__ phiy,
+                         XTab* __restrict__ xtab, double* __restrict__ phix) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const double* a = coef;
+    const double* b = coef + c.N;
+    if (m < c.nr) {
+        const double y = rad[m].y;
+        double lG, lZ;
+        dressing_eval(c, a, b, y, lG, lZ, phiy + (size_t)m * c.N);
+        YTab t;
+        t.lG = lG;
+        t.lZ = lZ;
+        t.G = exp(lG);
+        t.Z = exp(lZ);
+        t.pq = c.pG * lG + c.qZ * lZ;
+        t.yG = y * t.G;
+        t.pad0 = t.pad1 = 0.0;
+        ytab[m] = t;
+        return;
+    }
+    const int i = m - c.nr;
+    if (i < c.N) {
+        double lG, lZ;
+        dressing_eval(c, a, b, xcol[i], lG, lZ, phix + (size_t)i * c.N);
+        XTab t;
+        t.lG = lG;
+        t.lZ = lZ;
+        t.G = exp(lG);
+        t.Z = exp(lZ);
+        t.Ginv = exp(-lG);
+        t.Zinv = exp(-lZ);
+        t.pad0 = t.pad1 = 0.0;
+        xtab[i] = t;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Per external momentum r (rows 0..N-1: collocation points, N: x_Z, N+1: x_G):
+//   y-only contraction  Y_c[j] = sum_k U_c(r,k) phi_j(y_k),  c in {Q, M, G}
+//   z-part              V_c[j] = sum over radial splits of Vpart
+//   D[r] = (dPi_Z/da, dPi_Z/db, dPi_G/da, dPi_G/db, Pi_Z, Pi_G)
+// with  dPi_Z/da_j = K/(3x) q (Y_Q + V_Q),  dPi_Z/db_j = K/(3x) (p (Y_Q + V_Q) + Y_M + V_M),
+//       dPi_G/da_j = -K V_G,  dPi_G/db_j = -K Y_G   (Sec. 2 equations, derivative
+// closure d ln G(u)/d b_j = d ln Z(u)/d a_j = phi_j(u)).
+// For x_G = 0, z = y: the ghost row is y-only and V_G = Y_G.
+constexpr int kRowBlock = 256;
+constexpr int kChunkK = 256;
+
+template <bool FULL>
+__global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt, int KS, int nch,
+                                                         const Rad* __restrict__ rad, const Ang* __restrict__ ang,
+                                                         const Row* __restrict__ rows, const YTab* __restrict__ ytab,
+                                                         const double* __restrict__ phiy,
+                                                         const double* __restrict__ Upart,
+                                                         const double* __restrict__ Vpart, double* __restrict__ D) {
+    __shared__ double sU[kChunkK][3];
+    __shared__ double sPi[3];
+    __shared__ double sS4;
+    const int N = c.N;
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    int rt;
+    bool special = false;  // x_G = 0 ghost row
+    if (r < N) rt = r;
+    else if (r == N) rt = N;
+    else {
+        if (c.x_G > 0.0) rt = N + 1;
+        else { rt = -1; special = true; }
+    }
+    const bool gluon = r <= N;
+    const bool ghost = r != N;
+    if (tid == 0) {
+        sPi[0] = sPi[1] = sPi[2] = 0.0;
+        double s4 = 0.0;
+        if (special)
+            for (int l = 0; l < c.na; ++l) s4 += ang[l].w * ang[l].s4;
+        sS4 = s4;
+    }
+    // each thread owns up to DSE_MAX_CHEB / kRowBlock coefficients
+    constexpr int JPT = (DSE_MAX_CHEB + kRowBlock - 1) / kRowBlock;
+    double Y[3][JPT];
+#pragma unroll
+    for (int q = 0; q < JPT; ++q) Y[0][q] = Y[1][q] = Y[2][q] = 0.0;
+    __syncthreads();
+    for (int kb = 0; kb < c.nr; kb += kChunkK) {
+        const int kn = min(kChunkK, c.nr - kb);
+        for (int kk = tid; kk < kn; kk += kRowBlock) {
+            const int k = kb + kk;
+            double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+            if (special) {
+                const Rad rd = rad[k];
+                const YTab yt = ytab[k];
+                u2 = rd.W * yt.yG * yt.Z / (rd.y * rd.y) * sS4;
+            } else {
+                const double* up = Upart + ((size_t)rt * c.nr + k) * nch * 3;
+                for (int ch = 0; ch < nch; ++ch) {
+                    u0 += up[ch * 3 + 0];
+                    u1 += up[ch * 3 + 1];
+                    u2 += up[ch * 3 + 2];
+                }
+            }
+            sU[kk][0] = u0;
+            sU[kk][1] = u1;
+            sU[kk][2] = u2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (int kk = 0; kk < kn; ++kk) {
+                a0 += sU[kk][0];
+                a1 += sU[kk][1];
+                a2 += sU[kk][2];
+            }
+            sPi[0] += a0;
+            sPi[1] += a1;
+            sPi[2] += a2;
+        }
+        if (FULL) {
+#pragma unroll
+            for (int q = 0; q < JPT; ++q) {
+                const int j = tid + q * kRowBlock;
+                if (j < N) {
+                    for (int kk = 0; kk < kn; ++kk) {
+                        const double ph = phiy[(size_t)(kb + kk) * N + j];
+                        Y[0][q] = fma(sU[kk][0], ph, Y[0][q]);
+                        Y[1][q] = fma(sU[kk][1], ph, Y[1][q]);
+                        Y[2][q] = fma(sU[kk][2], ph, Y[2][q]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const Row rw = rows[rt >= 0 ? rt : 0];
+    const double pre = gluon ? rw.pre : 0.0;
+    double* out = D + (size_t)r * (4 * N + 2);
+    if (FULL) {
+#pragma unroll
+        for (int q = 0; q < JPT; ++q) {
+            const int j = tid + q * kRowBlock;
+            if (j >= N) continue;
+            double VQ = 0.0, VM = 0.0, VG = 0.0;
+            if (!special) {
+                const double* vp = Vpart + (size_t)rt * KS * 3 * N;
+                for (int s = 0; s < KS; ++s) {
+                    VQ += vp[(size_t)s * 3 * N + j];
+                    VM += vp[(size_t)s * 3 * N + N + j];
+                    VG += vp[(size_t)s * 3 * N + 2 * N + j];
+                }
+            } else {
+                VG = Y[2][q];
+            }
+            const double tq = Y[0][q] + VQ;
+            out[j] = gluon ? pre * c.qZ * tq : 0.0;
+            out[N + j] = gluon ? pre * (c.pG * tq + Y[1][q] + VM) : 0.0;
+            out[2 * N + j] = ghost ? -c.K * VG : 0.0;
+            out[3 * N + j] = ghost ? -c.K * Y[2][q] : 0.0;
+        }
+    }
+    if (tid == 0) {
+        out[4 * N] = gluon ? pre * (sPi[0] + sPi[1]) : 0.0;
+        out[4 * N + 1] = ghost ? -c.K * sPi[2] : 0.0;
+    }
+}
+
+// J and F from the per-row derivative vectors (Sec. 3 matrix layout):
+//   J[i][j]       = -Z(x_i)^{-1} phi_j(x_i) - dPi_Z(x_i)/da_j + dPi_Z(x_Z)/da_j
+//   J[i][N+j]     =                         - dPi_Z(x_i)/db_j + dPi_Z(x_Z)/db_j
+//   J[N+i][j]     =                         - dPi_G(x_i)/da_j + dPi_G(x_G)/da_j
+//   J[N+i][N+j]   = -G(x_i)^{-1} phi_j(x_i) - dPi_G(x_i)/db_j + dPi_G(x_G)/db_j
+//   F[i]   = Z(x_i)^{-1} - Z(x_Z)^{-1} - Pi_Z(x_i) + Pi_Z(x_Z)
+//   F[N+i] = G(x_i)^{-1} - G(x_G)^{-1} - Pi_G(x_i) + Pi_G(x_G)
+template <bool FULL>
+__global__ void k_assemble(const Consts c, const XTab* __restrict__ xtab, const double* __restrict__ phix,
+                           const double* __restrict__ D, double* __restrict__ J, double* __restrict__ F,
+                           int* __restrict__ status) {
+    const int N = c.N;
+    const int n = 2 * N;
+    const size_t ld = 4 * (size_t)N + 2;
+    const double* DZ = D + (size_t)N * ld;        // x_Z row
+    const double* DG = D + (size_t)(N + 1) * ld;  // x_G row
+    const size_t total = FULL ? (size_t)n * n : 0;
+    bool bad = false;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total + n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        if (e < total) {
+            const int i = (int)(e / n);
+            const int j = (int)(e % n);
+            double v;
+            if (i < N) {
+                const double* Di = D + (size_t)i * ld;
+                if (j < N) v = -xtab[i].Zinv * phix[(size_t)i * N + j] - Di[j] + DZ[j];
+                else v = -Di[j] + DZ[j];
+            } else {
+                const int ii = i - N;
+                const double* Di = D + (size_t)ii * ld;
+                if (j < N) v = -Di[2 * N + j] + DG[2 * N + j];
+                else v = -xtab[ii].Ginv * phix[(size_t)ii * N + (j - N)] - Di[2 * N + j] + DG[2 * N + j];
+            }
+            J[e] = v;
+            bad |= !isfinite(v);
+        } else {
+            const int i = (int)(e - total);
+            if (F) {
+                double v;
+                if (i < N) v = xtab[i].Zinv - c.zinv_Z - D[(size_t)i * ld + 4 * N] + DZ[4 * N];
+                else {
+                    const int ii = i - N;
+                    v = xtab[ii].Ginv - c.ginv_G - D[(size_t)ii * ld + 4 * N + 1] + DG[4 * N + 1];
+                }
+                F[i] = v;
+                bad |= !isfinite(v);
+            }
+        }
+    }
+    if (bad) atomicOr(status, kStatusNonfinite);
+}
+
+// ------------------------------------------------------------------------
+// Newton step (Sec. 3): J Delta = F by LU with partial pivoting (one block,
+// matrix in place in global memory), then c <- c - rho Delta.  work holds
+// 2n doubles (right-hand side, solution).  stats: ||F||_inf,
+// ||diag(Z(x_i), G(x_i)) F||_inf, ||Delta||_inf.
+constexpr int kLuThreads = 512;
+
+__global__ void __launch_bounds__(kLuThreads) k_lu_newton(const Consts c, double* __restrict__ A,
+                                                          const double* __restrict__ F,
+                                                          const XTab* __restrict__ xtab, double* __restrict__ coef,
+                                                          double rho, double* __restrict__ work,
+                                                          double* __restrict__ stats, int* __restrict__ status) {
+    __shared__ double sv[kLuThreads / 32];
+    __shared__ int si[kLuThreads / 32];
+    __shared__ int s_piv;
+    __shared__ int s_fail;
+    __shared__ double s_red[3][kLuThreads / 32];
+    const int N = c.N;
+    const int n = 2 * N;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int WARPS = kLuThreads / 32;
+    double* b = work;
+    double* x = work + n;
+    // norms of F (and a copy as right-hand side)
+    double mF = 0.0, mS = 0.0;
+    for (int i = tid; i < n; i += kLuThreads) {
+        const double f = F[i];
+        b[i] = f;
+        const double sc = i < N ? xtab[i].Z : xtab[i - N].G;
+        mF = fmax(mF, fabs(f));
+        mS = fmax(mS, fabs(f) * sc);
+        if (!isfinite(f)) mF = INFINITY;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        mF = fmax(mF, __shfl_xor_sync(kFullMask, mF, off));
+        mS = fmax(mS, __shfl_xor_sync(kFullMask, mS, off));
+    }
+    if (lane == 0) {
+        s_red[0][warp] = mF;
+        s_red[1][warp] = mS;
+    }
+    if (tid == 0) s_fail = (*status) & (kStatusNonfinite | kStatusSingular);
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, bb = 0.0;
+        for (int w = 0; w < WARPS; ++w) {
+            a = fmax(a, s_red[0][w]);
+            bb = fmax(bb, s_red[1][w]);
+        }
+        stats[0] = a;
+        stats[1] = bb;
+        stats[2] = 0.0;
+        if (!isfinite(a)) s_fail |= kStatusNonfinite;
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+    for (int k = 0; k < n; ++k) {
+        // pivot search in column k (ties: smallest row index)
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += kLuThreads) {
+            const double v = fabs(A[(size_t)i * n + k]);
+            if (v > best || (v == best && i < bi)) {
+                best = v;
+                bi = i;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(kFullMask, best, off);
+            const int oi = __shfl_xor_sync(kFullMask, bi, off);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            sv[warp] = best;
+            si[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = sv[0];
+            int bix = si[0];
+            for (int w = 1; w < WARPS; ++w)
+                if (sv[w] > bv || (sv[w] == bv && si[w] < bix)) {
+                    bv = sv[w];
+                    bix = si[w];
+                }
+            s_piv = bix;
+            if (!(bv > 1e-300) || !isfinite(bv)) s_fail = kStatusSingular;
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const int p = s_piv;
+        if (p != k) {
+            for (int j = tid; j < n; j += kLuThreads) {
+                const double t = A[(size_t)k * n + j];
+                A[(size_t)k * n + j] = A[(size_t)p * n + j];
+                A[(size_t)p * n + j] = t;
+            }
+            if (tid == 0) {
+                const double t = b[k];
+                b[k] = b[p];
+                b[p] = t;
+            }
+        }
+        __syncthreads();
+        const double dkk = A[(size_t)k * n + k];
+        for (int i = k + 1 + tid; i < n; i += kLuThreads) {
+            const double l = A[(size_t)i * n + k] / dkk;
+            A[(size_t)i * n + k] = l;
+        }
+        __syncthreads();
+        const int m = n - k - 1;
+        const double bk = b[k];
+        for (int idx = tid; idx < m * m; idx += kLuThreads) {
+            const int i = k + 1 + idx / m;
+            const int j = k + 1 + idx % m;
+            A[(size_t)i * n + j] = fma(-A[(size_t)i * n + k], A[(size_t)k * n + j], A[(size_t)i * n + j]);
+        }
+        for (int i = k + 1 + tid; i < n; i += kLuThreads) b[i] = fma(-A[(size_t)i * n + k], bk, b[i]);
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+    // back substitution
+    for (int i = n - 1; i >= 0; --i) {
+        if (tid == 0) x[i] = b[i] / A[(size_t)i * n + i];
+        __syncthreads();
+        const double xi = x[i];
+        for (int t = tid; t < i; t += kLuThreads) b[t] = fma(-A[(size_t)t * n + i], xi, b[t]);
+        __syncthreads();
+    }
+    double mD = 0.0;
+    bool bad = false;
+    for (int i = tid; i < n; i += kLuThreads) {
+        mD = fmax(mD, fabs(x[i]));
+        bad |= !isfinite(x[i]);
+    }
+    for (int off = 16; off > 0; off >>= 1) mD = fmax(mD, __shfl_xor_sync(kFullMask, mD, off));
+    bad = __any_sync(kFullMask, bad);
+    if (lane == 0) {
+        s_red[2][warp] = mD;
+        if (bad) atomicOr(&s_fail, kStatusNonfinite);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int w = 0; w < WARPS; ++w) a = fmax(a, s_red[2][w]);
+        stats[2] = a;
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+    for (int i = tid; i < n; i += kLuThreads) coef[i] = fma(-rho, x[i], coef[i]);
+}
+
+// ------------------------------------------------------------------------
+__global__ void k_dressing(const Consts c, const double* __restrict__ coef, int n, const double* __restrict__ x,
+                           double* __restrict__ lG, double* __restrict__ lZ, int* __restrict__ status) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const double xm = x[m];
+    if (!(xm > 0.0)) {
+        lG[m] = lZ[m] = NAN;
+        atomicOr(status, kStatusNonfinite);
+        return;
+    }
+    double g, z;
+    dressing_eval(c, coef, coef + c.N, xm, g, z, nullptr);
+    lG[m] = g;
+    lZ[m] = z;
+}
+
+// Schwinger function (Sec. 2.2, Sec. 5): nodes in u = ln p^2 over
+// [ln eps2, ln lambda2], p = e^{u/2}, d|p| = (p/2) du.
+__global__ void k_schwinger_map(const Consts c, int n, const double* __restrict__ gx, const double* __restrict__ gw,
+                                double* __restrict__ pn, double* __restrict__ wn) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double u = c.L0 + c.L1 * gx[i];
+    const double p = exp(0.5 * u);
+    pn[i] = p;
+    wn[i] = c.L1 * gw[i] * 0.5 * p;
+}
+
+// sigw_n = w_n Z(p_n^2) / (pi p_n^2)
+__global__ void k_schwinger_weights(const Consts c, const double* __restrict__ coef, int n,
+                                    const double* __restrict__ pn, const double* __restrict__ wn,
+                                    double* __restrict__ sigw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double p = pn[i];
+    const double x = p * p;
+    double g, z;
+    dressing_eval(c, coef, coef + c.N, x, g, z, nullptr);
+    sigw[i] = wn[i] * exp(z) / x / kPi;
+}
+
+// partial[s][m] = sum over nodes of split s of sigw_n cos(t_m p_n).
+// Block: kSchT times x kSchPh phases; nodes staged through shared memory.
+constexpr int kSchT = 32;
+constexpr int kSchPh = 8;
+constexpr int kSchTile = 512;
+
+__global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, const double* __restrict__ pn,
+                                                                  const double* __restrict__ sigw,
+                                                                  const double* __restrict__ t, int n_t,
+                                                                  int nsplit, double* __restrict__ partial) {
+    __shared__ double sp[kSchTile];
+    __shared__ double sw[kSchTile];
+    __shared__ double sred[kSchPh][kSchT];
+    const int tl = threadIdx.x % kSchT;
+    const int ph = threadIdx.x / kSchT;
+    const int m = blockIdx.x * kSchT + tl;
+    const int s = blockIdx.y;
+    const int per = (n_nodes + nsplit - 1) / nsplit;
+    const int n0 = s * per;
+    const int n1 = min(n_nodes, n0 + per);
+    const double tm = m < n_t ? t[m] : 0.0;
+    double acc = 0.0;
+    for (int base = n0; base < n1; base += kSchTile) {
+        const int cnt = min(kSchTile, n1 - base);
+        for (int q = threadIdx.x; q < cnt; q += kSchT * kSchPh) {
+            sp[q] = pn[base + q];
+            sw[q] = sigw[base + q];
+        }
+        __syncthreads();
+        for (int q = ph; q < cnt; q += kSchPh) acc = fma(sw[q], cos(tm * sp[q]), acc);
+        __syncthreads();
+    }
+    sred[ph][tl] = acc;
+    __syncthreads();
+    if (ph == 0 && m < n_t) {
+        double v = 0.0;
+        for (int q = 0; q < kSchPh; ++q) v += sred[q][tl];
+        partial[(size_t)s * n_t + m] = v;
+    }
+}
+
+__global__ void k_schwinger_reduce(int n_t, int nsplit, const double* __restrict__ partial,
+                                   double* __restrict__ delta, int* __restrict__ status) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_t) return;
+    double v = 0.0;
+    for (int s = 0; s < nsplit; ++s) v += partial[(size_t)s * n_t + m];
+    delta[m] = v;
+    if (!isfinite(v)) atomicOr(status, kStatusNonfinite);
+}
+
+inline int blocks_for(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t launch_gauss_legendre(int n, double* inv, double* x, double* w, cudaStream_t s) {
+    // inv: n + 2 doubles of scratch for the table 1/k used by the recurrence
+    k_inverse_table<<<blocks_for(n + 1, 256), 256, 0, s>>>(n, inv);
+    k_gauss_legendre<<<blocks_for((n + 1) / 2, 128), 128, 0, s>>>(n, inv, x, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_rules(const Consts& c, const double* gl_r, const double* gw_r, const double* gl_a,
+                               const double* gw_a, Rad* rad, Ang* ang, double* theta, double* xcol, Row* rows,
+                               int Rt, cudaStream_t s) {
+    const long long total = (long long)c.nr + c.na + c.N + Rt;
+    k_setup_rules<<<blocks_for(total, 128), 128, 0, s>>>(c, gl_r, gw_r, gl_a, gw_a, rad, ang, theta, xcol, rows, Rt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const Consts& c, const double* coef, const Rad* rad, const double* xcol, YTab* ytab,
+                          double* phiy, XTab* xtab, double* phix, cudaStream_t s) {
+    k_tables<<<blocks_for((long long)c.nr + c.N, 64), 64, 0, s>>>(c, coef, rad, xcol, ytab, phiy, xtab, phix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch, const Rad* rad, const Ang* ang,
+                             const Row* rows, const YTab* ytab, const double* phiy, const double* Upart,
+                             const double* Vpart, double* D, cudaStream_t s) {
+    (void)Rt;
+    if (full)
+        k_rowreduce<true><<<c.N + 2, kRowBlock, 0, s>>>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D);
+    else
+        k_rowreduce<false><<<c.N + 2, kRowBlock, 0, s>>>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix, const double* D,
+                            double* J, double* F, int* status, cudaStream_t s) {
+    const long long total = (full ? 4LL * c.N * c.N : 0) + 2LL * c.N;
+    const int nb = blocks_for(total, 256);
+    if (full) k_assemble<true><<<nb, 256, 0, s>>>(c, xtab, phix, D, J, F, status);
+    else k_assemble<false><<<nb, 256, 0, s>>>(c, xtab, phix, D, J, F, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
+                             double* work, double* stats, int* status, cudaStream_t s) {
+    k_lu_newton<<<1, kLuThreads, 0, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dressing(const Consts& c, const double* coef, int n, const double* x, double* lG, double* lZ,
+                            int* status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_dressing<<<blocks_for(n, 128), 128, 0, s>>>(c, coef, n, x, lG, lZ, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schwinger_map(const Consts& c, int n, const double* gx, const double* gw, double* pn, double* wn,
+                                 cudaStream_t s) {
+    k_schwinger_map<<<blocks_for(n, 128), 128, 0, s>>>(c, n, gx, gw, pn, wn);
+    return cudaGetLastError();
+}
+
+int schwinger_splits(int n_t, int n_nodes) {
+    const int tb = (n_t + kSchT - 1) / kSchT;
+    int ns = (4 * 152 + tb - 1) / (tb > 0 ? tb : 1);
+    const int maxs = (n_nodes + kSchTile - 1) / kSchTile;
+    if (ns > maxs) ns = maxs;
+    if (ns < 1) ns = 1;
+    return ns;
+}
+
+cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, const double* pn, const double* wn,
+                             double* sigw, const double* t, int n_t, double* partial, int nsplit, double* delta,
+                             int* status, cudaStream_t s) {
+    k_schwinger_weights<<<blocks_for(n_nodes, 128), 128, 0, s>>>(c, coef, n_nodes, pn, wn, sigw);
+    if (n_t <= 0) return cudaGetLastError();
+    const dim3 grid((n_t + kSchT - 1) / kSchT, nsplit);
+    k_schwinger_sum<<<grid, kSchT * kSchPh, 0, s>>>(n_nodes, pn, sigw, t, n_t, nsplit, partial);
+    k_schwinger_reduce<<<blocks_for(n_t, 256), 256, 0, s>>>(n_t, nsplit, partial, delta, status);
+    return cudaGetLastError();
+}
+
+}  // namespace dse

@@ -1,0 +1,475 @@
+// dse_plan.cu -- plan object and the C ABI entry points declared in include/dse.h.
+// Host code only orchestrates: every step of the computation runs in the
+// kernels of dse_triple.cu and dse_kernels.cu on the plan's stream.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "dse_internal.cuh"
+
+using namespace dse;
+
+struct dse_plan {
+    dse_problem prob;
+    Consts c;
+    cudaStream_t stream;
+    int Rt, KB, KS, nch;
+    // fixed workspace (one allocation)
+    void* ws;
+    Rad* rad;
+    Ang* ang;
+    double* theta;
+    Row* rows;
+    double* xcol;
+    YTab* ytab;
+    double* phiy;
+    XTab* xtab;
+    double* phix;
+    double* Upart;
+    double* Vpart;
+    double* D;
+    double* J;
+    double* F;
+    double* work;
+    double* stats;  // 4 doubles, followed by the int status word
+    int* status;
+    // Schwinger-function rule (allocated on first use, per node count)
+    int sch_n;
+    double* sch;  // gx, gw, inv, pn, wn, sigw
+    double* sch_partial;
+    size_t sch_partial_cap;
+    // pinned host mirror of stats + status
+    double* h_misc;
+    // instrumentation
+    long long launches;
+    int profiling;
+    int n_ev;
+    cudaEvent_t ev[2 * 4096];
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? DSE_OK : DSE_ERR_CUDA; }
+
+int check_problem(const dse_problem* p) {
+    if (!p) return DSE_ERR_ARG;
+    if (p->n_cheb < 1 || p->n_cheb > DSE_MAX_CHEB) return DSE_ERR_ARG;
+    if (p->n_radial < 1 || p->n_radial > DSE_MAX_NODES) return DSE_ERR_ARG;
+    if (p->n_angular < 1 || p->n_angular > DSE_MAX_NODES) return DSE_ERR_ARG;
+    if (!(p->eps2 > 0.0) || !(p->lambda2 > p->eps2) || !isfinite(p->lambda2)) return DSE_ERR_ARG;
+    if (!(p->x_Z > 0.0) || !isfinite(p->x_Z) || !(p->x_G >= 0.0) || !isfinite(p->x_G)) return DSE_ERR_ARG;
+    if (!isfinite(p->g2nc) || !isfinite(p->kappa) || !isfinite(p->delta) || !isfinite(p->ginv_G) ||
+        !isfinite(p->zinv_Z))
+        return DSE_ERR_ARG;
+    if (p->radial_mode != 0 || p->precision != 0) return DSE_ERR_UNSUPPORTED;
+    if (p->extrap_mode != 0 && p->extrap_mode != 1) return DSE_ERR_UNSUPPORTED;
+    return DSE_OK;
+}
+
+Consts make_consts(const dse_problem* p) {
+    Consts c;
+    c.N = p->n_cheb;
+    c.nr = p->n_radial;
+    c.na = p->n_angular;
+    c.extrap = p->extrap_mode;
+    c.eps2 = p->eps2;
+    c.lam2 = p->lambda2;
+    c.ln_eps2 = log(p->eps2);
+    c.ln_lam2 = log(p->lambda2);
+    c.L0 = 0.5 * (c.ln_eps2 + c.ln_lam2);
+    c.L1 = 0.5 * (c.ln_lam2 - c.ln_eps2);
+    c.invL1 = 1.0 / c.L1;
+    c.K = p->g2nc / (8.0 * kPi * kPi * kPi);
+    c.kappa = p->kappa;
+    c.delta = p->delta;
+    c.gam = -1.0 - 2.0 * p->delta;
+    c.pG = -2.0 - 6.0 * p->delta;
+    c.qZ = -3.0 * p->delta;
+    c.omega = 11.0 * p->g2nc / (48.0 * kPi * kPi);
+    c.x_G = p->x_G;
+    c.x_Z = p->x_Z;
+    c.ginv_G = p->ginv_G;
+    c.zinv_Z = p->zinv_Z;
+    return c;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Radial nodes per block: balance Rt * KS blocks over the resident slots.
+void choose_split(dse_plan* pl) {
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int occ = triple_max_blocks_per_sm(true, pl->c.N);
+    if (occ < 1) occ = 1;
+    const double slots = (double)nsm * occ;
+    const int warps = triple_block_threads(pl->c.N) / 32;
+    const int nr = pl->c.nr;
+    double best = 1e300;
+    int bestKB = nr;
+    for (int KB = 1; KB <= nr; ++KB) {
+        const int KS = (nr + KB - 1) / KB;
+        if (KS > 64) continue;
+        const double blocks = (double)pl->Rt * KS;
+        const double waves = ceil(blocks / slots);
+        const double tiles = ceil((double)KB * pl->nch / warps);
+        const double cost = waves * (tiles + 0.25);
+        if (cost < best - 1e-9) {
+            best = cost;
+            bestKB = KB;
+        }
+    }
+    pl->KB = bestKB;
+    pl->KS = (nr + bestKB - 1) / bestKB;
+}
+
+void release_events(dse_plan* pl) {
+    for (int i = 0; i < 2 * pl->n_ev; ++i) cudaEventDestroy(pl->ev[i]);
+    pl->n_ev = 0;
+}
+
+void free_plan(dse_plan* pl) {
+    if (!pl) return;
+    release_events(pl);
+    if (pl->ws) cudaFree(pl->ws);
+    if (pl->sch) cudaFree(pl->sch);
+    if (pl->sch_partial) cudaFree(pl->sch_partial);
+    if (pl->h_misc) cudaFreeHost(pl->h_misc);
+    delete pl;
+}
+
+TripleArgs triple_args(const dse_plan* pl, const double* coef) {
+    TripleArgs a;
+    a.c = pl->c;
+    a.Rt = pl->Rt;
+    a.KB = pl->KB;
+    a.KS = pl->KS;
+    a.nch = pl->nch;
+    a.rad = pl->rad;
+    a.ang = pl->ang;
+    a.rows = pl->rows;
+    a.ytab = pl->ytab;
+    a.coef = coef;
+    a.Upart = pl->Upart;
+    a.Vpart = pl->Vpart;
+    return a;
+}
+
+// tables -> triple kernel -> per-row contraction -> assembly
+int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool full) {
+    cudaError_t e = launch_tables(pl->c, coef, pl->rad, pl->xcol, pl->ytab, pl->phiy, pl->xtab, pl->phix, pl->stream);
+    const bool timed = pl->profiling && pl->n_ev < 4096;
+    if (timed && e == cudaSuccess) {
+        e = cudaEventCreate(&pl->ev[2 * pl->n_ev]);
+        if (e == cudaSuccess) {
+            e = cudaEventCreate(&pl->ev[2 * pl->n_ev + 1]);
+            if (e != cudaSuccess) cudaEventDestroy(pl->ev[2 * pl->n_ev]);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(pl->ev[2 * pl->n_ev], pl->stream);
+    }
+    if (e == cudaSuccess) e = launch_triple(full, triple_args(pl, coef), pl->stream);
+    if (timed && e == cudaSuccess) {
+        e = cudaEventRecord(pl->ev[2 * pl->n_ev + 1], pl->stream);
+        ++pl->n_ev;
+    }
+    pl->launches += 4;
+    if (e == cudaSuccess)
+        e = launch_rowreduce(full, pl->c, pl->Rt, pl->KS, pl->nch, pl->rad, pl->ang, pl->rows, pl->ytab, pl->phiy,
+                             pl->Upart, pl->Vpart, pl->D, pl->stream);
+    if (e == cudaSuccess) e = launch_assemble(full, pl->c, pl->xtab, pl->phix, pl->D, J, F, pl->status, pl->stream);
+    return cuda_status(e);
+}
+
+int read_status(dse_plan* pl, double* h_stats) {
+    cudaError_t e = cudaMemcpyAsync(pl->h_misc, pl->stats, 4 * sizeof(double) + sizeof(int), cudaMemcpyDeviceToHost,
+                                    pl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    int st = 0;
+    memcpy(&st, pl->h_misc + 4, sizeof(int));
+    if (h_stats) memcpy(h_stats, pl->h_misc, 3 * sizeof(double));
+    if (st) {
+        e = cudaMemsetAsync(pl->status, 0, sizeof(int), pl->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+        if (e != cudaSuccess) return DSE_ERR_CUDA;
+    }
+    if (st & kStatusSingular) return DSE_ERR_SINGULAR;
+    if (st & kStatusNonfinite) return DSE_ERR_NONFINITE;
+    return DSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** out) {
+    if (!out) return DSE_ERR_ARG;
+    *out = nullptr;
+    int st = check_problem(problem);
+    if (st) return st;
+    dse_plan* pl = new (std::nothrow) dse_plan();
+    if (!pl) return DSE_ERR_CUDA;
+    memset(pl, 0, sizeof(*pl));
+    pl->prob = *problem;
+    pl->c = make_consts(problem);
+    pl->stream = (cudaStream_t)cuda_stream;
+    const int N = pl->c.N, nr = pl->c.nr, na = pl->c.na;
+    pl->Rt = N + 1 + (problem->x_G > 0.0 ? 1 : 0);
+    pl->nch = (na + 31) / 32;
+    choose_split(pl);
+    const int n = 2 * N;
+    const int gmax = nr > na ? nr : na;
+
+    size_t off = 0;
+    size_t o_rad = off; off = align_up(off + sizeof(Rad) * nr);
+    size_t o_ang = off; off = align_up(off + sizeof(Ang) * na);
+    size_t o_th = off; off = align_up(off + sizeof(double) * na);
+    size_t o_rows = off; off = align_up(off + sizeof(Row) * pl->Rt);
+    size_t o_xcol = off; off = align_up(off + sizeof(double) * N);
+    size_t o_ytab = off; off = align_up(off + sizeof(YTab) * nr);
+    size_t o_phiy = off; off = align_up(off + sizeof(double) * (size_t)nr * N);
+    size_t o_xtab = off; off = align_up(off + sizeof(XTab) * N);
+    size_t o_phix = off; off = align_up(off + sizeof(double) * (size_t)N * N);
+    size_t o_U = off; off = align_up(off + sizeof(double) * (size_t)pl->Rt * nr * pl->nch * 3);
+    size_t o_V = off; off = align_up(off + sizeof(double) * (size_t)pl->Rt * pl->KS * 3 * N);
+    size_t o_D = off; off = align_up(off + sizeof(double) * (size_t)(N + 2) * (4 * N + 2));
+    size_t o_J = off; off = align_up(off + sizeof(double) * (size_t)n * n);
+    size_t o_F = off; off = align_up(off + sizeof(double) * n);
+    size_t o_work = off; off = align_up(off + sizeof(double) * 2 * n);
+    size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + sizeof(int));
+    // Gauss-Legendre scratch (set-up only): nodes/weights for both rules and 1/k
+    size_t o_gl = off; off = align_up(off + sizeof(double) * (2 * (size_t)nr + 2 * (size_t)na + gmax + 2));
+
+    cudaError_t e = cudaMalloc(&pl->ws, off);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return DSE_ERR_CUDA;
+    }
+    char* base = (char*)pl->ws;
+    pl->rad = (Rad*)(base + o_rad);
+    pl->ang = (Ang*)(base + o_ang);
+    pl->theta = (double*)(base + o_th);
+    pl->rows = (Row*)(base + o_rows);
+    pl->xcol = (double*)(base + o_xcol);
+    pl->ytab = (YTab*)(base + o_ytab);
+    pl->phiy = (double*)(base + o_phiy);
+    pl->xtab = (XTab*)(base + o_xtab);
+    pl->phix = (double*)(base + o_phix);
+    pl->Upart = (double*)(base + o_U);
+    pl->Vpart = (double*)(base + o_V);
+    pl->D = (double*)(base + o_D);
+    pl->J = (double*)(base + o_J);
+    pl->F = (double*)(base + o_F);
+    pl->work = (double*)(base + o_work);
+    pl->stats = (double*)(base + o_misc);
+    pl->status = (int*)(base + o_misc + 4 * sizeof(double));
+    double* gl = (double*)(base + o_gl);
+    double* glr = gl;
+    double* gwr = glr + nr;
+    double* gla = gwr + nr;
+    double* gwa = gla + na;
+    double* inv = gwa + na;
+
+    e = cudaMallocHost(&pl->h_misc, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->ws, 0, off, pl->stream);
+    if (e == cudaSuccess) e = launch_gauss_legendre(nr, inv, glr, gwr, pl->stream);
+    if (e == cudaSuccess) e = launch_gauss_legendre(na, inv, gla, gwa, pl->stream);
+    if (e == cudaSuccess)
+        e = launch_setup_rules(pl->c, glr, gwr, gla, gwa, pl->rad, pl->ang, pl->theta, pl->xcol, pl->rows, pl->Rt,
+                               pl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return DSE_ERR_CUDA;
+    }
+    pl->launches = 5;
+    *out = pl;
+    return DSE_OK;
+}
+
+int dse_plan_destroy(dse_plan* plan) {
+    if (!plan) return DSE_OK;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+    return cuda_status(e);
+}
+
+int dse_plan_set_stream(dse_plan* plan, void* cuda_stream) {
+    if (!plan) return DSE_ERR_ARG;
+    plan->stream = (cudaStream_t)cuda_stream;
+    return DSE_OK;
+}
+
+int dse_plan_status(dse_plan* plan) {
+    if (!plan) return DSE_ERR_ARG;
+    return read_status(plan, nullptr);
+}
+
+int dse_quadrature(dse_plan* plan, double* d_y, double* d_W, double* d_theta, double* d_wt, double* d_x) {
+    if (!plan) return DSE_ERR_ARG;
+    const int nr = plan->c.nr, na = plan->c.na, N = plan->c.N;
+    cudaError_t e = cudaSuccess;
+    cudaStream_t s = plan->stream;
+    if (d_y && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_y, sizeof(double), &plan->rad->y, sizeof(Rad), sizeof(double), nr,
+                              cudaMemcpyDeviceToDevice, s);
+    if (d_W && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_W, sizeof(double), &plan->rad->W, sizeof(Rad), sizeof(double), nr,
+                              cudaMemcpyDeviceToDevice, s);
+    if (d_wt && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_wt, sizeof(double), &plan->ang->w, sizeof(Ang), sizeof(double), na,
+                              cudaMemcpyDeviceToDevice, s);
+    if (d_theta && e == cudaSuccess)
+        e = cudaMemcpyAsync(d_theta, plan->theta, sizeof(double) * na, cudaMemcpyDeviceToDevice, s);
+    if (d_x && e == cudaSuccess) e = cudaMemcpyAsync(d_x, plan->xcol, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+    return cuda_status(e);
+}
+
+int dse_dressing(dse_plan* plan, const double* d_coeffs, int n, const double* d_x, double* d_lnG, double* d_lnZ) {
+    if (!plan || n < 0) return DSE_ERR_ARG;
+    if (n == 0) return DSE_OK;
+    if (!d_coeffs || !d_x || !d_lnG || !d_lnZ) return DSE_ERR_ARG;
+    plan->launches += 1;
+    return cuda_status(launch_dressing(plan->c, d_coeffs, n, d_x, d_lnG, d_lnZ, plan->status, plan->stream));
+}
+
+int dse_residual(dse_plan* plan, const double* d_coeffs, double* d_F) {
+    if (!plan || !d_coeffs || !d_F) return DSE_ERR_ARG;
+    return build_system(plan, d_coeffs, nullptr, d_F, false);
+}
+
+int dse_newton_matrix(dse_plan* plan, const double* d_coeffs, double* d_J, double* d_F) {
+    if (!plan || !d_coeffs || !d_J) return DSE_ERR_ARG;
+    return build_system(plan, d_coeffs, d_J, d_F, true);
+}
+
+int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stats) {
+    if (!plan || !d_coeffs || !isfinite(rho)) return DSE_ERR_ARG;
+    int st = build_system(plan, d_coeffs, plan->J, plan->F, true);
+    if (st) return st;
+    cudaError_t e = launch_lu_newton(plan->c, plan->J, plan->F, plan->xtab, d_coeffs, rho, plan->work, plan->stats,
+                                     plan->status, plan->stream);
+    plan->launches += 1;
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    return read_status(plan, h_stats);
+}
+
+int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double rho_relax, int n_relax,
+              int* h_iters, double* h_stats) {
+    if (!plan || !d_coeffs || !(tol > 0.0) || max_iter < 1 || !isfinite(rho_relax) || n_relax < 0) return DSE_ERR_ARG;
+    double st3[3] = {0.0, 0.0, 0.0};
+    int it = 0;
+    int st = DSE_ERR_NOT_CONVERGED;
+    for (; it < max_iter; ++it) {
+        const double rho = it < n_relax ? rho_relax : 1.0;
+        const int s = dse_newton_step(plan, d_coeffs, rho, st3);
+        if (s) {
+            st = s;
+            ++it;
+            break;
+        }
+        if (st3[1] < tol) {
+            st = DSE_OK;
+            ++it;
+            break;
+        }
+    }
+    if (h_iters) *h_iters = it;
+    if (h_stats) memcpy(h_stats, st3, sizeof(st3));
+    return st;
+}
+
+int dse_schwinger(dse_plan* plan, const double* d_coeffs, const double* d_t, int n_t, int n_nodes, double* d_delta) {
+    if (!plan || !d_coeffs || n_t < 0 || n_nodes < 1 || n_nodes > DSE_MAX_SCHWINGER_NODES) return DSE_ERR_ARG;
+    if (n_t > 0 && (!d_t || !d_delta)) return DSE_ERR_ARG;
+    cudaError_t e = cudaSuccess;
+    cudaStream_t s = plan->stream;
+    if (plan->sch_n != n_nodes) {
+        if (plan->sch) {
+            e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) e = cudaFree(plan->sch);
+            plan->sch = nullptr;
+            plan->sch_n = 0;
+            if (e != cudaSuccess) return DSE_ERR_CUDA;
+        }
+        e = cudaMalloc(&plan->sch, sizeof(double) * (6 * (size_t)n_nodes + 2));
+        if (e != cudaSuccess) {
+            plan->sch = nullptr;
+            return DSE_ERR_CUDA;
+        }
+        double* gx = plan->sch;
+        double* gw = gx + n_nodes;
+        double* pn = gw + n_nodes;
+        double* wn = pn + n_nodes;
+        double* inv = wn + 2 * (size_t)n_nodes;  // n + 2 doubles (overlaps nothing live)
+        e = launch_gauss_legendre(n_nodes, inv, gx, gw, s);
+        if (e == cudaSuccess) e = launch_schwinger_map(plan->c, n_nodes, gx, gw, pn, wn, s);
+        plan->launches += 3;
+        if (e != cudaSuccess) return DSE_ERR_CUDA;
+        plan->sch_n = n_nodes;
+    }
+    const int nsplit = schwinger_splits(n_t, n_nodes);
+    const size_t need = (size_t)nsplit * (size_t)(n_t > 0 ? n_t : 1);
+    if (need > plan->sch_partial_cap) {
+        if (plan->sch_partial) {
+            e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) e = cudaFree(plan->sch_partial);
+            plan->sch_partial = nullptr;
+            plan->sch_partial_cap = 0;
+            if (e != cudaSuccess) return DSE_ERR_CUDA;
+        }
+        e = cudaMalloc(&plan->sch_partial, sizeof(double) * need);
+        if (e != cudaSuccess) return DSE_ERR_CUDA;
+        plan->sch_partial_cap = need;
+    }
+    double* pn = plan->sch + 2 * (size_t)n_nodes;
+    double* wn = pn + n_nodes;
+    double* sigw = wn + n_nodes;
+    e = launch_schwinger(plan->c, d_coeffs, n_nodes, pn, wn, sigw, d_t, n_t, plan->sch_partial, nsplit, d_delta,
+                         plan->status, s);
+    plan->launches += n_t > 0 ? 3 : 1;
+    return cuda_status(e);
+}
+
+int dse_plan_profile(dse_plan* plan, int enable) {
+    if (!plan) return DSE_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    release_events(plan);
+    plan->profiling = enable != 0;
+    return cuda_status(e);
+}
+
+int dse_plan_counters(dse_plan* plan, long long* h_launches, int* h_timed, double* h_timed_ms) {
+    if (!plan) return DSE_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    double total = 0.0;
+    for (int i = 0; i < plan->n_ev; ++i) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, plan->ev[2 * i], plan->ev[2 * i + 1]);
+        if (e != cudaSuccess) return DSE_ERR_CUDA;
+        total += ms;
+    }
+    if (h_launches) *h_launches = plan->launches;
+    if (h_timed) *h_timed = plan->n_ev;
+    if (h_timed_ms) *h_timed_ms = total;
+    return DSE_OK;
+}
+
+const char* dse_status_string(int status) {
+    switch (status) {
+        case DSE_OK: return "ok";
+        case DSE_ERR_ARG: return "invalid argument";
+        case DSE_ERR_NONFINITE: return "non-finite value in residual, matrix or update";
+        case DSE_ERR_SINGULAR: return "singular Newton matrix";
+        case DSE_ERR_CUDA: return "CUDA runtime error";
+        case DSE_ERR_UNSUPPORTED: return "unsupported mode";
+        case DSE_ERR_NOT_CONVERGED: return "Newton iteration did not converge";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,302 @@
+// dse_triple.cu -- the fused radial x angular quadrature kernel (the hot path).
+//
+// For every triple (external momentum x_r, radial node y_k, angular node theta_l)
+// it forms z = x + y - 2 sqrt(xy) cos(theta) (as d + 2 b sin^2(theta/2)), evaluates
+// ln G(z), ln Z(z) by the Chebyshev recurrence (Sec. 3; IR/UV forms of Sec. 2
+// outside [eps2, lambda2]) and the three integrands of the ghost and gluon
+// equations of Sec. 2:
+//   hQ = W_k w_l sin^2 Q W                 (gluon loop, vertex model W)
+//   hM = W_k w_l sin^2 M G(y) G(z)         (ghost loop in the gluon equation)
+//   hG = W_k w_l y G(y) sin^4 Z(z)/z^2     (ghost equation)
+// with M = y sin^2/z and Q = quartic(sin^2(theta/2))/(2 z^2), the cancellation-free
+// forms of the printed kernels.  Outputs per block:
+//   Upart[r][k][chunk][3]  warp-shuffle sums over 32 angular nodes of (hQ, hM, hG);
+//   Vpart[r][split][3][N]  sums of (hQ, hM, hG) * phi_j(z) over the block's triples
+// (FULL mode only).  The phi_j(y) part of the Newton-matrix entries depends on y
+// alone and is contracted from Upart afterwards.
+//
+// Data flow per tile of BT triples (one warp = 32 angular nodes of one radial node):
+//   phase A: each thread builds its triple, stores phi_j(z) (j < N) into a
+//            shared-memory row and its three weights;
+//   phase B: thread (group g, coefficient j) accumulates weight * phi_j(z) over
+//            its group's rows: three FP64 FMAs per (triple, j).
+// The block's coefficient vector lives in shared memory (broadcast reads).
+#include "dse_internal.cuh"
+
+namespace dse {
+
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+__host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 : 64; }
+
+__host__ __device__ inline int groups_for(int N, int BT) {
+    const int nact = N < BT ? N : BT;
+    return BT / nact;
+}
+
+__host__ __device__ inline size_t tile_doubles(bool full, int N, int BT) {
+    if (!full) return 0;
+    const size_t t = (size_t)BT * (size_t)(N + 1);
+    const size_t red = (size_t)groups_for(N, BT) * 3u * (size_t)N;
+    return t > red ? t : red;
+}
+
+__host__ __device__ inline size_t smem_doubles(bool full, int N, int BT) {
+    return tile_doubles(full, N, BT) + 3u * (size_t)BT + 2u * (size_t)N;
+}
+
+template <int BT, int NJ, bool FULL>
+__global__ void __launch_bounds__(BT) k_triple(const __grid_constant__ TripleArgs A) {
+    extern __shared__ __align__(16) double smem[];
+    const Consts& c = A.c;
+    const int N = c.N;
+    const int ldT = N + 1;
+    double* sT = smem;
+    double* sh = smem + tile_doubles(FULL, N, BT);
+    double* sa = sh + 3 * BT;
+    double* sb = sa + N;
+    constexpr int WARPS = BT / 32;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+
+    for (int j = tid; j < N; j += BT) {
+        sa[j] = A.coef[j];
+        sb[j] = A.coef[N + j];
+    }
+    const int rt = blockIdx.y;
+    const int ks = blockIdx.x;
+    const Row row = A.rows[rt];
+    const bool gluon = (row.flags & kRowGluon) != 0;
+    const bool ghost = (row.flags & kRowGhost) != 0;
+    const int k0 = ks * A.KB;
+    const int k1 = min(c.nr, k0 + A.KB);
+    const int nch = A.nch;
+    const int nunits = k1 > k0 ? (k1 - k0) * nch : 0;
+
+    // phase-B mapping: NG groups of nact threads, thread owns j = jb + jj*nact
+    const int nact = N < BT ? N : BT;
+    const int NG = BT / nact;
+    const int g = tid / nact;
+    const int jb = tid - g * nact;
+    const bool bact = g < NG;
+    const int mlo = (g * BT) / NG;
+    const int mhi = ((g + 1) * BT) / NG;
+
+    double acc[3][NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) acc[0][jj] = acc[1][jj] = acc[2][jj] = 0.0;
+
+    __syncthreads();
+
+    for (int base = 0; base < nunits; base += WARPS) {
+        const int u = base + warp;
+        double hQ = 0.0, hM = 0.0, hG = 0.0;
+        double* Trow = sT + (size_t)tid * ldT;
+        bool live = false;
+        int k = 0, ch = 0;
+        if (u < nunits) {
+            const int kk = u / nch;
+            ch = u - kk * nch;
+            k = k0 + kk;
+            const int l = ch * 32 + lane;
+            if (l < c.na) {
+                live = true;
+                const Rad rd = A.rad[k];
+                const YTab yt = A.ytab[k];
+                const Ang an = A.ang[l];
+                const double d0 = row.sx - rd.sy;
+                const double d = d0 * d0;
+                const double b = 2.0 * row.sx * rd.sy;
+                const double z = fma(2.0 * b, an.sig, d);
+                const double lz = log(z);
+                double s = (lz - c.L0) * c.invL1;
+                s = fmin(1.0, fmax(-1.0, s));
+                double lg = 0.5 * sb[0];
+                double lzz = 0.5 * sa[0];
+                if (FULL) Trow[0] = 0.5;
+                if (N > 1) {
+                    lg = fma(sb[1], s, lg);
+                    lzz = fma(sa[1], s, lzz);
+                    if (FULL) Trow[1] = s;
+                }
+                double t0 = 1.0, t1 = s;
+                const double s2x = 2.0 * s;
+                for (int j = 2; j < N; ++j) {
+                    const double t2 = fma(s2x, t1, -t0);
+                    t0 = t1;
+                    t1 = t2;
+                    lg = fma(sb[j], t2, lg);
+                    lzz = fma(sa[j], t2, lzz);
+                    if (FULL) Trow[j] = t2;
+                }
+                if (c.extrap == 0) {
+                    if (z < c.eps2) {
+                        const double r = lz - c.ln_eps2;
+                        lg = fma(-c.kappa, r, lg);
+                        lzz = fma(2.0 * c.kappa, r, lzz);
+                    } else if (z > c.lam2) {
+                        const double L = log1p(c.omega * (lz - c.ln_lam2));
+                        lg = fma(c.delta, L, lg);
+                        lzz = fma(c.gam, L, lzz);
+                    }
+                }
+                const double wgt = rd.W * an.w;
+                const double iz = 1.0 / z;
+                const double iz2 = iz * iz;
+                if (ghost) {
+                    const double Zz = exp(lzz);
+                    hG = wgt * yt.yG * an.s4 * Zz * iz2;
+                }
+                if (gluon) {
+                    const double Gz = exp(lg);
+                    const double Wv = exp(yt.pq + c.pG * lg + c.qZ * lzz);
+                    const double dd = d * d, db = d * b, bb = b * b;
+                    const double n0 = 7.5 * dd;
+                    const double n1 = -(48.0 * dd + 18.0 * db + 12.0 * bb);
+                    const double n2 = 48.0 * dd - 48.0 * db - 38.0 * bb;
+                    const double n3 = 96.0 * db + 64.0 * bb;
+                    const double n4 = 16.0 * bb;
+                    const double sg = an.sig;
+                    const double num = fma(sg, fma(sg, fma(sg, fma(sg, n4, n3), n2), n1), n0);
+                    const double Q = 0.5 * num * iz2;
+                    const double M = rd.y * an.s2 * iz;
+                    hQ = wgt * an.s2 * Q * Wv;
+                    hM = wgt * an.s2 * M * yt.G * Gz;
+                }
+            }
+        }
+        if (FULL && !live) {
+            for (int j = 0; j < N; ++j) Trow[j] = 0.0;
+        }
+        // angular sums over the warp's 32 nodes (same radial node for the whole warp)
+        double rQ = hQ, rM = hM, rG = hG;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            rQ += __shfl_xor_sync(kFullMask, rQ, off);
+            rM += __shfl_xor_sync(kFullMask, rM, off);
+            rG += __shfl_xor_sync(kFullMask, rG, off);
+        }
+        if (u < nunits && lane == 0) {
+            double* up = A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3;
+            up[0] = rQ;
+            up[1] = rM;
+            up[2] = rG;
+        }
+        if (FULL) {
+            sh[tid] = hQ;
+            sh[BT + tid] = hM;
+            sh[2 * BT + tid] = hG;
+            __syncthreads();
+            if (bact) {
+                for (int m = mlo; m < mhi; ++m) {
+                    const double q = sh[m];
+                    const double mm = sh[BT + m];
+                    const double gg = sh[2 * BT + m];
+                    const double* Tm = sT + (size_t)m * ldT;
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        const int j = jb + jj * nact;
+                        if (j < N) {
+                            const double t = Tm[j];
+                            acc[0][jj] = fma(q, t, acc[0][jj]);
+                            acc[1][jj] = fma(mm, t, acc[1][jj]);
+                            acc[2][jj] = fma(gg, t, acc[2][jj]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    if (FULL) {
+        // combine the groups in a fixed order and write this block's split
+        double* red = sT;  // [NG][3][N]
+        if (bact) {
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) {
+                const int j = jb + jj * nact;
+                if (j < N) {
+                    red[(g * 3 + 0) * N + j] = acc[0][jj];
+                    red[(g * 3 + 1) * N + j] = acc[1][jj];
+                    red[(g * 3 + 2) * N + j] = acc[2][jj];
+                }
+            }
+        }
+        __syncthreads();
+        double* out = A.Vpart + ((size_t)rt * A.KS + ks) * 3 * (size_t)N;
+        for (int idx = tid; idx < 3 * N; idx += BT) {
+            double s = 0.0;
+            for (int gg = 0; gg < NG; ++gg) s += red[(size_t)gg * 3 * N + idx];
+            out[idx] = s;
+        }
+    }
+}
+
+template <int BT, bool FULL>
+cudaError_t launch_bt(const TripleArgs& a, cudaStream_t s) {
+    const int N = a.c.N;
+    const size_t smem = smem_doubles(FULL, N, BT) * sizeof(double);
+    const dim3 grid(a.KS, a.Rt);
+    const int nj = (N + BT - 1) / BT;
+    cudaError_t e = cudaSuccess;
+    if (nj <= 1) {
+        e = cudaFuncSetAttribute(k_triple<BT, 1, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_triple<BT, 1, FULL><<<grid, BT, smem, s>>>(a);
+    } else if (nj <= 2) {
+        e = cudaFuncSetAttribute(k_triple<BT, 2, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_triple<BT, 2, FULL><<<grid, BT, smem, s>>>(a);
+    } else if (nj <= 4) {
+        e = cudaFuncSetAttribute(k_triple<BT, 4, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_triple<BT, 4, FULL><<<grid, BT, smem, s>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int BT, bool FULL>
+int occupancy_bt(int N) {
+    const size_t smem = smem_doubles(FULL, N, BT) * sizeof(double);
+    const int nj = (N + BT - 1) / BT;
+    int nb = 0;
+    cudaError_t e;
+    if (nj <= 1) {
+        cudaFuncSetAttribute(k_triple<BT, 1, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple<BT, 1, FULL>, BT, smem);
+    } else if (nj <= 2) {
+        cudaFuncSetAttribute(k_triple<BT, 2, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple<BT, 2, FULL>, BT, smem);
+    } else {
+        cudaFuncSetAttribute(k_triple<BT, 4, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple<BT, 4, FULL>, BT, smem);
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+}  // namespace
+
+int triple_block_threads(int N) { return block_threads_for(N); }
+
+size_t triple_smem_bytes(bool full, int N) {
+    return smem_doubles(full, N, block_threads_for(N)) * sizeof(double);
+}
+
+int triple_max_blocks_per_sm(bool full, int N) {
+    if (block_threads_for(N) == 128) return full ? occupancy_bt<128, true>(N) : occupancy_bt<128, false>(N);
+    return full ? occupancy_bt<64, true>(N) : occupancy_bt<64, false>(N);
+}
+
+cudaError_t launch_triple(bool full, const TripleArgs& a, cudaStream_t s) {
+    if (a.KS <= 0 || a.Rt <= 0) return cudaSuccess;
+    if (block_threads_for(a.c.N) == 128) return full ? launch_bt<128, true>(a, s) : launch_bt<128, false>(a, s);
+    return full ? launch_bt<64, true>(a, s) : launch_bt<64, false>(a, s);
+}
+
+}  // namespace dse

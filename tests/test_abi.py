@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI (no GPU work): the library loads, exports every
+entry point declared in include/dse.h, and rejects bad arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1206_1779_gb300 import build, load
+    build.build()
+    return load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dse.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dse_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_match_header(lib):
+    from paper_1206_1779_gb300 import EXPORTS
+    names = declared_functions()
+    assert set(names) == set(EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layout_matches_header():
+    from paper_1206_1779_gb300 import Problem
+    # 3 ints (padded to 16), 9 doubles, 3 ints (padded to 8)
+    assert ctypes.sizeof(Problem) == 16 + 9 * 8 + 16
+
+
+def test_status_strings(lib):
+    for code in [0, -1, -2, -3, -4, -5, -6]:
+        assert lib.dse_status_string(code)
+    assert lib.dse_status_string(-99) == b"unknown status"
+
+
+@pytest.mark.parametrize("bad", [dict(n_cheb=0), dict(n_cheb=300), dict(n_radial=0), dict(n_angular=-3),
+                                 dict(eps2=0.0), dict(lambda2=1e-9), dict(x_Z=0.0), dict(x_G=-1.0),
+                                 dict(g2nc=float("nan"))])
+def test_plan_create_rejects_bad_problem(lib, inputs, bad):
+    from paper_1206_1779_gb300 import DSE_ERR_ARG, Problem
+    p = inputs.problem(8, 16, 16)
+    p.update(bad)
+    prob = Problem.from_params(p)
+    h = ctypes.c_void_p(123)
+    assert lib.dse_plan_create(ctypes.byref(prob), None, ctypes.byref(h)) == DSE_ERR_ARG
+    assert not h.value
+
+
+def test_plan_create_rejects_unsupported_modes(lib, inputs):
+    from paper_1206_1779_gb300 import DSE_ERR_UNSUPPORTED, Problem
+    for over in [dict(radial_mode=1), dict(precision=1), dict(extrap_mode=7)]:
+        p = inputs.problem(8, 16, 16)
+        p.update(over)
+        h = ctypes.c_void_p()
+        assert lib.dse_plan_create(ctypes.byref(Problem.from_params(p)), None, ctypes.byref(h)) == DSE_ERR_UNSUPPORTED
+
+
+def test_null_plan_arguments(lib):
+    from paper_1206_1779_gb300 import DSE_ERR_ARG, DSE_OK
+    assert lib.dse_plan_create(None, None, None) == DSE_ERR_ARG
+    assert lib.dse_plan_destroy(None) == DSE_OK
+    assert lib.dse_residual(None, None, None) == DSE_ERR_ARG
+    assert lib.dse_newton_matrix(None, None, None, None) == DSE_ERR_ARG
+    assert lib.dse_newton_step(None, None, 1.0, None) == DSE_ERR_ARG
+    assert lib.dse_schwinger(None, None, None, 0, 1, None) == DSE_ERR_ARG
+    assert lib.dse_plan_status(None) == DSE_ERR_ARG
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1206_1779_gb300 import _binding
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_binding._build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _binding.load()

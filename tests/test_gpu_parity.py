@@ -1,0 +1,200 @@
+"""GPU parity: the sm_103a path through the C ABI against the FP64 CPU oracle
+(arXiv:1206.1779 Sec. 2-3: quadrature rules, dressing functions with IR/UV
+continuation, residual, Newton matrix, Newton step and solve; Sec. 2.2 / 5:
+Schwinger function).  Bar: relative 1e-11 per entry with a 1e-13 row floor."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import matrix_ok, residual_ok, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dse():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import paper_1206_1779_gb300 as m
+    m.load(build_if_missing=True)
+    return m
+
+
+CASES = {
+    "tiny": dict(n_cheb=2, n_radial=4, n_angular=4),
+    "n3": dict(n_cheb=3, n_radial=5, n_angular=7),
+    "ragged": dict(n_cheb=13, n_radial=37, n_angular=45),
+    "wide_angular": dict(n_cheb=9, n_radial=11, n_angular=100),
+    "ghost_point": dict(n_cheb=7, n_radial=30, n_angular=33, x_G=3e-3, ginv_G=0.02, x_Z=4e4),
+    "constant_extrap": dict(n_cheb=8, n_radial=24, n_angular=32, extrap_mode=1, zinv_Z=2.5),
+    "narrow_range": dict(n_cheb=11, n_radial=40, n_angular=64, eps2=1e-3, lambda2=1e3, x_Z=1e3),
+    "newton_step_n16": dict(n_cheb=16, n_radial=64, n_angular=32),
+    "n100": dict(n_cheb=100, n_radial=64, n_angular=32),
+    "n160": dict(n_cheb=160, n_radial=40, n_angular=24),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_newton_matrix_parity(dse, oracle, inputs, name):
+    p = inputs.problem(**CASES[name])
+    c = inputs.starting_guess(p, seed=11)
+    with dse.Plan(p) as plan:
+        J, F = plan.newton_matrix(to_dev(c))
+        J, F = to_host(J), to_host(F)
+        Fr = to_host(plan.residual(to_dev(c)))
+        assert plan.status() == dse.DSE_OK
+    Jo, Fo = oracle.newton_matrix(p, c)
+    ok, rel, nbad = matrix_ok(J, Jo)
+    assert ok, (name, rel, nbad)
+    okF, relF = residual_ok(F, Fo, Jo)
+    assert okF, (name, relF)
+    okR, relR = residual_ok(Fr, Fo, Jo)
+    assert okR, (name, relR)
+
+
+def test_quadrature_and_collocation(dse, oracle, inputs):
+    p = inputs.problem(10, 77, 41)
+    y, W, th, wt = oracle.quadrature(p)
+    xo = oracle.collocation(p)
+    with dse.Plan(p) as plan:
+        gy, gW, gth, gwt, gx = [to_host(t) for t in plan.quadrature()]
+    for a, b in [(gy, y), (gW, W), (gth, th), (gwt, wt), (gx, xo)]:
+        assert np.allclose(a, b, rtol=1e-14, atol=0)
+
+
+def test_dressing_parity_all_regions(dse, oracle, inputs):
+    for extrap in [0, 1]:
+        p = inputs.problem(24, 8, 8, extrap_mode=extrap)
+        c = inputs.starting_guess(p, seed=5)
+        x = np.exp(np.linspace(math.log(1e-12), math.log(1e12), 301))
+        lG, lZ = oracle.dressing(p, c, x)
+        with dse.Plan(p) as plan:
+            gG, gZ = plan.dressing(to_dev(c), to_dev(x))
+            gG, gZ = to_host(gG), to_host(gZ)
+        assert np.allclose(gG, lG, rtol=1e-13, atol=1e-13)
+        assert np.allclose(gZ, lZ, rtol=1e-13, atol=1e-13)
+
+
+def test_full_size_matrix_parity(dse, oracle, inputs):
+    # the launch configuration of the benchmark: N = 64, 256 x 128 nodes
+    p = inputs.workload_problem("full_solve_n64")
+    c = inputs.starting_guess(p, seed=0)
+    with dse.Plan(p) as plan:
+        J, F = plan.newton_matrix(to_dev(c))
+        J, F = to_host(J), to_host(F)
+    Jo, Fo = oracle.newton_matrix(p, c)
+    ok, rel, nbad = matrix_ok(J, Jo)
+    assert ok, (rel, nbad)
+    assert residual_ok(F, Fo, Jo)[0]
+
+
+def test_newton_step_parity(dse, oracle, inputs):
+    p = inputs.workload_problem("newton_step_n16")
+    c = inputs.starting_guess(p, seed=0)
+    co, so = oracle.newton_step(p, c, rho=0.7)
+    with dse.Plan(p) as plan:
+        ct = to_dev(c)
+        sg = plan.newton_step(ct, rho=0.7)
+        cg = to_host(ct)
+    # the update solves a system with cond ~1e15 (rows of very different scale):
+    # compare the update on the scale of the step
+    d_o = c - co
+    d_g = c - cg
+    assert np.max(np.abs(d_g - d_o)) <= 1e-8 * np.max(np.abs(d_o))
+    assert abs(sg[0] / so[0] - 1) < 1e-10
+    assert abs(sg[1] / so[1] - 1) < 1e-10
+    assert abs(sg[2] / so[2] - 1) < 1e-8
+
+
+def test_solve_parity(dse, oracle, inputs):
+    p = inputs.workload_problem("newton_step_n16")
+    c0 = inputs.starting_guess(p, seed=0)
+    co, ito, _ = oracle.solve(p, c0, tol=1e-10)
+    with dse.Plan(p) as plan:
+        ct = to_dev(c0)
+        it, st = plan.solve(ct, tol=1e-10, max_iter=30)
+        cg = to_host(ct)
+        x = np.exp(np.linspace(math.log(1e-6), math.log(1e6), 97))
+        gG, gZ = plan.dressing(ct, to_dev(x))
+        gG, gZ = to_host(gG), to_host(gZ)
+    assert st[1] < 1e-10
+    assert abs(it - (ito + 1)) <= 1
+    lG, lZ = oracle.dressing(p, co, x)
+    # converged dressing functions agree to 1e-8 (the accuracy target of a solve)
+    assert np.max(np.abs(gG - lG)) < 1e-8 and np.max(np.abs(gZ - lZ)) < 1e-8
+
+
+@pytest.mark.parametrize("n_t,n_nodes", [(1, 1), (37, 129), (300, 1000)])
+def test_schwinger_parity(dse, oracle, inputs, n_t, n_nodes):
+    p = inputs.problem(12, 8, 8)
+    c = inputs.starting_guess(p, seed=2)
+    t = inputs.schwinger_times(n_t, seed=4)
+    do = oracle.schwinger(p, c, t, n_nodes)
+    pn, wn = oracle.schwinger_nodes(p, n_nodes)
+    lG, lZ = oracle.dressing(p, c, pn * pn)
+    scale = np.sum(np.abs(wn * np.exp(lZ) / (pn * pn))) / math.pi
+    with dse.Plan(p) as plan:
+        dg = to_host(plan.schwinger(to_dev(c), to_dev(t), n_nodes))
+    assert np.all(np.abs(dg - do) <= 1e-11 * np.abs(do) + 1e-14 * scale)
+
+
+def test_schwinger_full_size(dse, oracle, inputs):
+    p = inputs.workload_problem("full_solve_n64")
+    c = inputs.starting_guess(p, seed=0)
+    t = inputs.schwinger_times(4096, seed=0)
+    do = oracle.schwinger(p, c, t, 8192)
+    pn, wn = oracle.schwinger_nodes(p, 8192)
+    lG, lZ = oracle.dressing(p, c, pn * pn)
+    scale = np.sum(np.abs(wn * np.exp(lZ) / (pn * pn))) / math.pi
+    with dse.Plan(p) as plan:
+        dg = to_host(plan.schwinger(to_dev(c), to_dev(t), 8192))
+        dg2 = to_host(plan.schwinger(to_dev(c), to_dev(t), 8192))
+    assert np.array_equal(dg, dg2)  # fixed reduction order
+    assert np.all(np.abs(dg - do) <= 1e-11 * np.abs(do) + 1e-14 * scale)
+
+
+def test_deterministic_matrix(dse, inputs):
+    p = inputs.problem(20, 48, 64)
+    c = inputs.starting_guess(p, seed=3)
+    with dse.Plan(p) as plan:
+        J1, _ = plan.newton_matrix(to_dev(c))
+        J2, _ = plan.newton_matrix(to_dev(c))
+        assert np.array_equal(to_host(J1), to_host(J2))
+
+
+def test_nonfinite_coefficients_reported(dse, inputs):
+    p = inputs.problem(6, 16, 16)
+    c = inputs.starting_guess(p, seed=0)
+    c[3] = float("nan")
+    with dse.Plan(p) as plan:
+        ct = to_dev(c)
+        with pytest.raises(dse.DseError) as ei:
+            plan.newton_step(ct)
+        assert ei.value.code == dse.DSE_ERR_NONFINITE
+        # coefficients untouched, plan usable afterwards
+        assert np.isnan(to_host(ct)[3])
+        c2 = inputs.starting_guess(p, seed=0)
+        plan.newton_step(to_dev(c2))
+
+
+def test_solve_not_converged_status(dse, inputs):
+    p = inputs.problem(6, 16, 16)
+    c = inputs.starting_guess(p, seed=0)
+    with dse.Plan(p) as plan:
+        with pytest.raises(dse.DseError) as ei:
+            plan.solve(to_dev(c), tol=1e-10, max_iter=2)
+        assert ei.value.code == dse.DSE_ERR_NOT_CONVERGED
+
+
+def test_binding_rejects_bad_tensors(dse, inputs):
+    import torch
+    p = inputs.problem(4, 8, 8)
+    with dse.Plan(p) as plan:
+        with pytest.raises(ValueError):
+            plan.residual(torch.zeros(8, dtype=torch.float32, device="cuda"))
+        with pytest.raises(ValueError):
+            plan.residual(torch.zeros(8, dtype=torch.float64))
+        with pytest.raises(ValueError):
+            plan.residual(torch.zeros(3, dtype=torch.float64, device="cuda"))
