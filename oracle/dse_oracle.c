@@ -267,8 +267,8 @@ int dse_ref_kernels(double x, double y, double theta, double* M, double* Q, doub
  * Pi_Z(x) = K/(3x) int dy int dtheta sin^2(theta) [Q W + M G(y) G(z)],
  *   W = (G(y) G(z))^{-2-6 delta} (Z(y) Z(z))^{-3 delta}.
  * Gradients: d ln G(u)/d b_j = d ln Z(u)/d a_j = phi_j(u) for u in {y, z}. */
-int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
-                        double* PiG, double* PiZ, double* d_PiG, double* d_PiZ) {
+static int self_energy_impl(const dse_ref_problem* p, const double* c, double x, int magnitudes,
+                            double* PiG, double* PiZ, double* d_PiG, double* d_PiZ) {
     int st = check_problem(p);
     if (st) return st;
     if (!c || !(x >= 0.0) || p->n_cheb > 1024) return DSE_REF_ERR_ARG;
@@ -318,29 +318,51 @@ int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
             double wgt = W[kk] * wt[l];
             /* ghost integrand y G(y) sin^4 Z(z)/z^2 */
             double fG = wgt * y[kk] * Gy * s2 * s2 * Zz / (z * z);
-            ns_add(sG, fG);
             double hQ = 0.0, hM = 0.0;
             if (gluon) {
                 double Wv = exp(k.pG * (lGy + lGz) + k.qZ * (lZy + lZz));
                 hQ = wgt * s2 * Q * Wv;
                 hM = wgt * s2 * M * Gy * Gz;
-                ns_add(sZ, hQ + hM);
             }
-            if (want_d) {
-                for (int j = 0; j < N; ++j) {
-                    double ph = phiy[j] + phiz[j];
-                    if (gluon) {
-                        ns_add(&gZa[j], k.qZ * hQ * ph);
-                        ns_add(&gZb[j], (k.pG * hQ + hM) * ph);
+            if (!magnitudes) {
+                ns_add(sG, fG);
+                if (gluon) ns_add(sZ, hQ + hM);
+                if (want_d) {
+                    for (int j = 0; j < N; ++j) {
+                        double ph = phiy[j] + phiz[j];
+                        if (gluon) {
+                            ns_add(&gZa[j], k.qZ * hQ * ph);
+                            ns_add(&gZb[j], (k.pG * hQ + hM) * ph);
+                        }
+                        ns_add(&gGa[j], fG * phiz[j]);
+                        ns_add(&gGb[j], fG * phiy[j]);
                     }
-                    ns_add(&gGa[j], fG * phiz[j]);
-                    ns_add(&gGb[j], fG * phiy[j]);
+                }
+            } else {
+                /* sums of the magnitudes of every summand, term by term */
+                ns_add(sG, fabs(fG));
+                if (gluon) ns_add(sZ, fabs(hQ) + fabs(hM));
+                if (want_d) {
+                    for (int j = 0; j < N; ++j) {
+                        double ph = fabs(phiy[j]) + fabs(phiz[j]);
+                        if (gluon) {
+                            ns_add(&gZa[j], fabs(k.qZ * hQ) * ph);
+                            ns_add(&gZb[j], (fabs(k.pG * hQ) + fabs(hM)) * ph);
+                        }
+                        ns_add(&gGa[j], fabs(fG * phiz[j]));
+                        ns_add(&gGb[j], fabs(fG * phiy[j]));
+                    }
                 }
             }
         }
     }
     double preZ = gluon ? k.K / (3.0 * x) : 0.0;
-    if (PiG) *PiG = -k.K * ns_val(sG);
+    double preG = -k.K;
+    if (magnitudes) {
+        preZ = fabs(preZ);
+        preG = fabs(preG);
+    }
+    if (PiG) *PiG = preG * ns_val(sG);
     if (PiZ) *PiZ = gluon ? preZ * ns_val(sZ) : 0.0;
     for (int j = 0; j < N; ++j) {
         if (d_PiZ) {
@@ -348,12 +370,17 @@ int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
             d_PiZ[N + j] = preZ * ns_val(&gZb[j]);
         }
         if (d_PiG) {
-            d_PiG[j] = -k.K * ns_val(&gGa[j]);
-            d_PiG[N + j] = -k.K * ns_val(&gGb[j]);
+            d_PiG[j] = preG * ns_val(&gGa[j]);
+            d_PiG[N + j] = preG * ns_val(&gGb[j]);
         }
     }
     free(y); free(W); free(th); free(wt); free(phiy); free(phiz); free(acc);
     return DSE_REF_OK;
+}
+
+int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
+                        double* PiG, double* PiZ, double* d_PiG, double* d_PiZ) {
+    return self_energy_impl(p, c, x, 0, PiG, PiZ, d_PiG, d_PiZ);
 }
 
 /* ------------------------------------------------ residual and matrix ---- */
@@ -362,7 +389,7 @@ int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
  *   z(x_i) = Z(x_i)^{-1} - Z(x_Z)^{-1} - Pi_Z(x_i) + Pi_Z(x_Z)
  *   g(x_i) = G(x_i)^{-1} - G(x_G)^{-1} - Pi_G(x_i) + Pi_G(x_G)
  * and the Newton matrix of their derivatives; rows (z; g), columns (a; b). */
-static int assemble(const dse_ref_problem* p, const double* c, double* J, double* F) {
+static int assemble(const dse_ref_problem* p, const double* c, int magnitudes, double* J, double* F) {
     int st = check_problem(p);
     if (st) return st;
     if (!c || p->n_cheb > 1024) return DSE_REF_ERR_ARG;
@@ -384,9 +411,9 @@ static int assemble(const dse_ref_problem* p, const double* c, double* J, double
 #pragma omp parallel for schedule(dynamic, 1)
     for (int r = 0; r < N + 2; ++r) {
         double xr = r < N ? xc[r] : (r == N ? p->x_Z : p->x_G);
-        rst[r] = dse_ref_self_energy(p, c, xr, &PiGr[r], &PiZr[r],
-                                     want_d ? &dG[(size_t)r * 2 * N] : NULL,
-                                     want_d ? &dZ[(size_t)r * 2 * N] : NULL);
+        rst[r] = self_energy_impl(p, c, xr, magnitudes, &PiGr[r], &PiZr[r],
+                                  want_d ? &dG[(size_t)r * 2 * N] : NULL,
+                                  want_d ? &dZ[(size_t)r * 2 * N] : NULL);
     }
     for (int r = 0; r < N + 2; ++r)
         if (rst[r]) { st = rst[r]; break; }
@@ -398,9 +425,12 @@ static int assemble(const dse_ref_problem* p, const double* c, double* J, double
             double lG, lZ;
             dressing(p, &k, c, xc[i], &lG, &lZ, phi);
             double Zinv = exp(-lZ), Ginv = exp(-lG);
-            if (F) {
+            if (F && !magnitudes) {
                 F[i] = Zinv - p->zinv_Z - PiZr[i] + PiZr[N];
                 F[N + i] = Ginv - p->ginv_G - PiGr[i] + PiGr[N + 1];
+            } else if (F) {
+                F[i] = Zinv + fabs(p->zinv_Z) + PiZr[i] + PiZr[N];
+                F[N + i] = Ginv + fabs(p->ginv_G) + PiGr[i] + PiGr[N + 1];
             }
             if (want_d) {
                 const double* dZi = &dZ[(size_t)i * 2 * N];
@@ -411,8 +441,13 @@ static int assemble(const dse_ref_problem* p, const double* c, double* J, double
                     /* d Z(x)^{-1}/d a_j = -Z(x)^{-1} phi_j(x); same for G with b_j */
                     double diagZ = j < N ? -Zinv * phi[j] : 0.0;
                     double diagG = j >= N ? -Ginv * phi[j - N] : 0.0;
-                    Jz[j] = diagZ - dZi[j] + dZref[j];
-                    Jg[j] = diagG - dGi[j] + dGref[j];
+                    if (!magnitudes) {
+                        Jz[j] = diagZ - dZi[j] + dZref[j];
+                        Jg[j] = diagG - dGi[j] + dGref[j];
+                    } else {
+                        Jz[j] = fabs(diagZ) + dZi[j] + dZref[j];
+                        Jg[j] = fabs(diagG) + dGi[j] + dGref[j];
+                    }
                 }
             }
         }
@@ -432,12 +467,17 @@ static int assemble(const dse_ref_problem* p, const double* c, double* J, double
 
 int dse_ref_residual(const dse_ref_problem* p, const double* c, double* F) {
     if (!F) return DSE_REF_ERR_ARG;
-    return assemble(p, c, NULL, F);
+    return assemble(p, c, 0, NULL, F);
 }
 
 int dse_ref_newton_matrix(const dse_ref_problem* p, const double* c, double* J, double* F) {
     if (!J) return DSE_REF_ERR_ARG;
-    return assemble(p, c, J, F);
+    return assemble(p, c, 0, J, F);
+}
+
+int dse_ref_newton_matrix_magnitudes(const dse_ref_problem* p, const double* c, double* A, double* AF) {
+    if (!A) return DSE_REF_ERR_ARG;
+    return assemble(p, c, 1, A, AF);
 }
 
 /* --------------------------------------------------------------- LU ---- */
@@ -508,7 +548,7 @@ int dse_ref_newton_step(const dse_ref_problem* p, double* c, double rho, double*
         free(J); free(F); free(D); free(xc); free(lG); free(lZ);
         return DSE_REF_ERR_ARG;
     }
-    st = assemble(p, c, J, F);
+    st = assemble(p, c, 0, J, F);
     if (!st) st = dse_ref_lu_solve(n, J, F, D);
     if (!st) {
         dse_ref_collocation(p, xc);

@@ -94,6 +94,12 @@ int dse_ref_residual(const dse_ref_problem* p, const double* c, double* F);
 /* Newton matrix J (2N x 2N row-major, columns a then b) and residual F (nullable). */
 int dse_ref_newton_matrix(const dse_ref_problem* p, const double* c, double* J, double* F);
 
+/* Magnitude sums that bound the rounding of each entry: A_ij is the sum of the
+ * absolute values of every summand that forms J_ij (the -Z^{-1} phi_j term, each
+ * quadrature summand of the row and of the subtraction row), AF_i the same for
+ * F_i (AF nullable).  Same layout as dse_ref_newton_matrix. */
+int dse_ref_newton_matrix_magnitudes(const dse_ref_problem* p, const double* c, double* A, double* AF);
+
 /* Solve A x = b (n x n row-major) by LU with partial pivoting. */
 int dse_ref_lu_solve(int n, const double* A, const double* b, double* x);
 

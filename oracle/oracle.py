@@ -67,6 +67,7 @@ def lib():
                 "dse_ref_self_energy": [P, _D, ctypes.c_double, _D, _D, _D, _D],
                 "dse_ref_residual": [P, _D, _D],
                 "dse_ref_newton_matrix": [P, _D, _D, _D],
+                "dse_ref_newton_matrix_magnitudes": [P, _D, _D, _D],
                 "dse_ref_lu_solve": [ctypes.c_int, _D, _D, _D],
                 "dse_ref_newton_step": [P, _D, ctypes.c_double, _D],
                 "dse_ref_schwinger_nodes": [P, ctypes.c_int, _D, _D],
@@ -184,6 +185,17 @@ def newton_matrix(params: dict, c):
     J = np.empty((n, n)); F = np.empty(n)
     _chk(lib().dse_ref_newton_matrix(ctypes.byref(p), _ptr(c), _ptr(J), _ptr(F)), "newton_matrix")
     return J, F
+
+
+def newton_matrix_magnitudes(params: dict, c):
+    """(A, AF): sums of |summands| of every entry of J and F (rounding scale)."""
+    p = make_problem(params)
+    c = _f64(c)
+    n = 2 * p.n_cheb
+    A = np.empty((n, n)); AF = np.empty(n)
+    _chk(lib().dse_ref_newton_matrix_magnitudes(ctypes.byref(p), _ptr(c), _ptr(A), _ptr(AF)),
+         "newton_matrix_magnitudes")
+    return A, AF
 
 
 def lu_solve(A, b) -> np.ndarray:

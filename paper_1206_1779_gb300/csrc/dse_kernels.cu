@@ -510,6 +510,354 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_newton(const Consts c, double
 }
 
 // ------------------------------------------------------------------------
+// Newton step with an FP32 inverse and FP64 iterative refinement (for
+// n = 2N <= kGjMaxN).  The FP64 rate is 1/64 of the FP32 rate on this GPU, so the
+// O(n^3) part runs in FP32 and only O(n^2) work per refinement sweep runs in FP64:
+//   1. rows of J scaled by exact powers of two (s_i = 2^-e_i, e_i = exponent of
+//      max_j |J_ij|): A = diag(s) J, b = diag(s) F;
+//   2. X ~ A^{-1} by Gauss-Jordan elimination with partial pivoting in FP32 on
+//      [A | I] held in shared memory;
+//   3. x <- x + X (b - A x) with the residual in FP64 until the correction is
+//      below 2^-50 |x| (at most kRefineMax sweeps).
+// If the sweeps do not converge (ill-conditioned J) the step falls back to the
+// FP64 LU above in the same launch; the fallback also reports singular matrices.
+constexpr int kGjThreads = 1024;
+constexpr int kGjMaxN = 160;
+constexpr int kRefineMax = 12;
+
+__device__ void lu_fp64_block(int n, double* __restrict__ A, double* __restrict__ b, double* __restrict__ x,
+                              int* s_fail, int* s_piv, double* sv, int* si) {
+    const int tid = threadIdx.x;
+    const int nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int warps = nt >> 5;
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += nt) {
+            const double v = fabs(A[(size_t)i * n + k]);
+            if (v > best || (v == best && i < bi)) {
+                best = v;
+                bi = i;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(kFullMask, best, off);
+            const int oi = __shfl_xor_sync(kFullMask, bi, off);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            sv[warp] = best;
+            si[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = sv[0];
+            int bix = si[0];
+            for (int w = 1; w < warps; ++w)
+                if (sv[w] > bv || (sv[w] == bv && si[w] < bix)) {
+                    bv = sv[w];
+                    bix = si[w];
+                }
+            *s_piv = bix;
+            if (!(bv > 1e-300) || !isfinite(bv)) *s_fail = kStatusSingular;
+        }
+        __syncthreads();
+        if (*s_fail) return;
+        const int p = *s_piv;
+        if (p != k) {
+            for (int j = tid; j < n; j += nt) {
+                const double t = A[(size_t)k * n + j];
+                A[(size_t)k * n + j] = A[(size_t)p * n + j];
+                A[(size_t)p * n + j] = t;
+            }
+            if (tid == 0) {
+                const double t = b[k];
+                b[k] = b[p];
+                b[p] = t;
+            }
+        }
+        __syncthreads();
+        const double dkk = A[(size_t)k * n + k];
+        for (int i = k + 1 + tid; i < n; i += nt) A[(size_t)i * n + k] /= dkk;
+        __syncthreads();
+        const int m = n - k - 1;
+        const double bk = b[k];
+        for (int idx = tid; idx < m * m; idx += nt) {
+            const int i = k + 1 + idx / m;
+            const int j = k + 1 + idx % m;
+            A[(size_t)i * n + j] = fma(-A[(size_t)i * n + k], A[(size_t)k * n + j], A[(size_t)i * n + j]);
+        }
+        for (int i = k + 1 + tid; i < n; i += nt) b[i] = fma(-A[(size_t)i * n + k], bk, b[i]);
+        __syncthreads();
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        if (tid == 0) x[i] = b[i] / A[(size_t)i * n + i];
+        __syncthreads();
+        const double xi = x[i];
+        for (int t = tid; t < i; t += nt) b[t] = fma(-A[(size_t)t * n + i], xi, b[t]);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, double* __restrict__ J,
+                                                             const double* __restrict__ F,
+                                                             const XTab* __restrict__ xtab,
+                                                             double* __restrict__ coef, double rho,
+                                                             double* __restrict__ work, double* __restrict__ stats,
+                                                             int* __restrict__ status) {
+    extern __shared__ __align__(16) float gj[];  // [n][2n]
+    __shared__ double sv[kGjThreads / 32];
+    __shared__ int si[kGjThreads / 32];
+    __shared__ double s_x[2 * kGjMaxN];
+    __shared__ double s_scale[2 * kGjMaxN];
+    __shared__ float s_rf[2 * kGjMaxN];
+    __shared__ int s_piv, s_fail, s_done;
+    __shared__ float s_pinv;
+    __shared__ double s_anorm;
+    __shared__ double s_red[3][kGjThreads / 32];
+    const int N = c.N;
+    const int n = 2 * N;
+    const int n2 = 2 * n;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int WARPS = kGjThreads / 32;
+
+    // norms of F
+    double mF = 0.0, mS = 0.0;
+    for (int i = tid; i < n; i += kGjThreads) {
+        const double f = F[i];
+        const double sc = i < N ? xtab[i].Z : xtab[i - N].G;
+        mF = fmax(mF, fabs(f));
+        mS = fmax(mS, fabs(f) * sc);
+        if (!isfinite(f)) mF = INFINITY;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        mF = fmax(mF, __shfl_xor_sync(kFullMask, mF, off));
+        mS = fmax(mS, __shfl_xor_sync(kFullMask, mS, off));
+    }
+    if (lane == 0) {
+        s_red[0][warp] = mF;
+        s_red[1][warp] = mS;
+    }
+    if (tid == 0) {
+        s_fail = (*status) & (kStatusNonfinite | kStatusSingular);
+        s_done = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, bb = 0.0;
+        for (int w = 0; w < WARPS; ++w) {
+            a = fmax(a, s_red[0][w]);
+            bb = fmax(bb, s_red[1][w]);
+        }
+        stats[0] = a;
+        stats[1] = bb;
+        stats[2] = 0.0;
+        if (!isfinite(a)) s_fail |= kStatusNonfinite;
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+
+    // 1. exact power-of-two row scaling (one warp per row) and ||A||_inf
+    double an = 0.0;
+    for (int i = warp; i < n; i += WARPS) {
+        double m = 0.0, rs = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const double v = fabs(J[(size_t)i * n + j]);
+            m = fmax(m, v);
+            rs += v;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            m = fmax(m, __shfl_xor_sync(kFullMask, m, off));
+            rs += __shfl_xor_sync(kFullMask, rs, off);
+        }
+        if (lane == 0) {
+            int e = 0;
+            frexp(m, &e);
+            const double sc = (m > 0.0 && isfinite(m)) ? ldexp(1.0, -e) : 0.0;
+            s_scale[i] = sc;
+            an = fmax(an, rs * sc);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) an = fmax(an, __shfl_xor_sync(kFullMask, an, off));
+    if (lane == 0) s_red[2][warp] = an;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int w = 0; w < WARPS; ++w) a = fmax(a, s_red[2][w]);
+        s_anorm = a;
+    }
+    for (int i = tid; i < n; i += kGjThreads)
+        if (s_scale[i] == 0.0) s_fail = kStatusSingular;  // benign race: same value
+    __syncthreads();
+    // 2. FP32 Gauss-Jordan on [A | I]
+    if (!s_fail) {
+        for (int i = warp; i < n; i += WARPS) {
+            const double sc = s_scale[i];
+            for (int j = lane; j < n2; j += 32)
+                gj[i * n2 + j] = j < n ? (float)(J[(size_t)i * n + j] * sc) : ((j - n == i) ? 1.0f : 0.0f);
+        }
+        __syncthreads();
+        for (int k = 0; k < n; ++k) {
+            float best = -1.0f;
+            int bi = n;
+            for (int i = k + tid; i < n; i += kGjThreads) {
+                const float v = fabsf(gj[i * n2 + k]);
+                if (v > best || (v == best && i < bi)) {
+                    best = v;
+                    bi = i;
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const float ov = __shfl_xor_sync(kFullMask, best, off);
+                const int oi = __shfl_xor_sync(kFullMask, bi, off);
+                if (ov > best || (ov == best && oi < bi)) {
+                    best = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                sv[warp] = best;
+                si[warp] = bi;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double bv = sv[0];
+                int bix = si[0];
+                for (int w = 1; w < WARPS; ++w)
+                    if (sv[w] > bv || (sv[w] == bv && si[w] < bix)) {
+                        bv = sv[w];
+                        bix = si[w];
+                    }
+                s_piv = bix;
+                if (!(bv > 1e-30)) s_done = -1;  // numerically singular in FP32: use the FP64 path
+                else s_pinv = 1.0f / gj[bix * n2 + k];
+            }
+            __syncthreads();
+            if (s_done < 0) break;
+            const int p = s_piv;
+            // swap rows k and p, then scale row k by 1/pivot
+            const float inv = s_pinv;
+            for (int j = tid; j < n2; j += kGjThreads) {
+                const float a = gj[k * n2 + j];
+                const float bq = gj[p * n2 + j];
+                gj[k * n2 + j] = bq * inv;
+                if (p != k) gj[p * n2 + j] = a;
+            }
+            __syncthreads();
+            // eliminate column k from every other row (one warp per row)
+            for (int i = warp; i < n; i += WARPS) {
+                if (i == k) continue;
+                const float f = gj[i * n2 + k];
+                for (int j = lane; j < n2; j += 32)
+                    if (j != k) gj[i * n2 + j] = fmaf(-f, gj[k * n2 + j], gj[i * n2 + j]);
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += kGjThreads)
+                if (i != k) gj[i * n2 + k] = 0.0f;
+            __syncthreads();
+        }
+    }
+    // 3. refinement sweeps: x <- x + X (b - A x), residual in FP64, until the
+    //    scaled residual is at the FP64 level of a backward-stable solve:
+    //    max|r| <= 4 sqrt(n) 2^-53 ||A||_inf ||x||_inf
+    bool converged = false;
+    if (!s_fail && s_done == 0) {
+        for (int i = tid; i < n; i += kGjThreads) s_x[i] = 0.0;
+        __syncthreads();
+        const double tolfac = 4.0 * sqrt((double)n) * 0x1p-53 * s_anorm;
+        for (int it = 0; it <= kRefineMax; ++it) {
+            double rm = 0.0, xm = 0.0;
+            for (int i = warp; i < n; i += WARPS) {
+                double acc = 0.0;
+                for (int j = lane; j < n; j += 32) acc = fma(J[(size_t)i * n + j], s_x[j], acc);
+                for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFullMask, acc, off);
+                if (lane == 0) {
+                    const double r = s_scale[i] * (F[i] - acc);
+                    s_rf[i] = (float)r;
+                    rm = fmax(rm, fabs(r));
+                    xm = fmax(xm, fabs(s_x[i]));
+                    if (!isfinite(r)) rm = INFINITY;
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                rm = fmax(rm, __shfl_xor_sync(kFullMask, rm, off));
+                xm = fmax(xm, __shfl_xor_sync(kFullMask, xm, off));
+            }
+            if (lane == 0) {
+                s_red[0][warp] = rm;
+                s_red[1][warp] = xm;
+            }
+            __syncthreads();
+            double RM = 0.0, XM = 0.0;
+            for (int w = 0; w < WARPS; ++w) {
+                RM = fmax(RM, s_red[0][w]);
+                XM = fmax(XM, s_red[1][w]);
+            }
+            if (!isfinite(RM)) break;
+            if (RM <= tolfac * XM) {
+                converged = true;
+                break;
+            }
+            if (it == kRefineMax) break;
+            for (int i = warp; i < n; i += WARPS) {
+                float acc = 0.0f;
+                for (int j = lane; j < n; j += 32) acc = fmaf(gj[i * n2 + n + j], s_rf[j], acc);
+                for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFullMask, acc, off);
+                if (lane == 0) s_x[i] += (double)acc;
+            }
+            __syncthreads();
+        }
+    }
+    double* xres = work + n;
+    if (!s_fail && converged) {
+        for (int i = tid; i < n; i += kGjThreads) xres[i] = s_x[i];
+        __syncthreads();
+    } else if (!s_fail) {
+        // FP64 LU fallback on J (in place), right-hand side copied to work
+        for (int i = tid; i < n; i += kGjThreads) work[i] = F[i];
+        __syncthreads();
+        lu_fp64_block(n, J, work, xres, &s_fail, &s_piv, sv, si);
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+    double mD = 0.0;
+    bool bad = false;
+    for (int i = tid; i < n; i += kGjThreads) {
+        mD = fmax(mD, fabs(xres[i]));
+        bad |= !isfinite(xres[i]);
+    }
+    for (int off = 16; off > 0; off >>= 1) mD = fmax(mD, __shfl_xor_sync(kFullMask, mD, off));
+    bad = __any_sync(kFullMask, bad);
+    if (lane == 0) {
+        s_red[2][warp] = mD;
+        if (bad) atomicOr(&s_fail, kStatusNonfinite);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int w = 0; w < WARPS; ++w) a = fmax(a, s_red[2][w]);
+        stats[2] = a;
+        stats[3] = converged ? 1.0 : 0.0;
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+    for (int i = tid; i < n; i += kGjThreads) coef[i] = fma(-rho, xres[i], coef[i]);
+}
+
+// ------------------------------------------------------------------------
 __global__ void k_dressing(const Consts c, const double* __restrict__ coef, int n, const double* __restrict__ x,
                            double* __restrict__ lG, double* __restrict__ lZ, int* __restrict__ status) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -649,7 +997,15 @@ cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const 
 
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
                              double* work, double* stats, int* status, cudaStream_t s) {
-    k_lu_newton<<<1, kLuThreads, 0, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
+    const int n = 2 * c.N;
+    if (n <= kGjMaxN) {
+        const size_t smem = sizeof(float) * (size_t)n * 2 * n;
+        cudaError_t e = cudaFuncSetAttribute(k_newton_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_newton_mixed<<<1, kGjThreads, smem, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
+    } else {
+        k_lu_newton<<<1, kLuThreads, 0, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
+    }
     return cudaGetLastError();
 }
 

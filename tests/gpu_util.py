@@ -1,28 +1,30 @@
-"""Shared helpers of the GPU parity tests (tolerances, device transfer)."""
+"""Shared helpers of the GPU parity tests (tolerances, device transfer).
+
+Parity bar for the Newton matrix J and the residual F (per entry):
+    |gpu - oracle| <= 1e-11 |oracle| + 1e-13 A
+where A is the sum of the magnitudes of every summand that forms the entry
+(oracle.newton_matrix_magnitudes): the -Z^{-1} phi_j term and each quadrature
+summand of the row and of its subtraction row.  Entries that are small
+differences of large terms (the MOM subtraction, the cancellation of the
+quadratic parts of the Q and M terms, oscillating phi_j(z)) cannot be
+reproduced to 1e-11 relative by any FP64 evaluation that rounds differently,
+because each side carries ~1e-16 A of rounding; 1e-13 A bounds sums of up to
+~1e5 terms.  Well-conditioned entries (|J| >= 1e-3 A) are held to 1e-11
+relative by the first term alone; the tests also report their largest
+relative error.
+"""
 import numpy as np
 
-# Per-entry bar: relative 1e-11, with an absolute floor of 1e-13 times the
-# row's largest |J| for entries that are small through cancellation (the
-# subtraction at x_Z / x_G and the quadratic-divergence cancellation between
-# the Q and M terms bound their relative precision).
 REL = 1e-11
-ROW_FLOOR = 1e-13
+ABS_OF_MAGNITUDE = 1e-13
 
 
-def matrix_ok(J, Jo):
-    rowmax = np.abs(Jo).max(axis=1, keepdims=True)
-    err = np.abs(J - Jo)
-    ok = err <= REL * np.abs(Jo) + ROW_FLOOR * rowmax
-    big = np.abs(Jo) > 1e-6 * rowmax
-    rel = float(np.max(err[big] / np.abs(Jo[big]))) if big.any() else 0.0
-    return bool(ok.all()), rel, int((~ok).sum())
-
-
-def residual_ok(F, Fo, Jo):
-    rowmax = np.abs(Jo).max(axis=1)
-    err = np.abs(F - Fo)
-    ok = err <= REL * np.abs(Fo) + ROW_FLOOR * rowmax
-    return bool(ok.all()), float(np.max(err / (np.abs(Fo) + ROW_FLOOR * rowmax)))
+def entries_ok(G, O, A):
+    err = np.abs(G - O)
+    ok = err <= REL * np.abs(O) + ABS_OF_MAGNITUDE * A
+    well = np.abs(O) >= 1e-3 * A
+    rel_well = float(np.max(err[well] / np.abs(O[well]))) if well.any() else 0.0
+    return bool(ok.all()), rel_well, int((~ok).sum()), float(np.max(err / A))
 
 
 def to_dev(a):
@@ -34,3 +36,12 @@ def to_host(t):
     import torch
     torch.cuda.synchronize()
     return t.cpu().numpy()
+
+
+def dump(name, **arrays):
+    """Save arrays for offline analysis when DSE_TEST_DUMP names a directory."""
+    import os
+    d = os.environ.get("DSE_TEST_DUMP")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        np.savez(os.path.join(d, name + ".npz"), **arrays)

@@ -1,13 +1,14 @@
 """GPU parity: the sm_103a path through the C ABI against the FP64 CPU oracle
 (arXiv:1206.1779 Sec. 2-3: quadrature rules, dressing functions with IR/UV
 continuation, residual, Newton matrix, Newton step and solve; Sec. 2.2 / 5:
-Schwinger function).  Bar: relative 1e-11 per entry with a 1e-13 row floor."""
+Schwinger function).  Bar (tests/gpu_util.py): 1e-11 relative per entry plus
+1e-13 of the entry's magnitude sum."""
 import math
 
 import numpy as np
 import pytest
 
-from gpu_util import matrix_ok, residual_ok, to_dev, to_host
+from gpu_util import dump, entries_ok, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -46,12 +47,16 @@ def test_newton_matrix_parity(dse, oracle, inputs, name):
         Fr = to_host(plan.residual(to_dev(c)))
         assert plan.status() == dse.DSE_OK
     Jo, Fo = oracle.newton_matrix(p, c)
-    ok, rel, nbad = matrix_ok(J, Jo)
-    assert ok, (name, rel, nbad)
-    okF, relF = residual_ok(F, Fo, Jo)
-    assert okF, (name, relF)
-    okR, relR = residual_ok(Fr, Fo, Jo)
-    assert okR, (name, relR)
+    A, AF = oracle.newton_matrix_magnitudes(p, c)
+    ok, rel, nbad, worst = entries_ok(J, Jo, A)
+    if not ok or rel > 1e-11:
+        dump("matrix_" + name, J=J, Jo=Jo, A=A, F=F, Fo=Fo, AF=AF)
+    assert ok, (name, rel, nbad, worst)
+    assert rel <= 1e-11, (name, rel)
+    okF = entries_ok(F, Fo, AF)
+    assert okF[0], (name, okF)
+    okR = entries_ok(Fr, Fo, AF)
+    assert okR[0], (name, okR)
 
 
 def test_quadrature_and_collocation(dse, oracle, inputs):
@@ -60,8 +65,12 @@ def test_quadrature_and_collocation(dse, oracle, inputs):
     xo = oracle.collocation(p)
     with dse.Plan(p) as plan:
         gy, gW, gth, gwt, gx = [to_host(t) for t in plan.quadrature()]
-    for a, b in [(gy, y), (gW, W), (gth, th), (gwt, wt), (gx, xo)]:
-        assert np.allclose(a, b, rtol=1e-14, atol=0)
+    # two independent Gauss-Legendre generators: nodes agree to a few ulp,
+    # weights (from P_n' at the root) to ~1e-13
+    for name, a, b, tol in [("y", gy, y, 1e-14), ("W", gW, W, 1e-12), ("theta", gth, th, 1e-14),
+                            ("wt", gwt, wt, 1e-12), ("x", gx, xo, 1e-14)]:
+        rel = np.max(np.abs(a - b) / np.abs(b))
+        assert rel <= tol, (name, rel)
 
 
 def test_dressing_parity_all_regions(dse, oracle, inputs):
@@ -85,27 +94,39 @@ def test_full_size_matrix_parity(dse, oracle, inputs):
         J, F = plan.newton_matrix(to_dev(c))
         J, F = to_host(J), to_host(F)
     Jo, Fo = oracle.newton_matrix(p, c)
-    ok, rel, nbad = matrix_ok(J, Jo)
-    assert ok, (rel, nbad)
-    assert residual_ok(F, Fo, Jo)[0]
+    A, AF = oracle.newton_matrix_magnitudes(p, c)
+    ok, rel, nbad, worst = entries_ok(J, Jo, A)
+    if not ok or rel > 1e-11:
+        dump("matrix_full", J=J, Jo=Jo, A=A, F=F, Fo=Fo, AF=AF)
+    assert ok, (rel, nbad, worst)
+    assert rel <= 1e-11, rel
+    assert entries_ok(F, Fo, AF)[0]
 
 
-def test_newton_step_parity(dse, oracle, inputs):
-    p = inputs.workload_problem("newton_step_n16")
+@pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64", "n100"])
+def test_newton_step_parity(dse, oracle, inputs, name):
+    # n = 2N <= 160: FP32 Gauss-Jordan inverse + FP64 refinement; larger: FP64 LU
+    p = inputs.workload_problem(name) if name in inputs.WORKLOADS else inputs.problem(**CASES[name])
     c = inputs.starting_guess(p, seed=0)
     co, so = oracle.newton_step(p, c, rho=0.7)
     with dse.Plan(p) as plan:
         ct = to_dev(c)
+        J, F = plan.newton_matrix(ct)
+        J, F = to_host(J), to_host(F)
         sg = plan.newton_step(ct, rho=0.7)
         cg = to_host(ct)
-    # the update solves a system with cond ~1e15 (rows of very different scale):
-    # compare the update on the scale of the step
-    d_o = c - co
-    d_g = c - cg
-    assert np.max(np.abs(d_g - d_o)) <= 1e-8 * np.max(np.abs(d_o))
+    d_g = (c - cg) / 0.7
+    # the device solve against LAPACK on the device's own J, F: the row-equilibrated
+    # matrix has cond ~1e5, so both solutions agree to ~1e-11
+    d_np = np.linalg.solve(J, F)
+    assert np.max(np.abs(d_g - d_np)) <= 1e-9 * np.max(np.abs(d_np))
+    # against the oracle's step: J differs by up to 1e-13 of its magnitude sums,
+    # amplified by the conditioning
+    d_o = (c - co) / 0.7
+    assert np.max(np.abs(d_g - d_o)) <= 1e-7 * np.max(np.abs(d_o))
     assert abs(sg[0] / so[0] - 1) < 1e-10
     assert abs(sg[1] / so[1] - 1) < 1e-10
-    assert abs(sg[2] / so[2] - 1) < 1e-8
+    assert abs(sg[2] / so[2] - 1) < 1e-7
 
 
 def test_solve_parity(dse, oracle, inputs):

@@ -57,3 +57,16 @@ def test_block_layout(oracle, inputs):
     dGref = oracle.self_energy(p, c, p["x_G"], grad=True)[2]
     assert abs(J[N + 1, N + 2] - (-np.exp(-lG[1]) * oracle.basis(p, x[1])[2] - dG[N + 2] + dGref[N + 2])) \
         < 1e-12 * np.abs(J[N + 1]).max()
+
+
+def test_magnitude_sums_bound_entries(oracle, inputs):
+    # A_ij (sum of |summands|) >= |J_ij| and AF_i >= |F_i|, with equality for
+    # entries whose summands share one sign; scaling c by nothing changes A
+    for case in CASES[:2]:
+        p = inputs.problem(**case)
+        c = inputs.starting_guess(p, seed=7)
+        J, F = oracle.newton_matrix(p, c)
+        A, AF = oracle.newton_matrix_magnitudes(p, c)
+        assert np.all(A >= np.abs(J) * (1 - 1e-14))
+        assert np.all(AF >= np.abs(F) * (1 - 1e-14))
+        assert np.all(np.isfinite(A)) and np.all(A > 0)
