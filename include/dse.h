@@ -112,10 +112,14 @@ int dse_residual(dse_plan* plan, const double* d_coeffs, double* d_F);
  * quadrature, and the residual F (d_F may be NULL). */
 int dse_newton_matrix(dse_plan* plan, const double* d_coeffs, double* d_J, double* d_F);
 
-/* One Newton-Raphson step (Sec. 3): J Delta = F by LU with partial pivoting on
- * the device, then c <- c - rho Delta in place.  h_stats (host, 3 doubles,
- * nullable): ||F||_inf, ||diag(Z(x_i), G(x_i)) F||_inf (the dimensionless residual
- * used as the stopping test), ||Delta||_inf, all for the coefficients on entry.
+/* One Newton-Raphson step (Sec. 3): J Delta = F solved on the device, then
+ * c <- c - rho Delta in place.  For 2N <= 160 the rows of J are scaled by powers
+ * of two, inverted in FP32 and the solution refined in FP64 to a backward-stable
+ * residual; otherwise (or if refinement stalls) LU with partial pivoting in FP64.
+ * h_stats (host, 4 doubles, nullable): ||F||_inf, ||diag(Z(x_i), G(x_i)) F||_inf
+ * (the dimensionless residual used as the stopping test), ||Delta||_inf, all for
+ * the coefficients on entry, and the number of FP64 refinement sweeps (-1 when
+ * the FP64 LU solved the system).
  * Waits for the stream.  On DSE_ERR_SINGULAR / DSE_ERR_NONFINITE the
  * coefficients are left unchanged. */
 int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stats);
@@ -123,7 +127,8 @@ int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stat
 /* Newton iteration from d_coeffs until the dimensionless residual (h_stats[1]
  * of dse_newton_step) drops below tol: the first n_relax steps use rho_relax,
  * the rest rho = 1 (under-relaxation of Sec. 3).  *h_iters receives the number
- * of steps taken, h_stats (nullable) the stats of the last step.  Returns
+ * of steps taken, h_stats (nullable, 3 doubles) the first three stats of the
+ * last step.  Returns
  * DSE_ERR_NOT_CONVERGED after max_iter steps. */
 int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double rho_relax,
               int n_relax, int* h_iters, double* h_stats);

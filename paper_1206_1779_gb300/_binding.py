@@ -198,8 +198,9 @@ class Plan:
         return J, F
 
     def newton_step(self, coeffs, rho: float = 1.0):
-        """In-place Newton step; returns (||F||inf, scaled ||F||inf, ||Delta||inf) on entry."""
-        st = (ctypes.c_double * 3)()
+        """In-place Newton step; returns (||F||inf, scaled ||F||inf, ||Delta||inf) on entry
+        and the number of FP64 refinement sweeps (-1: FP64 LU)."""
+        st = (ctypes.c_double * 4)()
         self._sync_stream()
         _check(self._L.dse_newton_step(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), float(rho),
                                        ctypes.cast(st, _D)), "dse_newton_step")

@@ -398,6 +398,7 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_newton(const Consts c, double
         stats[0] = a;
         stats[1] = bb;
         stats[2] = 0.0;
+        stats[3] = -1.0;
         if (!isfinite(a)) s_fail |= kStatusNonfinite;
     }
     __syncthreads();
@@ -769,6 +770,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
     //    scaled residual is at the FP64 level of a backward-stable solve:
     //    max|r| <= 4 sqrt(n) 2^-53 ||A||_inf ||x||_inf
     bool converged = false;
+    int sweeps = 0;
     if (!s_fail && s_done == 0) {
         for (int i = tid; i < n; i += kGjThreads) s_x[i] = 0.0;
         __syncthreads();
@@ -807,6 +809,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
                 break;
             }
             if (it == kRefineMax) break;
+            ++sweeps;
             for (int i = warp; i < n; i += WARPS) {
                 float acc = 0.0f;
                 for (int j = lane; j < n; j += 32) acc = fmaf(gj[i * n2 + n + j], s_rf[j], acc);
@@ -848,7 +851,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
         double a = 0.0;
         for (int w = 0; w < WARPS; ++w) a = fmax(a, s_red[2][w]);
         stats[2] = a;
-        stats[3] = converged ? 1.0 : 0.0;
+        stats[3] = converged ? (double)sweeps : -1.0;
     }
     if (s_fail) {
         if (tid == 0) atomicOr(status, s_fail);

@@ -190,7 +190,7 @@ int read_status(dse_plan* pl, double* h_stats) {
     if (e != cudaSuccess) return DSE_ERR_CUDA;
     int st = 0;
     memcpy(&st, pl->h_misc + 4, sizeof(int));
-    if (h_stats) memcpy(h_stats, pl->h_misc, 3 * sizeof(double));
+    if (h_stats) memcpy(h_stats, pl->h_misc, 4 * sizeof(double));
     if (st) {
         e = cudaMemsetAsync(pl->status, 0, sizeof(int), pl->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
@@ -360,7 +360,7 @@ int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stat
 int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double rho_relax, int n_relax,
               int* h_iters, double* h_stats) {
     if (!plan || !d_coeffs || !(tol > 0.0) || max_iter < 1 || !isfinite(rho_relax) || n_relax < 0) return DSE_ERR_ARG;
-    double st3[3] = {0.0, 0.0, 0.0};
+    double st3[4] = {0.0, 0.0, 0.0, 0.0};
     int it = 0;
     int st = DSE_ERR_NOT_CONVERGED;
     for (; it < max_iter; ++it) {
@@ -378,7 +378,7 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
         }
     }
     if (h_iters) *h_iters = it;
-    if (h_stats) memcpy(h_stats, st3, sizeof(st3));
+    if (h_stats) memcpy(h_stats, st3, 3 * sizeof(double));
     return st;
 }
 
