@@ -141,6 +141,33 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
 int dse_schwinger(dse_plan* plan, const double* d_coeffs, const double* d_t, int n_t,
                   int n_nodes, double* d_delta);
 
+/* Allocation-free residual.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code that runs where device
+ * memory is owned by another allocator (a framework's caching pool, a fixed
+ * memory budget) or where the implicit device synchronisation of cudaMalloc /
+ * cudaFree is not acceptable.  It computes the same F as dse_residual (Gauss-
+ * Legendre rules, dressing tables, quadrature kernel, contraction, assembly),
+ * but needs no plan: every intermediate buffer is carved out of one static
+ * device array of DSE_STATIC_SCRATCH_BYTES compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *  - d_coeffs (2N) and d_F (2N) are caller-owned device buffers; cuda_stream is
+ *    a cudaStream_t (NULL = legacy default stream).  Queued without waiting.
+ *  - Returns DSE_ERR_ARG for bad arguments and when the problem needs more than
+ *    DSE_STATIC_SCRATCH_BYTES of scratch (about 14 MB for N = 128 with
+ *    512 x 256 nodes; the size grows with N (n_cheb) x n_radial x n_angular / 32);
+ *    nothing is queued then.  Non-finite values are not reported: they appear
+ *    in d_F.
+ *  - It calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ *    call on each device looks up the array's device address (once per device,
+ *    with that device current); make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the previous call's contents:
+ *    calls that overlap on the GPU (different streams, or different host
+ *    threads on the same device) race on it and must be serialised by the
+ *    caller. */
+#define DSE_STATIC_SCRATCH_BYTES (16u << 20)
+int dse_residual_static(const dse_problem* problem, const double* d_coeffs, double* d_F,
+                        void* cuda_stream);
+
 /* Instrumentation.  dse_plan_profile(plan, 1) makes every later assembly record
  * CUDA events around its quadrature kernel (the hot kernel) on the plan's
  * stream; dse_plan_counters waits for the stream and reports the number of

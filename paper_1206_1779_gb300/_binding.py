@@ -21,7 +21,7 @@ DSE_MAX_CHEB = 256
 
 EXPORTS = ["dse_plan_create", "dse_plan_destroy", "dse_plan_set_stream", "dse_plan_status", "dse_quadrature",
            "dse_dressing", "dse_residual", "dse_newton_matrix", "dse_newton_step", "dse_solve", "dse_schwinger",
-           "dse_plan_profile", "dse_plan_counters", "dse_status_string"]
+           "dse_plan_profile", "dse_plan_counters", "dse_residual_static", "dse_status_string"]
 
 
 class DseError(RuntimeError):
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = False):
                       ctypes.POINTER(ctypes.c_int), _D],
         "dse_schwinger": [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP],
         "dse_plan_profile": [_VP, ctypes.c_int],
+        "dse_residual_static": [PP, _VP, _VP, _VP],
         "dse_plan_counters": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_double)],
     }
