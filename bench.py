@@ -221,6 +221,11 @@ def run_gb300(args):
     peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     traffic = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
 
+    # mixed precision (FP32 integrands for the Newton matrix, FP64 residual)
+    mixed = None
+    if not args.no_mixed:
+        mixed = measure_mixed(dse, p, c0_dev, t_dev, coef, args, total_ms / args.steps)
+
     # end to end through the public API with host buffers (pinned), copies timed
     c0_host = torch.from_numpy(c0).pin_memory()
     t_host = torch.from_numpy(tt).pin_memory()
@@ -269,9 +274,54 @@ def run_gb300(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if mixed is not None:
+            line["mixed_precision"] = mixed
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measure_mixed(dse, p, c0_dev, t_dev, coef_fp64, args, fp64_ms_per_step):
+    """The same step with precision = 1, and its accuracy against the FP64 solve."""
+    import torch
+    N, nr, na = p["n_cheb"], p["n_radial"], p["n_angular"]
+    plan = dse.Plan(dict(p, precision=1))
+    coef = torch.empty_like(c0_dev)
+    delta = torch.empty_like(t_dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        coef.copy_(c0_dev)
+        it, st = plan.solve(coef, tol=TOL, max_iter=50)
+        plan.schwinger(coef, t_dev, N_NODES, out=delta)
+        return it
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    times, iters = [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        iters.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    x = torch.from_numpy(np.exp(np.linspace(np.log(p["eps2"]), np.log(p["lambda2"]), 257))).cuda()
+    lg_m, lz_m = plan.dressing(coef, x)
+    lg_d, lz_d = plan.dressing(coef_fp64, x)
+    torch.cuda.synchronize()
+    dG = float((lg_m - lg_d).abs().max())
+    dZ = float((lz_m - lz_d).abs().max())
+    plan.close()
+    mats = float(np.mean(iters))
+    return {"ms_per_step": ms, "solves_per_s": 1e3 / ms, "newton_matrices_per_step": mats,
+            "value": mats * 4.0 * N * N * nr * na / (ms * 1e-3), "unit": UNIT,
+            "speedup_vs_fp64_step": fp64_ms_per_step / ms,
+            "max_abs_dlnG_vs_fp64_solve": dG, "max_abs_dlnZ_vs_fp64_solve": dZ,
+            "note": "Newton matrix from FP32 integrands with FP64 block sums; FP64 residual near convergence"}
 
 
 def cpu_baseline_sample(p, c0, budget_s: float = 12.0):
@@ -337,6 +387,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -71,7 +71,7 @@ typedef struct {
     double delta;     /* ghost anomalous dimension; gamma = -1 - 2 delta                 */
     int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2]         */
     int extrap_mode;  /* 0: IR power laws and UV logarithms; 1: constant continuation    */
-    int precision;    /* 0: FP64 throughout                                              */
+    int precision;    /* 0: FP64 throughout; 1: mixed (FP32 integrands for J, FP64 F)   */
 } dse_problem;
 
 typedef struct dse_plan dse_plan;

@@ -60,6 +60,8 @@ cudaError_t launch_setup_rules(const Consts& c, const double* gl_r, const double
 cudaError_t launch_tables(const Consts& c, const double* coef, const Rad* rad, const double* xcol,
                           YTab* ytab, double* phiy, XTab* xtab, double* phix, cudaStream_t s);
 cudaError_t launch_triple(bool full, const TripleArgs& a, cudaStream_t s);
+// FP32-integrand variant (mixed precision), same outputs and layouts.
+cudaError_t launch_triple32(bool full, const TripleArgs& a, cudaStream_t s);
 size_t triple_smem_bytes(bool full, int N);
 int triple_block_threads(int N);
 int triple_max_blocks_per_sm(bool full, int N);
@@ -68,9 +70,11 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
                              const double* Upart, const double* Vpart, double* D, cudaStream_t s);
 cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix,
                             const double* D, double* J, double* F, int* status, cudaStream_t s);
+// Newton step: J Delta = F, c <- c - rho Delta.  As (n*n floats) and rowinfo
+// (n double2) are scratch for the row-scaled FP32 copy of J.
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab,
-                             double* coef, double rho, double* work, double* stats, int* status,
-                             cudaStream_t s);
+                             double* coef, double rho, double* work, float* As, double2* rowinfo,
+                             double* stats, int* status, cudaStream_t s);
 cudaError_t launch_dressing(const Consts& c, const double* coef, int n, const double* x, double* lG,
                             double* lZ, int* status, cudaStream_t s);
 cudaError_t launch_schwinger_map(const Consts& c, int n, const double* gx, const double* gw, double* pn,

@@ -173,8 +173,13 @@ __global__ void k_tables(const Consts c, const double* __restrict__ coef, const 
 // closure d ln G(u)/d b_j = d ln Z(u)/d a_j = phi_j(u)).
 // For x_G = 0, z = y: the ghost row is y-only and V_G = Y_G.
 constexpr int kRowBlock = 256;
+constexpr int kRowJ = 32;                   // coefficients per block (one per lane)
+constexpr int kRowKG = kRowBlock / kRowJ;   // radial-node groups per block
 constexpr int kChunkK = 256;
 
+// Grid: (row r, block of 32 coefficients).  Thread (k-group kg, lane) owns
+// coefficient j = 32 jb + lane and the radial nodes kk = kg mod 8 of each chunk;
+// the 8 partial sums are combined in a fixed order at the end.
 template <bool FULL>
 __global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt, int KS, int nch,
                                                          const Rad* __restrict__ rad, const Ang* __restrict__ ang,
@@ -183,11 +188,14 @@ __global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt,
                                                          const double* __restrict__ Upart,
                                                          const double* __restrict__ Vpart, double* __restrict__ D) {
     __shared__ double sU[kChunkK][3];
-    __shared__ double sPi[3];
+    __shared__ double sY[kRowKG][3][kRowJ];
     __shared__ double sS4;
     const int N = c.N;
     const int r = blockIdx.x;
+    const int jb = blockIdx.y;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int kg = tid >> 5;
     int rt;
     bool special = false;  // x_G = 0 ghost row
     if (r < N) rt = r;
@@ -198,18 +206,17 @@ __global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt,
     }
     const bool gluon = r <= N;
     const bool ghost = r != N;
-    if (tid == 0) {
-        sPi[0] = sPi[1] = sPi[2] = 0.0;
+    const bool do_pi = (jb == 0);
+    if (special && kg == 0) {
+        // sum_l w_l sin^4(theta_l) by warp 0 (fixed order)
         double s4 = 0.0;
-        if (special)
-            for (int l = 0; l < c.na; ++l) s4 += ang[l].w * ang[l].s4;
-        sS4 = s4;
+        for (int l = lane; l < c.na; l += 32) s4 += ang[l].w * ang[l].s4;
+        for (int off = 16; off > 0; off >>= 1) s4 += __shfl_xor_sync(kFullMask, s4, off);
+        if (lane == 0) sS4 = s4;
     }
-    // each thread owns up to DSE_MAX_CHEB / kRowBlock coefficients
-    constexpr int JPT = (DSE_MAX_CHEB + kRowBlock - 1) / kRowBlock;
-    double Y[3][JPT];
-#pragma unroll
-    for (int q = 0; q < JPT; ++q) Y[0][q] = Y[1][q] = Y[2][q] = 0.0;
+    const int j = jb * kRowJ + lane;
+    double Y0 = 0.0, Y1 = 0.0, Y2 = 0.0;
+    double P0 = 0.0, P1 = 0.0, P2 = 0.0;  // warp 0: sums of U for Pi
     __syncthreads();
     for (int kb = 0; kb < c.nr; kb += kChunkK) {
         const int kn = min(kChunkK, c.nr - kb);
@@ -233,62 +240,66 @@ __global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt,
             sU[kk][2] = u2;
         }
         __syncthreads();
-        if (tid == 0) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-            for (int kk = 0; kk < kn; ++kk) {
-                a0 += sU[kk][0];
-                a1 += sU[kk][1];
-                a2 += sU[kk][2];
+        if (do_pi && kg == 0) {
+            for (int kk = lane; kk < kn; kk += 32) {
+                P0 += sU[kk][0];
+                P1 += sU[kk][1];
+                P2 += sU[kk][2];
             }
-            sPi[0] += a0;
-            sPi[1] += a1;
-            sPi[2] += a2;
         }
-        if (FULL) {
-#pragma unroll
-            for (int q = 0; q < JPT; ++q) {
-                const int j = tid + q * kRowBlock;
-                if (j < N) {
-                    for (int kk = 0; kk < kn; ++kk) {
-                        const double ph = phiy[(size_t)(kb + kk) * N + j];
-                        Y[0][q] = fma(sU[kk][0], ph, Y[0][q]);
-                        Y[1][q] = fma(sU[kk][1], ph, Y[1][q]);
-                        Y[2][q] = fma(sU[kk][2], ph, Y[2][q]);
-                    }
-                }
+        if (FULL && j < N) {
+            for (int kk = kg; kk < kn; kk += kRowKG) {
+                const double ph = phiy[(size_t)(kb + kk) * N + j];
+                Y0 = fma(sU[kk][0], ph, Y0);
+                Y1 = fma(sU[kk][1], ph, Y1);
+                Y2 = fma(sU[kk][2], ph, Y2);
             }
         }
         __syncthreads();
     }
+    if (FULL) {
+        sY[kg][0][lane] = Y0;
+        sY[kg][1][lane] = Y1;
+        sY[kg][2][lane] = Y2;
+    }
+    __syncthreads();
     const Row rw = rows[rt >= 0 ? rt : 0];
     const double pre = gluon ? rw.pre : 0.0;
     double* out = D + (size_t)r * (4 * N + 2);
-    if (FULL) {
-#pragma unroll
-        for (int q = 0; q < JPT; ++q) {
-            const int j = tid + q * kRowBlock;
-            if (j >= N) continue;
-            double VQ = 0.0, VM = 0.0, VG = 0.0;
-            if (!special) {
-                const double* vp = Vpart + (size_t)rt * KS * 3 * N;
-                for (int s = 0; s < KS; ++s) {
-                    VQ += vp[(size_t)s * 3 * N + j];
-                    VM += vp[(size_t)s * 3 * N + N + j];
-                    VG += vp[(size_t)s * 3 * N + 2 * N + j];
-                }
-            } else {
-                VG = Y[2][q];
-            }
-            const double tq = Y[0][q] + VQ;
-            out[j] = gluon ? pre * c.qZ * tq : 0.0;
-            out[N + j] = gluon ? pre * (c.pG * tq + Y[1][q] + VM) : 0.0;
-            out[2 * N + j] = ghost ? -c.K * VG : 0.0;
-            out[3 * N + j] = ghost ? -c.K * Y[2][q] : 0.0;
+    if (FULL && kg == 0 && j < N) {
+        double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+        for (int q = 0; q < kRowKG; ++q) {
+            y0 += sY[q][0][lane];
+            y1 += sY[q][1][lane];
+            y2 += sY[q][2][lane];
         }
+        double VQ = 0.0, VM = 0.0, VG = 0.0;
+        if (!special) {
+            const double* vp = Vpart + (size_t)rt * KS * 3 * N;
+            for (int sp = 0; sp < KS; ++sp) {
+                VQ += vp[(size_t)sp * 3 * N + j];
+                VM += vp[(size_t)sp * 3 * N + N + j];
+                VG += vp[(size_t)sp * 3 * N + 2 * N + j];
+            }
+        } else {
+            VG = y2;
+        }
+        const double tq = y0 + VQ;
+        out[j] = gluon ? pre * c.qZ * tq : 0.0;
+        out[N + j] = gluon ? pre * (c.pG * tq + y1 + VM) : 0.0;
+        out[2 * N + j] = ghost ? -c.K * VG : 0.0;
+        out[3 * N + j] = ghost ? -c.K * y2 : 0.0;
     }
-    if (tid == 0) {
-        out[4 * N] = gluon ? pre * (sPi[0] + sPi[1]) : 0.0;
-        out[4 * N + 1] = ghost ? -c.K * sPi[2] : 0.0;
+    if (do_pi && kg == 0) {
+        for (int off = 16; off > 0; off >>= 1) {
+            P0 += __shfl_xor_sync(kFullMask, P0, off);
+            P1 += __shfl_xor_sync(kFullMask, P1, off);
+            P2 += __shfl_xor_sync(kFullMask, P2, off);
+        }
+        if (lane == 0) {
+            out[4 * N] = gluon ? pre * (P0 + P1) : 0.0;
+            out[4 * N + 1] = ghost ? -c.K * P2 : 0.0;
+        }
     }
 }
 
@@ -861,6 +872,342 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
 }
 
 // ------------------------------------------------------------------------
+// Row scaling for the Newton step (one block per row of J, many SMs): the
+// exact power of two s_i = 2^(1022 - E_i), E_i the largest biased exponent in
+// row i (integer arithmetic on the exponent fields), A_i = s_i J_i converted to
+// FP32, and the row sum of |A_i| (for ||A||_inf).  A zero row is singular.
+constexpr int kScaleThreads = 128;
+constexpr int kColPad = 144;  // >= 128 + 16 - 1, multiple of 4
+
+__global__ void __launch_bounds__(kScaleThreads) k_scale_rows(int n, const double* __restrict__ J,
+                                                              float* __restrict__ As, double2* __restrict__ rowinfo,
+                                                              int* __restrict__ status) {
+    __shared__ int s_e[kScaleThreads / 32];
+    __shared__ float s_sum[kScaleThreads / 32];
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double* row = J + (size_t)i * n;
+    int e = 0;
+    for (int j = tid; j < n; j += kScaleThreads) e = max(e, (__double2hiint(row[j]) >> 20) & 0x7ff);
+    e = __reduce_max_sync(kFullMask, e);
+    if (lane == 0) s_e[warp] = e;
+    __syncthreads();
+    int E = s_e[0];
+    for (int w = 1; w < kScaleThreads / 32; ++w) E = max(E, s_e[w]);
+    // E = 0: zero (or subnormal) row; E = 0x7ff: Inf/NaN (already flagged by the assembly)
+    const bool ok = E > 0 && E < 0x7ff;
+    const double sc = ok ? __hiloint2double((1022 - E + 1023) << 20, 0) : 0.0;
+    float sum = 0.0f;
+    for (int j = tid; j < n; j += kScaleThreads) {
+        const float a = ok ? (float)(row[j] * sc) : 0.0f;
+        As[(size_t)i * n + j] = a;
+        sum += fabsf(a);
+    }
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFullMask, sum, off);
+    if (lane == 0) s_sum[warp] = sum;
+    __syncthreads();
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < kScaleThreads / 32; ++w) t += s_sum[w];
+        rowinfo[i] = make_double2(sc, (double)t);
+        if (!ok) atomicOr(status, E == 0 ? kStatusSingular : kStatusNonfinite);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Newton step for n = 2N <= 128 on one SM, FP64 work kept to O(n^2):
+//   - the row-scaled FP32 matrix A = diag(s) J (k_scale_rows) is inverted in
+//     place by Gauss-Jordan elimination held in registers: thread t owns column
+//     j = t mod n of the R consecutive rows g R .. g R + R - 1 (g = t div n);
+//   - pivoting is by columns (partial pivoting of A^T): step k takes the
+//     largest unused entry of row k, so the row of the step is static and the
+//     loop over it unrolls with every register index known at compile time;
+//     row k and the pivot column travel through double-buffered shared memory,
+//     two barriers per step, R FMAs per thread;
+//   - with pivot column q_k at step k the inverse is X[q_k][m] = a[k][q_m];
+//   - x <- x + X (b - A x) with the residual in FP64 (J copied to shared
+//     memory, one thread per row) until max|r| <= 4 sqrt(n) 2^-53 ||A|| ||x||;
+//   - FP64 LU fallback if the sweeps stall.
+template <int R>
+__global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, double* __restrict__ J,
+                                                           const float* __restrict__ As,
+                                                           const double2* __restrict__ rowinfo,
+                                                           const double* __restrict__ F,
+                                                           const XTab* __restrict__ xtab, double* __restrict__ coef,
+                                                           double rho, double* __restrict__ work,
+                                                           double* __restrict__ stats, int* __restrict__ status) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ __align__(16) float s_colq[2][kColPad];
+    __shared__ float s_rowk[2][128];
+    __shared__ float s_wc[2][8];
+    __shared__ int s_wi[2][8];
+    __shared__ int s_q[128];
+    __shared__ int s_qinv[128];
+    __shared__ double sv[kGjThreads / 32];
+    __shared__ int si[kGjThreads / 32];
+    __shared__ double s_x[128];
+    __shared__ double s_scale[128];
+    __shared__ float s_rf[128];
+    __shared__ double s_red[2][4];
+    __shared__ int s_piv, s_fail, s_done, s_conv;
+    __shared__ double s_anorm;
+    const int N = c.N;
+    const int n = 2 * N;
+    const int ldj = n + 1;
+    double* Js = dsm;                                             // [n][n+1] FP64 copy of J
+    float* Xs = reinterpret_cast<float*>(dsm + (size_t)n * ldj);  // [n][n] inverse
+    // G groups of R consecutive rows; G * R <= n + R - 1 < kColPad and
+    // G * n <= 1024 because the launcher picks R >= n / min(1024 / n, 32)
+    const int G = (n + R - 1) / R;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int j = tid % n;
+    const int g = tid / n;
+    const bool owner = g < G;
+    const int i0 = g * R;  // first owned row
+
+    // warp 0: norms of F, ||A||_inf, status
+    if (warp == 0) {
+        double mF = 0.0, mS = 0.0, an = 0.0;
+        bool bad = false;
+        for (int i = lane; i < n; i += 32) {
+            const double f = F[i];
+            const double sc = i < N ? xtab[i].Z : xtab[i - N].G;
+            mF = fmax(mF, fabs(f));
+            mS = fmax(mS, fabs(f) * sc);
+            bad |= !isfinite(f);
+            an = fmax(an, rowinfo[i].y);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            mF = fmax(mF, __shfl_xor_sync(kFullMask, mF, off));
+            mS = fmax(mS, __shfl_xor_sync(kFullMask, mS, off));
+            an = fmax(an, __shfl_xor_sync(kFullMask, an, off));
+        }
+        bad = __any_sync(kFullMask, bad);
+        if (lane == 0) {
+            stats[0] = bad ? INFINITY : mF;
+            stats[1] = mS;
+            stats[2] = 0.0;
+            s_anorm = an;
+            s_fail = ((*status) & (kStatusNonfinite | kStatusSingular)) | (bad ? kStatusNonfinite : 0);
+            s_done = 0;
+        }
+    }
+    for (int i = tid; i < n; i += kGjThreads) s_scale[i] = rowinfo[i].x;
+    for (int i = n + tid; i < kColPad; i += kGjThreads) s_colq[0][i] = s_colq[1][i] = 0.0f;  // rows past n
+    for (int idx = tid; idx < n * n; idx += kGjThreads) Js[(idx / n) * ldj + (idx % n)] = J[idx];
+    float v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + r;
+        v[r] = (owner && i < n) ? As[(size_t)i * n + j] : 0.0f;
+    }
+    bool used = false;  // this thread's column has been a pivot column
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+
+    for (int gs = 0; gs < G; ++gs) {
+        // warps that hold threads of group gs
+        const int w0 = (gs * n) >> 5;
+        const int w1 = (gs * n + n - 1) >> 5;
+        const bool in_group_warp = warp >= w0 && warp <= w1;
+#pragma unroll
+        for (int rs = 0; rs < R; ++rs) {
+            const int k = gs * R + rs;
+            if (k >= n) break;  // uniform
+            const int b = k & 1;
+            // [A] group gs publishes row k and per-warp candidates over its unused columns
+            if (in_group_warp) {
+                const bool mine = owner && g == gs;
+                float a = -1.0f;
+                int idx = 1 << 30;
+                if (mine) {
+                    s_rowk[b][j] = v[rs];
+                    if (!used) {
+                        a = fabsf(v[rs]);
+                        idx = j;
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float oa = __shfl_xor_sync(kFullMask, a, off);
+                    const int oi = __shfl_xor_sync(kFullMask, idx, off);
+                    if (oa > a || (oa == a && oi < idx)) {
+                        a = oa;
+                        idx = oi;
+                    }
+                }
+                if (lane == 0) {
+                    s_wc[b][warp - w0] = a;
+                    s_wi[b][warp - w0] = idx;
+                }
+            }
+            __syncthreads();
+            // [B] pivot column q; its owners publish it
+            float best = s_wc[b][0];
+            int q = s_wi[b][0];
+            for (int w = 1; w <= w1 - w0; ++w) {
+                const float a = s_wc[b][w];
+                const int qi = s_wi[b][w];
+                if (a > best || (a == best && qi < q)) {
+                    best = a;
+                    q = qi;
+                }
+            }
+            if (!(best > 1e-30f)) {
+                if (tid == 0) s_done = -1;
+                goto elimination_done;  // uniform: every thread read the same candidates
+            }
+            if (tid == 0) s_q[k] = q;
+            if (owner && j == q) {
+                used = true;
+#pragma unroll
+                for (int r = 0; r < R; ++r) s_colq[b][i0 + r] = v[r];
+            }
+            __syncthreads();
+            // [C] eliminate column q from every row but k, scale row k
+            if (owner) {
+                const float inv = 1.0f / s_rowk[b][q];
+                const float nk = (j == q) ? inv : s_rowk[b][j] * inv;
+                if (j == q) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] = 0.0f;
+                }
+                if (R >= 4) {
+                    const float4* col4 = reinterpret_cast<const float4*>(&s_colq[b][i0]);
+#pragma unroll
+                    for (int qq = 0; qq < R / 4; ++qq) {
+                        const float4 m = col4[qq];
+                        v[4 * qq + 0] = fmaf(-m.x, nk, v[4 * qq + 0]);
+                        v[4 * qq + 1] = fmaf(-m.y, nk, v[4 * qq + 1]);
+                        v[4 * qq + 2] = fmaf(-m.z, nk, v[4 * qq + 2]);
+                        v[4 * qq + 3] = fmaf(-m.w, nk, v[4 * qq + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] = fmaf(-s_colq[b][i0 + r], nk, v[r]);
+                }
+                if (g == gs) v[rs] = nk;
+            }
+        }
+    }
+elimination_done:
+    __syncthreads();
+    // X[q_k][m] = a[k][q_m]
+    if (tid < n && s_done == 0) s_qinv[s_q[tid]] = tid;
+    __syncthreads();
+    if (owner && s_done == 0) {
+        const int m = s_qinv[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = i0 + r;
+            if (i < n) Xs[s_q[i] * n + m] = v[r];
+        }
+    }
+    if (tid < n) s_x[tid] = 0.0;
+    if (tid == 0) s_conv = 0;
+    __syncthreads();
+
+    int sweeps = 0;
+    if (s_done == 0) {
+        const double tolfac = 4.0 * sqrt((double)n) * 0x1p-53 * s_anorm;
+        for (int it = 0; it <= kRefineMax; ++it) {
+            // FP64 residual, one thread per row (4 warps)
+            if (tid < 128) {
+                double rm = 0.0, xm = 0.0;
+                if (tid < n) {
+                    const double* Jr = Js + (size_t)tid * ldj;
+                    double a0 = 0.0, a1 = 0.0;
+                    int jj = 0;
+                    for (; jj + 1 < n; jj += 2) {
+                        a0 = fma(Jr[jj], s_x[jj], a0);
+                        a1 = fma(Jr[jj + 1], s_x[jj + 1], a1);
+                    }
+                    if (jj < n) a0 = fma(Jr[jj], s_x[jj], a0);
+                    const double r = s_scale[tid] * (F[tid] - (a0 + a1));
+                    s_rf[tid] = (float)r;
+                    rm = isfinite(r) ? fabs(r) : INFINITY;
+                    xm = fabs(s_x[tid]);
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    rm = fmax(rm, __shfl_xor_sync(kFullMask, rm, off));
+                    xm = fmax(xm, __shfl_xor_sync(kFullMask, xm, off));
+                }
+                if (lane == 0) {
+                    s_red[0][warp] = rm;
+                    s_red[1][warp] = xm;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const double RM = fmax(fmax(s_red[0][0], s_red[0][1]), fmax(s_red[0][2], s_red[0][3]));
+                const double XM = fmax(fmax(s_red[1][0], s_red[1][1]), fmax(s_red[1][2], s_red[1][3]));
+                int st = 0;                      // 0: continue, 1: converged, 2: give up
+                if (!isfinite(RM)) st = 2;
+                else if (RM <= tolfac * XM) st = 1;
+                else if (it == kRefineMax) st = 2;
+                s_conv = st;
+            }
+            __syncthreads();
+            const int st = s_conv;
+            if (st) break;
+            ++sweeps;
+            // x += X r  (FP32 products, 8 threads per row)
+            {
+                const int i = tid >> 3, part = tid & 7;
+                float acc = 0.0f;
+                if (i < n)
+                    for (int jj = part; jj < n; jj += 8) acc = fmaf(Xs[i * n + jj], s_rf[jj], acc);
+                acc += __shfl_xor_sync(kFullMask, acc, 4);
+                acc += __shfl_xor_sync(kFullMask, acc, 2);
+                acc += __shfl_xor_sync(kFullMask, acc, 1);
+                if (part == 0 && i < n) s_x[i] += (double)acc;
+            }
+            __syncthreads();
+        }
+    }
+    const bool converged = (s_done == 0) && (s_conv == 1);
+    double* xres = work + n;
+    if (converged) {
+        if (tid < n) xres[tid] = s_x[tid];
+        __syncthreads();
+    } else {
+        for (int i = tid; i < n; i += kGjThreads) work[i] = F[i];
+        __syncthreads();
+        lu_fp64_block(n, J, work, xres, &s_fail, &s_piv, sv, si);
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+    if (warp == 0) {
+        double mD = 0.0;
+        bool bad = false;
+        for (int i = lane; i < n; i += 32) {
+            mD = fmax(mD, fabs(xres[i]));
+            bad |= !isfinite(xres[i]);
+        }
+        for (int off = 16; off > 0; off >>= 1) mD = fmax(mD, __shfl_xor_sync(kFullMask, mD, off));
+        bad = __any_sync(kFullMask, bad);
+        if (lane == 0) {
+            stats[2] = mD;
+            stats[3] = converged ? (double)sweeps : -1.0;
+            if (bad) s_fail = kStatusNonfinite;
+        }
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) atomicOr(status, s_fail);
+        return;
+    }
+    for (int i = tid; i < n; i += kGjThreads) coef[i] = fma(-rho, xres[i], coef[i]);
+}
+
+// ------------------------------------------------------------------------
 __global__ void k_dressing(const Consts c, const double* __restrict__ coef, int n, const double* __restrict__ x,
                            double* __restrict__ lG, double* __restrict__ lZ, int* __restrict__ status) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -982,10 +1329,11 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
                              const Row* rows, const YTab* ytab, const double* phiy, const double* Upart,
                              const double* Vpart, double* D, cudaStream_t s) {
     (void)Rt;
+    const dim3 grid(c.N + 2, full ? (c.N + kRowJ - 1) / kRowJ : 1);
     if (full)
-        k_rowreduce<true><<<c.N + 2, kRowBlock, 0, s>>>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D);
+        k_rowreduce<true><<<grid, kRowBlock, 0, s>>>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D);
     else
-        k_rowreduce<false><<<c.N + 2, kRowBlock, 0, s>>>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D);
+        k_rowreduce<false><<<grid, kRowBlock, 0, s>>>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D);
     return cudaGetLastError();
 }
 
@@ -999,11 +1347,29 @@ cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const 
 }
 
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
-                             double* work, double* stats, int* status, cudaStream_t s) {
+                             double* work, float* As, double2* rowinfo, double* stats, int* status, cudaStream_t s) {
     const int n = 2 * c.N;
-    if (n <= kGjMaxN) {
+    cudaError_t e = cudaSuccess;
+    if (n <= 128) {
+        k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const size_t smem = sizeof(double) * (size_t)n * (n + 1) + sizeof(float) * (size_t)n * n;
+        const int G = kGjThreads / n < 32 ? kGjThreads / n : 32;  // same as in the kernel
+        const int R = (n + G - 1) / G;
+#define DSE_LAUNCH_REG(RR)                                                                                   \
+    e = cudaFuncSetAttribute(k_newton_reg<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    if (e != cudaSuccess) return e;                                                                          \
+    k_newton_reg<RR><<<1, kGjThreads, smem, s>>>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status);
+        if (R <= 1) { DSE_LAUNCH_REG(1) }
+        else if (R <= 2) { DSE_LAUNCH_REG(2) }
+        else if (R <= 4) { DSE_LAUNCH_REG(4) }
+        else if (R <= 8) { DSE_LAUNCH_REG(8) }
+        else { DSE_LAUNCH_REG(16) }
+#undef DSE_LAUNCH_REG
+    } else if (n <= kGjMaxN) {
         const size_t smem = sizeof(float) * (size_t)n * 2 * n;
-        cudaError_t e = cudaFuncSetAttribute(k_newton_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_newton_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_newton_mixed<<<1, kGjThreads, smem, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
     } else {

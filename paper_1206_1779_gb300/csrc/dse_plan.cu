@@ -33,6 +33,8 @@ struct dse_plan {
     double* J;
     double* F;
     double* work;
+    float* As;          // row-scaled FP32 copy of J (Newton step)
+    double2* rowinfo;   // row scales and row sums (Newton step)
     double* stats;  // 4 doubles, followed by the int status word
     int* status;
     // Schwinger-function rule (allocated on first use, per node count)
@@ -65,7 +67,7 @@ int check_problem(const dse_problem* p) {
     if (!isfinite(p->g2nc) || !isfinite(p->kappa) || !isfinite(p->delta) || !isfinite(p->ginv_G) ||
         !isfinite(p->zinv_Z))
         return DSE_ERR_ARG;
-    if (p->radial_mode != 0 || p->precision != 0) return DSE_ERR_UNSUPPORTED;
+    if (p->radial_mode != 0 || (p->precision != 0 && p->precision != 1)) return DSE_ERR_UNSUPPORTED;
     if (p->extrap_mode != 0 && p->extrap_mode != 1) return DSE_ERR_UNSUPPORTED;
     return DSE_OK;
 }
@@ -158,10 +160,11 @@ TripleArgs triple_args(const dse_plan* pl, const double* coef) {
     return a;
 }
 
-// tables -> triple kernel -> per-row contraction -> assembly
-int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool full) {
+// tables -> quadrature kernel -> per-row contraction -> assembly.  fp32: the
+// FP32-integrand kernel (mixed precision) instead of the FP64 one.
+int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool full, bool fp32 = false) {
     cudaError_t e = launch_tables(pl->c, coef, pl->rad, pl->xcol, pl->ytab, pl->phiy, pl->xtab, pl->phix, pl->stream);
-    const bool timed = pl->profiling && pl->n_ev < 4096;
+    const bool timed = pl->profiling && pl->n_ev < 4096 && !fp32;
     if (timed && e == cudaSuccess) {
         e = cudaEventCreate(&pl->ev[2 * pl->n_ev]);
         if (e == cudaSuccess) {
@@ -170,7 +173,9 @@ int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool fu
         }
         if (e == cudaSuccess) e = cudaEventRecord(pl->ev[2 * pl->n_ev], pl->stream);
     }
-    if (e == cudaSuccess) e = launch_triple(full, triple_args(pl, coef), pl->stream);
+    if (e == cudaSuccess)
+        e = fp32 ? launch_triple32(full, triple_args(pl, coef), pl->stream)
+                 : launch_triple(full, triple_args(pl, coef), pl->stream);
     if (timed && e == cudaSuccess) {
         e = cudaEventRecord(pl->ev[2 * pl->n_ev + 1], pl->stream);
         ++pl->n_ev;
@@ -180,6 +185,22 @@ int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool fu
         e = launch_rowreduce(full, pl->c, pl->Rt, pl->KS, pl->nch, pl->rad, pl->ang, pl->rows, pl->ytab, pl->phiy,
                              pl->Upart, pl->Vpart, pl->D, pl->stream);
     if (e == cudaSuccess) e = launch_assemble(full, pl->c, pl->xtab, pl->phix, pl->D, J, F, pl->status, pl->stream);
+    return cuda_status(e);
+}
+
+// Newton matrix of the plan's precision: FP64 throughout, or (mixed) J from FP32
+// integrands followed by an FP64 residual pass that overwrites F (f64_residual).
+int build_newton(dse_plan* pl, const double* coef, double* J, double* F, bool f64_residual) {
+    if (pl->prob.precision == 0) return build_system(pl, coef, J, F, true, false);
+    int st = build_system(pl, coef, J, F, true, true);
+    if (st || !f64_residual || !F) return st;
+    // the FP64 residual pass reuses the tables, writes Upart and the Pi entries of D only
+    cudaError_t e = launch_triple(false, triple_args(pl, coef), pl->stream);
+    if (e == cudaSuccess)
+        e = launch_rowreduce(false, pl->c, pl->Rt, pl->KS, pl->nch, pl->rad, pl->ang, pl->rows, pl->ytab, pl->phiy,
+                             pl->Upart, pl->Vpart, pl->D, pl->stream);
+    if (e == cudaSuccess) e = launch_assemble(false, pl->c, pl->xtab, pl->phix, pl->D, nullptr, F, pl->status, pl->stream);
+    pl->launches += 3;
     return cuda_status(e);
 }
 
@@ -239,6 +260,8 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_J = off; off = align_up(off + sizeof(double) * (size_t)n * n);
     size_t o_F = off; off = align_up(off + sizeof(double) * n);
     size_t o_work = off; off = align_up(off + sizeof(double) * 2 * n);
+    size_t o_As = off; off = align_up(off + sizeof(float) * (size_t)n * n);
+    size_t o_ri = off; off = align_up(off + sizeof(double2) * n);
     size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + sizeof(int));
     // Gauss-Legendre scratch (set-up only): nodes/weights for both rules and 1/k
     size_t o_gl = off; off = align_up(off + sizeof(double) * (2 * (size_t)nr + 2 * (size_t)na + gmax + 2));
@@ -264,6 +287,8 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->J = (double*)(base + o_J);
     pl->F = (double*)(base + o_F);
     pl->work = (double*)(base + o_work);
+    pl->As = (float*)(base + o_As);
+    pl->rowinfo = (double2*)(base + o_ri);
     pl->stats = (double*)(base + o_misc);
     pl->status = (int*)(base + o_misc + 4 * sizeof(double));
     double* gl = (double*)(base + o_gl);
@@ -343,18 +368,26 @@ int dse_residual(dse_plan* plan, const double* d_coeffs, double* d_F) {
 
 int dse_newton_matrix(dse_plan* plan, const double* d_coeffs, double* d_J, double* d_F) {
     if (!plan || !d_coeffs || !d_J) return DSE_ERR_ARG;
-    return build_system(plan, d_coeffs, d_J, d_F, true);
+    return build_newton(plan, d_coeffs, d_J, d_F, true);
 }
+
+namespace {
+// One Newton step; in mixed precision f64_residual selects the FP64 residual
+// (otherwise F comes from the FP32 integrands as well).
+int newton_step_impl(dse_plan* plan, double* d_coeffs, double rho, double* h_stats, bool f64_residual) {
+    int st = build_newton(plan, d_coeffs, plan->J, plan->F, f64_residual);
+    if (st) return st;
+    cudaError_t e = launch_lu_newton(plan->c, plan->J, plan->F, plan->xtab, d_coeffs, rho, plan->work, plan->As,
+                                     plan->rowinfo, plan->stats, plan->status, plan->stream);
+    plan->launches += 2 * plan->c.N <= 128 ? 2 : 1;
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    return read_status(plan, h_stats);
+}
+}  // namespace
 
 int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stats) {
     if (!plan || !d_coeffs || !isfinite(rho)) return DSE_ERR_ARG;
-    int st = build_system(plan, d_coeffs, plan->J, plan->F, true);
-    if (st) return st;
-    cudaError_t e = launch_lu_newton(plan->c, plan->J, plan->F, plan->xtab, d_coeffs, rho, plan->work, plan->stats,
-                                     plan->status, plan->stream);
-    plan->launches += 1;
-    if (e != cudaSuccess) return DSE_ERR_CUDA;
-    return read_status(plan, h_stats);
+    return newton_step_impl(plan, d_coeffs, rho, h_stats, true);
 }
 
 int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double rho_relax, int n_relax,
@@ -363,9 +396,18 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
     double st3[4] = {0.0, 0.0, 0.0, 0.0};
     int it = 0;
     int st = DSE_ERR_NOT_CONVERGED;
+    // mixed precision: FP32 residual while the dimensionless residual is above
+    // kSwitch (where FP32 rounding cannot stall the iteration), FP64 after
+    const double kSwitch = 1e-5;
+    bool f64_res = plan->prob.precision == 0;
     for (; it < max_iter; ++it) {
         const double rho = it < n_relax ? rho_relax : 1.0;
-        const int s = dse_newton_step(plan, d_coeffs, rho, st3);
+        const int s = newton_step_impl(plan, d_coeffs, rho, st3, f64_res);
+        if (!s && !f64_res && st3[1] < kSwitch) {
+            // this step's residual was FP32: continue from here with FP64 residuals
+            f64_res = true;
+            continue;
+        }
         if (s) {
             st = s;
             ++it;

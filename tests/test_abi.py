@@ -58,7 +58,7 @@ def test_plan_create_rejects_bad_problem(lib, inputs, bad):
 
 def test_plan_create_rejects_unsupported_modes(lib, inputs):
     from paper_1206_1779_gb300 import DSE_ERR_UNSUPPORTED, Problem
-    for over in [dict(radial_mode=1), dict(precision=1), dict(extrap_mode=7)]:
+    for over in [dict(radial_mode=1), dict(precision=2), dict(extrap_mode=7)]:
         p = inputs.problem(8, 16, 16)
         p.update(over)
         h = ctypes.c_void_p()
