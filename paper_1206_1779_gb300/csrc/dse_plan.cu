@@ -397,17 +397,20 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
     int it = 0;
     int st = DSE_ERR_NOT_CONVERGED;
     // mixed precision: FP32 residual while the dimensionless residual is above
-    // kSwitch (where FP32 rounding cannot stall the iteration), FP64 after
+    // kSwitch and still falling by at least a half per step (FP32 rounding has
+    // not become the floor), FP64 residual after
     const double kSwitch = 1e-5;
     bool f64_res = plan->prob.precision == 0;
+    double prev = INFINITY;
     for (; it < max_iter; ++it) {
         const double rho = it < n_relax ? rho_relax : 1.0;
         const int s = newton_step_impl(plan, d_coeffs, rho, st3, f64_res);
-        if (!s && !f64_res && st3[1] < kSwitch) {
+        if (!s && !f64_res && (st3[1] < kSwitch || (it >= n_relax && st3[1] > 0.5 * prev))) {
             // this step's residual was FP32: continue from here with FP64 residuals
             f64_res = true;
             continue;
         }
+        prev = st3[1];
         if (s) {
             st = s;
             ++it;
