@@ -188,8 +188,18 @@ int dse_ref_basis(const dse_ref_problem* p, double x, double* phi) {
  * above lambda2  G = G_UV [omega ln(x/lambda2) + 1]^delta,
  * Z = Z_UV [...]^gamma, with A, B, G_UV, Z_UV matched to the series at the
  * end points (Sec. 2).  extrap_mode 1 continues the end values as constants. */
+static void dressing_w(const dse_ref_problem* p, const consts* k, const double* c, double x,
+                       double* lnG, double* lnZ, double* phi_out, double* dG_dw, double* dZ_dw);
+
 static void dressing(const dse_ref_problem* p, const consts* k, const double* c, double x,
                      double* lnG, double* lnZ, double* phi_out) {
+    dressing_w(p, k, c, x, lnG, lnZ, phi_out, NULL, NULL);
+}
+
+/* ... and the derivatives of ln G(x), ln Z(x) with respect to omega, which
+ * enters only the UV form: d/d omega of ln(1 + omega ln(x/lambda2)). */
+static void dressing_w(const dse_ref_problem* p, const consts* k, const double* c, double x,
+                       double* lnG, double* lnZ, double* phi_out, double* dG_dw, double* dZ_dw) {
     double phi_local[1024];
     double* phi = phi_out ? phi_out : phi_local;
     basis(k, x, phi);
@@ -205,11 +215,19 @@ static void dressing(const dse_ref_problem* p, const consts* k, const double* c,
             lg += -p->kappa * r;
             lz += 2.0 * p->kappa * r;
         } else if (x > p->lambda2) {
-            double L = log1p(k->omega * (log(x) - k->ln_lam2));
+            double lu = log(x) - k->ln_lam2;
+            double L = log1p(k->omega * lu);
             lg += p->delta * L;
             lz += k->gam * L;
+            if (dG_dw) *dG_dw = p->delta * lu / (1.0 + k->omega * lu);
+            if (dZ_dw) *dZ_dw = k->gam * lu / (1.0 + k->omega * lu);
+            *lnG = lg;
+            *lnZ = lz;
+            return;
         }
     }
+    if (dG_dw) *dG_dw = 0.0;
+    if (dZ_dw) *dZ_dw = 0.0;
     *lnG = lg;
     *lnZ = lz;
 }
@@ -381,6 +399,92 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
 int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
                         double* PiG, double* PiZ, double* d_PiG, double* d_PiZ) {
     return self_energy_impl(p, c, x, 0, PiG, PiZ, d_PiG, d_PiZ);
+}
+
+/* Derivatives of Pi_G(x), Pi_Z(x) with respect to g^2 Nc.  The coupling enters
+ * through the prefactor K = g^2 Nc/(2 pi)^3 (so Pi/g2nc) and through
+ * omega = 11 g^2 Nc/(48 pi^2) in the UV forms of G(z), Z(z) for z > lambda2:
+ *   d Pi/d g2nc = Pi/g2nc + (d omega/d g2nc) sum h * d ln h/d omega,
+ * with d ln W/d omega = p dlnG/dw + q dlnZ/dw, d ln G(z)/d omega for the M term
+ * and d ln Z(z)/d omega for the ghost term (y <= lambda2 carries no omega). */
+static int self_energy_dg2(const dse_ref_problem* p, const double* c, double x, double* dPiG, double* dPiZ) {
+    consts k = make_consts(p);
+    int N = p->n_cheb, nr = p->n_radial, na = p->n_angular;
+    int gluon = x > 0.0;
+    double* y = (double*)malloc(sizeof(double) * nr);
+    double* W = (double*)malloc(sizeof(double) * nr);
+    double* th = (double*)malloc(sizeof(double) * na);
+    double* wt = (double*)malloc(sizeof(double) * na);
+    if (!y || !W || !th || !wt) { free(y); free(W); free(th); free(wt); return DSE_REF_ERR_ARG; }
+    (void)N;
+    dse_ref_quadrature(p, y, W, th, wt);
+    nsum sG = {0, 0}, sZ = {0, 0}, wG = {0, 0}, wZ = {0, 0};
+    for (int kk = 0; kk < nr; ++kk) {
+        double lGy, lZy;
+        dressing(p, &k, c, y[kk], &lGy, &lZy, NULL);
+        double Gy = exp(lGy);
+        for (int l = 0; l < na; ++l) {
+            double sh = sin(0.5 * th[l]);
+            double sn = sin(th[l]);
+            double sig = sh * sh, s2 = sn * sn;
+            double M = 0.0, Q = 0.0, z;
+            if (gluon) kernels(x, y[kk], sig, s2, &M, &Q, &z);
+            else { double sy = sqrt(y[kk]); z = sy * sy; }
+            double lGz, lZz, gw, zw;
+            dressing_w(p, &k, c, z, &lGz, &lZz, NULL, &gw, &zw);
+            double wgt = W[kk] * wt[l];
+            double fG = wgt * y[kk] * Gy * s2 * s2 * exp(lZz) / (z * z);
+            ns_add(&sG, fG);
+            ns_add(&wG, fG * zw);
+            if (gluon) {
+                double Wv = exp(k.pG * (lGy + lGz) + k.qZ * (lZy + lZz));
+                double hQ = wgt * s2 * Q * Wv;
+                double hM = wgt * s2 * M * Gy * exp(lGz);
+                ns_add(&sZ, hQ + hM);
+                ns_add(&wZ, hQ * (k.pG * gw + k.qZ * zw) + hM * gw);
+            }
+        }
+    }
+    double dw = 11.0 / (48.0 * PI_D * PI_D);
+    double preZ = gluon ? k.K / (3.0 * x) : 0.0;
+    /* Pi_G = -K S_G, Pi_Z = preZ S_Z; K and preZ are proportional to g2nc */
+    *dPiG = -k.K * (ns_val(&sG) / p->g2nc + dw * ns_val(&wG));
+    *dPiZ = gluon ? preZ * (ns_val(&sZ) / p->g2nc + dw * ns_val(&wZ)) : 0.0;
+    free(y); free(W); free(th); free(wt);
+    return DSE_REF_OK;
+}
+
+int dse_ref_param_derivatives(const dse_ref_problem* p, const double* c, double* dF) {
+    int st = check_problem(p);
+    if (st) return st;
+    if (!c || !dF || p->n_cheb > 1024) return DSE_REF_ERR_ARG;
+    int N = p->n_cheb;
+    double* xc = (double*)malloc(sizeof(double) * N);
+    double* dG = (double*)malloc(sizeof(double) * (N + 2));
+    double* dZ = (double*)malloc(sizeof(double) * (N + 2));
+    int* rst = (int*)calloc((size_t)(N + 2), sizeof(int));
+    if (!xc || !dG || !dZ || !rst) { free(xc); free(dG); free(dZ); free(rst); return DSE_REF_ERR_ARG; }
+    dse_ref_collocation(p, xc);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < N + 2; ++r) {
+        double xr = r < N ? xc[r] : (r == N ? p->x_Z : p->x_G);
+        rst[r] = self_energy_dg2(p, c, xr, &dG[r], &dZ[r]);
+    }
+    for (int r = 0; r < N + 2; ++r)
+        if (rst[r]) { st = rst[r]; break; }
+    if (!st) {
+        /* columns: g2nc, ginv_G, zinv_Z */
+        for (int i = 0; i < N; ++i) {
+            dF[(size_t)i * 3 + 0] = -dZ[i] + dZ[N];
+            dF[(size_t)i * 3 + 1] = 0.0;
+            dF[(size_t)i * 3 + 2] = -1.0;
+            dF[(size_t)(N + i) * 3 + 0] = -dG[i] + dG[N + 1];
+            dF[(size_t)(N + i) * 3 + 1] = -1.0;
+            dF[(size_t)(N + i) * 3 + 2] = 0.0;
+        }
+    }
+    free(xc); free(dG); free(dZ); free(rst);
+    return st;
 }
 
 /* ------------------------------------------------ residual and matrix ---- */

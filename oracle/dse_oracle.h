@@ -100,6 +100,10 @@ int dse_ref_newton_matrix(const dse_ref_problem* p, const double* c, double* J, 
  * F_i (AF nullable).  Same layout as dse_ref_newton_matrix. */
 int dse_ref_newton_matrix_magnitudes(const dse_ref_problem* p, const double* c, double* A, double* AF);
 
+/* Derivatives of F (2N rows) with respect to the parameters (g2nc, ginv_G, zinv_Z),
+ * 2N x 3 row-major.  g2nc enters through K and through omega in the UV forms. */
+int dse_ref_param_derivatives(const dse_ref_problem* p, const double* c, double* dF);
+
 /* Solve A x = b (n x n row-major) by LU with partial pivoting. */
 int dse_ref_lu_solve(int n, const double* A, const double* b, double* x);
 

@@ -68,6 +68,7 @@ def lib():
                 "dse_ref_residual": [P, _D, _D],
                 "dse_ref_newton_matrix": [P, _D, _D, _D],
                 "dse_ref_newton_matrix_magnitudes": [P, _D, _D, _D],
+                "dse_ref_param_derivatives": [P, _D, _D],
                 "dse_ref_lu_solve": [ctypes.c_int, _D, _D, _D],
                 "dse_ref_newton_step": [P, _D, ctypes.c_double, _D],
                 "dse_ref_schwinger_nodes": [P, ctypes.c_int, _D, _D],
@@ -196,6 +197,15 @@ def newton_matrix_magnitudes(params: dict, c):
     _chk(lib().dse_ref_newton_matrix_magnitudes(ctypes.byref(p), _ptr(c), _ptr(A), _ptr(AF)),
          "newton_matrix_magnitudes")
     return A, AF
+
+
+def param_derivatives(params: dict, c) -> np.ndarray:
+    """dF/d(g2nc, ginv_G, zinv_Z): 2N x 3."""
+    p = make_problem(params)
+    c = _f64(c)
+    dF = np.empty((2 * p.n_cheb, 3))
+    _chk(lib().dse_ref_param_derivatives(ctypes.byref(p), _ptr(c), _ptr(dF)), "param_derivatives")
+    return dF
 
 
 def lu_solve(A, b) -> np.ndarray:

@@ -90,3 +90,15 @@ def starting_guess(params: dict, seed: int = 0, noise: float = 0.01) -> np.ndarr
 def schwinger_times(n_t: int = 4096, seed: int = 0, lo: float = 0.1, hi: float = 50.0) -> np.ndarray:
     """Euclidean times t ~ U[lo, hi] from numpy's default_rng(seed)."""
     return np.random.default_rng(seed).uniform(lo, hi, size=int(n_t)).astype(np.float64)
+
+
+def loss_momenta(n: int = 64, seed: int = 0, lo: float = 1e-4, hi: float = 1e4) -> np.ndarray:
+    """Momenta x = p^2 log-uniform in [lo, hi] from numpy's default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), size=int(n))).astype(np.float64)
+
+
+def target_factors(n: int = 64, seed: int = 1, spread: float = 0.05) -> np.ndarray:
+    """Factors 1 + spread * U(-1, 1) from numpy's default_rng(seed): targets are a
+    converged Z(x) times these."""
+    return (1.0 + spread * np.random.default_rng(seed).uniform(-1.0, 1.0, size=int(n))).astype(np.float64)
