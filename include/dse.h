@@ -141,6 +141,50 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
 int dse_schwinger(dse_plan* plan, const double* d_coeffs, const double* d_t, int n_t,
                   int n_nodes, double* d_delta);
 
+/* ---- Differentiation --------------------------------------------------------
+ * The residual F(c; g2nc, ginv_G, zinv_Z) of Sec. 3 as a function of the
+ * coefficients and of the coupling g^2 Nc and the two renormalisation
+ * (boundary) values G(x_G)^{-1}, Z(x_Z)^{-1} of Sec. 2.2.  All derivatives are
+ * FP64 whatever the plan's precision.  All calls are queued on the plan's
+ * stream without waiting, except dse_adjoint_solve. */
+
+/* Replace g2nc, ginv_G and zinv_Z of the plan's problem (the quadrature rules
+ * and workspace are kept).  Same argument checks as dse_plan_create. */
+int dse_plan_set_couplings(dse_plan* plan, double g2nc, double ginv_G, double zinv_Z);
+
+/* Vector-Jacobian product out_j = sum_i v_i dF_i/dc_j (2N each).  The products
+ * are contracted from the per-external-momentum derivative sums of Sec. 3
+ * without forming the 2N x 2N Newton matrix; d_F (nullable) receives F(c). */
+int dse_vjp(dse_plan* plan, const double* d_coeffs, const double* d_v, double* d_out, double* d_F);
+
+/* Parameter derivatives of F.  d_dF (nullable): 2N x 3 row-major, columns
+ * dF/d g2nc, dF/d ginv_G, dF/d zinv_Z.  g2nc enters through the prefactor
+ * g^2 Nc/(2 pi)^3 of both self-energies and through omega = 11 g^2 Nc/(48 pi^2)
+ * of the UV forms of G(z), Z(z) for z > lambda2 (Sec. 2); the boundary values
+ * enter the subtracted rows with coefficient -1.  d_v (nullable, 2N) with d_vdF
+ * (3): v^T dF.  At least one of d_dF, d_v.  DSE_ERR_ARG if g2nc = 0. */
+int dse_param_derivatives(dse_plan* plan, const double* d_coeffs, double* d_dF, const double* d_v,
+                          double* d_vdF);
+
+/* Adjoint of the Newton system at c: solves J(c)^T lambda = g (2N each; J the
+ * FP64 Newton matrix of dse_newton_matrix).  The rows of J are first scaled by
+ * exact powers of two (S), and (S J)^T mu = g is solved with the dense solver of
+ * dse_newton_step; lambda = S mu.  For the implicit function c*(theta) defined
+ * by F(c*, theta) = 0, dL/dtheta = -lambda^T dF/dtheta with g = dL/dc*.
+ * h_stats (nullable, 4): ||g||_inf, unused, ||lambda||_inf, refinement sweeps
+ * (-1: FP64 LU).  Waits for the stream. */
+int dse_adjoint_solve(dse_plan* plan, const double* d_coeffs, const double* d_g, double* d_lambda,
+                      double* h_stats);
+
+/* Vector-Jacobian product of dse_dressing at n points x (positive):
+ *   d_out[j] = sum_m gZ_m d ln Z(x_m)/d a_j,  d_out[N + j] = sum_m gG_m d ln G(x_m)/d b_j,
+ * i.e. sums of the basis phi_j(x_m) (s clamped to [-1, 1] outside [eps2, lambda2]);
+ * d_out_g2nc (nullable, 1 double): sum_m gG_m d ln G/d g2nc + gZ_m d ln Z/d g2nc,
+ * non-zero only through the UV form for x_m > lambda2.  Non-positive x flag
+ * DSE_ERR_NONFINITE in the plan status. */
+int dse_dressing_vjp(dse_plan* plan, int n, const double* d_x, const double* d_gG, const double* d_gZ,
+                     double* d_out, double* d_out_g2nc);
+
 /* Allocation-free residual.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code that runs where device
  * memory is owned by another allocator (a framework's caching pool, a fixed

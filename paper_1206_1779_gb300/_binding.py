@@ -21,7 +21,8 @@ DSE_MAX_CHEB = 256
 
 EXPORTS = ["dse_plan_create", "dse_plan_destroy", "dse_plan_set_stream", "dse_plan_status", "dse_quadrature",
            "dse_dressing", "dse_residual", "dse_newton_matrix", "dse_newton_step", "dse_solve", "dse_schwinger",
-           "dse_plan_profile", "dse_plan_counters", "dse_residual_static", "dse_status_string"]
+           "dse_plan_profile", "dse_plan_counters", "dse_residual_static", "dse_status_string",
+           "dse_plan_set_couplings", "dse_vjp", "dse_param_derivatives", "dse_adjoint_solve", "dse_dressing_vjp"]
 
 
 class DseError(RuntimeError):
@@ -87,6 +88,11 @@ def load(build_if_missing: bool = False):
         "dse_residual_static": [PP, _VP, _VP, _VP],
         "dse_plan_counters": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_double)],
+        "dse_plan_set_couplings": [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+        "dse_vjp": [_VP, _VP, _VP, _VP, _VP],
+        "dse_param_derivatives": [_VP, _VP, _VP, _VP, _VP],
+        "dse_adjoint_solve": [_VP, _VP, _VP, _VP, _D],
+        "dse_dressing_vjp": [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -222,6 +228,61 @@ class Plan:
         self._sync_stream()
         _check(self._L.dse_schwinger(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), _dev_ptr(t, n_t, "t"), n_t,
                                      int(n_nodes), _dev_ptr(out, n_t, "delta")), "dse_schwinger")
+        return out
+
+    def set_couplings(self, g2nc: float, ginv_G: float, zinv_Z: float) -> None:
+        self._sync_stream()
+        _check(self._L.dse_plan_set_couplings(self._h, float(g2nc), float(ginv_G), float(zinv_Z)),
+               "dse_plan_set_couplings")
+        self.params.update(g2nc=float(g2nc), ginv_G=float(ginv_G), zinv_Z=float(zinv_Z))
+
+    def vjp(self, coeffs, v, out=None, F=None):
+        """v^T dF/dc (2N); F (optional tensor) receives the residual."""
+        n = 2 * self.N
+        out = out if out is not None else self._new(n)
+        self._sync_stream()
+        _check(self._L.dse_vjp(self._h, _dev_ptr(coeffs, n, "coeffs"), _dev_ptr(v, n, "v"), _dev_ptr(out, n, "out"),
+                               _dev_ptr(F, n, "F") if F is not None else None), "dse_vjp")
+        return out
+
+    def param_derivatives(self, coeffs):
+        """dF/d(g2nc, ginv_G, zinv_Z): 2N x 3."""
+        n = 2 * self.N
+        dF = self._new(n, 3)
+        self._sync_stream()
+        _check(self._L.dse_param_derivatives(self._h, _dev_ptr(coeffs, n, "coeffs"), _dev_ptr(dF, 3 * n, "dF"),
+                                             None, None), "dse_param_derivatives")
+        return dF
+
+    def param_vjp(self, coeffs, v, out=None):
+        """v^T dF/d(g2nc, ginv_G, zinv_Z): 3."""
+        n = 2 * self.N
+        out = out if out is not None else self._new(3)
+        self._sync_stream()
+        _check(self._L.dse_param_derivatives(self._h, _dev_ptr(coeffs, n, "coeffs"), None, _dev_ptr(v, n, "v"),
+                                             _dev_ptr(out, 3, "vdF")), "dse_param_derivatives")
+        return out
+
+    def adjoint_solve(self, coeffs, g, out=None):
+        """lambda with J(c)^T lambda = g; returns (lambda, stats)."""
+        n = 2 * self.N
+        out = out if out is not None else self._new(n)
+        st = (ctypes.c_double * 4)()
+        self._sync_stream()
+        _check(self._L.dse_adjoint_solve(self._h, _dev_ptr(coeffs, n, "coeffs"), _dev_ptr(g, n, "g"),
+                                         _dev_ptr(out, n, "lambda"), ctypes.cast(st, _D)), "dse_adjoint_solve")
+        return out, tuple(st)
+
+    def dressing_vjp(self, x, gG, gZ, out=None, out_g2nc=None):
+        """(sum gZ dlnZ/da, sum gG dlnG/db) as one 2N vector, and optionally d/d g2nc into out_g2nc (1)."""
+        m = x.numel()
+        n = 2 * self.N
+        out = out if out is not None else self._new(n)
+        self._sync_stream()
+        _check(self._L.dse_dressing_vjp(self._h, m, _dev_ptr(x, m, "x"), _dev_ptr(gG, m, "gG"), _dev_ptr(gZ, m, "gZ"),
+                                        _dev_ptr(out, n, "out"),
+                                        _dev_ptr(out_g2nc, 1, "out_g2nc") if out_g2nc is not None else None),
+               "dse_dressing_vjp")
         return out
 
     def status(self) -> int:

@@ -84,4 +84,23 @@ cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, c
                              int nsplit, double* delta, int* status, cudaStream_t s);
 int schwinger_splits(int n_t, int n_nodes);
 
+// Differentiation (dse_adjoint.cu).
+constexpr int kDressingVjpMaxSplits = 64;
+// dPi: 2 (N + 2) scratch; dF (2N x 3) and/or vdF = v^T dF (3) are outputs.
+cudaError_t launch_param_derivatives(const Consts& c, const Rad* rad, const Ang* ang, const Row* rows,
+                                     const YTab* ytab, const double* coef, const double* D, double g2nc,
+                                     double* dPi, double* dF, const double* v, double* vdF, cudaStream_t s);
+cudaError_t launch_vjp(const Consts& c, const XTab* xtab, const double* phix, const double* D, const double* v,
+                       double* out, int* status, cudaStream_t s);
+// A <- (S A)^T with S the power-of-two row equilibration (scale: n doubles out);
+// then lambda <- S lambda and stats[2] = ||lambda||_inf after the solve.
+cudaError_t launch_equilibrate_transpose(int n, double* A, double* scale, cudaStream_t s);
+cudaError_t launch_adjoint_finish(int n, const double* scale, double* lam, double* stats, cudaStream_t s);
+int dressing_vjp_splits(int n);
+// part: dressing_vjp_splits(n) * (2N + 1) scratch
+cudaError_t launch_dressing_vjp(const Consts& c, int n, const double* x, const double* gG, const double* gZ,
+                                double* part, int nsplit, double* out, double* out_g2nc, int* status,
+                                cudaStream_t s);
+cudaError_t launch_row_prefactors(const Consts& c, Row* rows, int Rt, cudaStream_t s);
+
 }  // namespace dse

@@ -35,6 +35,7 @@ struct dse_plan {
     double* work;
     float* As;          // row-scaled FP32 copy of J (Newton step)
     double2* rowinfo;   // row scales and row sums (Newton step)
+    double* aux;        // derivative scratch: dPi rows, dressing-VJP partial sums
     double* stats;  // 4 doubles, followed by the int status word
     int* status;
     // Schwinger-function rule (allocated on first use, per node count)
@@ -160,9 +161,9 @@ TripleArgs triple_args(const dse_plan* pl, const double* coef) {
     return a;
 }
 
-// tables -> quadrature kernel -> per-row contraction -> assembly.  fp32: the
+// tables -> quadrature kernel -> per-row contraction (the D vectors).  fp32: the
 // FP32-integrand kernel (mixed precision) instead of the FP64 one.
-int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool full, bool fp32 = false) {
+cudaError_t build_rows(dse_plan* pl, const double* coef, bool full, bool fp32) {
     cudaError_t e = launch_tables(pl->c, coef, pl->rad, pl->xcol, pl->ytab, pl->phiy, pl->xtab, pl->phix, pl->stream);
     const bool timed = pl->profiling && pl->n_ev < 4096 && !fp32;
     if (timed && e == cudaSuccess) {
@@ -184,6 +185,12 @@ int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool fu
     if (e == cudaSuccess)
         e = launch_rowreduce(full, pl->c, pl->Rt, pl->KS, pl->nch, pl->rad, pl->ang, pl->rows, pl->ytab, pl->phiy,
                              pl->Upart, pl->Vpart, pl->D, pl->stream);
+    return e;
+}
+
+// ... followed by the assembly of J (full) and F.
+int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool full, bool fp32 = false) {
+    cudaError_t e = build_rows(pl, coef, full, fp32);
     if (e == cudaSuccess) e = launch_assemble(full, pl->c, pl->xtab, pl->phix, pl->D, J, F, pl->status, pl->stream);
     return cuda_status(e);
 }
@@ -262,6 +269,9 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_work = off; off = align_up(off + sizeof(double) * 2 * n);
     size_t o_As = off; off = align_up(off + sizeof(float) * (size_t)n * n);
     size_t o_ri = off; off = align_up(off + sizeof(double2) * n);
+    const size_t n_aux_a = 2 * (size_t)(N + 2) + 3;
+    const size_t n_aux_b = (size_t)kDressingVjpMaxSplits * (2 * (size_t)N + 1);
+    size_t o_aux = off; off = align_up(off + sizeof(double) * (n_aux_a > n_aux_b ? n_aux_a : n_aux_b));
     size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + sizeof(int));
     // Gauss-Legendre scratch (set-up only): nodes/weights for both rules and 1/k
     size_t o_gl = off; off = align_up(off + sizeof(double) * (2 * (size_t)nr + 2 * (size_t)na + gmax + 2));
@@ -289,6 +299,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->work = (double*)(base + o_work);
     pl->As = (float*)(base + o_As);
     pl->rowinfo = (double2*)(base + o_ri);
+    pl->aux = (double*)(base + o_aux);
     pl->stats = (double*)(base + o_misc);
     pl->status = (int*)(base + o_misc + 4 * sizeof(double));
     double* gl = (double*)(base + o_gl);
@@ -476,6 +487,76 @@ int dse_schwinger(dse_plan* plan, const double* d_coeffs, const double* d_t, int
     e = launch_schwinger(plan->c, d_coeffs, n_nodes, pn, wn, sigw, d_t, n_t, plan->sch_partial, nsplit, d_delta,
                          plan->status, s);
     plan->launches += n_t > 0 ? 3 : 1;
+    return cuda_status(e);
+}
+
+int dse_plan_set_couplings(dse_plan* plan, double g2nc, double ginv_G, double zinv_Z) {
+    if (!plan) return DSE_ERR_ARG;
+    dse_problem p = plan->prob;
+    p.g2nc = g2nc;
+    p.ginv_G = ginv_G;
+    p.zinv_Z = zinv_Z;
+    const int st = check_problem(&p);
+    if (st) return st;
+    plan->prob = p;
+    plan->c = make_consts(&p);
+    plan->launches += 1;
+    return cuda_status(launch_row_prefactors(plan->c, plan->rows, plan->Rt, plan->stream));
+}
+
+int dse_vjp(dse_plan* plan, const double* d_coeffs, const double* d_v, double* d_out, double* d_F) {
+    if (!plan || !d_coeffs || !d_v || !d_out) return DSE_ERR_ARG;
+    cudaError_t e = build_rows(plan, d_coeffs, true, false);
+    if (e == cudaSuccess && d_F)
+        e = launch_assemble(false, plan->c, plan->xtab, plan->phix, plan->D, nullptr, d_F, plan->status, plan->stream);
+    if (e == cudaSuccess) e = launch_vjp(plan->c, plan->xtab, plan->phix, plan->D, d_v, d_out, plan->status, plan->stream);
+    plan->launches += d_F ? 2 : 1;
+    return cuda_status(e);
+}
+
+int dse_param_derivatives(dse_plan* plan, const double* d_coeffs, double* d_dF, const double* d_v, double* d_vdF) {
+    if (!plan || !d_coeffs || (!d_dF && !d_v) || (!d_v != !d_vdF)) return DSE_ERR_ARG;
+    if (!(plan->prob.g2nc != 0.0)) return DSE_ERR_ARG;
+    cudaError_t e = build_rows(plan, d_coeffs, false, false);
+    if (e == cudaSuccess)
+        e = launch_param_derivatives(plan->c, plan->rad, plan->ang, plan->rows, plan->ytab, d_coeffs, plan->D,
+                                     plan->prob.g2nc, plan->aux, d_dF, d_v, d_vdF, plan->stream);
+    plan->launches += 2;
+    return cuda_status(e);
+}
+
+int dse_adjoint_solve(dse_plan* plan, const double* d_coeffs, const double* d_g, double* d_lambda, double* h_stats) {
+    if (!plan || !d_coeffs || !d_g || !d_lambda) return DSE_ERR_ARG;
+    const int n = 2 * plan->c.N;
+    int st = build_system(plan, d_coeffs, plan->J, plan->F, true, false);
+    if (st) return st;
+    // (S J)^T mu = g with S the power-of-two row equilibration of J, lambda = S mu
+    cudaError_t e = launch_equilibrate_transpose(n, plan->J, plan->aux, plan->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_lambda, 0, sizeof(double) * n, plan->stream);
+    // mu = 0 - (-1) Delta with (S J)^T Delta = g
+    if (e == cudaSuccess)
+        e = launch_lu_newton(plan->c, plan->J, d_g, plan->xtab, d_lambda, -1.0, plan->work, plan->As, plan->rowinfo,
+                             plan->stats, plan->status, plan->stream);
+    if (e == cudaSuccess) e = launch_adjoint_finish(n, plan->aux, d_lambda, plan->stats, plan->stream);
+    plan->launches += n <= 128 ? 5 : 4;
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    return read_status(plan, h_stats);
+}
+
+int dse_dressing_vjp(dse_plan* plan, int n, const double* d_x, const double* d_gG, const double* d_gZ, double* d_out,
+                     double* d_out_g2nc) {
+    if (!plan || n < 0 || !d_out) return DSE_ERR_ARG;
+    if (n > 0 && (!d_x || !d_gG || !d_gZ)) return DSE_ERR_ARG;
+    cudaError_t e;
+    if (n == 0) {
+        e = cudaMemsetAsync(d_out, 0, sizeof(double) * 2 * plan->c.N, plan->stream);
+        if (e == cudaSuccess && d_out_g2nc) e = cudaMemsetAsync(d_out_g2nc, 0, sizeof(double), plan->stream);
+        return cuda_status(e);
+    }
+    const int nsplit = dressing_vjp_splits(n);
+    e = launch_dressing_vjp(plan->c, n, d_x, d_gG, d_gZ, plan->aux, nsplit, d_out, d_out_g2nc, plan->status,
+                            plan->stream);
+    plan->launches += 2;
     return cuda_status(e);
 }
 
