@@ -45,7 +45,7 @@ static double ns_val(const nsum* a) { return a->s + a->c; }
  * q = -3 delta on Z (three-gluon vertex model with a = b = 3 delta),
  * omega = 11 Nc alpha / (12 pi) with alpha = g^2/(4 pi). */
 typedef struct {
-    int N;
+    int NZ, NG, N;            /* orders of ln Z and ln G; N = max(NZ, NG) */
     double K, gam, pG, qZ, omega;
     double L0, L1;            /* ln x = L0 + L1 s */
     double ln_eps2, ln_lam2;
@@ -53,7 +53,8 @@ typedef struct {
 
 static int check_problem(const dse_ref_problem* p) {
     if (!p) return DSE_REF_ERR_ARG;
-    if (p->n_cheb < 1 || p->n_radial < 1 || p->n_angular < 1) return DSE_REF_ERR_ARG;
+    if (p->n_cheb < 1 || p->n_cheb_G < 0 || p->n_radial < 1 || p->n_angular < 1) return DSE_REF_ERR_ARG;
+    if (p->n_cheb > 1024 || p->n_cheb_G > 1024) return DSE_REF_ERR_ARG;
     if (!(p->eps2 > 0.0) || !(p->lambda2 > p->eps2)) return DSE_REF_ERR_ARG;
     if (!(p->x_Z > 0.0) || !(p->x_G >= 0.0)) return DSE_REF_ERR_ARG;
     if (!isfinite(p->g2nc) || !isfinite(p->kappa) || !isfinite(p->delta)) return DSE_REF_ERR_ARG;
@@ -64,7 +65,9 @@ static int check_problem(const dse_ref_problem* p) {
 
 static consts make_consts(const dse_ref_problem* p) {
     consts k;
-    k.N = p->n_cheb;
+    k.NZ = p->n_cheb;
+    k.NG = p->n_cheb_G > 0 ? p->n_cheb_G : p->n_cheb;
+    k.N = k.NZ > k.NG ? k.NZ : k.NG;
     k.K = p->g2nc / (8.0 * PI_D * PI_D * PI_D);
     k.gam = -1.0 - 2.0 * p->delta;
     k.pG = -2.0 - 6.0 * p->delta;
@@ -145,16 +148,29 @@ double dse_ref_map(const dse_ref_problem* p, double x) {
     return (log(x) - k.L0) / k.L1;
 }
 
+/* the n mapped roots of T_n, ascending */
+static void mapped_roots(const consts* k, int n, double* x) {
+    for (int i = 0; i < n; ++i) {
+        double s = -cos(PI_D * (2.0 * i + 1.0) / (2.0 * n));
+        x[i] = exp(k->L0 + k->L1 * s);
+    }
+}
+
 int dse_ref_collocation(const dse_ref_problem* p, double* x) {
     int st = check_problem(p);
     if (st) return st;
     if (!x) return DSE_REF_ERR_ARG;
     consts k = make_consts(p);
-    int N = p->n_cheb;
-    for (int i = 0; i < N; ++i) {
-        double s = -cos(PI_D * (2.0 * i + 1.0) / (2.0 * N));
-        x[i] = exp(k.L0 + k.L1 * s);
-    }
+    mapped_roots(&k, k.NZ, x);
+    return DSE_REF_OK;
+}
+
+int dse_ref_collocation_ghost(const dse_ref_problem* p, double* x) {
+    int st = check_problem(p);
+    if (st) return st;
+    if (!x) return DSE_REF_ERR_ARG;
+    consts k = make_consts(p);
+    mapped_roots(&k, k.NG, x);
     return DSE_REF_OK;
 }
 
@@ -203,12 +219,9 @@ static void dressing_w(const dse_ref_problem* p, const consts* k, const double* 
     double phi_local[1024];
     double* phi = phi_out ? phi_out : phi_local;
     basis(k, x, phi);
-    int N = k->N;
     double lg = 0.0, lz = 0.0;
-    for (int j = 0; j < N; ++j) {
-        lz += c[j] * phi[j];
-        lg += c[N + j] * phi[j];
-    }
+    for (int j = 0; j < k->NZ; ++j) lz += c[j] * phi[j];
+    for (int j = 0; j < k->NG; ++j) lg += c[k->NZ + j] * phi[j];
     if (p->extrap_mode == 0) {
         if (x < p->eps2) {
             double r = log(x) - k->ln_eps2;
@@ -236,7 +249,7 @@ int dse_ref_dressing(const dse_ref_problem* p, const double* c, int n, const dou
                      double* lnG, double* lnZ) {
     int st = check_problem(p);
     if (st) return st;
-    if (!c || !x || !lnG || !lnZ || n < 0 || p->n_cheb > 1024) return DSE_REF_ERR_ARG;
+    if (!c || !x || !lnG || !lnZ || n < 0) return DSE_REF_ERR_ARG;
     consts k = make_consts(p);
     for (int m = 0; m < n; ++m) {
         if (!(x[m] > 0.0)) return DSE_REF_ERR_ARG;
@@ -289,9 +302,9 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
                             double* PiG, double* PiZ, double* d_PiG, double* d_PiZ) {
     int st = check_problem(p);
     if (st) return st;
-    if (!c || !(x >= 0.0) || p->n_cheb > 1024) return DSE_REF_ERR_ARG;
+    if (!c || !(x >= 0.0)) return DSE_REF_ERR_ARG;
     consts k = make_consts(p);
-    int N = p->n_cheb, nr = p->n_radial, na = p->n_angular;
+    int N = k.N, NZ = k.NZ, NG = k.NG, nr = p->n_radial, na = p->n_angular;
     int want_d = (d_PiG != NULL) || (d_PiZ != NULL);
     int gluon = x > 0.0;
 
@@ -301,7 +314,7 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
     double* wt = (double*)malloc(sizeof(double) * na);
     double* phiy = (double*)malloc(sizeof(double) * N);
     double* phiz = (double*)malloc(sizeof(double) * N);
-    nsum* acc = (nsum*)calloc((size_t)(2 + 4 * N), sizeof(nsum));
+    nsum* acc = (nsum*)calloc((size_t)(2 + 2 * (NZ + NG)), sizeof(nsum));
     if (!y || !W || !th || !wt || !phiy || !phiz || !acc) {
         free(y); free(W); free(th); free(wt); free(phiy); free(phiz); free(acc);
         return DSE_REF_ERR_ARG;
@@ -309,10 +322,10 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
     dse_ref_quadrature(p, y, W, th, wt);
     nsum* sG = &acc[0];
     nsum* sZ = &acc[1];
-    nsum* gZa = &acc[2];          /* d Pi_Z / d a_j (without prefactor) */
-    nsum* gZb = &acc[2 + N];      /* d Pi_Z / d b_j */
-    nsum* gGa = &acc[2 + 2 * N];  /* d Pi_G / d a_j */
-    nsum* gGb = &acc[2 + 3 * N];  /* d Pi_G / d b_j */
+    nsum* gZa = &acc[2];                 /* d Pi_Z / d a_j (without prefactor), j < NZ */
+    nsum* gZb = &acc[2 + NZ];            /* d Pi_Z / d b_j, j < NG */
+    nsum* gGa = &acc[2 + NZ + NG];       /* d Pi_G / d a_j */
+    nsum* gGb = &acc[2 + 2 * NZ + NG];   /* d Pi_G / d b_j */
 
     for (int kk = 0; kk < nr; ++kk) {
         double lGy, lZy;
@@ -346,13 +359,12 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
                 ns_add(sG, fG);
                 if (gluon) ns_add(sZ, hQ + hM);
                 if (want_d) {
-                    for (int j = 0; j < N; ++j) {
-                        double ph = phiy[j] + phiz[j];
-                        if (gluon) {
-                            ns_add(&gZa[j], k.qZ * hQ * ph);
-                            ns_add(&gZb[j], (k.pG * hQ + hM) * ph);
-                        }
+                    for (int j = 0; j < NZ; ++j) {
+                        if (gluon) ns_add(&gZa[j], k.qZ * hQ * (phiy[j] + phiz[j]));
                         ns_add(&gGa[j], fG * phiz[j]);
+                    }
+                    for (int j = 0; j < NG; ++j) {
+                        if (gluon) ns_add(&gZb[j], (k.pG * hQ + hM) * (phiy[j] + phiz[j]));
                         ns_add(&gGb[j], fG * phiy[j]);
                     }
                 }
@@ -361,13 +373,12 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
                 ns_add(sG, fabs(fG));
                 if (gluon) ns_add(sZ, fabs(hQ) + fabs(hM));
                 if (want_d) {
-                    for (int j = 0; j < N; ++j) {
-                        double ph = fabs(phiy[j]) + fabs(phiz[j]);
-                        if (gluon) {
-                            ns_add(&gZa[j], fabs(k.qZ * hQ) * ph);
-                            ns_add(&gZb[j], (fabs(k.pG * hQ) + fabs(hM)) * ph);
-                        }
+                    for (int j = 0; j < NZ; ++j) {
+                        if (gluon) ns_add(&gZa[j], fabs(k.qZ * hQ) * (fabs(phiy[j]) + fabs(phiz[j])));
                         ns_add(&gGa[j], fabs(fG * phiz[j]));
+                    }
+                    for (int j = 0; j < NG; ++j) {
+                        if (gluon) ns_add(&gZb[j], (fabs(k.pG * hQ) + fabs(hM)) * (fabs(phiy[j]) + fabs(phiz[j])));
                         ns_add(&gGb[j], fabs(fG * phiy[j]));
                     }
                 }
@@ -382,15 +393,13 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
     }
     if (PiG) *PiG = preG * ns_val(sG);
     if (PiZ) *PiZ = gluon ? preZ * ns_val(sZ) : 0.0;
-    for (int j = 0; j < N; ++j) {
-        if (d_PiZ) {
-            d_PiZ[j] = preZ * ns_val(&gZa[j]);
-            d_PiZ[N + j] = preZ * ns_val(&gZb[j]);
-        }
-        if (d_PiG) {
-            d_PiG[j] = preG * ns_val(&gGa[j]);
-            d_PiG[N + j] = preG * ns_val(&gGb[j]);
-        }
+    for (int j = 0; j < NZ; ++j) {
+        if (d_PiZ) d_PiZ[j] = preZ * ns_val(&gZa[j]);
+        if (d_PiG) d_PiG[j] = preG * ns_val(&gGa[j]);
+    }
+    for (int j = 0; j < NG; ++j) {
+        if (d_PiZ) d_PiZ[NZ + j] = preZ * ns_val(&gZb[j]);
+        if (d_PiG) d_PiG[NZ + j] = preG * ns_val(&gGb[j]);
     }
     free(y); free(W); free(th); free(wt); free(phiy); free(phiz); free(acc);
     return DSE_REF_OK;
@@ -454,118 +463,143 @@ static int self_energy_dg2(const dse_ref_problem* p, const double* c, double x, 
     return DSE_REF_OK;
 }
 
+/* External momenta at which the self-energies are evaluated: the collocation
+ * points (shared by both equations when N_Z = N_G; otherwise the N_Z gluon points
+ * followed by the N_G ghost points), then x_Z and x_G.  xr holds N_Z + N_G + 2
+ * doubles.  Returns the number Rc of collocation rows; *gofs is the row of the
+ * first ghost point. */
+static int row_points(const dse_ref_problem* p, const consts* k, double* xr, int* gofs) {
+    int Rc;
+    mapped_roots(k, k->NZ, xr);
+    if (k->NZ == k->NG) {
+        Rc = k->NZ;
+        *gofs = 0;
+    } else {
+        mapped_roots(k, k->NG, xr + k->NZ);
+        Rc = k->NZ + k->NG;
+        *gofs = k->NZ;
+    }
+    xr[Rc] = p->x_Z;
+    xr[Rc + 1] = p->x_G;
+    return Rc;
+}
+
 int dse_ref_param_derivatives(const dse_ref_problem* p, const double* c, double* dF) {
     int st = check_problem(p);
     if (st) return st;
-    if (!c || !dF || p->n_cheb > 1024) return DSE_REF_ERR_ARG;
-    int N = p->n_cheb;
-    double* xc = (double*)malloc(sizeof(double) * N);
-    double* dG = (double*)malloc(sizeof(double) * (N + 2));
-    double* dZ = (double*)malloc(sizeof(double) * (N + 2));
-    int* rst = (int*)calloc((size_t)(N + 2), sizeof(int));
-    if (!xc || !dG || !dZ || !rst) { free(xc); free(dG); free(dZ); free(rst); return DSE_REF_ERR_ARG; }
-    dse_ref_collocation(p, xc);
+    if (!c || !dF) return DSE_REF_ERR_ARG;
+    consts k = make_consts(p);
+    int NZ = k.NZ, NG = k.NG, gofs;
+    double* xr = (double*)malloc(sizeof(double) * (NZ + NG + 2));
+    double* dG = (double*)malloc(sizeof(double) * (NZ + NG + 2));
+    double* dZ = (double*)malloc(sizeof(double) * (NZ + NG + 2));
+    int* rst = (int*)calloc((size_t)(NZ + NG + 2), sizeof(int));
+    if (!xr || !dG || !dZ || !rst) { free(xr); free(dG); free(dZ); free(rst); return DSE_REF_ERR_ARG; }
+    int Rc = row_points(p, &k, xr, &gofs);
+    int R = Rc + 2;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int r = 0; r < N + 2; ++r) {
-        double xr = r < N ? xc[r] : (r == N ? p->x_Z : p->x_G);
-        rst[r] = self_energy_dg2(p, c, xr, &dG[r], &dZ[r]);
-    }
-    for (int r = 0; r < N + 2; ++r)
+    for (int r = 0; r < R; ++r) rst[r] = self_energy_dg2(p, c, xr[r], &dG[r], &dZ[r]);
+    for (int r = 0; r < R; ++r)
         if (rst[r]) { st = rst[r]; break; }
     if (!st) {
         /* columns: g2nc, ginv_G, zinv_Z */
-        for (int i = 0; i < N; ++i) {
-            dF[(size_t)i * 3 + 0] = -dZ[i] + dZ[N];
+        for (int i = 0; i < NZ; ++i) {
+            dF[(size_t)i * 3 + 0] = -dZ[i] + dZ[Rc];
             dF[(size_t)i * 3 + 1] = 0.0;
             dF[(size_t)i * 3 + 2] = -1.0;
-            dF[(size_t)(N + i) * 3 + 0] = -dG[i] + dG[N + 1];
-            dF[(size_t)(N + i) * 3 + 1] = -1.0;
-            dF[(size_t)(N + i) * 3 + 2] = 0.0;
+        }
+        for (int i = 0; i < NG; ++i) {
+            dF[(size_t)(NZ + i) * 3 + 0] = -dG[gofs + i] + dG[Rc + 1];
+            dF[(size_t)(NZ + i) * 3 + 1] = -1.0;
+            dF[(size_t)(NZ + i) * 3 + 2] = 0.0;
         }
     }
-    free(xc); free(dG); free(dZ); free(rst);
+    free(xr); free(dG); free(dZ); free(rst);
     return st;
 }
 
 /* ------------------------------------------------ residual and matrix ---- */
 
 /* Residuals at the collocation points (Sec. 3, MOM scheme of Sec. 2):
- *   z(x_i) = Z(x_i)^{-1} - Z(x_Z)^{-1} - Pi_Z(x_i) + Pi_Z(x_Z)
- *   g(x_i) = G(x_i)^{-1} - G(x_G)^{-1} - Pi_G(x_i) + Pi_G(x_G)
+ *   z(x_i) = Z(x_i)^{-1} - Z(x_Z)^{-1} - Pi_Z(x_i) + Pi_Z(x_Z)   (N_Z gluon points)
+ *   g(x_i) = G(x_i)^{-1} - G(x_G)^{-1} - Pi_G(x_i) + Pi_G(x_G)   (N_G ghost points)
  * and the Newton matrix of their derivatives; rows (z; g), columns (a; b). */
 static int assemble(const dse_ref_problem* p, const double* c, int magnitudes, double* J, double* F) {
     int st = check_problem(p);
     if (st) return st;
-    if (!c || p->n_cheb > 1024) return DSE_REF_ERR_ARG;
-    int N = p->n_cheb;
-    int want_d = J != NULL;
+    if (!c) return DSE_REF_ERR_ARG;
     consts k = make_consts(p);
-    double* xc = (double*)malloc(sizeof(double) * N);
-    double* PiGr = (double*)malloc(sizeof(double) * (N + 2));
-    double* PiZr = (double*)malloc(sizeof(double) * (N + 2));
-    double* dG = want_d ? (double*)malloc(sizeof(double) * (size_t)(N + 2) * 2 * N) : NULL;
-    double* dZ = want_d ? (double*)malloc(sizeof(double) * (size_t)(N + 2) * 2 * N) : NULL;
-    int* rst = (int*)calloc((size_t)(N + 2), sizeof(int));
-    if (!xc || !PiGr || !PiZr || !rst || (want_d && (!dG || !dZ))) {
-        free(xc); free(PiGr); free(PiZr); free(dG); free(dZ); free(rst);
+    int NZ = k.NZ, NG = k.NG, n = NZ + NG, gofs;
+    int want_d = J != NULL;
+    double* xr = (double*)malloc(sizeof(double) * (n + 2));
+    double* PiGr = (double*)malloc(sizeof(double) * (n + 2));
+    double* PiZr = (double*)malloc(sizeof(double) * (n + 2));
+    double* dG = want_d ? (double*)malloc(sizeof(double) * (size_t)(n + 2) * n) : NULL;
+    double* dZ = want_d ? (double*)malloc(sizeof(double) * (size_t)(n + 2) * n) : NULL;
+    int* rst = (int*)calloc((size_t)(n + 2), sizeof(int));
+    double* phi = (double*)malloc(sizeof(double) * k.N);
+    if (!xr || !PiGr || !PiZr || !rst || !phi || (want_d && (!dG || !dZ))) {
+        free(xr); free(PiGr); free(PiZr); free(dG); free(dZ); free(rst); free(phi);
         return DSE_REF_ERR_ARG;
     }
-    dse_ref_collocation(p, xc);
-    /* rows 0..N-1: collocation points; row N: x_Z (gluon); row N+1: x_G (ghost) */
+    int Rc = row_points(p, &k, xr, &gofs);
+    int R = Rc + 2;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int r = 0; r < N + 2; ++r) {
-        double xr = r < N ? xc[r] : (r == N ? p->x_Z : p->x_G);
-        rst[r] = self_energy_impl(p, c, xr, magnitudes, &PiGr[r], &PiZr[r],
-                                  want_d ? &dG[(size_t)r * 2 * N] : NULL,
-                                  want_d ? &dZ[(size_t)r * 2 * N] : NULL);
+    for (int r = 0; r < R; ++r) {
+        rst[r] = self_energy_impl(p, c, xr[r], magnitudes, &PiGr[r], &PiZr[r],
+                                  want_d ? &dG[(size_t)r * n] : NULL,
+                                  want_d ? &dZ[(size_t)r * n] : NULL);
     }
-    for (int r = 0; r < N + 2; ++r)
+    for (int r = 0; r < R; ++r)
         if (rst[r]) { st = rst[r]; break; }
     if (!st) {
-        double* phi = (double*)malloc(sizeof(double) * N);
-        const double* dZref = want_d ? &dZ[(size_t)N * 2 * N] : NULL;
-        const double* dGref = want_d ? &dG[(size_t)(N + 1) * 2 * N] : NULL;
-        for (int i = 0; i < N; ++i) {
+        const double* dZref = want_d ? &dZ[(size_t)Rc * n] : NULL;
+        const double* dGref = want_d ? &dG[(size_t)(Rc + 1) * n] : NULL;
+        /* gluon rows */
+        for (int i = 0; i < NZ; ++i) {
             double lG, lZ;
-            dressing(p, &k, c, xc[i], &lG, &lZ, phi);
-            double Zinv = exp(-lZ), Ginv = exp(-lG);
-            if (F && !magnitudes) {
-                F[i] = Zinv - p->zinv_Z - PiZr[i] + PiZr[N];
-                F[N + i] = Ginv - p->ginv_G - PiGr[i] + PiGr[N + 1];
-            } else if (F) {
-                F[i] = Zinv + fabs(p->zinv_Z) + PiZr[i] + PiZr[N];
-                F[N + i] = Ginv + fabs(p->ginv_G) + PiGr[i] + PiGr[N + 1];
-            }
+            dressing(p, &k, c, xr[i], &lG, &lZ, phi);
+            double Zinv = exp(-lZ);
+            if (F) F[i] = magnitudes ? Zinv + fabs(p->zinv_Z) + PiZr[i] + PiZr[Rc]
+                                     : Zinv - p->zinv_Z - PiZr[i] + PiZr[Rc];
             if (want_d) {
-                const double* dZi = &dZ[(size_t)i * 2 * N];
-                const double* dGi = &dG[(size_t)i * 2 * N];
-                double* Jz = &J[(size_t)i * 2 * N];
-                double* Jg = &J[(size_t)(N + i) * 2 * N];
-                for (int j = 0; j < 2 * N; ++j) {
-                    /* d Z(x)^{-1}/d a_j = -Z(x)^{-1} phi_j(x); same for G with b_j */
-                    double diagZ = j < N ? -Zinv * phi[j] : 0.0;
-                    double diagG = j >= N ? -Ginv * phi[j - N] : 0.0;
-                    if (!magnitudes) {
-                        Jz[j] = diagZ - dZi[j] + dZref[j];
-                        Jg[j] = diagG - dGi[j] + dGref[j];
-                    } else {
-                        Jz[j] = fabs(diagZ) + dZi[j] + dZref[j];
-                        Jg[j] = fabs(diagG) + dGi[j] + dGref[j];
-                    }
+                const double* dZi = &dZ[(size_t)i * n];
+                double* Jz = &J[(size_t)i * n];
+                for (int j = 0; j < n; ++j) {
+                    /* d Z(x)^{-1}/d a_j = -Z(x)^{-1} phi_j(x) */
+                    double diagZ = j < NZ ? -Zinv * phi[j] : 0.0;
+                    Jz[j] = magnitudes ? fabs(diagZ) + dZi[j] + dZref[j] : diagZ - dZi[j] + dZref[j];
                 }
             }
         }
-        free(phi);
+        /* ghost rows */
+        for (int i = 0; i < NG; ++i) {
+            int r = gofs + i;
+            double lG, lZ;
+            dressing(p, &k, c, xr[r], &lG, &lZ, phi);
+            double Ginv = exp(-lG);
+            if (F) F[NZ + i] = magnitudes ? Ginv + fabs(p->ginv_G) + PiGr[r] + PiGr[Rc + 1]
+                                          : Ginv - p->ginv_G - PiGr[r] + PiGr[Rc + 1];
+            if (want_d) {
+                const double* dGi = &dG[(size_t)r * n];
+                double* Jg = &J[(size_t)(NZ + i) * n];
+                for (int j = 0; j < n; ++j) {
+                    /* d G(x)^{-1}/d b_j = -G(x)^{-1} phi_j(x) */
+                    double diagG = j >= NZ ? -Ginv * phi[j - NZ] : 0.0;
+                    Jg[j] = magnitudes ? fabs(diagG) + dGi[j] + dGref[j] : diagG - dGi[j] + dGref[j];
+                }
+            }
+        }
         if (F) {
-            for (int i = 0; i < 2 * N; ++i)
+            for (int i = 0; i < n; ++i)
                 if (!isfinite(F[i])) { st = DSE_REF_ERR_NONFINITE; break; }
         }
         if (!st && want_d) {
-            for (size_t e = 0; e < (size_t)4 * N * N; ++e)
+            for (size_t e = 0; e < (size_t)n * n; ++e)
                 if (!isfinite(J[e])) { st = DSE_REF_ERR_NONFINITE; break; }
         }
     }
-    free(xc); free(PiGr); free(PiZr); free(dG); free(dZ); free(rst);
+    free(xr); free(PiGr); free(PiZr); free(dG); free(dZ); free(rst); free(phi);
     return st;
 }
 
@@ -641,33 +675,38 @@ int dse_ref_newton_step(const dse_ref_problem* p, double* c, double rho, double*
     int st = check_problem(p);
     if (st) return st;
     if (!c || !isfinite(rho)) return DSE_REF_ERR_ARG;
-    int N = p->n_cheb, n = 2 * N;
+    consts k = make_consts(p);
+    int NZ = k.NZ, NG = k.NG, n = NZ + NG;
     double* J = (double*)malloc(sizeof(double) * (size_t)n * n);
     double* F = (double*)malloc(sizeof(double) * n);
     double* D = (double*)malloc(sizeof(double) * n);
-    double* xc = (double*)malloc(sizeof(double) * N);
-    double* lG = (double*)malloc(sizeof(double) * N);
-    double* lZ = (double*)malloc(sizeof(double) * N);
-    if (!J || !F || !D || !xc || !lG || !lZ) {
-        free(J); free(F); free(D); free(xc); free(lG); free(lZ);
+    double* xz = (double*)malloc(sizeof(double) * NZ);
+    double* xg = (double*)malloc(sizeof(double) * NG);
+    double* lG = (double*)malloc(sizeof(double) * n);
+    double* lZ = (double*)malloc(sizeof(double) * n);
+    if (!J || !F || !D || !xz || !xg || !lG || !lZ) {
+        free(J); free(F); free(D); free(xz); free(xg); free(lG); free(lZ);
         return DSE_REF_ERR_ARG;
     }
     st = assemble(p, c, 0, J, F);
     if (!st) st = dse_ref_lu_solve(n, J, F, D);
     if (!st) {
-        dse_ref_collocation(p, xc);
-        dse_ref_dressing(p, c, N, xc, lG, lZ);
+        /* dimensionless residual: Z(x_i) z_i at the gluon points, G(x_i) g_i at the ghost points */
+        dse_ref_collocation(p, xz);
+        dse_ref_collocation_ghost(p, xg);
+        dse_ref_dressing(p, c, NZ, xz, lG, lZ);
+        dse_ref_dressing(p, c, NG, xg, lG + NZ, lZ + NZ);
         double nF = 0.0, nS = 0.0, nD = 0.0;
         for (int i = 0; i < n; ++i) {
             nF = fmax(nF, fabs(F[i]));
-            double scale = i < N ? exp(lZ[i]) : exp(lG[i - N]);
+            double scale = i < NZ ? exp(lZ[i]) : exp(lG[i]);
             nS = fmax(nS, fabs(F[i]) * scale);
             nD = fmax(nD, fabs(D[i]));
         }
         for (int i = 0; i < n; ++i) c[i] -= rho * D[i];
         if (stats) { stats[0] = nF; stats[1] = nS; stats[2] = nD; }
     }
-    free(J); free(F); free(D); free(xc); free(lG); free(lZ);
+    free(J); free(F); free(D); free(xz); free(xg); free(lG); free(lZ);
     return st;
 }
 

@@ -34,9 +34,11 @@ extern "C" {
 #define DSE_REF_ERR_UNSUPPORTED (-5)
 
 /* Problem definition (same field order as the product's dse_problem, defined
- * independently here).  n_cheb = N Chebyshev coefficients per dressing
- * function; the unknown vector is c = (a_0..a_{N-1}, b_0..b_{N-1}) with a for
- * ln Z (gluon) and b for ln G (ghost), Sec. 3. */
+ * independently here).  n_cheb = N_Z Chebyshev coefficients of ln Z, n_cheb_G =
+ * N_G coefficients of ln G (0: N_G = N_Z); the unknown vector is
+ * c = (a_0..a_{N_Z-1}, b_0..b_{N_G-1}) with a for ln Z (gluon) and b for ln G
+ * (ghost), Sec. 3.  The gluon residual rows sit at the N_Z mapped roots of
+ * T_{N_Z}, the ghost rows at the N_G roots of T_{N_G}. */
 typedef struct {
     int n_cheb;
     int n_radial;
@@ -53,6 +55,7 @@ typedef struct {
     int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2] */
     int extrap_mode;  /* 0: IR power laws / UV logarithms; 1: constant continuation */
     int precision;    /* 0: FP64 */
+    int n_cheb_G;     /* N_G (0: equal to n_cheb) */
 } dse_ref_problem;
 
 /* n-point Gauss-Legendre rule on [-1,1], nodes ascending (Newton iteration on
@@ -64,17 +67,19 @@ int dse_ref_gauss_legendre(int n, double* x, double* w);
  * theta_l, weights w_l with int_0^pi dtheta g ~ sum_l w_l g(theta_l). */
 int dse_ref_quadrature(const dse_ref_problem* p, double* y, double* W, double* theta, double* wt);
 
-/* Collocation points x_i, i < N: the mapped roots of T_N, ascending (Sec. 3). */
+/* Collocation points x_i, i < N_Z: the mapped roots of T_{N_Z}, ascending (Sec. 3);
+ * the gluon rows of the residual.  _ghost: the N_G roots of T_{N_G} (ghost rows). */
 int dse_ref_collocation(const dse_ref_problem* p, double* x);
+int dse_ref_collocation_ghost(const dse_ref_problem* p, double* x);
 
 /* Mapping s(x) = log(x/(Lambda eps)) / log(Lambda/eps) of Sec. 3 (unclamped). */
 double dse_ref_map(const dse_ref_problem* p, double x);
 
-/* phi_j(x) = d ln G(x) / d b_j = d ln Z(x) / d a_j for j < N (1/2 for j = 0,
- * T_j(s(x)) otherwise, x clamped into [eps2, lambda2]). */
+/* phi_j(x) = d ln G(x) / d b_j = d ln Z(x) / d a_j for j < max(N_Z, N_G) (1/2 for
+ * j = 0, T_j(s(x)) otherwise, x clamped into [eps2, lambda2]). */
 int dse_ref_basis(const dse_ref_problem* p, double x, double* phi);
 
-/* ln G(x_m), ln Z(x_m) for m < n from coefficients c (2N): Chebyshev series
+/* ln G(x_m), ln Z(x_m) for m < n from coefficients c (N_Z + N_G): Chebyshev series
  * inside [eps2, lambda2], the paper's IR/UV forms outside (Sec. 2, Sec. 3). */
 int dse_ref_dressing(const dse_ref_problem* p, const double* c, int n, const double* x,
                      double* lnG, double* lnZ);
@@ -84,14 +89,14 @@ int dse_ref_dressing(const dse_ref_problem* p, const double* c, int n, const dou
 int dse_ref_kernels(double x, double y, double theta, double* M, double* Q, double* z);
 
 /* Self-energies Pi_G(x), Pi_Z(x) (Pi_Z only for x > 0) and, if d_PiG / d_PiZ are
- * non-NULL, their gradients (2N each) with respect to c = (a, b). */
+ * non-NULL, their gradients (N_Z + N_G each) with respect to c = (a, b). */
 int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
                         double* PiG, double* PiZ, double* d_PiG, double* d_PiZ);
 
-/* Residual F (2N): rows z(x_0..x_{N-1}) then g(x_0..x_{N-1}), Sec. 3. */
+/* Residual F (n = N_Z + N_G): rows z at the N_Z gluon points, then g at the N_G ghost points, Sec. 3. */
 int dse_ref_residual(const dse_ref_problem* p, const double* c, double* F);
 
-/* Newton matrix J (2N x 2N row-major, columns a then b) and residual F (nullable). */
+/* Newton matrix J (n x n row-major, columns a then b) and residual F (nullable). */
 int dse_ref_newton_matrix(const dse_ref_problem* p, const double* c, double* J, double* F);
 
 /* Magnitude sums that bound the rounding of each entry: A_ij is the sum of the
@@ -100,8 +105,8 @@ int dse_ref_newton_matrix(const dse_ref_problem* p, const double* c, double* J, 
  * F_i (AF nullable).  Same layout as dse_ref_newton_matrix. */
 int dse_ref_newton_matrix_magnitudes(const dse_ref_problem* p, const double* c, double* A, double* AF);
 
-/* Derivatives of F (2N rows) with respect to the parameters (g2nc, ginv_G, zinv_Z),
- * 2N x 3 row-major.  g2nc enters through K and through omega in the UV forms. */
+/* Derivatives of F (n rows) with respect to the parameters (g2nc, ginv_G, zinv_Z),
+ * n x 3 row-major.  g2nc enters through K and through omega in the UV forms. */
 int dse_ref_param_derivatives(const dse_ref_problem* p, const double* c, double* dF);
 
 /* Solve A x = b (n x n row-major) by LU with partial pivoting. */

@@ -45,6 +45,7 @@ class Problem(ctypes.Structure):
         ("x_Z", ctypes.c_double), ("zinv_Z", ctypes.c_double),
         ("kappa", ctypes.c_double), ("delta", ctypes.c_double),
         ("radial_mode", ctypes.c_int), ("extrap_mode", ctypes.c_int), ("precision", ctypes.c_int),
+        ("n_cheb_G", ctypes.c_int),
     ]
 
 
@@ -61,6 +62,7 @@ def lib():
                 "dse_ref_gauss_legendre": [ctypes.c_int, _D, _D],
                 "dse_ref_quadrature": [P, _D, _D, _D, _D],
                 "dse_ref_collocation": [P, _D],
+                "dse_ref_collocation_ghost": [P, _D],
                 "dse_ref_basis": [P, ctypes.c_double, _D],
                 "dse_ref_dressing": [P, _D, ctypes.c_int, _D, _D, _D],
                 "dse_ref_kernels": [ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D, _D],
@@ -109,6 +111,18 @@ def make_problem(params: dict) -> Problem:
     return p
 
 
+def orders(params: dict):
+    """(N_Z, N_G): Chebyshev orders of ln Z and ln G (n_cheb_G = 0 means N_G = N_Z)."""
+    nz = int(params["n_cheb"])
+    ng = int(params.get("n_cheb_G", 0) or 0)
+    return nz, (ng if ng > 0 else nz)
+
+
+def n_unknowns(params: dict) -> int:
+    nz, ng = orders(params)
+    return nz + ng
+
+
 def gauss_legendre(n: int):
     x = np.empty(n); w = np.empty(n)
     _chk(lib().dse_ref_gauss_legendre(n, _ptr(x), _ptr(w)), "gauss_legendre")
@@ -123,10 +137,16 @@ def quadrature(params: dict):
     return y, W, th, wt
 
 
-def collocation(params: dict) -> np.ndarray:
+def collocation(params: dict, ghost: bool = False) -> np.ndarray:
+    """Gluon collocation points (N_Z), or the ghost points (N_G) with ghost=True."""
     p = make_problem(params)
-    x = np.empty(p.n_cheb)
-    _chk(lib().dse_ref_collocation(ctypes.byref(p), _ptr(x)), "collocation")
+    nz, ng = orders(params)
+    if ghost:
+        x = np.empty(ng)
+        _chk(lib().dse_ref_collocation_ghost(ctypes.byref(p), _ptr(x)), "collocation_ghost")
+    else:
+        x = np.empty(nz)
+        _chk(lib().dse_ref_collocation(ctypes.byref(p), _ptr(x)), "collocation")
     return x
 
 
@@ -137,7 +157,7 @@ def map_s(params: dict, x: float) -> float:
 
 def basis(params: dict, x: float) -> np.ndarray:
     p = make_problem(params)
-    phi = np.empty(p.n_cheb)
+    phi = np.empty(max(orders(params)))
     _chk(lib().dse_ref_basis(ctypes.byref(p), float(x), _ptr(phi)), "basis")
     return phi
 
@@ -161,9 +181,9 @@ def self_energy(params: dict, c, x: float, grad: bool = False):
     p = make_problem(params)
     c = _f64(c)
     PiG = ctypes.c_double(); PiZ = ctypes.c_double()
-    N = p.n_cheb
-    dG = np.empty(2 * N) if grad else None
-    dZ = np.empty(2 * N) if grad else None
+    n = n_unknowns(params)
+    dG = np.empty(n) if grad else None
+    dZ = np.empty(n) if grad else None
     _chk(lib().dse_ref_self_energy(ctypes.byref(p), _ptr(c), float(x), ctypes.byref(PiG), ctypes.byref(PiZ),
                                    _ptr(dG) if grad else None, _ptr(dZ) if grad else None), "self_energy")
     if grad:
@@ -174,7 +194,7 @@ def self_energy(params: dict, c, x: float, grad: bool = False):
 def residual(params: dict, c) -> np.ndarray:
     p = make_problem(params)
     c = _f64(c)
-    F = np.empty(2 * p.n_cheb)
+    F = np.empty(n_unknowns(params))
     _chk(lib().dse_ref_residual(ctypes.byref(p), _ptr(c), _ptr(F)), "residual")
     return F
 
@@ -182,7 +202,7 @@ def residual(params: dict, c) -> np.ndarray:
 def newton_matrix(params: dict, c):
     p = make_problem(params)
     c = _f64(c)
-    n = 2 * p.n_cheb
+    n = n_unknowns(params)
     J = np.empty((n, n)); F = np.empty(n)
     _chk(lib().dse_ref_newton_matrix(ctypes.byref(p), _ptr(c), _ptr(J), _ptr(F)), "newton_matrix")
     return J, F
@@ -192,7 +212,7 @@ def newton_matrix_magnitudes(params: dict, c):
     """(A, AF): sums of |summands| of every entry of J and F (rounding scale)."""
     p = make_problem(params)
     c = _f64(c)
-    n = 2 * p.n_cheb
+    n = n_unknowns(params)
     A = np.empty((n, n)); AF = np.empty(n)
     _chk(lib().dse_ref_newton_matrix_magnitudes(ctypes.byref(p), _ptr(c), _ptr(A), _ptr(AF)),
          "newton_matrix_magnitudes")
@@ -200,10 +220,10 @@ def newton_matrix_magnitudes(params: dict, c):
 
 
 def param_derivatives(params: dict, c) -> np.ndarray:
-    """dF/d(g2nc, ginv_G, zinv_Z): 2N x 3."""
+    """dF/d(g2nc, ginv_G, zinv_Z): n x 3."""
     p = make_problem(params)
     c = _f64(c)
-    dF = np.empty((2 * p.n_cheb, 3))
+    dF = np.empty((n_unknowns(params), 3))
     _chk(lib().dse_ref_param_derivatives(ctypes.byref(p), _ptr(c), _ptr(dF)), "param_derivatives")
     return dF
 

@@ -33,13 +33,14 @@ WORKLOADS = {
 def problem(n_cheb: int, n_radial: int, n_angular: int, eps2: float = 1e-6, lambda2: float = 1e6,
             g2nc: float = G2NC, x_G: float = 0.0, ginv_G: float = 0.0, x_Z: float | None = None,
             zinv_Z: float = 1.0 / 0.256, kappa: float = KAPPA, delta: float = DELTA,
-            radial_mode: int = 0, extrap_mode: int = 0, precision: int = 0) -> dict:
-    """Problem parameters as a plain dict (field names of dse_problem)."""
+            radial_mode: int = 0, extrap_mode: int = 0, precision: int = 0, n_cheb_G: int = 0) -> dict:
+    """Problem parameters as a plain dict (field names of dse_problem).  n_cheb is
+    the order N_Z of ln Z, n_cheb_G the order N_G of ln G (0: N_G = N_Z)."""
     return dict(n_cheb=int(n_cheb), n_radial=int(n_radial), n_angular=int(n_angular),
                 eps2=float(eps2), lambda2=float(lambda2), g2nc=float(g2nc), x_G=float(x_G),
                 ginv_G=float(ginv_G), x_Z=float(lambda2 if x_Z is None else x_Z), zinv_Z=float(zinv_Z),
                 kappa=float(kappa), delta=float(delta), radial_mode=int(radial_mode),
-                extrap_mode=int(extrap_mode), precision=int(precision))
+                extrap_mode=int(extrap_mode), precision=int(precision), n_cheb_G=int(n_cheb_G))
 
 
 def workload_problem(name: str, **over) -> dict:
@@ -59,7 +60,8 @@ def starting_guess(params: dict, seed: int = 0, noise: float = 0.01) -> np.ndarr
     s = ln(x / sqrt(eps2 lambda2)) / (ln(lambda2/eps2)/2) and converted to the
     b_0/2, a_0/2 convention of the expansion.
     """
-    N = params["n_cheb"]
+    NZ = int(params["n_cheb"])
+    NG = int(params.get("n_cheb_G", 0) or 0) or NZ
     kappa, delta = params["kappa"], params["delta"]
     gamma = -1.0 - 2.0 * delta
     w = 11.0 * params["g2nc"] / (48.0 * math.pi ** 2)
@@ -75,15 +77,14 @@ def starting_guess(params: dict, seed: int = 0, noise: float = 0.01) -> np.ndarr
         return 2 * kappa * np.log(x / (1 + x)) + gamma * np.log1p(w * np.log1p(x))
 
     zs = -math.log(params["zinv_Z"]) - float(lnZ0_raw(np.array([1.0]))[0])
-    cb = np.polynomial.chebyshev.chebinterpolate(lnG0, N - 1)
-    ca = np.polynomial.chebyshev.chebinterpolate(lambda s: lnZ0_raw(s) + zs, N - 1)
+    cb = np.polynomial.chebyshev.chebinterpolate(lnG0, NG - 1)
+    ca = np.polynomial.chebyshev.chebinterpolate(lambda s: lnZ0_raw(s) + zs, NZ - 1)
     cb = np.asarray(cb, dtype=np.float64); ca = np.asarray(ca, dtype=np.float64)
     cb[0] *= 2.0
     ca[0] *= 2.0
     rng = np.random.default_rng(seed)
-    j = np.arange(N)
-    ca = ca + noise * rng.standard_normal(N) / (j + 1)
-    cb = cb + noise * rng.standard_normal(N) / (j + 1)
+    ca = ca + noise * rng.standard_normal(NZ) / (np.arange(NZ) + 1)
+    cb = cb + noise * rng.standard_normal(NG) / (np.arange(NG) + 1)
     return np.concatenate([ca, cb]).astype(np.float64)
 
 
