@@ -226,6 +226,16 @@ def run_gb300(args):
     if not args.no_mixed:
         mixed = measure_mixed(dse, p, c0_dev, t_dev, coef, args, total_ms / args.steps)
 
+    diff = None
+    if rank == 0 and not args.no_grad:
+        diff = measure_differentiation(dse, args)
+    n128 = None
+    if rank == 0 and not args.no_n128:
+        n128 = measure_mixed_n128(dse, args)
+    sweep = None
+    if rank == 0 and not args.no_batch:
+        sweep = measure_batch(dse, args)
+
     # end to end through the public API with host buffers (pinned), copies timed
     c0_host = torch.from_numpy(c0).pin_memory()
     t_host = torch.from_numpy(tt).pin_memory()
@@ -276,6 +286,12 @@ def run_gb300(args):
             line["cpu_baseline"] = cpu
         if mixed is not None:
             line["mixed_precision"] = mixed
+        if n128 is not None:
+            line["mixed_precision_n128"] = n128
+        if diff is not None:
+            line["differentiation"] = diff
+        if sweep is not None:
+            line["batched_sweep"] = sweep
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -322,6 +338,135 @@ def measure_mixed(dse, p, c0_dev, t_dev, coef_fp64, args, fp64_ms_per_step):
             "speedup_vs_fp64_step": fp64_ms_per_step / ms,
             "max_abs_dlnG_vs_fp64_solve": dG, "max_abs_dlnZ_vs_fp64_solve": dZ,
             "note": "Newton matrix from FP32 integrands with FP64 block sums; FP64 residual near convergence"}
+
+
+def measure_differentiation(dse, args):
+    """Loss gradient through the converged solve (N = 64, 256 x 128 nodes,
+    G(x_G)^{-1} = 0.01): forward = solve from the seeded guess (rho = 1/2 for six
+    steps) + ln Z at 64 seeded momenta; backward = dressing VJP, adjoint solve
+    J^T lambda = dL/dc and lambda^T dF/dtheta."""
+    import torch
+    from paper_1206_1779_gb300 import autograd as ad
+    p = inputs.workload_problem(WORKLOAD, ginv_G=0.01)
+    c0 = torch.from_numpy(inputs.starting_guess(p, seed=0)).cuda()
+    x = torch.from_numpy(inputs.loss_momenta(64)).cuda()
+    fac = torch.from_numpy(inputs.target_factors(64)).cuda()
+    plan = dse.Plan(p)
+    stream = torch.cuda.current_stream()
+
+    def run():
+        theta = torch.tensor([p["g2nc"], p["ginv_G"]], dtype=torch.float64, requires_grad=True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        cs = ad.solve(plan, theta, c0, tol=TOL, max_iter=60, rho_relax=0.5, n_relax=6)
+        _, lZ = ad.dressing(plan, cs, theta, x)
+        Z = torch.exp(lZ)
+        L = ((Z - Z.detach() * fac) ** 2).sum()
+        e[1].record(stream)
+        L.backward()
+        e[2].record(stream)
+        e[2].synchronize()
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), theta.grad.numpy().copy()
+
+    for _ in range(2):
+        run()
+    fw, bw = [], []
+    for _ in range(max(1, min(args.steps, 5))):
+        f, b, g = run()
+        fw.append(f)
+        bw.append(b)
+    plan.close()
+    return {"workload": "full_solve_n64 with G(x_G)^-1 = 0.01, loss over 64 momenta",
+            "forward_ms": float(np.mean(fw)), "backward_ms": float(np.mean(bw)),
+            "dL_dg2nc": float(g[0]), "dL_dginv_G": float(g[1]),
+            "note": "backward: dressing VJP + FP64 Newton matrix + adjoint solve + parameter derivatives"}
+
+
+def measure_mixed_n128(dse, args):
+    """Mixed precision at N = 128 with 512 x 256 nodes (matrix_n128): a solve from
+    the seeded guess in mixed precision and in FP64, their Newton-matrix times,
+    and the largest difference of the converged ln G, ln Z."""
+    import torch
+    p = inputs.workload_problem("matrix_n128")
+    N, nr, na = p["n_cheb"], p["n_radial"], p["n_angular"]
+    c0 = torch.from_numpy(inputs.starting_guess(p, seed=0)).cuda()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "matrix_n128", "n_cheb": N, "n_radial": nr, "n_angular": na}
+    coefs = {}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        plan = dse.Plan(dict(p, precision=prec))
+        coef = c0.clone()
+        J = torch.empty(2 * N, 2 * N, dtype=torch.float64, device="cuda")
+        F = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+        plan.newton_matrix(coef, J, F)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        for _ in range(3):
+            plan.newton_matrix(coef, J, F)
+        e[1].record(stream)
+        e[2].record(stream)
+        it, _ = plan.solve(coef, tol=TOL, max_iter=50)
+        e[3].record(stream)
+        e[3].synchronize()
+        out[name] = {"newton_matrix_ms": e[0].elapsed_time(e[1]) / 3, "solve_ms": e[2].elapsed_time(e[3]),
+                     "newton_steps": it}
+        coefs[name] = coef
+        plan.close()
+    xg = torch.from_numpy(np.exp(np.linspace(np.log(p["eps2"]), np.log(p["lambda2"]), 257))).cuda()
+    with dse.Plan(p) as plan:
+        lg_d, lz_d = plan.dressing(coefs["fp64"], xg)
+        lg_m, lz_m = plan.dressing(coefs["mixed"], xg)
+        torch.cuda.synchronize()
+    out["max_abs_dlnG_mixed_vs_fp64"] = float((lg_m - lg_d).abs().max())
+    out["max_abs_dlnZ_mixed_vs_fp64"] = float((lz_m - lz_d).abs().max())
+    out["solve_speedup"] = out["fp64"]["solve_ms"] / out["mixed"]["solve_ms"]
+    return out
+
+
+def measure_batch(dse, args):
+    """The parameter sweep: 256 problems with N_Z, N_G in {24, 32, 48, 64},
+    quadrature 128 x 64 or 256 x 128 and G(x_G)^{-1} log-uniform in [1e-3, 1e-1],
+    solved together (rho = 1/2 for six steps) to a dimensionless residual below
+    1e-10; one CUDA graph (one persistent quadrature launch) per Newton step."""
+    import torch
+    probs = inputs.batch_problems(256)
+    c0 = torch.from_numpy(np.concatenate([inputs.starting_guess(p, seed=b) for b, p in enumerate(probs)])).cuda()
+    stream = torch.cuda.current_stream()
+    batch = dse.Batch(probs)
+    t0 = time.perf_counter()
+    units, tune_ms = batch.tune(c0)
+    tune_s = time.perf_counter() - t0
+    coef = torch.empty_like(c0)
+    res = None
+    times = []
+    for rep in range(1 + max(1, min(args.steps, 3))):
+        coef.copy_(c0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, status, stats = batch.solve(coef, tol=TOL, max_iter=40, rho_relax=0.5, n_relax=6, check=False)
+        e1.record(stream)
+        e1.synchronize()
+        if rep > 0:
+            times.append(e0.elapsed_time(e1))
+        res = (its, status, stats)
+    launches, graphs, _ = batch.counters()
+    batch.close()
+    its, status, stats = res
+    ms = float(np.mean(times))
+    entries_nodes = 0.0
+    for b, p in enumerate(probs):
+        nz = p["n_cheb"]
+        ng = p["n_cheb_G"] or nz
+        entries_nodes += its[b] * float(nz + ng) ** 2 * p["n_radial"] * p["n_angular"]
+    return {"workload": "sweep of 256 problems: N_Z, N_G in {24,32,48,64}, 128x64 or 256x128 nodes, "
+                        "G(x_G)^-1 log-uniform in [1e-3, 1e-1]",
+            "ms_per_sweep": ms, "solves_per_s": 256 / (ms * 1e-3),
+            "value": entries_nodes / (ms * 1e-3), "unit": UNIT,
+            "converged": int(sum(1 for v in status if v == 0)), "newton_steps_max": int(max(its)),
+            "newton_steps_total": int(sum(its)), "max_scaled_residual": float(max(s[1] for s in stats)),
+            "units_per_item": units, "tune_ms_per_candidate": tune_ms, "tune_s": tune_s,
+            "graph_launches_per_sweep": int(max(its))}
 
 
 def cpu_baseline_sample(p, c0, budget_s: float = 12.0):
@@ -388,6 +533,9 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-n128", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -5,10 +5,13 @@
  *
  * The ghost and gluon dressing functions G(x), Z(x) are expanded as
  *   ln G(x) = b_0/2 + sum_{j>=1} b_j T_j(s(x)),   ln Z(x) = a_0/2 + sum_{j>=1} a_j T_j(s(x))
- * in the mapped variable s(x) = log(x/(Lambda eps)) / log(Lambda/eps)  (Sec. 3).
- * The unknown vector is  c = (a_0 .. a_{N-1}, b_0 .. b_{N-1})  (2N doubles).
- * The residual F has the rows  z(x_0..x_{N-1}), g(x_0..x_{N-1})  at the mapped
- * Chebyshev roots x_i (Sec. 3, residual equations), with
+ * in the mapped variable s(x) = log(x/(Lambda eps)) / log(Lambda/eps)  (Sec. 3),
+ * with N_Z coefficients a_j and N_G coefficients b_j (N_G = N_Z unless
+ * n_cheb_G says otherwise).  The unknown vector is
+ * c = (a_0 .. a_{N_Z-1}, b_0 .. b_{N_G-1})  (n = N_Z + N_G doubles).
+ * The residual F has the rows  z(x_0..x_{N_Z-1})  at the N_Z mapped Chebyshev
+ * roots of T_{N_Z}, then  g(x_0..x_{N_G-1})  at the roots of T_{N_G} (Sec. 3,
+ * residual equations; one shared set of points when N_Z = N_G), with
  *   z(x) = Z(x)^{-1} - Z(x_Z)^{-1} - Pi_Z(x) + Pi_Z(x_Z)
  *   g(x) = G(x)^{-1} - G(x_G)^{-1} - Pi_G(x) + Pi_G(x_G)
  * and the self-energies of the ghost and gluon equations of Sec. 2 (bare
@@ -49,7 +52,7 @@ extern "C" {
 #define DSE_ERR_NOT_CONVERGED (-6) /* dse_solve reached max_iter                */
 
 /* Limits of this build. */
-#define DSE_MAX_CHEB 256           /* N per dressing function                   */
+#define DSE_MAX_CHEB 256           /* N_Z, N_G per dressing function            */
 #define DSE_MAX_NODES 65536        /* n_radial, n_angular                       */
 #define DSE_MAX_SCHWINGER_NODES (1 << 20)
 
@@ -57,7 +60,7 @@ extern "C" {
  * there: g2nc = 12 pi (alpha(mu^2) = 1, N_c = 3), x_Z = lambda2, Z(x_Z) = 0.256,
  * x_G = 0, ginv_G = 0 for the scaling solution, delta = -9/44, kappa ~ 0.595353). */
 typedef struct {
-    int n_cheb;       /* N Chebyshev coefficients per dressing function, 1..DSE_MAX_CHEB   */
+    int n_cheb;       /* N_Z Chebyshev coefficients of ln Z, 1..DSE_MAX_CHEB              */
     int n_radial;     /* radial Gauss-Legendre nodes in ln y                             */
     int n_angular;    /* angular Gauss-Legendre nodes in theta                           */
     double eps2;      /* IR matching point epsilon^2 (> 0)                               */
@@ -72,6 +75,7 @@ typedef struct {
     int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2]         */
     int extrap_mode;  /* 0: IR power laws and UV logarithms; 1: constant continuation    */
     int precision;    /* 0: FP64 throughout; 1: mixed (FP32 integrands for J, FP64 F)   */
+    int n_cheb_G;     /* N_G Chebyshev coefficients of ln G, 0..DSE_MAX_CHEB (0: N_Z)    */
 } dse_problem;
 
 typedef struct dse_plan dse_plan;
@@ -95,25 +99,28 @@ int dse_plan_status(dse_plan* plan);
 
 /* Copy the plan's rules: d_y, d_W (n_radial; int_{eps2}^{lambda2} dy f ~ sum W_k f(y_k)),
  * d_theta, d_wt (n_angular; int_0^pi dtheta g ~ sum w_l g(theta_l)), d_x
- * (n_cheb collocation points, ascending).  Any pointer may be NULL. */
+ * (the collocation points: N_Z ascending points shared by both equations when
+ * N_Z = N_G, otherwise the N_Z gluon points followed by the N_G ghost points).
+ * Any pointer may be NULL. */
 int dse_quadrature(dse_plan* plan, double* d_y, double* d_W, double* d_theta, double* d_wt,
                    double* d_x);
 
 /* ln G(x_m), ln Z(x_m) for m < n (Sec. 3 expansion; Sec. 2 IR/UV forms outside
- * [eps2, lambda2]).  d_coeffs: 2N; d_x: n positive momenta; outputs n each. */
+ * [eps2, lambda2]).  d_coeffs: N_Z + N_G; d_x: n positive momenta; outputs n each. */
 int dse_dressing(dse_plan* plan, const double* d_coeffs, int n, const double* d_x,
                  double* d_lnG, double* d_lnZ);
 
-/* Residual F (2N): z(x_0..x_{N-1}) then g(x_0..x_{N-1})  (Sec. 3, residual equations). */
+/* Residual F (N_Z + N_G): z at the N_Z gluon points, then g at the N_G ghost
+ * points (Sec. 3, residual equations). */
 int dse_residual(dse_plan* plan, const double* d_coeffs, double* d_F);
 
-/* Newton matrix J (2N x 2N, row-major; rows z then g, columns a then b, the
+/* Newton matrix J (n x n with n = N_Z + N_G, row-major; rows z then g, columns a then b, the
  * layout of Sec. 3) with every entry dF_i/dc_j an analytic radial x angular
  * quadrature, and the residual F (d_F may be NULL). */
 int dse_newton_matrix(dse_plan* plan, const double* d_coeffs, double* d_J, double* d_F);
 
 /* One Newton-Raphson step (Sec. 3): J Delta = F solved on the device, then
- * c <- c - rho Delta in place.  For 2N <= 160 the rows of J are scaled by powers
+ * c <- c - rho Delta in place.  For n <= 160 the rows of J are scaled by powers
  * of two, inverted in FP32 and the solution refined in FP64 to a backward-stable
  * residual; otherwise (or if refinement stalls) LU with partial pivoting in FP64.
  * h_stats (host, 4 doubles, nullable): ||F||_inf, ||diag(Z(x_i), G(x_i)) F||_inf
@@ -152,21 +159,21 @@ int dse_schwinger(dse_plan* plan, const double* d_coeffs, const double* d_t, int
  * and workspace are kept).  Same argument checks as dse_plan_create. */
 int dse_plan_set_couplings(dse_plan* plan, double g2nc, double ginv_G, double zinv_Z);
 
-/* Vector-Jacobian product out_j = sum_i v_i dF_i/dc_j (2N each).  The products
+/* Vector-Jacobian product out_j = sum_i v_i dF_i/dc_j (n each).  The products
  * are contracted from the per-external-momentum derivative sums of Sec. 3
- * without forming the 2N x 2N Newton matrix; d_F (nullable) receives F(c). */
+ * without forming the n x n Newton matrix; d_F (nullable) receives F(c). */
 int dse_vjp(dse_plan* plan, const double* d_coeffs, const double* d_v, double* d_out, double* d_F);
 
-/* Parameter derivatives of F.  d_dF (nullable): 2N x 3 row-major, columns
+/* Parameter derivatives of F.  d_dF (nullable): n x 3 row-major, columns
  * dF/d g2nc, dF/d ginv_G, dF/d zinv_Z.  g2nc enters through the prefactor
  * g^2 Nc/(2 pi)^3 of both self-energies and through omega = 11 g^2 Nc/(48 pi^2)
  * of the UV forms of G(z), Z(z) for z > lambda2 (Sec. 2); the boundary values
- * enter the subtracted rows with coefficient -1.  d_v (nullable, 2N) with d_vdF
+ * enter the subtracted rows with coefficient -1.  d_v (nullable, n) with d_vdF
  * (3): v^T dF.  At least one of d_dF, d_v.  DSE_ERR_ARG if g2nc = 0. */
 int dse_param_derivatives(dse_plan* plan, const double* d_coeffs, double* d_dF, const double* d_v,
                           double* d_vdF);
 
-/* Adjoint of the Newton system at c: solves J(c)^T lambda = g (2N each; J the
+/* Adjoint of the Newton system at c: solves J(c)^T lambda = g (n each; J the
  * FP64 Newton matrix of dse_newton_matrix).  The rows of J are first scaled by
  * exact powers of two (S), and (S J)^T mu = g is solved with the dense solver of
  * dse_newton_step; lambda = S mu.  For the implicit function c*(theta) defined
@@ -177,13 +184,63 @@ int dse_adjoint_solve(dse_plan* plan, const double* d_coeffs, const double* d_g,
                       double* h_stats);
 
 /* Vector-Jacobian product of dse_dressing at n points x (positive):
- *   d_out[j] = sum_m gZ_m d ln Z(x_m)/d a_j,  d_out[N + j] = sum_m gG_m d ln G(x_m)/d b_j,
+ *   d_out[j] = sum_m gZ_m d ln Z(x_m)/d a_j (j < N_Z),  d_out[N_Z + j] = sum_m gG_m d ln G(x_m)/d b_j,
  * i.e. sums of the basis phi_j(x_m) (s clamped to [-1, 1] outside [eps2, lambda2]);
  * d_out_g2nc (nullable, 1 double): sum_m gG_m d ln G/d g2nc + gZ_m d ln Z/d g2nc,
  * non-zero only through the UV form for x_m > lambda2.  Non-positive x flag
  * DSE_ERR_NONFINITE in the plan status. */
 int dse_dressing_vjp(dse_plan* plan, int n, const double* d_x, const double* d_gG, const double* d_gZ,
                      double* d_out, double* d_out_g2nc);
+
+/* ---- Batches of independent problems ------------------------------------------
+ * A parameter sweep: n_problems problems, each with its own orders N_Z, N_G,
+ * quadrature sizes and parameters (precision 0, N_Z + N_G <= 128 each).  Their
+ * coefficient vectors are concatenated in problem order; dse_batch_offsets
+ * gives the offsets (n_problems + 1 entries; problem b owns
+ * [off[b], off[b+1]) = N_Z + N_G doubles, the same for F) and the offsets of
+ * the concatenated Newton matrices (n_b^2 each).  One Newton step of the whole
+ * batch is a CUDA graph of six launches, the quadrature of all problems in one
+ * persistent kernel that takes (problem, external momentum, radial block) work
+ * items longest first from a device counter; the radial nodes per work item
+ * come from dse_batch_tune.  The paper solves one problem at a time; the batch
+ * is its Newton method (Sec. 3) applied to many problems at once. */
+typedef struct dse_batch dse_batch;
+
+/* Create the batch (workspace for every problem, rules and collocation points
+ * set up on the device; waits for the set-up).  DSE_ERR_UNSUPPORTED for
+ * N_Z + N_G > 128, precision != 0 or an unsupported mode. */
+int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_stream, dse_batch** out);
+int dse_batch_destroy(dse_batch* batch);
+int dse_batch_set_stream(dse_batch* batch, void* cuda_stream);
+
+/* h_offsets (nullable): n_problems + 1 coefficient offsets; h_matrix_offsets
+ * (nullable): n_problems + 1 offsets of the concatenated Newton matrices. */
+int dse_batch_offsets(const dse_batch* batch, long long* h_offsets, long long* h_matrix_offsets);
+
+/* Time the quadrature pass for 8, 16, 32, 64 and 128 radial nodes per work
+ * item at d_coeffs and keep the fastest.  h_units (nullable): the choice;
+ * h_ms (nullable, 5 doubles): the time of each candidate.  Waits. */
+int dse_batch_tune(dse_batch* batch, const double* d_coeffs, int* h_units, double* h_ms);
+
+/* Newton matrices and residuals of every problem at d_coeffs into the
+ * concatenated d_J (matrix offsets) and d_F (coefficient offsets; nullable).
+ * Queued without waiting. */
+int dse_batch_newton_matrix(dse_batch* batch, const double* d_coeffs, double* d_J, double* d_F);
+
+/* Newton iteration of every problem from d_coeffs (in place), as dse_solve:
+ * rho_relax for the first n_relax steps, stop when the dimensionless residual
+ * drops below tol.  Converged problems leave the iteration (their work items
+ * are skipped); the loop ends when none is left or after max_iter steps.
+ * Per problem (nullable): h_iters steps taken, h_status DSE_OK /
+ * DSE_ERR_NOT_CONVERGED / DSE_ERR_SINGULAR / DSE_ERR_NONFINITE, h_stats three
+ * doubles of the last step (as dse_solve).  Returns DSE_OK when every problem
+ * converged, else DSE_ERR_NOT_CONVERGED.  Waits. */
+int dse_batch_solve(dse_batch* batch, double* d_coeffs, double tol, int max_iter, double rho_relax,
+                    int n_relax, int* h_iters, int* h_status, double* h_stats);
+
+/* Kernels launched by the batch since creation, graph launches, and the radial
+ * nodes per work item in use; any pointer may be NULL. */
+int dse_batch_counters(dse_batch* batch, long long* h_launches, long long* h_graph_launches, int* h_units);
 
 /* Allocation-free residual.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code that runs where device
@@ -194,11 +251,11 @@ int dse_dressing_vjp(dse_plan* plan, int n, const double* d_x, const double* d_g
  * but needs no plan: every intermediate buffer is carved out of one static
  * device array of DSE_STATIC_SCRATCH_BYTES compiled into the library, which
  * every GPU that loads the library holds until the process exits.
- *  - d_coeffs (2N) and d_F (2N) are caller-owned device buffers; cuda_stream is
+ *  - d_coeffs (n) and d_F (n) are caller-owned device buffers; cuda_stream is
  *    a cudaStream_t (NULL = legacy default stream).  Queued without waiting.
  *  - Returns DSE_ERR_ARG for bad arguments and when the problem needs more than
  *    DSE_STATIC_SCRATCH_BYTES of scratch (about 14 MB for N = 128 with
- *    512 x 256 nodes; the size grows with N (n_cheb) x n_radial x n_angular / 32);
+ *    512 x 256 nodes; the size grows with max(N_Z, N_G) x n_radial x n_angular / 32);
  *    nothing is queued then.  Non-finite values are not reported: they appear
  *    in d_F.
  *  - It calls no cudaMalloc, cudaFree or other allocating routine.  The first

@@ -22,7 +22,9 @@ DSE_MAX_CHEB = 256
 EXPORTS = ["dse_plan_create", "dse_plan_destroy", "dse_plan_set_stream", "dse_plan_status", "dse_quadrature",
            "dse_dressing", "dse_residual", "dse_newton_matrix", "dse_newton_step", "dse_solve", "dse_schwinger",
            "dse_plan_profile", "dse_plan_counters", "dse_residual_static", "dse_status_string",
-           "dse_plan_set_couplings", "dse_vjp", "dse_param_derivatives", "dse_adjoint_solve", "dse_dressing_vjp"]
+           "dse_plan_set_couplings", "dse_vjp", "dse_param_derivatives", "dse_adjoint_solve", "dse_dressing_vjp",
+           "dse_batch_create", "dse_batch_destroy", "dse_batch_set_stream", "dse_batch_offsets", "dse_batch_tune",
+           "dse_batch_newton_matrix", "dse_batch_solve", "dse_batch_counters"]
 
 
 class DseError(RuntimeError):
@@ -39,13 +41,14 @@ class Problem(ctypes.Structure):
         ("x_Z", ctypes.c_double), ("zinv_Z", ctypes.c_double),
         ("kappa", ctypes.c_double), ("delta", ctypes.c_double),
         ("radial_mode", ctypes.c_int), ("extrap_mode", ctypes.c_int), ("precision", ctypes.c_int),
+        ("n_cheb_G", ctypes.c_int),
     ]
 
     @classmethod
     def from_params(cls, params: dict) -> "Problem":
         p = cls()
         for name, _ in cls._fields_:
-            setattr(p, name, params[name])
+            setattr(p, name, params.get(name, 0) if name == "n_cheb_G" else params[name])
         return p
 
 
@@ -93,6 +96,16 @@ def load(build_if_missing: bool = False):
         "dse_param_derivatives": [_VP, _VP, _VP, _VP, _VP],
         "dse_adjoint_solve": [_VP, _VP, _VP, _VP, _D],
         "dse_dressing_vjp": [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP],
+        "dse_batch_create": [PP, ctypes.c_int, _VP, ctypes.POINTER(_VP)],
+        "dse_batch_destroy": [_VP],
+        "dse_batch_set_stream": [_VP, _VP],
+        "dse_batch_offsets": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+        "dse_batch_tune": [_VP, _VP, ctypes.POINTER(ctypes.c_int), _D],
+        "dse_batch_newton_matrix": [_VP, _VP, _VP, _VP],
+        "dse_batch_solve": [_VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
+        "dse_batch_counters": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -139,7 +152,11 @@ class Plan:
         import torch
         self._L = load()
         self.params = dict(params)
-        self.N = int(params["n_cheb"])
+        self.NZ = int(params["n_cheb"])
+        self.NG = int(params.get("n_cheb_G", 0) or 0) or self.NZ
+        self.N = max(self.NZ, self.NG)
+        self.n = self.NZ + self.NG
+        self.n_collocation = self.N if self.NZ == self.NG else self.n
         self.n_radial = int(params["n_radial"])
         self.n_angular = int(params["n_angular"])
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -174,7 +191,7 @@ class Plan:
 
     def quadrature(self):
         y, W, th, wt, x = (self._new(self.n_radial), self._new(self.n_radial), self._new(self.n_angular),
-                           self._new(self.n_angular), self._new(self.N))
+                           self._new(self.n_angular), self._new(self.n_collocation))
         self._sync_stream()
         _check(self._L.dse_quadrature(self._h, *[ctypes.c_void_p(t.data_ptr()) for t in (y, W, th, wt, x)]),
                "dse_quadrature")
@@ -184,19 +201,19 @@ class Plan:
         n = x.numel()
         lG, lZ = self._new(n), self._new(n)
         self._sync_stream()
-        _check(self._L.dse_dressing(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), n, _dev_ptr(x, n, "x"),
+        _check(self._L.dse_dressing(self._h, _dev_ptr(coeffs, self.n, "coeffs"), n, _dev_ptr(x, n, "x"),
                                     ctypes.c_void_p(lG.data_ptr()), ctypes.c_void_p(lZ.data_ptr())), "dse_dressing")
         return lG, lZ
 
     def residual(self, coeffs, out=None):
-        F = out if out is not None else self._new(2 * self.N)
+        F = out if out is not None else self._new(self.n)
         self._sync_stream()
-        _check(self._L.dse_residual(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), _dev_ptr(F, 2 * self.N, "F")),
+        _check(self._L.dse_residual(self._h, _dev_ptr(coeffs, self.n, "coeffs"), _dev_ptr(F, self.n, "F")),
                "dse_residual")
         return F
 
     def newton_matrix(self, coeffs, J=None, F=None):
-        n = 2 * self.N
+        n = self.n
         J = J if J is not None else self._new(n, n)
         F = F if F is not None else self._new(n)
         self._sync_stream()
@@ -209,7 +226,7 @@ class Plan:
         and the number of FP64 refinement sweeps (-1: FP64 LU)."""
         st = (ctypes.c_double * 4)()
         self._sync_stream()
-        _check(self._L.dse_newton_step(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), float(rho),
+        _check(self._L.dse_newton_step(self._h, _dev_ptr(coeffs, self.n, "coeffs"), float(rho),
                                        ctypes.cast(st, _D)), "dse_newton_step")
         return tuple(st)
 
@@ -218,7 +235,7 @@ class Plan:
         st = (ctypes.c_double * 3)()
         it = ctypes.c_int(0)
         self._sync_stream()
-        _check(self._L.dse_solve(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), float(tol), int(max_iter),
+        _check(self._L.dse_solve(self._h, _dev_ptr(coeffs, self.n, "coeffs"), float(tol), int(max_iter),
                                  float(rho_relax), int(n_relax), ctypes.byref(it), ctypes.cast(st, _D)), "dse_solve")
         return it.value, tuple(st)
 
@@ -226,7 +243,7 @@ class Plan:
         n_t = t.numel()
         out = out if out is not None else self._new(n_t)
         self._sync_stream()
-        _check(self._L.dse_schwinger(self._h, _dev_ptr(coeffs, 2 * self.N, "coeffs"), _dev_ptr(t, n_t, "t"), n_t,
+        _check(self._L.dse_schwinger(self._h, _dev_ptr(coeffs, self.n, "coeffs"), _dev_ptr(t, n_t, "t"), n_t,
                                      int(n_nodes), _dev_ptr(out, n_t, "delta")), "dse_schwinger")
         return out
 
@@ -238,7 +255,7 @@ class Plan:
 
     def vjp(self, coeffs, v, out=None, F=None):
         """v^T dF/dc (2N); F (optional tensor) receives the residual."""
-        n = 2 * self.N
+        n = self.n
         out = out if out is not None else self._new(n)
         self._sync_stream()
         _check(self._L.dse_vjp(self._h, _dev_ptr(coeffs, n, "coeffs"), _dev_ptr(v, n, "v"), _dev_ptr(out, n, "out"),
@@ -247,7 +264,7 @@ class Plan:
 
     def param_derivatives(self, coeffs):
         """dF/d(g2nc, ginv_G, zinv_Z): 2N x 3."""
-        n = 2 * self.N
+        n = self.n
         dF = self._new(n, 3)
         self._sync_stream()
         _check(self._L.dse_param_derivatives(self._h, _dev_ptr(coeffs, n, "coeffs"), _dev_ptr(dF, 3 * n, "dF"),
@@ -256,7 +273,7 @@ class Plan:
 
     def param_vjp(self, coeffs, v, out=None):
         """v^T dF/d(g2nc, ginv_G, zinv_Z): 3."""
-        n = 2 * self.N
+        n = self.n
         out = out if out is not None else self._new(3)
         self._sync_stream()
         _check(self._L.dse_param_derivatives(self._h, _dev_ptr(coeffs, n, "coeffs"), None, _dev_ptr(v, n, "v"),
@@ -265,7 +282,7 @@ class Plan:
 
     def adjoint_solve(self, coeffs, g, out=None):
         """lambda with J(c)^T lambda = g; returns (lambda, stats)."""
-        n = 2 * self.N
+        n = self.n
         out = out if out is not None else self._new(n)
         st = (ctypes.c_double * 4)()
         self._sync_stream()
@@ -276,7 +293,7 @@ class Plan:
     def dressing_vjp(self, x, gG, gZ, out=None, out_g2nc=None):
         """(sum gZ dlnZ/da, sum gG dlnG/db) as one 2N vector, and optionally d/d g2nc into out_g2nc (1)."""
         m = x.numel()
-        n = 2 * self.N
+        n = self.n
         out = out if out is not None else self._new(n)
         self._sync_stream()
         _check(self._L.dse_dressing_vjp(self._h, m, _dev_ptr(x, m, "x"), _dev_ptr(gG, m, "gG"), _dev_ptr(gZ, m, "gZ"),
@@ -299,3 +316,99 @@ class Plan:
         _check(self._L.dse_plan_counters(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
                "dse_plan_counters")
         return n.value, k.value, ms.value
+
+
+class Batch:
+    """A dse_batch: independent problems solved together (coefficients concatenated
+    in problem order; offsets() gives the slices)."""
+
+    def __init__(self, problems):
+        import torch
+        self._L = load()
+        self.problems = [dict(p) for p in problems]
+        self.nb = len(self.problems)
+        arr = (Problem * self.nb)(*[Problem.from_params(p) for p in self.problems])
+        h = _VP()
+        _check(self._L.dse_batch_create(arr, self.nb, _stream_ptr(), ctypes.byref(h)), "dse_batch_create")
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        off = (ctypes.c_longlong * (self.nb + 1))()
+        moff = (ctypes.c_longlong * (self.nb + 1))()
+        _check(self._L.dse_batch_offsets(self._h, off, moff), "dse_batch_offsets")
+        self.offsets = [int(v) for v in off]
+        self.matrix_offsets = [int(v) for v in moff]
+        self.n_total = self.offsets[-1]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.dse_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _sync_stream(self) -> None:
+        self._L.dse_batch_set_stream(self._h, _stream_ptr())
+
+    def split(self, t):
+        """Per-problem views of a concatenated coefficient (or residual) vector."""
+        return [t[self.offsets[b]:self.offsets[b + 1]] for b in range(self.nb)]
+
+    def tune(self, coeffs):
+        """Pick the radial nodes per work item by timing; returns (choice, ms per candidate)."""
+        u = ctypes.c_int(0)
+        ms = (ctypes.c_double * 5)()
+        self._sync_stream()
+        _check(self._L.dse_batch_tune(self._h, _dev_ptr(coeffs, self.n_total, "coeffs"), ctypes.byref(u),
+                                      ctypes.cast(ms, _D)), "dse_batch_tune")
+        return u.value, list(ms)
+
+    def newton_matrix(self, coeffs):
+        """(J, F): concatenated Newton matrices (flat) and residuals."""
+        import torch
+        J = torch.empty(self.matrix_offsets[-1], dtype=torch.float64, device=self.device)
+        F = torch.empty(self.n_total, dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        _check(self._L.dse_batch_newton_matrix(self._h, _dev_ptr(coeffs, self.n_total, "coeffs"),
+                                               _dev_ptr(J, J.numel(), "J"), _dev_ptr(F, self.n_total, "F")),
+               "dse_batch_newton_matrix")
+        return J, F
+
+    def matrices(self, J):
+        """Per-problem n_b x n_b views of a concatenated matrix vector."""
+        out = []
+        for b in range(self.nb):
+            n = self.offsets[b + 1] - self.offsets[b]
+            out.append(J[self.matrix_offsets[b]:self.matrix_offsets[b + 1]].view(n, n))
+        return out
+
+    def solve(self, coeffs, tol: float = 1e-10, max_iter: int = 50, rho_relax: float = 1.0, n_relax: int = 0,
+              check: bool = True):
+        """In-place Newton iteration of every problem; returns (iterations, status codes, stats)."""
+        it = (ctypes.c_int * self.nb)()
+        st = (ctypes.c_int * self.nb)()
+        stats = (ctypes.c_double * (3 * self.nb))()
+        self._sync_stream()
+        code = self._L.dse_batch_solve(self._h, _dev_ptr(coeffs, self.n_total, "coeffs"), float(tol), int(max_iter),
+                                       float(rho_relax), int(n_relax), it, st, ctypes.cast(stats, _D))
+        if code not in (DSE_OK, DSE_ERR_NOT_CONVERGED) or (check and code != DSE_OK):
+            raise DseError(code, "dse_batch_solve")
+        return list(it), list(st), [tuple(stats[3 * b:3 * b + 3]) for b in range(self.nb)]
+
+    def counters(self):
+        """(kernel launches, graph launches, radial nodes per work item)."""
+        n = ctypes.c_longlong(0)
+        g = ctypes.c_longlong(0)
+        u = ctypes.c_int(0)
+        _check(self._L.dse_batch_counters(self._h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(u)),
+               "dse_batch_counters")
+        return n.value, g.value, u.value

@@ -26,14 +26,14 @@ constexpr int kDvThreads = 256;  // 32 coefficients x 8 point lanes
 // d omega / d(g^2 Nc)
 __device__ __forceinline__ double domega() { return 11.0 / (48.0 * kPi * kPi); }
 
-// Per row r (0..N-1 collocation, N: x_Z, N+1: x_G) the omega-weighted sums
+// Per row r (0..Rc-1 collocation, Rc: x_Z, Rc+1: x_G) the omega-weighted sums
 //   wZ = sum hQ (p dlnG/dw + q dlnZ/dw)(z) + hM dlnG/dw(z)   (gluon rows)
 //   wG = sum hG dlnZ/dw(z)                                   (ghost rows)
 // over the triples with z > lambda2, where ln G(z) = ln G(lambda2) + delta L,
 // ln Z(z) = ln Z(lambda2) + gamma L, L = ln(1 + omega ln(z/lambda2)) and
 // d ln G/d omega = delta l/(1 + omega l), l = ln(z/lambda2).  Then
 //   dPi_Z/dg = Pi_Z/g + K/(3x) omega' wZ,   dPi_G/dg = Pi_G/g - K omega' wG,
-// with Pi from the residual pass (D[r][4N], D[r][4N+1]).  Fixed-order
+// with Pi from the residual pass (D[r][2n], D[r][2n+1]).  Fixed-order
 // reductions: thread-strided sums, warp shuffles, then warps in order.
 __global__ void __launch_bounds__(kParamThreads) k_param_rows(const Consts c, const Rad* __restrict__ rad,
                                                                const Ang* __restrict__ ang,
@@ -43,21 +43,20 @@ __global__ void __launch_bounds__(kParamThreads) k_param_rows(const Consts c, co
                                                                const double* __restrict__ D, double g2nc,
                                                                double* __restrict__ dPi) {
     __shared__ double s_w[2][kParamThreads / 32];
-    const int N = c.N;
+    const int NZ = c.NZ, NG = c.NG, n = c.n, Rc = c.Rc;
     const int r = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool gluon = r <= N;
-    const bool ghost = r != N;
-    const bool special = (r == N + 1) && !(c.x_G > 0.0);  // x_G = 0: z = y <= lambda2
+    const bool special = (r == Rc + 1) && !(c.x_G > 0.0);  // x_G = 0: z = y <= lambda2
+    const int flags = special ? kRowGhost : rows[r].flags;
+    const bool gluon = (flags & kRowGluon) != 0;
+    const bool ghost = (flags & kRowGhost) != 0;
     double wZ = 0.0, wG = 0.0;
     if (!special && c.extrap == 0) {
         const Row row = rows[r];
         // Chebyshev part at s = 1: T_j(1) = 1, phi_0 = 1/2
-        double lZb = 0.5 * coef[0], lGb = 0.5 * coef[N];
-        for (int j = 1; j < N; ++j) {
-            lZb += coef[j];
-            lGb += coef[N + j];
-        }
+        double lZb = 0.5 * coef[0], lGb = 0.5 * coef[NZ];
+        for (int j = 1; j < NZ; ++j) lZb += coef[j];
+        for (int j = 1; j < NG; ++j) lGb += coef[NZ + j];
         const int total = c.nr * c.na;
         for (int t = tid; t < total; t += kParamThreads) {
             const int k = t / c.na;
@@ -119,32 +118,32 @@ __global__ void __launch_bounds__(kParamThreads) k_param_rows(const Consts c, co
             tZ += s_w[0][w];
             tG += s_w[1][w];
         }
-        const double* Dr = D + (size_t)r * (4 * (size_t)N + 2);
+        const double* Dr = D + (size_t)r * ldD(c);
         const double pre = (gluon && !special) ? rows[r].pre : 0.0;
-        dPi[2 * r] = gluon ? Dr[4 * N] / g2nc + pre * domega() * tZ : 0.0;
-        dPi[2 * r + 1] = ghost ? Dr[4 * N + 1] / g2nc - c.K * domega() * tG : 0.0;
+        dPi[2 * r] = gluon ? Dr[2 * n] / g2nc + pre * domega() * tZ : 0.0;
+        dPi[2 * r + 1] = ghost ? Dr[2 * n + 1] / g2nc - c.K * domega() * tG : 0.0;
     }
 }
 
-// dF (2N x 3, columns g^2 Nc, G(x_G)^{-1}, Z(x_Z)^{-1}) from the per-row dPi/dg:
+// dF (n x 3, columns g^2 Nc, G(x_G)^{-1}, Z(x_Z)^{-1}) from the per-row dPi/dg
+// (gluon rows i < NZ at row i, ghost rows i < NG at row gofs + i):
 //   dF_z,i/dg = -dPi_Z(x_i)/dg + dPi_Z(x_Z)/dg,   dF_z,i/dZinv = -1
 //   dF_g,i/dg = -dPi_G(x_i)/dg + dPi_G(x_G)/dg,   dF_g,i/dGinv = -1
 // and optionally w = v^T dF (3 values, fixed-order sums by one warp).
 __global__ void k_param_assemble(const Consts c, const double* __restrict__ dPi, double* __restrict__ dF,
                                  const double* __restrict__ v, double* __restrict__ vdF) {
-    const int N = c.N;
-    const int n = 2 * N;
+    const int NZ = c.NZ, n = c.n, Rc = c.Rc;
     const int tid = threadIdx.x;
     if (dF) {
         for (int i = tid; i < n; i += blockDim.x) {
             double d0, d1, d2;
-            if (i < N) {
-                d0 = -dPi[2 * i] + dPi[2 * N];
+            if (i < NZ) {
+                d0 = -dPi[2 * i] + dPi[2 * Rc];
                 d1 = 0.0;
                 d2 = -1.0;
             } else {
-                const int ii = i - N;
-                d0 = -dPi[2 * ii + 1] + dPi[2 * (N + 1) + 1];
+                const int r = c.gofs + (i - NZ);
+                d0 = -dPi[2 * r + 1] + dPi[2 * (Rc + 1) + 1];
                 d1 = -1.0;
                 d2 = 0.0;
             }
@@ -156,12 +155,12 @@ __global__ void k_param_assemble(const Consts c, const double* __restrict__ dPi,
     if (v && tid < 32) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int i = tid; i < n; i += 32) {
-            if (i < N) {
-                a0 = fma(v[i], -dPi[2 * i] + dPi[2 * N], a0);
+            if (i < NZ) {
+                a0 = fma(v[i], -dPi[2 * i] + dPi[2 * Rc], a0);
                 a2 -= v[i];
             } else {
-                const int ii = i - N;
-                a0 = fma(v[i], -dPi[2 * ii + 1] + dPi[2 * (N + 1) + 1], a0);
+                const int r = c.gofs + (i - NZ);
+                a0 = fma(v[i], -dPi[2 * r + 1] + dPi[2 * (Rc + 1) + 1], a0);
                 a1 -= v[i];
             }
         }
@@ -181,36 +180,29 @@ __global__ void k_param_assemble(const Consts c, const double* __restrict__ dPi,
 
 // out_j = sum_i v_i J[i][j] with the entries of J taken from the per-row
 // derivative vectors as the assembly does (Sec. 3 matrix layout), one thread
-// per column j, rows in order.
+// per column j, gluon rows then ghost rows in order.
 __global__ void __launch_bounds__(kVjpThreads) k_vjp(const Consts c, const XTab* __restrict__ xtab,
                                                       const double* __restrict__ phix,
                                                       const double* __restrict__ D,
                                                       const double* __restrict__ v, double* __restrict__ out,
                                                       int* __restrict__ status) {
-    const int N = c.N;
+    const int N = c.N, NZ = c.NZ, NG = c.NG, n = c.n;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= 2 * N) return;
-    const size_t ld = 4 * (size_t)N + 2;
-    const double* DZ = D + (size_t)N * ld;
-    const double* DG = D + (size_t)(N + 1) * ld;
+    if (j >= n) return;
+    const size_t ld = ldD(c);
+    const double* DZ = D + (size_t)c.Rc * ld;
+    const double* DG = D + (size_t)(c.Rc + 1) * ld;
     double acc = 0.0;
-    if (j < N) {
-        for (int i = 0; i < N; ++i) {
-            const double* Di = D + (size_t)i * ld;
-            const double jz = -xtab[i].Zinv * phix[(size_t)i * N + j] - Di[j] + DZ[j];
-            const double jg = -Di[2 * N + j] + DG[2 * N + j];
-            acc = fma(v[i], jz, acc);
-            acc = fma(v[N + i], jg, acc);
-        }
-    } else {
-        const int jj = j - N;
-        for (int i = 0; i < N; ++i) {
-            const double* Di = D + (size_t)i * ld;
-            const double jz = -Di[N + jj] + DZ[N + jj];
-            const double jg = -xtab[i].Ginv * phix[(size_t)i * N + jj] - Di[3 * N + jj] + DG[3 * N + jj];
-            acc = fma(v[i], jz, acc);
-            acc = fma(v[N + i], jg, acc);
-        }
+    for (int i = 0; i < NZ; ++i) {
+        const double* Di = D + (size_t)i * ld;
+        const double diag = j < NZ ? -xtab[i].Zinv * phix[(size_t)i * N + j] : 0.0;
+        acc = fma(v[i], diag - Di[j] + DZ[j], acc);
+    }
+    for (int i = 0; i < NG; ++i) {
+        const int r = c.gofs + i;
+        const double* Di = D + (size_t)r * ld;
+        const double diag = j >= NZ ? -xtab[r].Ginv * phix[(size_t)r * N + (j - NZ)] : 0.0;
+        acc = fma(v[NZ + i], diag - Di[n + j] + DG[n + j], acc);
     }
     out[j] = acc;
     if (!isfinite(acc)) atomicOr(status, kStatusNonfinite);
@@ -276,14 +268,14 @@ __global__ void __launch_bounds__(256) k_adjoint_finish(int n, const double* __r
 }
 
 // Vector-Jacobian product of the dressing functions at n points:
-//   out[j]     = sum_m gZ_m d ln Z(x_m)/d a_j = sum_m gZ_m phi_j(x_m)
-//   out[N + j] = sum_m gG_m d ln G(x_m)/d b_j = sum_m gG_m phi_j(x_m)
-//   out[2N]    = sum_m (gG_m delta + gZ_m gamma) l_m/(1 + omega l_m) omega'
+//   out[j]      = sum_m gZ_m d ln Z(x_m)/d a_j = sum_m gZ_m phi_j(x_m)   (j < NZ)
+//   out[NZ + j] = sum_m gG_m d ln G(x_m)/d b_j = sum_m gG_m phi_j(x_m)   (j < NG)
+//   out[n]      = sum_m (gG_m delta + gZ_m gamma) l_m/(1 + omega l_m) omega'
 //                over x_m > lambda2 (UV form, the only place g^2 Nc enters)
 // with phi_j(x) = 1/2 (j = 0), T_j(s(x)) and s clamped to [-1, 1] as in the
 // expansion itself (the IR/UV forms add no coefficient dependence).
 // Grid (coefficient block of 32, point split); thread (lane j, point lane p)
-// runs the Chebyshev recurrence to its own j.  Partial sums [split][2N+1].
+// runs the Chebyshev recurrence to its own j (j < N).  Partial sums [split][n+1].
 __global__ void __launch_bounds__(kDvThreads) k_dressing_vjp_part(const Consts c, int n,
                                                                    const double* __restrict__ x,
                                                                    const double* __restrict__ gG,
@@ -323,8 +315,8 @@ __global__ void __launch_bounds__(kDvThreads) k_dressing_vjp_part(const Consts c
                 }
                 t = t1;
             }
-            sa = fma(gZ[m], t, sa);
-            sb = fma(gG[m], t, sb);
+            if (j < c.NZ) sa = fma(gZ[m], t, sa);
+            if (j < c.NG) sb = fma(gG[m], t, sb);
         }
         if (j == 0 && c.extrap == 0 && xm > c.lam2) {
             const double lu = lx - c.ln_lam2;
@@ -343,23 +335,21 @@ __global__ void __launch_bounds__(kDvThreads) k_dressing_vjp_part(const Consts c
             tb += s_b[q][lane];
             tu += s_u[q][lane];
         }
-        double* out = part + (size_t)split * (2 * N + 1);
-        if (j < N) {
-            out[j] = ta;
-            out[N + j] = tb;
-        }
-        if (j == 0) out[2 * N] = tu;
+        double* out = part + (size_t)split * (c.n + 1);
+        if (j < c.NZ) out[j] = ta;
+        if (j < c.NG) out[c.NZ + j] = tb;
+        if (j == 0) out[c.n] = tu;
     }
     if (bad) atomicOr(status, kStatusNonfinite);
 }
 
-__global__ void k_dressing_vjp_reduce(int N, int nsplit, const double* __restrict__ part, double* __restrict__ out,
+__global__ void k_dressing_vjp_reduce(int n, int nsplit, const double* __restrict__ part, double* __restrict__ out,
                                       double* __restrict__ out_g2nc) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e > 2 * N) return;
+    if (e > n) return;
     double s = 0.0;
-    for (int q = 0; q < nsplit; ++q) s += part[(size_t)q * (2 * N + 1) + e];
-    if (e < 2 * N) out[e] = s;
+    for (int q = 0; q < nsplit; ++q) s += part[(size_t)q * (n + 1) + e];
+    if (e < n) out[e] = s;
     else if (out_g2nc) *out_g2nc = s;
 }
 
@@ -383,7 +373,7 @@ int blocks_for(long long total, int threads) {
 cudaError_t launch_param_derivatives(const Consts& c, const Rad* rad, const Ang* ang, const Row* rows,
                                      const YTab* ytab, const double* coef, const double* D, double g2nc,
                                      double* dPi, double* dF, const double* v, double* vdF, cudaStream_t s) {
-    k_param_rows<<<c.N + 2, kParamThreads, 0, s>>>(c, rad, ang, rows, ytab, coef, D, g2nc, dPi);
+    k_param_rows<<<c.Rc + 2, kParamThreads, 0, s>>>(c, rad, ang, rows, ytab, coef, D, g2nc, dPi);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_param_assemble<<<1, 256, 0, s>>>(c, dPi, dF, v, vdF);
@@ -392,7 +382,7 @@ cudaError_t launch_param_derivatives(const Consts& c, const Rad* rad, const Ang*
 
 cudaError_t launch_vjp(const Consts& c, const XTab* xtab, const double* phix, const double* D, const double* v,
                        double* out, int* status, cudaStream_t s) {
-    k_vjp<<<(2 * c.N + kVjpThreads - 1) / kVjpThreads, kVjpThreads, 0, s>>>(c, xtab, phix, D, v, out, status);
+    k_vjp<<<(c.n + kVjpThreads - 1) / kVjpThreads, kVjpThreads, 0, s>>>(c, xtab, phix, D, v, out, status);
     return cudaGetLastError();
 }
 
@@ -423,7 +413,7 @@ cudaError_t launch_dressing_vjp(const Consts& c, int n, const double* x, const d
     k_dressing_vjp_part<<<grid, kDvThreads, 0, s>>>(c, n, x, gG, gZ, part, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_dressing_vjp_reduce<<<(2 * c.N + 1 + 127) / 128, 128, 0, s>>>(c.N, nsplit, part, out, out_g2nc);
+    k_dressing_vjp_reduce<<<(c.n + 1 + 127) / 128, 128, 0, s>>>(c.n, nsplit, part, out, out_g2nc);
     return cudaGetLastError();
 }
 

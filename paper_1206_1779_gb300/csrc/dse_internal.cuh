@@ -13,8 +13,16 @@ namespace dse {
 enum : int { kStatusNonfinite = 1, kStatusSingular = 2 };
 
 // Derived constants of Sec. 2 / Sec. 3, passed by value to every kernel.
+// Orders: NZ coefficients a_j of ln Z, NG coefficients b_j of ln G, N = max(NZ, NG)
+// (length of the T_j recurrence and of every phi table row), n = NZ + NG unknowns
+// c = (a; b).  Collocation rows: Rc = N shared points when NZ = NG, otherwise the
+// NZ gluon points followed by the NG ghost points (gofs = index of the first
+// ghost point, 0 when shared).  Per-row derivative vectors D[r] (ldD() doubles):
+// dPi_Z/dc_j at j, dPi_G/dc_j at n + j (j < n), Pi_Z at 2n, Pi_G at 2n + 1, for
+// r < Rc (collocation), Rc (x_Z) and Rc + 1 (x_G).
 struct Consts {
     int N, nr, na, extrap;
+    int NZ, NG, n, Rc, gofs;
     double eps2, lam2, ln_eps2, ln_lam2;
     double L0, L1, invL1;          // ln x = L0 + L1 s
     double K;                      // g^2 Nc / (2 pi)^3
@@ -23,6 +31,8 @@ struct Consts {
     double omega;                  // UV log coefficient 11 g^2 Nc / (48 pi^2)
     double x_G, x_Z, ginv_G, zinv_Z;
 };
+
+__host__ __device__ inline size_t ldD(const Consts& c) { return 2 * (size_t)c.n + 2; }
 
 // Per radial node: y_k, quadrature weight W_k (Jacobian y_k included), sqrt(y_k).
 struct Rad { double y, W, sy, pad; };
@@ -47,10 +57,37 @@ struct TripleArgs {
     const Ang* ang;
     const Row* rows;
     const YTab* ytab;
-    const double* coef;   // 2N: a then b
+    const double* coef;   // n: a (NZ) then b (NG)
     double* Upart;        // [Rt][nr][nch][3]   angular sums per radial node
     double* Vpart;        // [Rt][KS][3][N]     z-derivative sums per split
 };
+
+// One problem of a batch: its constants, its slice of the batch workspace and its
+// Newton-iteration state (iter, active, result), read and written on the device.
+struct BatchProblem {
+    TripleArgs t;          // t.coef is unused: coefficients come from coef_base + coef_off
+    YTab* ytab;            // = t.ytab, writable
+    double* xcol;
+    double* phiy;
+    XTab* xtab;
+    double* phix;
+    double* D;
+    double* J;
+    double* F;
+    double* work;
+    float* As;
+    double2* rowinfo;
+    double* stats;         // 4 doubles of the last Newton step
+    int* status;
+    long long coef_off;    // offset of the problem's c (and F) in the concatenated vectors
+    long long J_off;       // offset of its J in a concatenated matrix output
+    int iter;              // Newton steps taken
+    int active;            // 1 while the problem still iterates
+    int result;            // 0 running, 1 converged, -1 non-finite, -2 singular
+    int pad;
+};
+// One work item of the persistent quadrature kernel.
+struct BatchItem { int b, rt, ks, pad; };
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_gauss_legendre(int n, double* inv, double* x, double* w, cudaStream_t s);
@@ -70,8 +107,8 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
                              const double* Upart, const double* Vpart, double* D, cudaStream_t s);
 cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix,
                             const double* D, double* J, double* F, int* status, cudaStream_t s);
-// Newton step: J Delta = F, c <- c - rho Delta.  As (n*n floats) and rowinfo
-// (n double2) are scratch for the row-scaled FP32 copy of J.
+// Newton step: J Delta = F, c <- c - rho Delta (n = NZ + NG).  As (n*n floats)
+// and rowinfo (n double2) are scratch for the row-scaled FP32 copy of J.
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab,
                              double* coef, double rho, double* work, float* As, double2* rowinfo,
                              double* stats, int* status, cudaStream_t s);
@@ -84,9 +121,28 @@ cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, c
                              int nsplit, double* delta, int* status, cudaStream_t s);
 int schwinger_splits(int n_t, int n_nodes);
 
+// Batched forms (dse_batch.cu drives them): one launch covers every problem of
+// the batch; problems with active == 0 are skipped.
+cudaError_t launch_triple_batched(bool full, const BatchProblem* P, const BatchItem* items, int n_items,
+                                  int* counter, const double* coef_base, int maxN, int grid, cudaStream_t s);
+int triple_batched_blocks_per_sm(bool full, int maxN);
+cudaError_t launch_tables_batched(const BatchProblem* P, int nb, int max_units, const double* coef_base,
+                                  cudaStream_t s);
+cudaError_t launch_rowreduce_batched(bool full, const BatchProblem* P, int nb, int max_rows, int maxN,
+                                     cudaStream_t s);
+// J_base/F_base: NULL = each problem's own J, F; else outputs at J_off / coef_off.
+cudaError_t launch_assemble_batched(bool full, const BatchProblem* P, int nb, double* J_base, double* F_base,
+                                    cudaStream_t s);
+// Newton step of every active problem (n <= 128): rho = rho_relax for the first
+// n_relax steps, 1 after; a problem whose dimensionless residual on entry is
+// below tol is marked converged (after its update, as dse_solve does).
+cudaError_t prepare_newton_batched(int max_n);  // sets the kernel's shared-memory limit (outside capture)
+cudaError_t launch_newton_batched(const BatchProblem* P, int nb, int max_n, double* coef_base, double tol,
+                                  double rho_relax, int n_relax, int* n_active, cudaStream_t s);
+
 // Differentiation (dse_adjoint.cu).
 constexpr int kDressingVjpMaxSplits = 64;
-// dPi: 2 (N + 2) scratch; dF (2N x 3) and/or vdF = v^T dF (3) are outputs.
+// dPi: 2 (Rc + 2) scratch; dF (n x 3) and/or vdF = v^T dF (3) are outputs.
 cudaError_t launch_param_derivatives(const Consts& c, const Rad* rad, const Ang* ang, const Row* rows,
                                      const YTab* ytab, const double* coef, const double* D, double g2nc,
                                      double* dPi, double* dF, const double* v, double* vdF, cudaStream_t s);
@@ -97,7 +153,7 @@ cudaError_t launch_vjp(const Consts& c, const XTab* xtab, const double* phix, co
 cudaError_t launch_equilibrate_transpose(int n, double* A, double* scale, cudaStream_t s);
 cudaError_t launch_adjoint_finish(int n, const double* scale, double* lam, double* stats, cudaStream_t s);
 int dressing_vjp_splits(int n);
-// part: dressing_vjp_splits(n) * (2N + 1) scratch
+// part: dressing_vjp_splits(m) * (n + 1) scratch for m points
 cudaError_t launch_dressing_vjp(const Consts& c, int n, const double* x, const double* gG, const double* gZ,
                                 double* part, int nsplit, double* out, double* out_g2nc, int* status,
                                 cudaStream_t s);

@@ -62,8 +62,16 @@ __global__ void k_gauss_legendre(int n, const double* __restrict__ inv, double* 
 }
 
 // Mapped rules: radial t = ln y = L0 + L1 tau (weight L1 omega y), angular
-// theta = pi/2 (1 + tau) (weight pi/2 omega), collocation points x_i at the
-// mapped roots s_i = -cos(pi (2i+1)/(2N)) of T_N (Sec. 3), triple-kernel rows.
+// theta = pi/2 (1 + tau) (weight pi/2 omega), collocation points at the mapped
+// roots s_i = -cos(pi (2i+1)/(2m)) of T_m (Sec. 3; m = NZ for the gluon rows,
+// NG for the ghost rows, one shared set when NZ = NG), triple-kernel rows.
+__device__ __forceinline__ double collocation_point(const Consts& c, int q) {
+    const int m = q < c.NZ ? c.NZ : c.NG;
+    const int i = q < c.NZ ? q : q - c.NZ;
+    const double s = -cos(kPi * (2.0 * i + 1.0) / (2.0 * m));
+    return exp(c.L0 + c.L1 * s);
+}
+
 __global__ void k_setup_rules(const Consts c, const double* __restrict__ gr, const double* __restrict__ wr,
                               const double* __restrict__ ga, const double* __restrict__ wa, Rad* __restrict__ rad,
                               Ang* __restrict__ ang, double* __restrict__ theta, double* __restrict__ xcol,
@@ -94,20 +102,18 @@ __global__ void k_setup_rules(const Consts c, const double* __restrict__ gr, con
         return;
     }
     q -= c.na;
-    if (q < c.N) {
-        const double s = -cos(kPi * (2.0 * q + 1.0) / (2.0 * c.N));
-        xcol[q] = exp(c.L0 + c.L1 * s);
+    if (q < c.Rc) {
+        xcol[q] = collocation_point(c, q);
         return;
     }
-    q -= c.N;
+    q -= c.Rc;
     if (q < Rt) {
         double x;
         int flags;
-        if (q < c.N) {
-            const double s = -cos(kPi * (2.0 * q + 1.0) / (2.0 * c.N));
-            x = exp(c.L0 + c.L1 * s);
-            flags = kRowGluon | kRowGhost;
-        } else if (q == c.N) {
+        if (q < c.Rc) {
+            x = collocation_point(c, q);
+            flags = c.gofs == 0 ? (kRowGluon | kRowGhost) : (q < c.NZ ? kRowGluon : kRowGhost);
+        } else if (q == c.Rc) {
             x = c.x_Z;
             flags = kRowGluon;
         } else {
@@ -126,12 +132,11 @@ __global__ void k_setup_rules(const Consts c, const double* __restrict__ gr, con
 
 // Dressing functions at the radial nodes and collocation points for the
 // current coefficients, with the basis tables phi_j(y_k), phi_j(x_i).
-__global__ void k_tables(const Consts c, const double* __restrict__ coef, const Rad* __restrict__ rad,
+__device__ __forceinline__ void tables_unit(const Consts& c, const double* __restrict__ coef, const Rad* __restrict__ rad,
                          const double* __restrict__ xcol, YTab* __restrict__ ytab, double* __restrict__ phiy,
-                         XTab* __restrict__ xtab, double* __restrict__ phix) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+                         XTab* __restrict__ xtab, double* __restrict__ phix, const int m) {
     const double* a = coef;
-    const double* b = coef + c.N;
+    const double* b = coef + c.NZ;
     if (m < c.nr) {
         const double y = rad[m].y;
         double lG, lZ;
@@ -148,7 +153,7 @@ __global__ void k_tables(const Consts c, const double* __restrict__ coef, const 
         return;
     }
     const int i = m - c.nr;
-    if (i < c.N) {
+    if (i < c.Rc) {
         double lG, lZ;
         dressing_eval(c, a, b, xcol[i], lG, lZ, phix + (size_t)i * c.N);
         XTab t;
@@ -163,11 +168,25 @@ __global__ void k_tables(const Consts c, const double* __restrict__ coef, const 
     }
 }
 
+__global__ void k_tables(const Consts c, const double* __restrict__ coef, const Rad* __restrict__ rad,
+                         const double* __restrict__ xcol, YTab* __restrict__ ytab, double* __restrict__ phiy,
+                         XTab* __restrict__ xtab, double* __restrict__ phix) {
+    tables_unit(c, coef, rad, xcol, ytab, phiy, xtab, phix, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_tables_batched(const BatchProblem* __restrict__ P, const double* __restrict__ coef_base) {
+    const BatchProblem& B = P[blockIdx.y];
+    if (!B.active) return;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= B.t.c.nr + B.t.c.Rc) return;
+    tables_unit(B.t.c, coef_base + B.coef_off, B.t.rad, B.xcol, B.ytab, B.phiy, B.xtab, B.phix, m);
+}
+
 // ------------------------------------------------------------------------
-// Per external momentum r (rows 0..N-1: collocation points, N: x_Z, N+1: x_G):
+// Per external momentum r (rows 0..Rc-1: collocation points, Rc: x_Z, Rc+1: x_G):
 //   y-only contraction  Y_c[j] = sum_k U_c(r,k) phi_j(y_k),  c in {Q, M, G}
 //   z-part              V_c[j] = sum over radial splits of Vpart
-//   D[r] = (dPi_Z/da, dPi_Z/db, dPi_G/da, dPi_G/db, Pi_Z, Pi_G)
+//   D[r] = (dPi_Z/da (NZ), dPi_Z/db (NG), dPi_G/da (NZ), dPi_G/db (NG), Pi_Z, Pi_G)
 // with  dPi_Z/da_j = K/(3x) q (Y_Q + V_Q),  dPi_Z/db_j = K/(3x) (p (Y_Q + V_Q) + Y_M + V_M),
 //       dPi_G/da_j = -K V_G,  dPi_G/db_j = -K Y_G   (Sec. 2 equations, derivative
 // closure d ln G(u)/d b_j = d ln Z(u)/d a_j = phi_j(u)).
@@ -181,31 +200,30 @@ constexpr int kChunkK = 256;
 // coefficient j = 32 jb + lane and the radial nodes kk = kg mod 8 of each chunk;
 // the 8 partial sums are combined in a fixed order at the end.
 template <bool FULL>
-__global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt, int KS, int nch,
-                                                         const Rad* __restrict__ rad, const Ang* __restrict__ ang,
-                                                         const Row* __restrict__ rows, const YTab* __restrict__ ytab,
-                                                         const double* __restrict__ phiy,
-                                                         const double* __restrict__ Upart,
-                                                         const double* __restrict__ Vpart, double* __restrict__ D) {
+__device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS, int nch,
+                                                const Rad* __restrict__ rad, const Ang* __restrict__ ang,
+                                                const Row* __restrict__ rows, const YTab* __restrict__ ytab,
+                                                const double* __restrict__ phiy, const double* __restrict__ Upart,
+                                                const double* __restrict__ Vpart, double* __restrict__ D, const int r,
+                                                const int jb) {
     __shared__ double sU[kChunkK][3];
     __shared__ double sY[kRowKG][3][kRowJ];
     __shared__ double sS4;
     const int N = c.N;
-    const int r = blockIdx.x;
-    const int jb = blockIdx.y;
+    const int NZ = c.NZ, NG = c.NG, n = c.n, Rc = c.Rc;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int kg = tid >> 5;
     int rt;
     bool special = false;  // x_G = 0 ghost row
-    if (r < N) rt = r;
-    else if (r == N) rt = N;
+    if (r <= Rc) rt = r;
     else {
-        if (c.x_G > 0.0) rt = N + 1;
+        if (c.x_G > 0.0) rt = Rc + 1;
         else { rt = -1; special = true; }
     }
-    const bool gluon = r <= N;
-    const bool ghost = r != N;
+    const int flags = special ? kRowGhost : rows[rt].flags;
+    const bool gluon = (flags & kRowGluon) != 0;
+    const bool ghost = (flags & kRowGhost) != 0;
     const bool do_pi = (jb == 0);
     if (special && kg == 0) {
         // sum_l w_l sin^4(theta_l) by warp 0 (fixed order)
@@ -265,7 +283,7 @@ __global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt,
     __syncthreads();
     const Row rw = rows[rt >= 0 ? rt : 0];
     const double pre = gluon ? rw.pre : 0.0;
-    double* out = D + (size_t)r * (4 * N + 2);
+    double* out = D + (size_t)r * ldD(c);
     if (FULL && kg == 0 && j < N) {
         double y0 = 0.0, y1 = 0.0, y2 = 0.0;
         for (int q = 0; q < kRowKG; ++q) {
@@ -285,10 +303,14 @@ __global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt,
             VG = y2;
         }
         const double tq = y0 + VQ;
-        out[j] = gluon ? pre * c.qZ * tq : 0.0;
-        out[N + j] = gluon ? pre * (c.pG * tq + y1 + VM) : 0.0;
-        out[2 * N + j] = ghost ? -c.K * VG : 0.0;
-        out[3 * N + j] = ghost ? -c.K * y2 : 0.0;
+        if (j < NZ) {
+            out[j] = gluon ? pre * c.qZ * tq : 0.0;
+            out[n + j] = ghost ? -c.K * VG : 0.0;
+        }
+        if (j < NG) {
+            out[NZ + j] = gluon ? pre * (c.pG * tq + y1 + VM) : 0.0;
+            out[n + NZ + j] = ghost ? -c.K * y2 : 0.0;
+        }
     }
     if (do_pi && kg == 0) {
         for (int off = 16; off > 0; off >>= 1) {
@@ -297,45 +319,68 @@ __global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt,
             P2 += __shfl_xor_sync(kFullMask, P2, off);
         }
         if (lane == 0) {
-            out[4 * N] = gluon ? pre * (P0 + P1) : 0.0;
-            out[4 * N + 1] = ghost ? -c.K * P2 : 0.0;
+            out[2 * n] = gluon ? pre * (P0 + P1) : 0.0;
+            out[2 * n + 1] = ghost ? -c.K * P2 : 0.0;
         }
     }
 }
 
-// J and F from the per-row derivative vectors (Sec. 3 matrix layout):
-//   J[i][j]       = -Z(x_i)^{-1} phi_j(x_i) - dPi_Z(x_i)/da_j + dPi_Z(x_Z)/da_j
-//   J[i][N+j]     =                         - dPi_Z(x_i)/db_j + dPi_Z(x_Z)/db_j
-//   J[N+i][j]     =                         - dPi_G(x_i)/da_j + dPi_G(x_G)/da_j
-//   J[N+i][N+j]   = -G(x_i)^{-1} phi_j(x_i) - dPi_G(x_i)/db_j + dPi_G(x_G)/db_j
-//   F[i]   = Z(x_i)^{-1} - Z(x_Z)^{-1} - Pi_Z(x_i) + Pi_Z(x_Z)
-//   F[N+i] = G(x_i)^{-1} - G(x_G)^{-1} - Pi_G(x_i) + Pi_G(x_G)
 template <bool FULL>
-__global__ void k_assemble(const Consts c, const XTab* __restrict__ xtab, const double* __restrict__ phix,
-                           const double* __restrict__ D, double* __restrict__ J, double* __restrict__ F,
-                           int* __restrict__ status) {
+__global__ void __launch_bounds__(kRowBlock) k_rowreduce(const Consts c, int Rt, int KS, int nch,
+                                                         const Rad* __restrict__ rad, const Ang* __restrict__ ang,
+                                                         const Row* __restrict__ rows, const YTab* __restrict__ ytab,
+                                                         const double* __restrict__ phiy,
+                                                         const double* __restrict__ Upart,
+                                                         const double* __restrict__ Vpart, double* __restrict__ D) {
+    rowreduce_block<FULL>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D, blockIdx.x, blockIdx.y);
+}
+
+// Grid (row, coefficient block, problem); rows and blocks past a problem's own
+// counts return at once.
+template <bool FULL>
+__global__ void __launch_bounds__(kRowBlock) k_rowreduce_batched(const BatchProblem* __restrict__ P) {
+    const BatchProblem& B = P[blockIdx.z];
+    if (!B.active) return;
+    const Consts& c = B.t.c;
+    if ((int)blockIdx.x >= c.Rc + 2) return;
+    if ((int)blockIdx.y >= (FULL ? (c.N + kRowJ - 1) / kRowJ : 1)) return;
+    rowreduce_block<FULL>(c, B.t.Rt, B.t.KS, B.t.nch, B.t.rad, B.t.ang, B.t.rows, B.t.ytab, B.phiy, B.t.Upart,
+                          B.t.Vpart, B.D, blockIdx.x, blockIdx.y);
+}
+
+// J and F from the per-row derivative vectors (Sec. 3 matrix layout; n = NZ + NG,
+// gluon rows i < NZ at D row i, ghost rows i < NG at D row gofs + i):
+//   J[i][j]      = -Z(x_i)^{-1} phi_j(x_i) [j < NZ] - dPi_Z(x_i)/dc_j + dPi_Z(x_Z)/dc_j
+//   J[NZ+i][j]   = -G(x_i)^{-1} phi_{j-NZ}(x_i) [j >= NZ] - dPi_G(x_i)/dc_j + dPi_G(x_G)/dc_j
+//   F[i]    = Z(x_i)^{-1} - Z(x_Z)^{-1} - Pi_Z(x_i) + Pi_Z(x_Z)
+//   F[NZ+i] = G(x_i)^{-1} - G(x_G)^{-1} - Pi_G(x_i) + Pi_G(x_G)
+template <bool FULL>
+__device__ __forceinline__ void assemble_range(const Consts& c, const XTab* __restrict__ xtab,
+                                               const double* __restrict__ phix, const double* __restrict__ D,
+                                               double* __restrict__ J, double* __restrict__ F,
+                                               int* __restrict__ status, const size_t first, const size_t stride) {
     const int N = c.N;
-    const int n = 2 * N;
-    const size_t ld = 4 * (size_t)N + 2;
-    const double* DZ = D + (size_t)N * ld;        // x_Z row
-    const double* DG = D + (size_t)(N + 1) * ld;  // x_G row
+    const int NZ = c.NZ;
+    const int n = c.n;
+    const size_t ld = ldD(c);
+    const double* DZ = D + (size_t)c.Rc * ld;        // x_Z row
+    const double* DG = D + (size_t)(c.Rc + 1) * ld;  // x_G row
     const size_t total = FULL ? (size_t)n * n : 0;
     bool bad = false;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total + n;
-         e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = first; e < total + n; e += stride) {
         if (e < total) {
             const int i = (int)(e / n);
             const int j = (int)(e % n);
             double v;
-            if (i < N) {
+            if (i < NZ) {
                 const double* Di = D + (size_t)i * ld;
-                if (j < N) v = -xtab[i].Zinv * phix[(size_t)i * N + j] - Di[j] + DZ[j];
+                if (j < NZ) v = -xtab[i].Zinv * phix[(size_t)i * N + j] - Di[j] + DZ[j];
                 else v = -Di[j] + DZ[j];
             } else {
-                const int ii = i - N;
-                const double* Di = D + (size_t)ii * ld;
-                if (j < N) v = -Di[2 * N + j] + DG[2 * N + j];
-                else v = -xtab[ii].Ginv * phix[(size_t)ii * N + (j - N)] - Di[2 * N + j] + DG[2 * N + j];
+                const int r = c.gofs + (i - NZ);
+                const double* Di = D + (size_t)r * ld;
+                if (j < NZ) v = -Di[n + j] + DG[n + j];
+                else v = -xtab[r].Ginv * phix[(size_t)r * N + (j - NZ)] - Di[n + j] + DG[n + j];
             }
             J[e] = v;
             bad |= !isfinite(v);
@@ -343,10 +388,10 @@ __global__ void k_assemble(const Consts c, const XTab* __restrict__ xtab, const 
             const int i = (int)(e - total);
             if (F) {
                 double v;
-                if (i < N) v = xtab[i].Zinv - c.zinv_Z - D[(size_t)i * ld + 4 * N] + DZ[4 * N];
+                if (i < NZ) v = xtab[i].Zinv - c.zinv_Z - D[(size_t)i * ld + 2 * n] + DZ[2 * n];
                 else {
-                    const int ii = i - N;
-                    v = xtab[ii].Ginv - c.ginv_G - D[(size_t)ii * ld + 4 * N + 1] + DG[4 * N + 1];
+                    const int r = c.gofs + (i - NZ);
+                    v = xtab[r].Ginv - c.ginv_G - D[(size_t)r * ld + 2 * n + 1] + DG[2 * n + 1];
                 }
                 F[i] = v;
                 bad |= !isfinite(v);
@@ -354,6 +399,25 @@ __global__ void k_assemble(const Consts c, const XTab* __restrict__ xtab, const 
         }
     }
     if (bad) atomicOr(status, kStatusNonfinite);
+}
+
+template <bool FULL>
+__global__ void k_assemble(const Consts c, const XTab* __restrict__ xtab, const double* __restrict__ phix,
+                           const double* __restrict__ D, double* __restrict__ J, double* __restrict__ F,
+                           int* __restrict__ status) {
+    assemble_range<FULL>(c, xtab, phix, D, J, F, status, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                         (size_t)gridDim.x * blockDim.x);
+}
+
+template <bool FULL>
+__global__ void k_assemble_batched(const BatchProblem* __restrict__ P, double* __restrict__ J_base,
+                                   double* __restrict__ F_base) {
+    const BatchProblem& B = P[blockIdx.y];
+    if (!B.active) return;
+    double* J = J_base ? J_base + B.J_off : B.J;
+    double* F = F_base ? F_base + B.coef_off : B.F;
+    assemble_range<FULL>(B.t.c, B.xtab, B.phix, B.D, J, F, B.status, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                         (size_t)gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------------------
@@ -373,8 +437,7 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_newton(const Consts c, double
     __shared__ int s_piv;
     __shared__ int s_fail;
     __shared__ double s_red[3][kLuThreads / 32];
-    const int N = c.N;
-    const int n = 2 * N;
+    const int n = c.n;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int WARPS = kLuThreads / 32;
@@ -385,7 +448,7 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_newton(const Consts c, double
     for (int i = tid; i < n; i += kLuThreads) {
         const double f = F[i];
         b[i] = f;
-        const double sc = i < N ? xtab[i].Z : xtab[i - N].G;
+        const double sc = i < c.NZ ? xtab[i].Z : xtab[c.gofs + i - c.NZ].G;
         mF = fmax(mF, fabs(f));
         mS = fmax(mS, fabs(f) * sc);
         if (!isfinite(f)) mF = INFINITY;
@@ -631,8 +694,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
     __shared__ float s_pinv;
     __shared__ double s_anorm;
     __shared__ double s_red[3][kGjThreads / 32];
-    const int N = c.N;
-    const int n = 2 * N;
+    const int n = c.n;
     const int n2 = 2 * n;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -642,7 +704,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
     double mF = 0.0, mS = 0.0;
     for (int i = tid; i < n; i += kGjThreads) {
         const double f = F[i];
-        const double sc = i < N ? xtab[i].Z : xtab[i - N].G;
+        const double sc = i < c.NZ ? xtab[i].Z : xtab[c.gofs + i - c.NZ].G;
         mF = fmax(mF, fabs(f));
         mS = fmax(mS, fabs(f) * sc);
         if (!isfinite(f)) mF = INFINITY;
@@ -879,12 +941,10 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
 constexpr int kScaleThreads = 128;
 constexpr int kColPad = 144;  // >= 128 + 16 - 1, multiple of 4
 
-__global__ void __launch_bounds__(kScaleThreads) k_scale_rows(int n, const double* __restrict__ J,
-                                                              float* __restrict__ As, double2* __restrict__ rowinfo,
-                                                              int* __restrict__ status) {
+__device__ __forceinline__ void scale_row(int n, const double* __restrict__ J, float* __restrict__ As,
+                                          double2* __restrict__ rowinfo, int* __restrict__ status, const int i) {
     __shared__ int s_e[kScaleThreads / 32];
     __shared__ float s_sum[kScaleThreads / 32];
-    const int i = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double* row = J + (size_t)i * n;
     int e = 0;
@@ -914,8 +974,20 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale_rows(int n, const doubl
     }
 }
 
+__global__ void __launch_bounds__(kScaleThreads) k_scale_rows(int n, const double* __restrict__ J,
+                                                              float* __restrict__ As, double2* __restrict__ rowinfo,
+                                                              int* __restrict__ status) {
+    scale_row(n, J, As, rowinfo, status, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kScaleThreads) k_scale_rows_batched(const BatchProblem* __restrict__ P) {
+    const BatchProblem& B = P[blockIdx.y];
+    if (!B.active || (int)blockIdx.x >= B.t.c.n) return;
+    scale_row(B.t.c.n, B.J, B.As, B.rowinfo, B.status, blockIdx.x);
+}
+
 // ------------------------------------------------------------------------
-// Newton step for n = 2N <= 128 on one SM, FP64 work kept to O(n^2):
+// Newton step for n = NZ + NG <= 128 on one SM, FP64 work kept to O(n^2):
 //   - the row-scaled FP32 matrix A = diag(s) J (k_scale_rows) is inverted in
 //     place by Gauss-Jordan elimination held in registers: thread t owns column
 //     j = t mod n of the R consecutive rows g R .. g R + R - 1 (g = t div n);
@@ -929,13 +1001,11 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale_rows(int n, const doubl
 //     memory, one thread per row) until max|r| <= 4 sqrt(n) 2^-53 ||A|| ||x||;
 //   - FP64 LU fallback if the sweeps stall.
 template <int R>
-__global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, double* __restrict__ J,
-                                                           const float* __restrict__ As,
-                                                           const double2* __restrict__ rowinfo,
-                                                           const double* __restrict__ F,
-                                                           const XTab* __restrict__ xtab, double* __restrict__ coef,
-                                                           double rho, double* __restrict__ work,
-                                                           double* __restrict__ stats, int* __restrict__ status) {
+__device__ __forceinline__ void newton_reg_block(const Consts& c, double* __restrict__ J,
+                                                 const float* __restrict__ As, const double2* __restrict__ rowinfo,
+                                                 const double* __restrict__ F, const XTab* __restrict__ xtab,
+                                                 double* __restrict__ coef, const double rho, double* __restrict__ work,
+                                                 double* __restrict__ stats, int* __restrict__ status) {
     extern __shared__ __align__(16) double dsm[];
     __shared__ __align__(16) float s_colq[2][kColPad];
     __shared__ float s_rowk[2][128];
@@ -951,8 +1021,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, doubl
     __shared__ double s_red[2][4];
     __shared__ int s_piv, s_fail, s_done, s_conv;
     __shared__ double s_anorm;
-    const int N = c.N;
-    const int n = 2 * N;
+    const int n = c.n;
     const int ldj = n + 1;
     double* Js = dsm;                                             // [n][n+1] FP64 copy of J
     float* Xs = reinterpret_cast<float*>(dsm + (size_t)n * ldj);  // [n][n] inverse
@@ -972,7 +1041,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, doubl
         bool bad = false;
         for (int i = lane; i < n; i += 32) {
             const double f = F[i];
-            const double sc = i < N ? xtab[i].Z : xtab[i - N].G;
+            const double sc = i < c.NZ ? xtab[i].Z : xtab[c.gofs + i - c.NZ].G;
             mF = fmax(mF, fabs(f));
             mS = fmax(mS, fabs(f) * sc);
             bad |= !isfinite(f);
@@ -1207,6 +1276,47 @@ elimination_done:
     for (int i = tid; i < n; i += kGjThreads) coef[i] = fma(-rho, xres[i], coef[i]);
 }
 
+template <int R>
+__global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, double* __restrict__ J,
+                                                           const float* __restrict__ As,
+                                                           const double2* __restrict__ rowinfo,
+                                                           const double* __restrict__ F,
+                                                           const XTab* __restrict__ xtab, double* __restrict__ coef,
+                                                           double rho, double* __restrict__ work,
+                                                           double* __restrict__ stats, int* __restrict__ status) {
+    newton_reg_block<R>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status);
+}
+
+// One block per problem of a batch; afterwards thread 0 advances the problem's
+// iteration state: a failed step ends it (result -2 singular, -1 non-finite),
+// and so does a dimensionless residual on entry below tol (result 1, converged,
+// update applied).
+template <int R>
+__global__ void __launch_bounds__(kGjThreads) k_newton_reg_batched(BatchProblem* __restrict__ P,
+                                                                   double* __restrict__ coef_base, double tol,
+                                                                   double rho_relax, int n_relax,
+                                                                   int* __restrict__ n_active) {
+    BatchProblem& B = P[blockIdx.x];
+    if (!B.active) return;
+    const double rho = B.iter < n_relax ? rho_relax : 1.0;
+    newton_reg_block<R>(B.t.c, B.J, B.As, B.rowinfo, B.F, B.xtab, coef_base + B.coef_off, rho, B.work, B.stats,
+                        B.status);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        B.iter += 1;
+        const int stw = *B.status;
+        int res = 0;
+        if (stw & kStatusSingular) res = -2;
+        else if (stw & kStatusNonfinite) res = -1;
+        else if (B.stats[1] < tol) res = 1;
+        if (res != 0) {
+            B.result = res;
+            B.active = 0;
+            atomicSub(n_active, 1);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------
 __global__ void k_dressing(const Consts c, const double* __restrict__ coef, int n, const double* __restrict__ x,
                            double* __restrict__ lG, double* __restrict__ lZ, int* __restrict__ status) {
@@ -1219,7 +1329,7 @@ __global__ void k_dressing(const Consts c, const double* __restrict__ coef, int 
         return;
     }
     double g, z;
-    dressing_eval(c, coef, coef + c.N, xm, g, z, nullptr);
+    dressing_eval(c, coef, coef + c.NZ, xm, g, z, nullptr);
     lG[m] = g;
     lZ[m] = z;
 }
@@ -1245,7 +1355,7 @@ __global__ void k_schwinger_weights(const Consts c, const double* __restrict__ c
     const double p = pn[i];
     const double x = p * p;
     double g, z;
-    dressing_eval(c, coef, coef + c.N, x, g, z, nullptr);
+    dressing_eval(c, coef, coef + c.NZ, x, g, z, nullptr);
     sigw[i] = wn[i] * exp(z) / x / kPi;
 }
 
@@ -1314,14 +1424,14 @@ cudaError_t launch_gauss_legendre(int n, double* inv, double* x, double* w, cuda
 cudaError_t launch_setup_rules(const Consts& c, const double* gl_r, const double* gw_r, const double* gl_a,
                                const double* gw_a, Rad* rad, Ang* ang, double* theta, double* xcol, Row* rows,
                                int Rt, cudaStream_t s) {
-    const long long total = (long long)c.nr + c.na + c.N + Rt;
+    const long long total = (long long)c.nr + c.na + c.Rc + Rt;
     k_setup_rules<<<blocks_for(total, 128), 128, 0, s>>>(c, gl_r, gw_r, gl_a, gw_a, rad, ang, theta, xcol, rows, Rt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tables(const Consts& c, const double* coef, const Rad* rad, const double* xcol, YTab* ytab,
                           double* phiy, XTab* xtab, double* phix, cudaStream_t s) {
-    k_tables<<<blocks_for((long long)c.nr + c.N, 64), 64, 0, s>>>(c, coef, rad, xcol, ytab, phiy, xtab, phix);
+    k_tables<<<blocks_for((long long)c.nr + c.Rc, 64), 64, 0, s>>>(c, coef, rad, xcol, ytab, phiy, xtab, phix);
     return cudaGetLastError();
 }
 
@@ -1329,7 +1439,7 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
                              const Row* rows, const YTab* ytab, const double* phiy, const double* Upart,
                              const double* Vpart, double* D, cudaStream_t s) {
     (void)Rt;
-    const dim3 grid(c.N + 2, full ? (c.N + kRowJ - 1) / kRowJ : 1);
+    const dim3 grid(c.Rc + 2, full ? (c.N + kRowJ - 1) / kRowJ : 1);
     if (full)
         k_rowreduce<true><<<grid, kRowBlock, 0, s>>>(c, Rt, KS, nch, rad, ang, rows, ytab, phiy, Upart, Vpart, D);
     else
@@ -1339,7 +1449,7 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
 
 cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix, const double* D,
                             double* J, double* F, int* status, cudaStream_t s) {
-    const long long total = (full ? 4LL * c.N * c.N : 0) + 2LL * c.N;
+    const long long total = (full ? (long long)c.n * c.n : 0) + c.n;
     const int nb = blocks_for(total, 256);
     if (full) k_assemble<true><<<nb, 256, 0, s>>>(c, xtab, phix, D, J, F, status);
     else k_assemble<false><<<nb, 256, 0, s>>>(c, xtab, phix, D, J, F, status);
@@ -1348,7 +1458,7 @@ cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const 
 
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
                              double* work, float* As, double2* rowinfo, double* stats, int* status, cudaStream_t s) {
-    const int n = 2 * c.N;
+    const int n = c.n;
     cudaError_t e = cudaSuccess;
     if (n <= 128) {
         k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
@@ -1408,6 +1518,57 @@ cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, c
     const dim3 grid((n_t + kSchT - 1) / kSchT, nsplit);
     k_schwinger_sum<<<grid, kSchT * kSchPh, 0, s>>>(n_nodes, pn, sigw, t, n_t, nsplit, partial);
     k_schwinger_reduce<<<blocks_for(n_t, 256), 256, 0, s>>>(n_t, nsplit, partial, delta, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Batched launchers: grid dimension y (z for the row contraction) runs over the
+// problems of the batch.
+cudaError_t launch_tables_batched(const BatchProblem* P, int nb, int max_units, const double* coef_base,
+                                  cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const dim3 grid(blocks_for(max_units, 64), nb);
+    k_tables_batched<<<grid, 64, 0, s>>>(P, coef_base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowreduce_batched(bool full, const BatchProblem* P, int nb, int max_rows, int maxN,
+                                     cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const dim3 grid(max_rows, full ? (maxN + kRowJ - 1) / kRowJ : 1, nb);
+    if (full) k_rowreduce_batched<true><<<grid, kRowBlock, 0, s>>>(P);
+    else k_rowreduce_batched<false><<<grid, kRowBlock, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_batched(bool full, const BatchProblem* P, int nb, double* J_base, double* F_base,
+                                    cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    const dim3 grid(16, nb);
+    if (full) k_assemble_batched<true><<<grid, 256, 0, s>>>(P, J_base, F_base);
+    else k_assemble_batched<false><<<grid, 256, 0, s>>>(P, J_base, F_base);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_newton_batched(int max_n) {
+    if (max_n > 128) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * (size_t)max_n * (max_n + 1) + sizeof(float) * (size_t)max_n * max_n;
+    return cudaFuncSetAttribute(k_newton_reg_batched<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_newton_batched(const BatchProblem* P, int nb, int max_n, double* coef_base, double tol,
+                                  double rho_relax, int n_relax, int* n_active, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    if (max_n > 128) return cudaErrorInvalidValue;
+    k_scale_rows_batched<<<dim3(max_n, nb), kScaleThreads, 0, s>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // R = 16 serves every n <= 128: G = ceil(n/16) <= 8 groups, G n <= 1024 threads;
+    // the shared-memory limit was set by prepare_newton_batched (this launch may
+    // be captured into a graph)
+    const size_t smem = sizeof(double) * (size_t)max_n * (max_n + 1) + sizeof(float) * (size_t)max_n * max_n;
+    k_newton_reg_batched<16><<<nb, kGjThreads, smem, s>>>(const_cast<BatchProblem*>(P), coef_base, tol, rho_relax,
+                                                           n_relax, n_active);
     return cudaGetLastError();
 }
 

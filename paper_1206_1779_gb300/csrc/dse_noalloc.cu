@@ -49,20 +49,21 @@ struct Layout {
     size_t rad, ang, theta, rows, xcol, ytab, phiy, xtab, phix, U, D, gl, status, total;
 };
 
-Layout layout(int N, int nr, int na, int Rt, int nch) {
+Layout layout(const Consts& c, int Rt, int nch) {
+    const int N = c.N, nr = c.nr, na = c.na, Rc = c.Rc;
     Layout L;
     size_t off = 0;
     L.rad = off; off = up256(off + sizeof(Rad) * (size_t)nr);
     L.ang = off; off = up256(off + sizeof(Ang) * (size_t)na);
     L.theta = off; off = up256(off + sizeof(double) * (size_t)na);
     L.rows = off; off = up256(off + sizeof(Row) * (size_t)Rt);
-    L.xcol = off; off = up256(off + sizeof(double) * (size_t)N);
+    L.xcol = off; off = up256(off + sizeof(double) * (size_t)Rc);
     L.ytab = off; off = up256(off + sizeof(YTab) * (size_t)nr);
     L.phiy = off; off = up256(off + sizeof(double) * (size_t)nr * N);
-    L.xtab = off; off = up256(off + sizeof(XTab) * (size_t)N);
-    L.phix = off; off = up256(off + sizeof(double) * (size_t)N * N);
+    L.xtab = off; off = up256(off + sizeof(XTab) * (size_t)Rc);
+    L.phix = off; off = up256(off + sizeof(double) * (size_t)Rc * N);
     L.U = off; off = up256(off + sizeof(double) * (size_t)Rt * nr * nch * 3);
-    L.D = off; off = up256(off + sizeof(double) * (size_t)(N + 2) * (4 * (size_t)N + 2));
+    L.D = off; off = up256(off + sizeof(double) * (size_t)(Rc + 2) * ldD(c));
     const size_t gmax = nr > na ? nr : na;
     L.gl = off; off = up256(off + sizeof(double) * (2 * (size_t)nr + 2 * (size_t)na + gmax + 2));
     L.status = off; off = up256(off + sizeof(int));
@@ -76,7 +77,8 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
                                    void* cuda_stream) {
     if (!problem || !d_coeffs || !d_F) return DSE_ERR_ARG;
     const dse_problem* p = problem;
-    if (p->n_cheb < 1 || p->n_cheb > DSE_MAX_CHEB || p->n_radial < 1 || p->n_radial > DSE_MAX_NODES ||
+    if (p->n_cheb < 1 || p->n_cheb > DSE_MAX_CHEB || p->n_cheb_G < 0 || p->n_cheb_G > DSE_MAX_CHEB ||
+        p->n_radial < 1 || p->n_radial > DSE_MAX_NODES ||
         p->n_angular < 1 || p->n_angular > DSE_MAX_NODES)
         return DSE_ERR_ARG;
     if (!(p->eps2 > 0.0) || !(p->lambda2 > p->eps2) || !isfinite(p->lambda2) || !(p->x_Z > 0.0) ||
@@ -88,7 +90,12 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
 
     const double kPi = 3.14159265358979323846264338327950288;
     Consts c;
-    c.N = p->n_cheb;
+    c.NZ = p->n_cheb;
+    c.NG = p->n_cheb_G > 0 ? p->n_cheb_G : p->n_cheb;
+    c.N = c.NZ > c.NG ? c.NZ : c.NG;
+    c.n = c.NZ + c.NG;
+    c.Rc = c.NZ == c.NG ? c.N : c.n;
+    c.gofs = c.NZ == c.NG ? 0 : c.NZ;
     c.nr = p->n_radial;
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;
@@ -111,10 +118,10 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
     c.ginv_G = p->ginv_G;
     c.zinv_Z = p->zinv_Z;
 
-    const int N = c.N, nr = c.nr, na = c.na;
-    const int Rt = N + 1 + (p->x_G > 0.0 ? 1 : 0);
+    const int nr = c.nr, na = c.na;
+    const int Rt = c.Rc + 1 + (p->x_G > 0.0 ? 1 : 0);
     const int nch = (na + 31) / 32;
-    const Layout L = layout(N, nr, na, Rt, nch);
+    const Layout L = layout(c, Rt, nch);
     if (L.total > (size_t)DSE_STATIC_SCRATCH_BYTES) return DSE_ERR_ARG;  // does not fit the static scratch
 
     void* base = nullptr;

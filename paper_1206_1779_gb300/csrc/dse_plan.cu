@@ -61,6 +61,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? DSE_OK : DSE_ERR_CUDA
 int check_problem(const dse_problem* p) {
     if (!p) return DSE_ERR_ARG;
     if (p->n_cheb < 1 || p->n_cheb > DSE_MAX_CHEB) return DSE_ERR_ARG;
+    if (p->n_cheb_G < 0 || p->n_cheb_G > DSE_MAX_CHEB) return DSE_ERR_ARG;
     if (p->n_radial < 1 || p->n_radial > DSE_MAX_NODES) return DSE_ERR_ARG;
     if (p->n_angular < 1 || p->n_angular > DSE_MAX_NODES) return DSE_ERR_ARG;
     if (!(p->eps2 > 0.0) || !(p->lambda2 > p->eps2) || !isfinite(p->lambda2)) return DSE_ERR_ARG;
@@ -75,7 +76,12 @@ int check_problem(const dse_problem* p) {
 
 Consts make_consts(const dse_problem* p) {
     Consts c;
-    c.N = p->n_cheb;
+    c.NZ = p->n_cheb;
+    c.NG = p->n_cheb_G > 0 ? p->n_cheb_G : p->n_cheb;
+    c.N = c.NZ > c.NG ? c.NZ : c.NG;
+    c.n = c.NZ + c.NG;
+    c.Rc = c.NZ == c.NG ? c.N : c.n;
+    c.gofs = c.NZ == c.NG ? 0 : c.NZ;
     c.nr = p->n_radial;
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;
@@ -244,11 +250,11 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->prob = *problem;
     pl->c = make_consts(problem);
     pl->stream = (cudaStream_t)cuda_stream;
-    const int N = pl->c.N, nr = pl->c.nr, na = pl->c.na;
-    pl->Rt = N + 1 + (problem->x_G > 0.0 ? 1 : 0);
+    const int N = pl->c.N, nr = pl->c.nr, na = pl->c.na, Rc = pl->c.Rc;
+    pl->Rt = Rc + 1 + (problem->x_G > 0.0 ? 1 : 0);
     pl->nch = (na + 31) / 32;
     choose_split(pl);
-    const int n = 2 * N;
+    const int n = pl->c.n;
     const int gmax = nr > na ? nr : na;
 
     size_t off = 0;
@@ -256,21 +262,21 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_ang = off; off = align_up(off + sizeof(Ang) * na);
     size_t o_th = off; off = align_up(off + sizeof(double) * na);
     size_t o_rows = off; off = align_up(off + sizeof(Row) * pl->Rt);
-    size_t o_xcol = off; off = align_up(off + sizeof(double) * N);
+    size_t o_xcol = off; off = align_up(off + sizeof(double) * Rc);
     size_t o_ytab = off; off = align_up(off + sizeof(YTab) * nr);
     size_t o_phiy = off; off = align_up(off + sizeof(double) * (size_t)nr * N);
-    size_t o_xtab = off; off = align_up(off + sizeof(XTab) * N);
-    size_t o_phix = off; off = align_up(off + sizeof(double) * (size_t)N * N);
+    size_t o_xtab = off; off = align_up(off + sizeof(XTab) * Rc);
+    size_t o_phix = off; off = align_up(off + sizeof(double) * (size_t)Rc * N);
     size_t o_U = off; off = align_up(off + sizeof(double) * (size_t)pl->Rt * nr * pl->nch * 3);
     size_t o_V = off; off = align_up(off + sizeof(double) * (size_t)pl->Rt * pl->KS * 3 * N);
-    size_t o_D = off; off = align_up(off + sizeof(double) * (size_t)(N + 2) * (4 * N + 2));
+    size_t o_D = off; off = align_up(off + sizeof(double) * (size_t)(Rc + 2) * ldD(pl->c));
     size_t o_J = off; off = align_up(off + sizeof(double) * (size_t)n * n);
     size_t o_F = off; off = align_up(off + sizeof(double) * n);
     size_t o_work = off; off = align_up(off + sizeof(double) * 2 * n);
     size_t o_As = off; off = align_up(off + sizeof(float) * (size_t)n * n);
     size_t o_ri = off; off = align_up(off + sizeof(double2) * n);
-    const size_t n_aux_a = 2 * (size_t)(N + 2) + 3;
-    const size_t n_aux_b = (size_t)kDressingVjpMaxSplits * (2 * (size_t)N + 1);
+    const size_t n_aux_a = 2 * (size_t)(Rc + 2) + (size_t)n + 3;
+    const size_t n_aux_b = (size_t)kDressingVjpMaxSplits * ((size_t)n + 1);
     size_t o_aux = off; off = align_up(off + sizeof(double) * (n_aux_a > n_aux_b ? n_aux_a : n_aux_b));
     size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + sizeof(int));
     // Gauss-Legendre scratch (set-up only): nodes/weights for both rules and 1/k
@@ -346,7 +352,7 @@ int dse_plan_status(dse_plan* plan) {
 
 int dse_quadrature(dse_plan* plan, double* d_y, double* d_W, double* d_theta, double* d_wt, double* d_x) {
     if (!plan) return DSE_ERR_ARG;
-    const int nr = plan->c.nr, na = plan->c.na, N = plan->c.N;
+    const int nr = plan->c.nr, na = plan->c.na, Rc = plan->c.Rc;
     cudaError_t e = cudaSuccess;
     cudaStream_t s = plan->stream;
     if (d_y && e == cudaSuccess)
@@ -360,7 +366,7 @@ int dse_quadrature(dse_plan* plan, double* d_y, double* d_W, double* d_theta, do
                               cudaMemcpyDeviceToDevice, s);
     if (d_theta && e == cudaSuccess)
         e = cudaMemcpyAsync(d_theta, plan->theta, sizeof(double) * na, cudaMemcpyDeviceToDevice, s);
-    if (d_x && e == cudaSuccess) e = cudaMemcpyAsync(d_x, plan->xcol, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+    if (d_x && e == cudaSuccess) e = cudaMemcpyAsync(d_x, plan->xcol, sizeof(double) * Rc, cudaMemcpyDeviceToDevice, s);
     return cuda_status(e);
 }
 
@@ -390,7 +396,7 @@ int newton_step_impl(dse_plan* plan, double* d_coeffs, double rho, double* h_sta
     if (st) return st;
     cudaError_t e = launch_lu_newton(plan->c, plan->J, plan->F, plan->xtab, d_coeffs, rho, plan->work, plan->As,
                                      plan->rowinfo, plan->stats, plan->status, plan->stream);
-    plan->launches += 2 * plan->c.N <= 128 ? 2 : 1;
+    plan->launches += plan->c.n <= 128 ? 2 : 1;
     if (e != cudaSuccess) return DSE_ERR_CUDA;
     return read_status(plan, h_stats);
 }
@@ -527,7 +533,7 @@ int dse_param_derivatives(dse_plan* plan, const double* d_coeffs, double* d_dF, 
 
 int dse_adjoint_solve(dse_plan* plan, const double* d_coeffs, const double* d_g, double* d_lambda, double* h_stats) {
     if (!plan || !d_coeffs || !d_g || !d_lambda) return DSE_ERR_ARG;
-    const int n = 2 * plan->c.N;
+    const int n = plan->c.n;
     int st = build_system(plan, d_coeffs, plan->J, plan->F, true, false);
     if (st) return st;
     // (S J)^T mu = g with S the power-of-two row equilibration of J, lambda = S mu
@@ -549,7 +555,7 @@ int dse_dressing_vjp(dse_plan* plan, int n, const double* d_x, const double* d_g
     if (n > 0 && (!d_x || !d_gG || !d_gZ)) return DSE_ERR_ARG;
     cudaError_t e;
     if (n == 0) {
-        e = cudaMemsetAsync(d_out, 0, sizeof(double) * 2 * plan->c.N, plan->stream);
+        e = cudaMemsetAsync(d_out, 0, sizeof(double) * plan->c.n, plan->stream);
         if (e == cudaSuccess && d_out_g2nc) e = cudaMemsetAsync(d_out_g2nc, 0, sizeof(double), plan->stream);
         return cuda_status(e);
     }

@@ -7,8 +7,8 @@
 namespace dse {
 
 // s(x) = (ln x - L0)/L1 clamped to [-1, 1]; ln G, ln Z and optionally
-// phi_j(x) = d ln G/d b_j = d ln Z/d a_j (1/2 for j = 0, T_j(s) otherwise).
-// a, b: the N coefficients of ln Z and ln G.
+// phi_j(x) = d ln G/d b_j = d ln Z/d a_j (1/2 for j = 0, T_j(s) otherwise) for
+// j < N = max(NZ, NG).  a: the NZ coefficients of ln Z, b: the NG of ln G.
 __device__ __forceinline__ void dressing_eval(const Consts& c, const double* __restrict__ a,
                                               const double* __restrict__ b, double x, double& lG,
                                               double& lZ, double* __restrict__ phi) {
@@ -18,8 +18,8 @@ __device__ __forceinline__ void dressing_eval(const Consts& c, const double* __r
     double g = 0.5 * b[0], zz = 0.5 * a[0];
     if (phi) phi[0] = 0.5;
     if (c.N > 1) {
-        g = fma(b[1], s, g);
-        zz = fma(a[1], s, zz);
+        if (c.NG > 1) g = fma(b[1], s, g);
+        if (c.NZ > 1) zz = fma(a[1], s, zz);
         if (phi) phi[1] = s;
     }
     double t0 = 1.0, t1 = s;
@@ -28,8 +28,8 @@ __device__ __forceinline__ void dressing_eval(const Consts& c, const double* __r
         const double t2 = fma(s2, t1, -t0);
         t0 = t1;
         t1 = t2;
-        g = fma(b[j], t2, g);
-        zz = fma(a[j], t2, zz);
+        if (j < c.NG) g = fma(b[j], t2, g);
+        if (j < c.NZ) zz = fma(a[j], t2, zz);
         if (phi) phi[j] = t2;
     }
     if (c.extrap == 0) {

@@ -47,9 +47,10 @@ __host__ __device__ inline size_t smem_doubles(bool full, int N, int BT) {
     return tile_doubles(full, N, BT) + 3u * (size_t)BT + 2u * (size_t)N;
 }
 
+// One block's work: row rt, radial split ks of the problem in A.  smem holds
+// smem_doubles(FULL, N, BT) doubles.
 template <int BT, int NJ, bool FULL>
-__global__ void __launch_bounds__(BT) k_triple(const __grid_constant__ TripleArgs A) {
-    extern __shared__ __align__(16) double smem[];
+__device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, const int ks, double* smem) {
     const Consts& c = A.c;
     const int N = c.N;
     const int ldT = N + 1;
@@ -62,12 +63,11 @@ __global__ void __launch_bounds__(BT) k_triple(const __grid_constant__ TripleArg
     const int lane = tid & 31;
     const int warp = tid >> 5;
 
+    // a (NZ) and b (NG) zero-padded to N = max(NZ, NG): one recurrence serves both series
     for (int j = tid; j < N; j += BT) {
-        sa[j] = A.coef[j];
-        sb[j] = A.coef[N + j];
+        sa[j] = j < c.NZ ? A.coef[j] : 0.0;
+        sb[j] = j < c.NG ? A.coef[c.NZ + j] : 0.0;
     }
-    const int rt = blockIdx.y;
-    const int ks = blockIdx.x;
     const Row row = A.rows[rt];
     const bool gluon = (row.flags & kRowGluon) != 0;
     const bool ghost = (row.flags & kRowGhost) != 0;
@@ -236,6 +236,37 @@ __global__ void __launch_bounds__(BT) k_triple(const __grid_constant__ TripleArg
     }
 }
 
+template <int BT, int NJ, bool FULL>
+__global__ void __launch_bounds__(BT) k_triple(const __grid_constant__ TripleArgs A) {
+    extern __shared__ __align__(16) double smem[];
+    triple_tile<BT, NJ, FULL>(A, blockIdx.y, blockIdx.x, smem);
+}
+
+// Persistent form for a batch of independent problems: each block takes work
+// items (problem, row, radial split) from a global counter in the order of the
+// item list (longest first) until the list is exhausted; items of converged
+// problems are skipped.
+template <int BT, int NJ, bool FULL>
+__global__ void __launch_bounds__(BT) k_triple_batched(const BatchProblem* __restrict__ P,
+                                                       const BatchItem* __restrict__ items, int n_items,
+                                                       int* __restrict__ counter,
+                                                       const double* __restrict__ coef_base) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();  // also orders the previous item's shared-memory use before this one
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        if (!P[w.b].active) continue;
+        TripleArgs A = P[w.b].t;
+        A.coef = coef_base + P[w.b].coef_off;
+        triple_tile<BT, NJ, FULL>(A, w.rt, w.ks, smem);
+    }
+}
+
 template <int BT, bool FULL>
 cudaError_t launch_bt(const TripleArgs& a, cudaStream_t s) {
     const int N = a.c.N;
@@ -291,6 +322,59 @@ size_t triple_smem_bytes(bool full, int N) {
 int triple_max_blocks_per_sm(bool full, int N) {
     if (block_threads_for(N) == 128) return full ? occupancy_bt<128, true>(N) : occupancy_bt<128, false>(N);
     return full ? occupancy_bt<64, true>(N) : occupancy_bt<64, false>(N);
+}
+
+namespace {
+template <int BT, bool FULL>
+cudaError_t launch_batched_bt(const BatchProblem* P, const BatchItem* items, int n_items, int* counter,
+                              const double* coef_base, int maxN, int grid, cudaStream_t s) {
+    const size_t smem = smem_doubles(FULL, maxN, BT) * sizeof(double);
+    const int nj = (maxN + BT - 1) / BT;
+    // the shared-memory limit was set by triple_batched_blocks_per_sm (no attribute
+    // change here: this launch may be captured into a graph)
+#define DSE_LAUNCH_TB(NJ) k_triple_batched<BT, NJ, FULL><<<grid, BT, smem, s>>>(P, items, n_items, counter, coef_base);
+    if (nj <= 1) { DSE_LAUNCH_TB(1) }
+    else if (nj <= 2) { DSE_LAUNCH_TB(2) }
+    else if (nj <= 4) { DSE_LAUNCH_TB(4) }
+    else return cudaErrorInvalidValue;
+#undef DSE_LAUNCH_TB
+    return cudaGetLastError();
+}
+
+template <int BT, bool FULL>
+int batched_occupancy_bt(int maxN) {
+    const size_t smem = smem_doubles(FULL, maxN, BT) * sizeof(double);
+    const int nj = (maxN + BT - 1) / BT;
+    int nb = 0;
+    cudaError_t e;
+    if (nj <= 1) {
+        cudaFuncSetAttribute(k_triple_batched<BT, 1, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple_batched<BT, 1, FULL>, BT, smem);
+    } else if (nj <= 2) {
+        cudaFuncSetAttribute(k_triple_batched<BT, 2, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple_batched<BT, 2, FULL>, BT, smem);
+    } else {
+        cudaFuncSetAttribute(k_triple_batched<BT, 4, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple_batched<BT, 4, FULL>, BT, smem);
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+}  // namespace
+
+cudaError_t launch_triple_batched(bool full, const BatchProblem* P, const BatchItem* items, int n_items,
+                                  int* counter, const double* coef_base, int maxN, int grid, cudaStream_t s) {
+    if (n_items <= 0 || grid <= 0) return cudaSuccess;
+    if (block_threads_for(maxN) == 128)
+        return full ? launch_batched_bt<128, true>(P, items, n_items, counter, coef_base, maxN, grid, s)
+                    : launch_batched_bt<128, false>(P, items, n_items, counter, coef_base, maxN, grid, s);
+    return full ? launch_batched_bt<64, true>(P, items, n_items, counter, coef_base, maxN, grid, s)
+                : launch_batched_bt<64, false>(P, items, n_items, counter, coef_base, maxN, grid, s);
+}
+
+int triple_batched_blocks_per_sm(bool full, int maxN) {
+    if (block_threads_for(maxN) == 128)
+        return full ? batched_occupancy_bt<128, true>(maxN) : batched_occupancy_bt<128, false>(maxN);
+    return full ? batched_occupancy_bt<64, true>(maxN) : batched_occupancy_bt<64, false>(maxN);
 }
 
 cudaError_t launch_triple(bool full, const TripleArgs& a, cudaStream_t s) {

@@ -48,9 +48,10 @@ __global__ void __launch_bounds__(BT) k_triple32(const __grid_constant__ TripleA
     const int lane = tid & 31;
     const int warp = tid >> 5;
 
+    // a (NZ) and b (NG) zero-padded to N = max(NZ, NG): one recurrence serves both series
     for (int j = tid; j < N; j += BT) {
-        sa[j] = (float)A.coef[j];
-        sb[j] = (float)A.coef[N + j];
+        sa[j] = j < c.NZ ? (float)A.coef[j] : 0.0f;
+        sb[j] = j < c.NG ? (float)A.coef[c.NZ + j] : 0.0f;
     }
     const int rt = blockIdx.y;
     const int ks = blockIdx.x;

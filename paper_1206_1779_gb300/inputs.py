@@ -54,7 +54,9 @@ def starting_guess(params: dict, seed: int = 0, noise: float = 0.01) -> np.ndarr
     noise * N(0,1)/(j+1) drawn from numpy's default_rng(seed).
 
     The guess functions are  ln G0 = -kappa ln(x/(1+x)) + delta ln(1 + w ln(1+x))
-    and ln Z0 = 2 kappa ln(x/(1+x)) + gamma ln(1 + w ln(1+x)) + const with
+    (for G(x_G)^{-1} = ginv_G > 0: ln G0 = -ln(ginv_G + (x/(1+x))^kappa) + the same
+    UV term, so that G0 tends to 1/ginv_G in the infrared as the decoupling
+    solutions do) and ln Z0 = 2 kappa ln(x/(1+x)) + gamma ln(1 + w ln(1+x)) + const with
     w = 11 g^2 N_c / (48 pi^2) and const fixing Z0(lambda2) = 1/zinv_Z; they are
     interpolated by numpy's Chebyshev routine in the variable
     s = ln(x / sqrt(eps2 lambda2)) / (ln(lambda2/eps2)/2) and converted to the
@@ -68,9 +70,15 @@ def starting_guess(params: dict, seed: int = 0, noise: float = 0.01) -> np.ndarr
     l0 = 0.5 * math.log(params["eps2"] * params["lambda2"])
     l1 = 0.5 * math.log(params["lambda2"] / params["eps2"])
 
+    ginv = float(params.get("ginv_G", 0.0))
+
     def lnG0(s):
         x = np.exp(l0 + l1 * s)
-        return -kappa * np.log(x / (1 + x)) + delta * np.log1p(w * np.log1p(x))
+        uv = delta * np.log1p(w * np.log1p(x))
+        if ginv > 0.0:
+            # decoupling-type boundary value: G0 -> 1/ginv_G in the infrared
+            return -np.log(ginv + (x / (1 + x)) ** kappa) + uv
+        return -kappa * np.log(x / (1 + x)) + uv
 
     def lnZ0_raw(s):
         x = np.exp(l0 + l1 * s)
@@ -103,3 +111,23 @@ def target_factors(n: int = 64, seed: int = 1, spread: float = 0.05) -> np.ndarr
     """Factors 1 + spread * U(-1, 1) from numpy's default_rng(seed): targets are a
     converged Z(x) times these."""
     return (1.0 + spread * np.random.default_rng(seed).uniform(-1.0, 1.0, size=int(n))).astype(np.float64)
+
+
+BATCH_ORDERS = (24, 32, 48, 64)
+BATCH_QUADRATURES = ((128, 64), (256, 128))
+
+
+def batch_problems(n: int = 256, seed: int = 0, ginv_lo: float = 1e-3, ginv_hi: float = 1e-1) -> list:
+    """A sweep of independent problems: per problem, N_Z and N_G drawn from
+    BATCH_ORDERS, (n_radial, n_angular) from BATCH_QUADRATURES and G(x_G)^{-1}
+    log-uniform in [ginv_lo, ginv_hi], from numpy's default_rng(seed) in that
+    order; all other parameters as in problem()."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(int(n)):
+        nz = int(rng.choice(BATCH_ORDERS))
+        ng = int(rng.choice(BATCH_ORDERS))
+        nr, na = BATCH_QUADRATURES[int(rng.integers(len(BATCH_QUADRATURES)))]
+        ginv = float(math.exp(rng.uniform(math.log(ginv_lo), math.log(ginv_hi))))
+        out.append(problem(nz, nr, na, n_cheb_G=ng, ginv_G=ginv))
+    return out

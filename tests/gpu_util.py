@@ -23,8 +23,21 @@ ABS_OF_MAGNITUDE = 1e-13
 U = 2.0 ** -53
 
 
-def column_index(n_cols: int, N: int) -> np.ndarray:
-    return np.arange(n_cols) % N
+def orders(p):
+    """(N_Z, N_G) of a problem dict (n_cheb_G = 0 means N_G = N_Z)."""
+    nz = int(p["n_cheb"])
+    return nz, int(p.get("n_cheb_G", 0) or 0) or nz
+
+
+def n_unknowns(p) -> int:
+    nz, ng = orders(p)
+    return nz + ng
+
+
+def column_index(p) -> np.ndarray:
+    """Chebyshev index of every column of J (a_0..a_{N_Z-1}, b_0..b_{N_G-1})."""
+    nz, ng = orders(p)
+    return np.concatenate([np.arange(nz), np.arange(ng)])
 
 
 def entries_ok(G, O, A, jidx=None):

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import adjoint_ref as R
-from gpu_util import column_index, entries_ok, to_dev, to_host
+from gpu_util import column_index, entries_ok, n_unknowns, orders, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -43,13 +43,15 @@ CASES = {
     "narrow_range": dict(n_cheb=11, n_radial=40, n_angular=64, eps2=1e-3, lambda2=1e3, x_Z=1e3),
     "decoupling_n16": dict(n_cheb=16, n_radial=64, n_angular=32, ginv_G=0.01),
     "n100": dict(n_cheb=100, n_radial=64, n_angular=32),
+    "orders_24_48": dict(n_cheb=24, n_cheb_G=48, n_radial=40, n_angular=24, ginv_G=0.01),
+    "orders_13_6_ghost_point": dict(n_cheb=13, n_cheb_G=6, n_radial=30, n_angular=33, x_G=3e-3, ginv_G=0.02),
 }
 
 
 def matrix_bar(oracle, p, c):
     Jo, Fo = oracle.newton_matrix(p, c)
     A, AF = oracle.newton_matrix_magnitudes(p, c)
-    j = column_index(Jo.shape[1], p["n_cheb"]).astype(np.float64)
+    j = column_index(p).astype(np.float64)
     bar = 1e-11 * np.abs(Jo) + (1e-13 + 16.0 * j[None, :] ** 2 * U) * A
     return Jo, Fo, AF, bar
 
@@ -58,7 +60,7 @@ def matrix_bar(oracle, p, c):
 def test_vjp_parity(dse, oracle, inputs, name):
     p = inputs.problem(**CASES[name])
     c = inputs.starting_guess(p, seed=21)
-    n = 2 * p["n_cheb"]
+    n = n_unknowns(p)
     v = np.random.default_rng(3).standard_normal(n)
     with dse.Plan(p) as plan:
         F = to_dev(np.zeros(n))
@@ -77,7 +79,7 @@ def test_vjp_parity(dse, oracle, inputs, name):
 def test_param_derivatives_parity(dse, oracle, inputs, name):
     p = inputs.problem(**CASES[name])
     c = inputs.starting_guess(p, seed=22)
-    n = 2 * p["n_cheb"]
+    n = n_unknowns(p)
     v = np.random.default_rng(4).standard_normal(n)
     with dse.Plan(p) as plan:
         dF = to_host(plan.param_derivatives(to_dev(c)))
@@ -101,11 +103,11 @@ def test_param_derivatives_reject_zero_coupling(dse, inputs):
         assert e.value.code == dse.DSE_ERR_ARG
 
 
-@pytest.mark.parametrize("name", ["tiny", "ragged", "decoupling_n16", "n100"])
+@pytest.mark.parametrize("name", ["tiny", "ragged", "decoupling_n16", "n100", "orders_24_48"])
 def test_adjoint_solve_backward_error(dse, oracle, inputs, name):
     p = inputs.problem(**CASES[name])
     c = inputs.starting_guess(p, seed=23)
-    n = 2 * p["n_cheb"]
+    n = n_unknowns(p)
     g = np.random.default_rng(5).standard_normal(n)
     with dse.Plan(p) as plan:
         lam_t, st = plan.adjoint_solve(to_dev(c), to_dev(g))
@@ -118,9 +120,9 @@ def test_adjoint_solve_backward_error(dse, oracle, inputs, name):
 
 
 def test_dressing_vjp_parity(dse, oracle, inputs):
-    for extrap in (0, 1):
-        p = inputs.problem(24, 8, 8, extrap_mode=extrap)
-        N = p["n_cheb"]
+    for extrap, ng in ((0, 0), (1, 0), (0, 17)):
+        p = inputs.problem(24, 8, 8, extrap_mode=extrap, n_cheb_G=ng)
+        nz, ng = orders(p)
         rng = np.random.default_rng(6)
         # points below eps2, inside, and above lambda2
         x = np.exp(rng.uniform(np.log(1e-9), np.log(1e9), 777))
@@ -132,9 +134,9 @@ def test_dressing_vjp_parity(dse, oracle, inputs):
             wg = to_host(wg)[0]
             assert plan.status() == dse.DSE_OK
         phi = np.array([oracle.basis(p, xm) for xm in x])
-        ref = np.concatenate([phi.T @ gZ, phi.T @ gG])
-        mag = np.concatenate([np.abs(phi).T @ np.abs(gZ), np.abs(phi).T @ np.abs(gG)])
-        j = column_index(2 * N, N).astype(np.float64)
+        ref = np.concatenate([phi[:, :nz].T @ gZ, phi[:, :ng].T @ gG])
+        mag = np.concatenate([np.abs(phi[:, :nz]).T @ np.abs(gZ), np.abs(phi[:, :ng]).T @ np.abs(gG)])
+        j = column_index(p).astype(np.float64)
         assert np.all(np.abs(out - ref) <= (4 * x.size * U + 16 * j ** 2 * U) * mag)
         # d/d g2nc from central differences of the oracle dressing (the UV form is
         # smooth in omega; step 1e-5 relative)
@@ -181,7 +183,7 @@ def test_autograd_residual_matches_oracle(dse, oracle, inputs):
     from paper_1206_1779_gb300 import autograd as ad
     p = inputs.problem(**CASES["ragged"])
     c = inputs.starting_guess(p, seed=24)
-    n = 2 * p["n_cheb"]
+    n = n_unknowns(p)
     v = np.random.default_rng(9).standard_normal(n)
     with dse.Plan(p) as plan:
         ct = to_dev(c).requires_grad_(True)
@@ -238,9 +240,12 @@ def test_implicit_gradient_full_size(dse, oracle, inputs):
             lG, lZz = plan.dressing(cc, xt)
             return float(((torch.exp(lZz) - t) ** 2).sum())
 
+        # step 1e-6 max(|theta_k|, 1): the solves stop at the FP64 floor of the
+        # residual (~1e-12 dimensionless), so a step of 1e-8 on G(x_G)^{-1} = 0.01
+        # would leave the quotient noise-limited at ~1e-4
         fd = []
         for k, name in enumerate(("g2nc", "ginv_G")):
-            h = 1e-6 * p[name]
+            h = 1e-6 * max(abs(p[name]), 1.0)
             base = [p["g2nc"], p["ginv_G"]]
             up, dn = list(base), list(base)
             up[k] += h
@@ -255,6 +260,6 @@ def test_implicit_gradient_full_size(dse, oracle, inputs):
     dFo = oracle.param_derivatives(p, co)
     prop = np.array([np.abs(lam) @ bar @ np.abs(oracle.lu_solve(Jo, dFo[:, k])) for k in (0, 1)])
     bound = prop + 1e-7 * np.abs(go[:2])
-    print("grad gpu", grad, "fd", fd, "oracle", go[:2], "bound", bound)
+    print("grad gpu %r fd %r oracle %r bound %r" % (grad.tolist(), fd.tolist(), go[:2].tolist(), bound.tolist()))
     assert np.all(np.abs(grad - fd) <= 1e-5 * np.abs(fd)), (grad, fd)
     assert np.all(np.abs(grad - go[:2]) <= bound), (grad, go[:2], bound)

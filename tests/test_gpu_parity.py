@@ -8,7 +8,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import column_index, dump, entries_ok, to_dev, to_host
+from gpu_util import column_index, dump, entries_ok, n_unknowns, orders, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -34,6 +34,12 @@ CASES = {
     "newton_step_n16": dict(n_cheb=16, n_radial=64, n_angular=32),
     "n100": dict(n_cheb=100, n_radial=64, n_angular=32),
     "n160": dict(n_cheb=160, n_radial=40, n_angular=24),
+    # separate orders N_Z != N_G: gluon rows at the N_Z roots, ghost rows at the N_G roots
+    "orders_11_7": dict(n_cheb=11, n_cheb_G=7, n_radial=30, n_angular=40),
+    "orders_6_13_ghost_point": dict(n_cheb=6, n_cheb_G=13, n_radial=25, n_angular=33, x_G=2e-3, ginv_G=0.03,
+                                    x_Z=4e4),
+    "orders_64_24": dict(n_cheb=64, n_cheb_G=24, n_radial=128, n_angular=64),
+    "orders_48_64_constant_extrap": dict(n_cheb=48, n_cheb_G=64, n_radial=64, n_angular=32, extrap_mode=1),
 }
 
 
@@ -48,7 +54,7 @@ def test_newton_matrix_parity(dse, oracle, inputs, name):
         assert plan.status() == dse.DSE_OK
     Jo, Fo = oracle.newton_matrix(p, c)
     A, AF = oracle.newton_matrix_magnitudes(p, c)
-    ok, rel, nbad, worst = entries_ok(J, Jo, A, column_index(J.shape[1], p["n_cheb"]))
+    ok, rel, nbad, worst = entries_ok(J, Jo, A, column_index(p))
     if not ok or rel > 1e-11:
         dump("matrix_" + name, J=J, Jo=Jo, A=A, F=F, Fo=Fo, AF=AF)
     assert ok, (name, rel, nbad, worst)
@@ -96,7 +102,7 @@ def test_full_size_matrix_parity(dse, oracle, inputs):
         J, F = to_host(J), to_host(F)
     Jo, Fo = oracle.newton_matrix(p, c)
     A, AF = oracle.newton_matrix_magnitudes(p, c)
-    ok, rel, nbad, worst = entries_ok(J, Jo, A, column_index(J.shape[1], p["n_cheb"]))
+    ok, rel, nbad, worst = entries_ok(J, Jo, A, column_index(p))
     if not ok or rel > 1e-11:
         dump("matrix_full", J=J, Jo=Jo, A=A, F=F, Fo=Fo, AF=AF)
     assert ok, (rel, nbad, worst)
@@ -104,7 +110,7 @@ def test_full_size_matrix_parity(dse, oracle, inputs):
     assert entries_ok(F, Fo, AF)[0]
 
 
-@pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64", "n100"])
+@pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64", "n100", "orders_11_7", "orders_64_24"])
 def test_newton_step_parity(dse, oracle, inputs, name):
     # n = 2N <= 160: FP32 Gauss-Jordan inverse + FP64 refinement; larger: FP64 LU
     p = inputs.workload_problem(name) if name in inputs.WORKLOADS else inputs.problem(**CASES[name])
@@ -129,7 +135,7 @@ def test_newton_step_parity(dse, oracle, inputs, name):
     assert abs(sg[1] / so[1] - 1) < 1e-10
     assert abs(sg[2] / so[2] - 1) < 1e-7
     # the FP32-inverse + FP64-refinement solve converged (no FP64 LU fallback)
-    if 2 * p["n_cheb"] <= 160:
+    if n_unknowns(p) <= 160:
         assert 1 <= sg[3] <= 12, sg
     else:
         assert sg[3] == -1
@@ -150,6 +156,22 @@ def test_solve_parity(dse, oracle, inputs):
     assert abs(it - (ito + 1)) <= 1
     lG, lZ = oracle.dressing(p, co, x)
     # converged dressing functions agree to 1e-8 (the accuracy target of a solve)
+    assert np.max(np.abs(gG - lG)) < 1e-8 and np.max(np.abs(gZ - lZ)) < 1e-8
+
+
+def test_solve_parity_separate_orders(dse, oracle, inputs):
+    p = inputs.problem(24, 64, 32, n_cheb_G=16)
+    c0 = inputs.starting_guess(p, seed=0)
+    co, ito, _ = oracle.solve(p, c0, tol=1e-10)
+    with dse.Plan(p) as plan:
+        ct = to_dev(c0)
+        it, st = plan.solve(ct, tol=1e-10, max_iter=30)
+        x = np.exp(np.linspace(math.log(1e-6), math.log(1e6), 97))
+        gG, gZ = plan.dressing(ct, to_dev(x))
+        gG, gZ = to_host(gG), to_host(gZ)
+    assert st[1] < 1e-10
+    assert abs(it - (ito + 1)) <= 1
+    lG, lZ = oracle.dressing(p, co, x)
     assert np.max(np.abs(gG - lG)) < 1e-8 and np.max(np.abs(gZ - lZ)) < 1e-8
 
 

@@ -10,7 +10,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from gpu_util import entries_ok, to_dev, to_host
+from gpu_util import entries_ok, n_unknowns, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def test_static_residual_matches_plan_residual(dse, oracle, inputs, name):
             c = inputs.starting_guess(p, seed=seed)
             ct = to_dev(c)
             Fp = to_host(plan.residual(ct))
-            Fs = torch.full((2 * p["n_cheb"],), float("nan"), dtype=torch.float64, device="cuda")
+            Fs = torch.full((n_unknowns(p),), float("nan"), dtype=torch.float64, device="cuda")
             assert static_residual(dse, p, ct, Fs) == dse.DSE_OK
             Fs = to_host(Fs)
             ok, rel, nbad, worst = entries_ok(Fs, Fp, AF)
