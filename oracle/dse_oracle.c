@@ -58,7 +58,8 @@ static int check_problem(const dse_ref_problem* p) {
     if (!(p->eps2 > 0.0) || !(p->lambda2 > p->eps2)) return DSE_REF_ERR_ARG;
     if (!(p->x_Z > 0.0) || !(p->x_G >= 0.0)) return DSE_REF_ERR_ARG;
     if (!isfinite(p->g2nc) || !isfinite(p->kappa) || !isfinite(p->delta)) return DSE_REF_ERR_ARG;
-    if (p->radial_mode != 0 || p->precision != 0) return DSE_REF_ERR_UNSUPPORTED;
+    if ((p->radial_mode != 0 && p->radial_mode != 1) || p->precision != 0) return DSE_REF_ERR_UNSUPPORTED;
+    if (p->angular_mode != 0 && p->angular_mode != 1) return DSE_REF_ERR_UNSUPPORTED;
     if (p->extrap_mode != 0 && p->extrap_mode != 1) return DSE_REF_ERR_UNSUPPORTED;
     return DSE_REF_OK;
 }
@@ -115,29 +116,91 @@ int dse_ref_gauss_legendre(int n, double* x, double* w) {
     return DSE_REF_OK;
 }
 
-int dse_ref_quadrature(const dse_ref_problem* p, double* y, double* W, double* theta, double* wt) {
+/* Gauss-Legendre in t = ln y over [lo, hi] (ln y bounds), n nodes; dy = y dt.
+ * A zero-width interval gives zero weights. */
+static void log_gl(const double* tx, const double* tw, int n, double lo, double hi, double* y, double* W) {
+    double c = 0.5 * (lo + hi), h = 0.5 * (hi - lo);
+    for (int i = 0; i < n; ++i) {
+        double t = c + h * tx[i];
+        double yy = exp(t);
+        y[i] = yy;
+        W[i] = h * tw[i] * yy;
+    }
+}
+
+/* Radial rule at external momentum x (Sec. 2 radial integral, Sec. 3 interval split):
+ *  radial_mode 0: one Gauss-Legendre rule in ln y over [eps2, lambda2] (n_radial nodes);
+ *  radial_mode 1: the paper's split int_0^lambda2 = int_0^eps2 + int_eps2^x + int_x^lambda2
+ *    with n_radial Gauss-Legendre nodes in ln y per piece (3 n_radial nodes); the
+ *    piece [0, eps2] is taken over [1e-6 eps2, eps2] (the paper gives no mapping for
+ *    it; the dropped [0, 1e-6 eps2] is O(1e-12 eps2^2) for the ghost and O(1e-6 eps2)
+ *    for the gluon integrand relative to the first piece), x clamped into
+ *    [eps2, lambda2]. */
+int dse_ref_radial_rule(const dse_ref_problem* p, double x, double* y, double* W) {
     int st = check_problem(p);
     if (st) return st;
+    if (!y || !W || !(x >= 0.0)) return DSE_REF_ERR_ARG;
     consts k = make_consts(p);
-    int nr = p->n_radial, na = p->n_angular;
-    double* tx = (double*)malloc(sizeof(double) * (size_t)(nr > na ? nr : na));
-    double* tw = (double*)malloc(sizeof(double) * (size_t)(nr > na ? nr : na));
+    int nr = p->n_radial;
+    double* tx = (double*)malloc(sizeof(double) * (size_t)nr);
+    double* tw = (double*)malloc(sizeof(double) * (size_t)nr);
     if (!tx || !tw) { free(tx); free(tw); return DSE_REF_ERR_ARG; }
-    /* radial: Gauss-Legendre in t = ln y over [ln eps2, ln lambda2]; dy = y dt */
     dse_ref_gauss_legendre(nr, tx, tw);
-    for (int i = 0; i < nr; ++i) {
-        double t = k.L0 + k.L1 * tx[i];
-        double yy = exp(t);
-        if (y) y[i] = yy;
-        if (W) W[i] = k.L1 * tw[i] * yy;
+    if (p->radial_mode == 0) {
+        log_gl(tx, tw, nr, k.ln_eps2, k.ln_lam2, y, W);
+    } else {
+        double xs = x < p->eps2 ? p->eps2 : (x > p->lambda2 ? p->lambda2 : x);
+        double lx = log(xs);
+        log_gl(tx, tw, nr, k.ln_eps2 + log(1e-6), k.ln_eps2, y, W);
+        log_gl(tx, tw, nr, k.ln_eps2, lx, y + nr, W + nr);
+        log_gl(tx, tw, nr, lx, k.ln_lam2, y + 2 * nr, W + 2 * nr);
     }
-    /* angular: Gauss-Legendre in theta over [0, pi] */
+    free(tx); free(tw);
+    return DSE_REF_OK;
+}
+
+/* Nodes per external momentum of the radial rule. */
+static int radial_count(const dse_ref_problem* p) { return p->radial_mode == 1 ? 3 * p->n_radial : p->n_radial; }
+
+/* Angular rule with int_0^pi dtheta g(theta) ~ sum_l w_l g(theta_l):
+ *  angular_mode 0: Gauss-Legendre in theta over [0, pi];
+ *  angular_mode 1: the paper's tanh-sinh rule in xi = cos theta (Sec. 2): the
+ *    trapezoidal rule in t for xi = tanh(u), u = (pi/2) sinh t, with n_angular
+ *    points t_l = t_max - (l + 1/2) h, h = 2 t_max / n_angular, t_max = 4.  Then
+ *    theta = arccos(xi) = 2 atan(e^{-u}) and dtheta = (pi/2) cosh t / cosh u dt. */
+static void angular_rule(const dse_ref_problem* p, double* theta, double* wt) {
+    int na = p->n_angular;
+    if (p->angular_mode == 1) {
+        const double tmax = 4.0;
+        double h = 2.0 * tmax / na;
+        for (int l = 0; l < na; ++l) {
+            double t = tmax - (l + 0.5) * h;
+            double u = 0.5 * PI_D * sinh(t);
+            if (theta) theta[l] = 2.0 * atan(exp(-u));
+            if (wt) wt[l] = h * 0.5 * PI_D * cosh(t) / cosh(u);
+        }
+        return;
+    }
+    double* tx = (double*)malloc(sizeof(double) * (size_t)na);
+    double* tw = (double*)malloc(sizeof(double) * (size_t)na);
+    if (!tx || !tw) { free(tx); free(tw); return; }
     dse_ref_gauss_legendre(na, tx, tw);
     for (int i = 0; i < na; ++i) {
         if (theta) theta[i] = 0.5 * PI_D * (1.0 + tx[i]);
         if (wt) wt[i] = 0.5 * PI_D * tw[i];
     }
     free(tx); free(tw);
+}
+
+int dse_ref_quadrature(const dse_ref_problem* p, double* y, double* W, double* theta, double* wt) {
+    int st = check_problem(p);
+    if (st) return st;
+    if (y && W) {
+        /* radial_mode 1: the rule of x = lambda2 (dse_ref_radial_rule for other x) */
+        st = dse_ref_radial_rule(p, p->lambda2, y, W);
+        if (st) return st;
+    }
+    angular_rule(p, theta, wt);
     return DSE_REF_OK;
 }
 
@@ -308,6 +371,7 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
     int want_d = (d_PiG != NULL) || (d_PiZ != NULL);
     int gluon = x > 0.0;
 
+    nr = radial_count(p);
     double* y = (double*)malloc(sizeof(double) * nr);
     double* W = (double*)malloc(sizeof(double) * nr);
     double* th = (double*)malloc(sizeof(double) * na);
@@ -319,7 +383,8 @@ static int self_energy_impl(const dse_ref_problem* p, const double* c, double x,
         free(y); free(W); free(th); free(wt); free(phiy); free(phiz); free(acc);
         return DSE_REF_ERR_ARG;
     }
-    dse_ref_quadrature(p, y, W, th, wt);
+    dse_ref_radial_rule(p, x, y, W);
+    angular_rule(p, th, wt);
     nsum* sG = &acc[0];
     nsum* sZ = &acc[1];
     nsum* gZa = &acc[2];                 /* d Pi_Z / d a_j (without prefactor), j < NZ */
@@ -418,7 +483,7 @@ int dse_ref_self_energy(const dse_ref_problem* p, const double* c, double x,
  * and d ln Z(z)/d omega for the ghost term (y <= lambda2 carries no omega). */
 static int self_energy_dg2(const dse_ref_problem* p, const double* c, double x, double* dPiG, double* dPiZ) {
     consts k = make_consts(p);
-    int N = p->n_cheb, nr = p->n_radial, na = p->n_angular;
+    int N = p->n_cheb, nr = radial_count(p), na = p->n_angular;
     int gluon = x > 0.0;
     double* y = (double*)malloc(sizeof(double) * nr);
     double* W = (double*)malloc(sizeof(double) * nr);
@@ -426,7 +491,8 @@ static int self_energy_dg2(const dse_ref_problem* p, const double* c, double x, 
     double* wt = (double*)malloc(sizeof(double) * na);
     if (!y || !W || !th || !wt) { free(y); free(W); free(th); free(wt); return DSE_REF_ERR_ARG; }
     (void)N;
-    dse_ref_quadrature(p, y, W, th, wt);
+    dse_ref_radial_rule(p, x, y, W);
+    angular_rule(p, th, wt);
     nsum sG = {0, 0}, sZ = {0, 0}, wG = {0, 0}, wZ = {0, 0};
     for (int kk = 0; kk < nr; ++kk) {
         double lGy, lZy;

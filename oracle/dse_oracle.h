@@ -52,20 +52,30 @@ typedef struct {
     double zinv_Z;    /* Z(x_Z)^{-1} */
     double kappa;     /* IR exponent */
     double delta;     /* ghost anomalous dimension; gamma = -1 - 2 delta */
-    int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2] */
+    int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2];
+                         1: split at x with an infrared piece (3 n_radial nodes) */
     int extrap_mode;  /* 0: IR power laws / UV logarithms; 1: constant continuation */
     int precision;    /* 0: FP64 */
     int n_cheb_G;     /* N_G (0: equal to n_cheb) */
+    int angular_mode; /* 0: Gauss-Legendre in theta; 1: tanh-sinh in xi = cos theta */
 } dse_ref_problem;
 
 /* n-point Gauss-Legendre rule on [-1,1], nodes ascending (Newton iteration on
  * the three-term Legendre recurrence). */
 int dse_ref_gauss_legendre(int n, double* x, double* w);
 
-/* Radial nodes y_k and weights W_k with  int_{eps2}^{lambda2} dy f(y) ~ sum_k W_k f(y_k)
+/* Radial nodes y_k and weights W_k with  int dy f(y) ~ sum_k W_k f(y_k)
  * (Gauss-Legendre in t = ln y, Jacobian y included in W_k), and angular nodes
- * theta_l, weights w_l with int_0^pi dtheta g ~ sum_l w_l g(theta_l). */
+ * theta_l, weights w_l with int_0^pi dtheta g ~ sum_l w_l g(theta_l) (Gauss-Legendre
+ * in theta, or the paper's tanh-sinh rule in xi = cos theta for angular_mode 1).
+ * radial_mode 0: [eps2, lambda2], n_radial nodes; radial_mode 1: the rule of
+ * dse_ref_radial_rule at x = lambda2 (3 n_radial nodes). */
 int dse_ref_quadrature(const dse_ref_problem* p, double* y, double* W, double* theta, double* wt);
+
+/* The radial rule used for external momentum x: radial_mode 0 as above; radial_mode
+ * 1 the paper's split [0, eps2] + [eps2, x] + [x, lambda2] (Sec. 3), n_radial nodes
+ * in ln y per piece, the first piece over [1e-6 eps2, eps2].  3 n_radial nodes. */
+int dse_ref_radial_rule(const dse_ref_problem* p, double x, double* y, double* W);
 
 /* Collocation points x_i, i < N_Z: the mapped roots of T_{N_Z}, ascending (Sec. 3);
  * the gluon rows of the residual.  _ghost: the N_G roots of T_{N_G} (ghost rows). */

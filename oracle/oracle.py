@@ -45,7 +45,7 @@ class Problem(ctypes.Structure):
         ("x_Z", ctypes.c_double), ("zinv_Z", ctypes.c_double),
         ("kappa", ctypes.c_double), ("delta", ctypes.c_double),
         ("radial_mode", ctypes.c_int), ("extrap_mode", ctypes.c_int), ("precision", ctypes.c_int),
-        ("n_cheb_G", ctypes.c_int),
+        ("n_cheb_G", ctypes.c_int), ("angular_mode", ctypes.c_int),
     ]
 
 
@@ -61,6 +61,7 @@ def lib():
             sig = {
                 "dse_ref_gauss_legendre": [ctypes.c_int, _D, _D],
                 "dse_ref_quadrature": [P, _D, _D, _D, _D],
+                "dse_ref_radial_rule": [P, ctypes.c_double, _D, _D],
                 "dse_ref_collocation": [P, _D],
                 "dse_ref_collocation_ghost": [P, _D],
                 "dse_ref_basis": [P, ctypes.c_double, _D],
@@ -129,9 +130,23 @@ def gauss_legendre(n: int):
     return x, w
 
 
+def radial_count(params: dict) -> int:
+    return (3 if params.get("radial_mode", 0) == 1 else 1) * int(params["n_radial"])
+
+
+def radial_rule(params: dict, x: float):
+    """Radial nodes and weights used for external momentum x."""
+    p = make_problem(params)
+    n = radial_count(params)
+    y = np.empty(n); W = np.empty(n)
+    _chk(lib().dse_ref_radial_rule(ctypes.byref(p), float(x), _ptr(y), _ptr(W)), "radial_rule")
+    return y, W
+
+
 def quadrature(params: dict):
     p = make_problem(params)
-    y = np.empty(p.n_radial); W = np.empty(p.n_radial)
+    n = radial_count(params)
+    y = np.empty(n); W = np.empty(n)
     th = np.empty(p.n_angular); wt = np.empty(p.n_angular)
     _chk(lib().dse_ref_quadrature(ctypes.byref(p), _ptr(y), _ptr(W), _ptr(th), _ptr(wt)), "quadrature")
     return y, W, th, wt

@@ -33,14 +33,16 @@ WORKLOADS = {
 def problem(n_cheb: int, n_radial: int, n_angular: int, eps2: float = 1e-6, lambda2: float = 1e6,
             g2nc: float = G2NC, x_G: float = 0.0, ginv_G: float = 0.0, x_Z: float | None = None,
             zinv_Z: float = 1.0 / 0.256, kappa: float = KAPPA, delta: float = DELTA,
-            radial_mode: int = 0, extrap_mode: int = 0, precision: int = 0, n_cheb_G: int = 0) -> dict:
+            radial_mode: int = 0, extrap_mode: int = 0, precision: int = 0, n_cheb_G: int = 0,
+            angular_mode: int = 0) -> dict:
     """Problem parameters as a plain dict (field names of dse_problem).  n_cheb is
     the order N_Z of ln Z, n_cheb_G the order N_G of ln G (0: N_G = N_Z)."""
     return dict(n_cheb=int(n_cheb), n_radial=int(n_radial), n_angular=int(n_angular),
                 eps2=float(eps2), lambda2=float(lambda2), g2nc=float(g2nc), x_G=float(x_G),
                 ginv_G=float(ginv_G), x_Z=float(lambda2 if x_Z is None else x_Z), zinv_Z=float(zinv_Z),
                 kappa=float(kappa), delta=float(delta), radial_mode=int(radial_mode),
-                extrap_mode=int(extrap_mode), precision=int(precision), n_cheb_G=int(n_cheb_G))
+                extrap_mode=int(extrap_mode), precision=int(precision), n_cheb_G=int(n_cheb_G),
+                angular_mode=int(angular_mode))
 
 
 def workload_problem(name: str, **over) -> dict:
