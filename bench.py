@@ -235,6 +235,9 @@ def run_gb300(args):
     sweep = None
     if rank == 0 and not args.no_batch:
         sweep = measure_batch(dse, args)
+    paper = None
+    if rank == 0 and not args.no_paper:
+        paper = measure_paper_algorithm(dse, args)
 
     # end to end through the public API with host buffers (pinned), copies timed
     c0_host = torch.from_numpy(c0).pin_memory()
@@ -292,6 +295,8 @@ def run_gb300(args):
             line["differentiation"] = diff
         if sweep is not None:
             line["batched_sweep"] = sweep
+        if paper is not None:
+            line["paper_algorithm"] = paper
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -469,6 +474,48 @@ def measure_batch(dse, args):
             "graph_launches_per_sweep": int(max(its))}
 
 
+def measure_paper_algorithm(dse, args):
+    """The paper's own discretisation and Jacobian at the benchmark's size: N = 64,
+    the radial split [0, eps2] + [eps2, x] + [x, lambda2] with 85 nodes per piece
+    (255 per external momentum) and 128 tanh-sinh angular nodes.  Times the
+    paper's central-difference Newton matrix (2n = 256 perturbed residuals, one
+    batched launch) against the analytic one, and a full solve."""
+    import torch
+    p = inputs.problem(64, 85, 128, radial_mode=1, angular_mode=1)
+    c0 = torch.from_numpy(inputs.starting_guess(p, seed=0)).cuda()
+    stream = torch.cuda.current_stream()
+    n = 128
+    out = {"workload": "N=64, radial split 3x85 nodes, tanh-sinh 128 nodes"}
+    with dse.Plan(p) as plan:
+        J = torch.empty(n, n, dtype=torch.float64, device="cuda")
+        F = torch.empty(n, dtype=torch.float64, device="cuda")
+        Jf = torch.empty(n, n, dtype=torch.float64, device="cuda")
+        plan.newton_matrix(c0, J, F)
+        plan.newton_matrix_fd(c0, 1e-5, J=Jf)
+        reps = max(1, min(args.steps, 3))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        e[0].record(stream)
+        for _ in range(reps):
+            plan.newton_matrix(c0, J, F)
+        e[1].record(stream)
+        e[2].record(stream)
+        for _ in range(reps):
+            plan.newton_matrix_fd(c0, 1e-5, J=Jf)
+        e[3].record(stream)
+        coef = c0.clone()
+        e[4].record(stream)
+        it, st = plan.solve(coef, tol=TOL, max_iter=50)
+        e[5].record(stream)
+        e[5].synchronize()
+        an = e[0].elapsed_time(e[1]) / reps
+        fd = e[2].elapsed_time(e[3]) / reps
+        rowmax = J.abs().max(dim=1, keepdim=True).values
+        out.update({"newton_matrix_ms": an, "fd_newton_matrix_ms": fd, "fd_over_analytic": fd / an,
+                    "max_abs_fd_minus_analytic_over_rowmax": float(((Jf - J).abs() / rowmax).max()),
+                    "solve_ms": e[4].elapsed_time(e[5]), "newton_steps": it, "scaled_residual": st[1]})
+    return out
+
+
 def cpu_baseline_sample(p, c0, budget_s: float = 12.0):
     """The oracle as it stands, on this host's cores: Newton matrices of the
     same workload until about budget_s seconds of CPU work."""
@@ -536,6 +583,7 @@ def main():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-n128", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -17,9 +17,11 @@
  * and the self-energies of the ghost and gluon equations of Sec. 2 (bare
  * ghost-gluon vertex, three-gluon vertex model with a = b = 3 delta, kernels M and
  * Q including the +15/4 term, O(4) reduction with a sharp cutoff).  Every
- * integral is a radial Gauss-Legendre rule in ln y over [eps2, lambda2] times an
- * angular Gauss-Legendre rule in theta over [0, pi]; outside [eps2, lambda2] the
- * dressing functions follow the IR power laws and UV logarithms of Sec. 2.
+ * integral is a radial Gauss-Legendre rule in ln y over [eps2, lambda2] (or the
+ * paper's split of the radial range at x, radial_mode 1) times an angular rule in
+ * theta over [0, pi] (Gauss-Legendre, or the paper's tanh-sinh rule in cos theta,
+ * angular_mode 1); outside [eps2, lambda2] the dressing functions follow the IR
+ * power laws and UV logarithms of Sec. 2.
  *
  * Conventions for every entry point
  *  - Pointers prefixed d_ are CUDA device pointers (FP64, contiguous), owned by
@@ -61,8 +63,8 @@ extern "C" {
  * x_G = 0, ginv_G = 0 for the scaling solution, delta = -9/44, kappa ~ 0.595353). */
 typedef struct {
     int n_cheb;       /* N_Z Chebyshev coefficients of ln Z, 1..DSE_MAX_CHEB              */
-    int n_radial;     /* radial Gauss-Legendre nodes in ln y                             */
-    int n_angular;    /* angular Gauss-Legendre nodes in theta                           */
+    int n_radial;     /* radial Gauss-Legendre nodes in ln y (per piece in radial_mode 1) */
+    int n_angular;    /* angular nodes                                                   */
     double eps2;      /* IR matching point epsilon^2 (> 0)                               */
     double lambda2;   /* UV cutoff Lambda^2 (> eps2)                                     */
     double g2nc;      /* g^2 N_c; the equations carry K = g2nc/(2 pi)^3                  */
@@ -72,10 +74,16 @@ typedef struct {
     double zinv_Z;    /* Z(x_Z)^{-1}                                                     */
     double kappa;     /* IR exponent: Z ~ x^{2 kappa}, G ~ x^{-kappa} below eps2         */
     double delta;     /* ghost anomalous dimension; gamma = -1 - 2 delta                 */
-    int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2]         */
+    int radial_mode;  /* 0: one Gauss-Legendre rule in ln y over [eps2, lambda2];        *
+                       * 1: the paper's split [0,eps2] + [eps2,x] + [x,lambda2] (Sec. 3), *
+                       *    n_radial nodes in ln y per piece, the first piece over        *
+                       *    [1e-6 eps2, eps2]; every external momentum has its own rule   */
     int extrap_mode;  /* 0: IR power laws and UV logarithms; 1: constant continuation    */
     int precision;    /* 0: FP64 throughout; 1: mixed (FP32 integrands for J, FP64 F)   */
     int n_cheb_G;     /* N_G Chebyshev coefficients of ln G, 0..DSE_MAX_CHEB (0: N_Z)    */
+    int angular_mode; /* 0: Gauss-Legendre in theta; 1: the paper's tanh-sinh rule in    *
+                       *    xi = cos theta (Sec. 2): xi = tanh((pi/2) sinh t), trapezoidal *
+                       *    in t with n_angular points over |t| <= 4                       */
 } dse_problem;
 
 typedef struct dse_plan dse_plan;
@@ -97,7 +105,8 @@ int dse_plan_set_stream(dse_plan* plan, void* cuda_stream);
  * (DSE_OK, DSE_ERR_NONFINITE or DSE_ERR_SINGULAR); the flag is cleared. */
 int dse_plan_status(dse_plan* plan);
 
-/* Copy the plan's rules: d_y, d_W (n_radial; int_{eps2}^{lambda2} dy f ~ sum W_k f(y_k)),
+/* Copy the plan's rules: d_y, d_W (n_radial; int_{eps2}^{lambda2} dy f ~ sum W_k f(y_k);
+ * radial_mode 1: the 3 n_radial nodes of the x_Z row),
  * d_theta, d_wt (n_angular; int_0^pi dtheta g ~ sum w_l g(theta_l)), d_x
  * (the collocation points: N_Z ascending points shared by both equations when
  * N_Z = N_G, otherwise the N_Z gluon points followed by the N_G ghost points).
@@ -118,6 +127,16 @@ int dse_residual(dse_plan* plan, const double* d_coeffs, double* d_F);
  * layout of Sec. 3) with every entry dF_i/dc_j an analytic radial x angular
  * quadrature, and the residual F (d_F may be NULL). */
 int dse_newton_matrix(dse_plan* plan, const double* d_coeffs, double* d_J, double* d_F);
+
+/* The paper's Newton matrix (Sec. 4.2, central differences of the residual):
+ *   J[:, j] = (F(c + h_j e_j) - F(c - h_j e_j)) / ((c_j + h_j) - (c_j - h_j)),
+ *   h_j = rel_step * max(|c_j|, 1e-3)   (the paper uses about 1e-5 a_j),
+ * with the 2n perturbed residuals evaluated together as a batch (one persistent
+ * quadrature launch).  For comparisons with the analytic dse_newton_matrix, which
+ * the Newton steps use.  d_F (nullable) receives F(c).  The first call allocates
+ * the batch (2n copies of the plan's workspace) and the plan keeps it until
+ * dse_plan_destroy or dse_plan_set_couplings.  Queued without waiting. */
+int dse_newton_matrix_fd(dse_plan* plan, const double* d_coeffs, double rel_step, double* d_J, double* d_F);
 
 /* One Newton-Raphson step (Sec. 3): J Delta = F solved on the device, then
  * c <- c - rho Delta in place.  For n <= 160 the rows of J are scaled by powers
@@ -208,7 +227,8 @@ typedef struct dse_batch dse_batch;
 
 /* Create the batch (workspace for every problem, rules and collocation points
  * set up on the device; waits for the set-up).  DSE_ERR_UNSUPPORTED for
- * N_Z + N_G > 128, precision != 0 or an unsupported mode. */
+ * N_Z + N_G > 128, precision != 0 or an unsupported mode.  Both quadrature
+ * variants (radial_mode, angular_mode) are supported. */
 int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_stream, dse_batch** out);
 int dse_batch_destroy(dse_batch* batch);
 int dse_batch_set_stream(dse_batch* batch, void* cuda_stream);
@@ -221,6 +241,10 @@ int dse_batch_offsets(const dse_batch* batch, long long* h_offsets, long long* h
  * item at d_coeffs and keep the fastest.  h_units (nullable): the choice;
  * h_ms (nullable, 5 doubles): the time of each candidate.  Waits. */
 int dse_batch_tune(dse_batch* batch, const double* d_coeffs, int* h_units, double* h_ms);
+
+/* Residuals of every problem at d_coeffs into the concatenated d_F (coefficient
+ * offsets).  Queued without waiting. */
+int dse_batch_residual(dse_batch* batch, const double* d_coeffs, double* d_F);
 
 /* Newton matrices and residuals of every problem at d_coeffs into the
  * concatenated d_J (matrix offsets) and d_F (coefficient offsets; nullable).

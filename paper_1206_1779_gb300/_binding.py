@@ -24,7 +24,8 @@ EXPORTS = ["dse_plan_create", "dse_plan_destroy", "dse_plan_set_stream", "dse_pl
            "dse_plan_profile", "dse_plan_counters", "dse_residual_static", "dse_status_string",
            "dse_plan_set_couplings", "dse_vjp", "dse_param_derivatives", "dse_adjoint_solve", "dse_dressing_vjp",
            "dse_batch_create", "dse_batch_destroy", "dse_batch_set_stream", "dse_batch_offsets", "dse_batch_tune",
-           "dse_batch_newton_matrix", "dse_batch_solve", "dse_batch_counters"]
+           "dse_batch_newton_matrix", "dse_batch_solve", "dse_batch_counters", "dse_newton_matrix_fd",
+           "dse_batch_residual"]
 
 
 class DseError(RuntimeError):
@@ -41,14 +42,14 @@ class Problem(ctypes.Structure):
         ("x_Z", ctypes.c_double), ("zinv_Z", ctypes.c_double),
         ("kappa", ctypes.c_double), ("delta", ctypes.c_double),
         ("radial_mode", ctypes.c_int), ("extrap_mode", ctypes.c_int), ("precision", ctypes.c_int),
-        ("n_cheb_G", ctypes.c_int),
+        ("n_cheb_G", ctypes.c_int), ("angular_mode", ctypes.c_int),
     ]
 
     @classmethod
     def from_params(cls, params: dict) -> "Problem":
         p = cls()
         for name, _ in cls._fields_:
-            setattr(p, name, params.get(name, 0) if name == "n_cheb_G" else params[name])
+            setattr(p, name, params.get(name, 0) if name in ("n_cheb_G", "angular_mode") else params[name])
         return p
 
 
@@ -102,6 +103,8 @@ def load(build_if_missing: bool = False):
         "dse_batch_offsets": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
         "dse_batch_tune": [_VP, _VP, ctypes.POINTER(ctypes.c_int), _D],
         "dse_batch_newton_matrix": [_VP, _VP, _VP, _VP],
+        "dse_batch_residual": [_VP, _VP, _VP],
+        "dse_newton_matrix_fd": [_VP, _VP, ctypes.c_double, _VP, _VP],
         "dse_batch_solve": [_VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
         "dse_batch_counters": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
@@ -190,7 +193,8 @@ class Plan:
         return torch.empty(*shape, dtype=torch.float64, device=self.device)
 
     def quadrature(self):
-        y, W, th, wt, x = (self._new(self.n_radial), self._new(self.n_radial), self._new(self.n_angular),
+        nrad = self.n_radial * (3 if self.params.get("radial_mode", 0) == 1 else 1)
+        y, W, th, wt, x = (self._new(nrad), self._new(nrad), self._new(self.n_angular),
                            self._new(self.n_angular), self._new(self.n_collocation))
         self._sync_stream()
         _check(self._L.dse_quadrature(self._h, *[ctypes.c_void_p(t.data_ptr()) for t in (y, W, th, wt, x)]),
@@ -220,6 +224,16 @@ class Plan:
         _check(self._L.dse_newton_matrix(self._h, _dev_ptr(coeffs, n, "coeffs"), _dev_ptr(J, n * n, "J"),
                                          _dev_ptr(F, n, "F")), "dse_newton_matrix")
         return J, F
+
+    def newton_matrix_fd(self, coeffs, rel_step: float = 1e-5, J=None, F=None):
+        """The paper's central-difference Newton matrix (batched perturbed residuals)."""
+        n = self.n
+        J = J if J is not None else self._new(n, n)
+        self._sync_stream()
+        _check(self._L.dse_newton_matrix_fd(self._h, _dev_ptr(coeffs, n, "coeffs"), float(rel_step),
+                                            _dev_ptr(J, n * n, "J"), _dev_ptr(F, n, "F") if F is not None else None),
+               "dse_newton_matrix_fd")
+        return J
 
     def newton_step(self, coeffs, rho: float = 1.0):
         """In-place Newton step; returns (||F||inf, scaled ||F||inf, ||Delta||inf) on entry
@@ -371,6 +385,15 @@ class Batch:
         _check(self._L.dse_batch_tune(self._h, _dev_ptr(coeffs, self.n_total, "coeffs"), ctypes.byref(u),
                                       ctypes.cast(ms, _D)), "dse_batch_tune")
         return u.value, list(ms)
+
+    def residual(self, coeffs):
+        """Concatenated residuals."""
+        import torch
+        F = torch.empty(self.n_total, dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        _check(self._L.dse_batch_residual(self._h, _dev_ptr(coeffs, self.n_total, "coeffs"),
+                                          _dev_ptr(F, self.n_total, "F")), "dse_batch_residual")
+        return F
 
     def newton_matrix(self, coeffs):
         """(J, F): concatenated Newton matrices (flat) and residuals."""

@@ -61,14 +61,14 @@ __global__ void __launch_bounds__(kParamThreads) k_param_rows(const Consts c, co
         for (int t = tid; t < total; t += kParamThreads) {
             const int k = t / c.na;
             const int l = t - k * c.na;
-            const Rad rd = rad[k];
+            const Rad rd = rad[rad_offset(c, r) + k];
             const Ang an = ang[l];
             const double d0 = row.sx - rd.sy;
             const double d = d0 * d0;
             const double b = 2.0 * row.sx * rd.sy;
             const double z = fma(2.0 * b, an.sig, d);
             if (!(z > c.lam2)) continue;
-            const YTab yt = ytab[k];
+            const YTab yt = ytab[rad_offset(c, r) + k];
             const double lu = log(z) - c.ln_lam2;
             const double den = 1.0 / fma(c.omega, lu, 1.0);
             const double L = log1p(c.omega * lu);
@@ -353,6 +353,41 @@ __global__ void k_dressing_vjp_reduce(int n, int nsplit, const double* __restric
     else if (out_g2nc) *out_g2nc = s;
 }
 
+// Finite-difference Newton matrix (Sec. 4.2, the paper's Jacobian): the 2n
+// perturbed coefficient vectors c +- h_j e_j, h_j = rel max(|c_j|, 1e-3), stored
+// as vector v = 2 j (+) and 2 j + 1 (-), n entries each.
+__global__ void k_fd_perturb(int n, const double* __restrict__ coef, double rel, double* __restrict__ out) {
+    const size_t total = 2 * (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int v = (int)(e / n);
+        const int i = (int)(e - (size_t)v * n);
+        const int j = v >> 1;
+        double x = coef[i];
+        if (i == j) {
+            const double h = rel * fmax(fabs(x), 1e-3);
+            x = (v & 1) ? x - h : x + h;
+        }
+        out[e] = x;
+    }
+}
+
+// J[i][j] = (F(c + h e_j)_i - F(c - h e_j)_i) / ((c_j + h) - (c_j - h)), the
+// denominator taken from the perturbed values actually used.
+__global__ void k_fd_columns(int n, const double* __restrict__ pert, const double* __restrict__ Fall,
+                             double* __restrict__ J, int* __restrict__ status) {
+    const size_t total = (size_t)n * n;
+    bool bad = false;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n);
+        const int j = (int)(e - (size_t)i * n);
+        const size_t vp = 2 * (size_t)j * n, vm = vp + n;
+        const double v = (Fall[vp + i] - Fall[vm + i]) / (pert[vp + j] - pert[vm + j]);
+        J[e] = v;
+        bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(status, kStatusNonfinite);
+}
+
 // Row prefactors K/(3x) after a change of g^2 Nc.
 __global__ void k_row_prefactors(const Consts c, Row* __restrict__ rows, int Rt) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,6 +449,16 @@ cudaError_t launch_dressing_vjp(const Consts& c, int n, const double* x, const d
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_dressing_vjp_reduce<<<(c.n + 1 + 127) / 128, 128, 0, s>>>(c.n, nsplit, part, out, out_g2nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fd_perturb(int n, const double* coef, double rel, double* out, cudaStream_t s) {
+    k_fd_perturb<<<blocks_for(2LL * n * n, 256), 256, 0, s>>>(n, coef, rel, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fd_columns(int n, const double* pert, const double* Fall, double* J, int* status, cudaStream_t s) {
+    k_fd_columns<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(n, pert, Fall, J, status);
     return cudaGetLastError();
 }
 

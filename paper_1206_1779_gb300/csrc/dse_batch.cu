@@ -58,7 +58,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? DSE_OK : DSE_ERR_CUDA
 
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int check_batch_problem(const dse_problem* p) {
+int check_batch_problem(const dse_problem* p, bool newton) {
     if (p->n_cheb < 1 || p->n_cheb > DSE_MAX_CHEB || p->n_cheb_G < 0 || p->n_cheb_G > DSE_MAX_CHEB) return DSE_ERR_ARG;
     if (p->n_radial < 1 || p->n_radial > DSE_MAX_NODES || p->n_angular < 1 || p->n_angular > DSE_MAX_NODES)
         return DSE_ERR_ARG;
@@ -67,10 +67,11 @@ int check_batch_problem(const dse_problem* p) {
     if (!isfinite(p->g2nc) || !isfinite(p->kappa) || !isfinite(p->delta) || !isfinite(p->ginv_G) ||
         !isfinite(p->zinv_Z))
         return DSE_ERR_ARG;
-    if (p->radial_mode != 0 || p->precision != 0) return DSE_ERR_UNSUPPORTED;
+    if ((p->radial_mode != 0 && p->radial_mode != 1) || p->precision != 0) return DSE_ERR_UNSUPPORTED;
+    if (p->angular_mode != 0 && p->angular_mode != 1) return DSE_ERR_UNSUPPORTED;
     if (p->extrap_mode != 0 && p->extrap_mode != 1) return DSE_ERR_UNSUPPORTED;
     const int ng = p->n_cheb_G > 0 ? p->n_cheb_G : p->n_cheb;
-    if (p->n_cheb + ng > 128) return DSE_ERR_UNSUPPORTED;  // the batched Newton step holds n <= 128
+    if (newton && p->n_cheb + ng > 128) return DSE_ERR_UNSUPPORTED;  // the batched Newton step holds n <= 128
     return DSE_OK;
 }
 
@@ -82,7 +83,11 @@ Consts batch_consts(const dse_problem* p) {
     c.n = c.NZ + c.NG;
     c.Rc = c.NZ == c.NG ? c.N : c.n;
     c.gofs = c.NZ == c.NG ? 0 : c.NZ;
-    c.nr = p->n_radial;
+    c.nrule = p->n_radial;
+    c.radmode = p->radial_mode;
+    c.angmode = p->angular_mode;
+    c.nr = p->radial_mode == 1 ? 3 * p->n_radial : p->n_radial;
+    c.pad_ = 0;
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;
     c.eps2 = p->eps2;
@@ -115,13 +120,14 @@ Slice slice_layout(const Consts& c, int Rt, int nch, int ks_cap) {
     Slice L;
     size_t off = 0;
     const int N = c.N, n = c.n, nr = c.nr, na = c.na, Rc = c.Rc;
-    L.rad = off; off = up256(off + sizeof(Rad) * (size_t)nr);
+    const size_t nrad = rad_entries(c);
+    L.rad = off; off = up256(off + sizeof(Rad) * nrad);
     L.ang = off; off = up256(off + sizeof(Ang) * (size_t)na);
     L.theta = off; off = up256(off + sizeof(double) * (size_t)na);
     L.rows = off; off = up256(off + sizeof(Row) * (size_t)Rt);
     L.xcol = off; off = up256(off + sizeof(double) * (size_t)Rc);
-    L.ytab = off; off = up256(off + sizeof(YTab) * (size_t)nr);
-    L.phiy = off; off = up256(off + sizeof(double) * (size_t)nr * N);
+    L.ytab = off; off = up256(off + sizeof(YTab) * nrad);
+    L.phiy = off; off = up256(off + sizeof(double) * nrad * N);
     L.xtab = off; off = up256(off + sizeof(XTab) * (size_t)Rc);
     L.phix = off; off = up256(off + sizeof(double) * (size_t)Rc * N);
     L.U = off; off = up256(off + sizeof(double) * (size_t)Rt * nr * nch * 3);
@@ -133,8 +139,9 @@ Slice slice_layout(const Consts& c, int Rt, int nch, int ks_cap) {
     L.As = off; off = up256(off + sizeof(float) * (size_t)n * n);
     L.ri = off; off = up256(off + sizeof(double2) * (size_t)n);
     L.stats = off; off = up256(off + 4 * sizeof(double) + sizeof(int));
-    const size_t gmax = nr > na ? nr : na;
-    L.gl = off; off = up256(off + sizeof(double) * (2 * (size_t)nr + 2 * (size_t)na + gmax + 2));
+    const size_t nrule = c.nrule;
+    const size_t gmax = nrule > (size_t)na ? nrule : (size_t)na;
+    L.gl = off; off = up256(off + sizeof(double) * (2 * nrule + 2 * (size_t)na + gmax + 2));
     L.total = off;
     return L;
 }
@@ -226,6 +233,17 @@ cudaError_t enqueue_matrix(dse_batch* B, const double* coef, double* J_base, dou
     return e;
 }
 
+// Residuals only (no derivative sums, no Newton matrix).
+cudaError_t enqueue_residual(dse_batch* B, const double* coef, double* F_base, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_tables_batched(B->d_P, B->nb, B->max_units, coef, s);
+    if (e == cudaSuccess)
+        e = launch_triple_batched(false, B->d_P, B->d_items, B->n_items, B->d_counter, coef, B->maxN, B->grid, s);
+    if (e == cudaSuccess) e = launch_rowreduce_batched(false, B->d_P, B->nb, B->max_rows, B->maxN, s);
+    if (e == cudaSuccess) e = launch_assemble_batched(false, B->d_P, B->nb, nullptr, F_base, s);
+    return e;
+}
+
 cudaError_t enqueue_step(dse_batch* B, double* coef, double tol, double rho_relax, int n_relax, cudaStream_t s) {
     cudaError_t e = enqueue_matrix(B, coef, nullptr, nullptr, s);
     if (e == cudaSuccess)
@@ -262,14 +280,15 @@ int capture_step(dse_batch* B, double* coef, double tol, double rho_relax, int n
 
 }  // namespace
 
-extern "C" {
-
-int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_stream, dse_batch** out) {
+// Batch of problems for which only residuals and Newton matrices will be asked
+// (newton = false lifts the n <= 128 limit of the batched Newton step).
+int batch_create_impl(const dse_problem* problems, int n_problems, void* cuda_stream, bool newton,
+                      dse_batch** out) {
     if (!out) return DSE_ERR_ARG;
     *out = nullptr;
     if (!problems || n_problems < 1 || n_problems > 65535) return DSE_ERR_ARG;
     for (int b = 0; b < n_problems; ++b) {
-        const int st = check_batch_problem(&problems[b]);
+        const int st = check_batch_problem(&problems[b], newton);
         if (st) return st;
     }
     dse_batch* B = new (std::nothrow) dse_batch();
@@ -313,7 +332,7 @@ int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_str
         B->maxN = std::max(B->maxN, c.N);
         B->max_n = std::max(B->max_n, c.n);
         B->max_rows = std::max(B->max_rows, c.Rc + 2);
-        B->max_units = std::max(B->max_units, c.nr + c.Rc);
+        B->max_units = std::max(B->max_units, (int)rad_entries(c) + c.Rc);
         items_cap += Rt * ks_cap;
         BatchProblem& P = B->h_P[b];
         memset(&P, 0, sizeof(P));
@@ -383,11 +402,11 @@ int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_str
         const Consts& c = P.t.c;
         double* gl = (double*)(s + S.gl);
         double* glr = gl;
-        double* gwr = glr + c.nr;
-        double* gla = gwr + c.nr;
+        double* gwr = glr + c.nrule;
+        double* gla = gwr + c.nrule;
         double* gwa = gla + c.na;
         double* inv = gwa + c.na;
-        e = launch_gauss_legendre(c.nr, inv, glr, gwr, B->stream);
+        e = launch_gauss_legendre(c.nrule, inv, glr, gwr, B->stream);
         if (e == cudaSuccess) e = launch_gauss_legendre(c.na, inv, gla, gwa, B->stream);
         if (e == cudaSuccess)
             e = launch_setup_rules(c, glr, gwr, gla, gwa, (Rad*)P.t.rad, (Ang*)P.t.ang, (double*)(s + S.theta), P.xcol,
@@ -405,7 +424,7 @@ int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_str
     int occ = triple_batched_blocks_per_sm(true, B->maxN);
     if (occ < 1) occ = 1;
     B->grid = nsm * occ;
-    if (prepare_newton_batched(B->max_n) != cudaSuccess) {
+    if (B->max_n <= 128 && prepare_newton_batched(B->max_n) != cudaSuccess) {
         free_batch(B);
         return DSE_ERR_CUDA;
     }
@@ -416,6 +435,12 @@ int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_str
     }
     *out = B;
     return DSE_OK;
+}
+
+extern "C" {
+
+int dse_batch_create(const dse_problem* problems, int n_problems, void* cuda_stream, dse_batch** out) {
+    return batch_create_impl(problems, n_problems, cuda_stream, true, out);
 }
 
 int dse_batch_destroy(dse_batch* batch) {
@@ -447,6 +472,16 @@ int dse_batch_newton_matrix(dse_batch* batch, const double* d_coeffs, double* d_
     k_batch_reset<<<(B->nb + 127) / 128, 128, 0, B->stream>>>(B->d_P, B->nb, B->d_nactive);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = enqueue_matrix(B, d_coeffs, d_J, d_F, B->stream);
+    B->launches += 5;
+    return cuda_status(e);
+}
+
+int dse_batch_residual(dse_batch* batch, const double* d_coeffs, double* d_F) {
+    if (!batch || !d_coeffs || !d_F) return DSE_ERR_ARG;
+    dse_batch* B = batch;
+    k_batch_reset<<<(B->nb + 127) / 128, 128, 0, B->stream>>>(B->d_P, B->nb, B->d_nactive);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = enqueue_residual(B, d_coeffs, d_F, B->stream);
     B->launches += 5;
     return cuda_status(e);
 }
@@ -506,6 +541,7 @@ int dse_batch_solve(dse_batch* batch, double* d_coeffs, double tol, int max_iter
     if (!batch || !d_coeffs || !(tol > 0.0) || max_iter < 1 || !isfinite(rho_relax) || n_relax < 0)
         return DSE_ERR_ARG;
     dse_batch* B = batch;
+    if (B->max_n > 128) return DSE_ERR_UNSUPPORTED;
     int st = capture_step(B, d_coeffs, tol, rho_relax, n_relax);
     if (st) return st;
     k_batch_reset<<<(B->nb + 127) / 128, 128, 0, B->stream>>>(B->d_P, B->nb, B->d_nactive);

@@ -20,9 +20,15 @@ enum : int { kStatusNonfinite = 1, kStatusSingular = 2 };
 // ghost point, 0 when shared).  Per-row derivative vectors D[r] (ldD() doubles):
 // dPi_Z/dc_j at j, dPi_G/dc_j at n + j (j < n), Pi_Z at 2n, Pi_G at 2n + 1, for
 // r < Rc (collocation), Rc (x_Z) and Rc + 1 (x_G).
+// Radial rule: nr nodes per external momentum; radmode 0 shares one rule of
+// nrule = nr nodes between all rows, radmode 1 (the paper's split at x with an
+// infrared piece) gives every D row r its own nr = 3 nrule nodes, stored from
+// r * nr on (rowrad() = 1).  angmode 0: Gauss-Legendre in theta; 1: tanh-sinh in
+// xi = cos theta.
 struct Consts {
     int N, nr, na, extrap;
     int NZ, NG, n, Rc, gofs;
+    int nrule, radmode, angmode, pad_;
     double eps2, lam2, ln_eps2, ln_lam2;
     double L0, L1, invL1;          // ln x = L0 + L1 s
     double K;                      // g^2 Nc / (2 pi)^3
@@ -33,6 +39,14 @@ struct Consts {
 };
 
 __host__ __device__ inline size_t ldD(const Consts& c) { return 2 * (size_t)c.n + 2; }
+// offset of row r's radial tables (Rad, YTab, and phi_y in units of N)
+__host__ __device__ inline size_t rad_offset(const Consts& c, int r) {
+    return c.radmode == 1 ? (size_t)r * c.nr : 0;
+}
+// number of radial table entries: nr, or nr per D row (Rc + 2 rows)
+__host__ __device__ inline size_t rad_entries(const Consts& c) {
+    return c.radmode == 1 ? (size_t)(c.Rc + 2) * c.nr : (size_t)c.nr;
+}
 
 // Per radial node: y_k, quadrature weight W_k (Jacobian y_k included), sqrt(y_k).
 struct Rad { double y, W, sy, pad; };
@@ -158,5 +172,14 @@ cudaError_t launch_dressing_vjp(const Consts& c, int n, const double* x, const d
                                 double* part, int nsplit, double* out, double* out_g2nc, int* status,
                                 cudaStream_t s);
 cudaError_t launch_row_prefactors(const Consts& c, Row* rows, int Rt, cudaStream_t s);
+// Finite-difference Newton matrix: out (2n x n) = the perturbed vectors c +- h_j e_j;
+// J from the 2n residuals Fall (2n x n, same order).
+cudaError_t launch_fd_perturb(int n, const double* coef, double rel, double* out, cudaStream_t s);
+cudaError_t launch_fd_columns(int n, const double* pert, const double* Fall, double* J, int* status, cudaStream_t s);
 
 }  // namespace dse
+
+// Batch construction without the n <= 128 limit of the batched Newton step (for
+// batches that only evaluate residuals, as the finite-difference Newton matrix).
+int batch_create_impl(const dse_problem* problems, int n_problems, void* cuda_stream, bool newton,
+                      dse_batch** out);

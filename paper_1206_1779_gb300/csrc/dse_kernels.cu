@@ -77,25 +77,60 @@ __global__ void k_setup_rules(const Consts c, const double* __restrict__ gr, con
                               Ang* __restrict__ ang, double* __restrict__ theta, double* __restrict__ xcol,
                               Row* __restrict__ rows, int Rt) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < c.nr) {
-        const double y = exp(c.L0 + c.L1 * gr[m]);
+    const int nrad = (int)rad_entries(c);
+    if (m < nrad) {
         Rad r;
-        r.y = y;
-        r.W = c.L1 * wr[m] * y;
-        r.sy = sqrt(y);
+        if (c.radmode == 0) {
+            const double y = exp(c.L0 + c.L1 * gr[m]);
+            r.y = y;
+            r.W = c.L1 * wr[m] * y;
+        } else {
+            // row rr's split rule: [1e-6 eps2, eps2], [eps2, x], [x, lambda2] in ln y,
+            // x clamped into [eps2, lambda2]; nrule Gauss-Legendre nodes per piece
+            const int rr = m / c.nr;
+            const int k = m - rr * c.nr;
+            const int piece = k / c.nrule;
+            const int i = k - piece * c.nrule;
+            double x = rr < c.Rc ? collocation_point(c, rr) : (rr == c.Rc ? c.x_Z : c.x_G);
+            x = fmin(fmax(x, c.eps2), c.lam2);
+            const double lx = log(x);
+            const double lo = piece == 0 ? c.ln_eps2 + log(1e-6) : (piece == 1 ? c.ln_eps2 : lx);
+            const double hi = piece == 0 ? c.ln_eps2 : (piece == 1 ? lx : c.ln_lam2);
+            const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+            const double y = exp(mid + half * gr[i]);
+            r.y = y;
+            r.W = half * wr[i] * y;
+        }
+        r.sy = sqrt(r.y);
         r.pad = 0.0;
         rad[m] = r;
         return;
     }
-    int q = m - c.nr;
+    int q = m - nrad;
     if (q < c.na) {
-        const double th = 0.5 * kPi * (1.0 + ga[q]);
-        const double sh = sin(0.5 * th);
-        const double sn = sin(th);
         Ang a;
-        a.w = 0.5 * kPi * wa[q];
-        a.sig = sh * sh;
-        a.s2 = sn * sn;
+        double th;
+        if (c.angmode == 0) {
+            th = 0.5 * kPi * (1.0 + ga[q]);
+            const double sh = sin(0.5 * th);
+            const double sn = sin(th);
+            a.w = 0.5 * kPi * wa[q];
+            a.sig = sh * sh;
+            a.s2 = sn * sn;
+        } else {
+            // tanh-sinh in xi = cos theta = tanh u, u = (pi/2) sinh t, t = t_max - (q + 1/2) h:
+            // sin^2(theta/2) = 1/(1 + e^{2u}), sin^2 theta = 1/cosh^2 u, theta = 2 atan(e^{-u}),
+            // weight (pi/2) h cosh t / cosh u
+            const double tmax = 4.0;
+            const double h = 2.0 * tmax / c.na;
+            const double t = tmax - (q + 0.5) * h;
+            const double u = 0.5 * kPi * sinh(t);
+            const double cu = cosh(u);
+            th = 2.0 * atan(exp(-u));
+            a.w = h * 0.5 * kPi * cosh(t) / cu;
+            a.sig = 1.0 / (1.0 + exp(2.0 * u));
+            a.s2 = 1.0 / (cu * cu);
+        }
         a.s4 = a.s2 * a.s2;
         ang[q] = a;
         theta[q] = th;
@@ -137,7 +172,8 @@ __device__ __forceinline__ void tables_unit(const Consts& c, const double* __res
                          XTab* __restrict__ xtab, double* __restrict__ phix, const int m) {
     const double* a = coef;
     const double* b = coef + c.NZ;
-    if (m < c.nr) {
+    const int nrad = (int)rad_entries(c);
+    if (m < nrad) {
         const double y = rad[m].y;
         double lG, lZ;
         dressing_eval(c, a, b, y, lG, lZ, phiy + (size_t)m * c.N);
@@ -152,7 +188,7 @@ __device__ __forceinline__ void tables_unit(const Consts& c, const double* __res
         ytab[m] = t;
         return;
     }
-    const int i = m - c.nr;
+    const int i = m - nrad;
     if (i < c.Rc) {
         double lG, lZ;
         dressing_eval(c, a, b, xcol[i], lG, lZ, phix + (size_t)i * c.N);
@@ -178,7 +214,7 @@ __global__ void k_tables_batched(const BatchProblem* __restrict__ P, const doubl
     const BatchProblem& B = P[blockIdx.y];
     if (!B.active) return;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= B.t.c.nr + B.t.c.Rc) return;
+    if (m >= (int)rad_entries(B.t.c) + B.t.c.Rc) return;
     tables_unit(B.t.c, coef_base + B.coef_off, B.t.rad, B.xcol, B.ytab, B.phiy, B.xtab, B.phix, m);
 }
 
@@ -225,6 +261,10 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
     const bool gluon = (flags & kRowGluon) != 0;
     const bool ghost = (flags & kRowGhost) != 0;
     const bool do_pi = (jb == 0);
+    // this row's radial tables (the split rule gives every row its own)
+    rad += rad_offset(c, r);
+    ytab += rad_offset(c, r);
+    phiy += rad_offset(c, r) * N;
     if (special && kg == 0) {
         // sum_l w_l sin^4(theta_l) by warp 0 (fixed order)
         double s4 = 0.0;
@@ -1424,14 +1464,14 @@ cudaError_t launch_gauss_legendre(int n, double* inv, double* x, double* w, cuda
 cudaError_t launch_setup_rules(const Consts& c, const double* gl_r, const double* gw_r, const double* gl_a,
                                const double* gw_a, Rad* rad, Ang* ang, double* theta, double* xcol, Row* rows,
                                int Rt, cudaStream_t s) {
-    const long long total = (long long)c.nr + c.na + c.Rc + Rt;
+    const long long total = (long long)rad_entries(c) + c.na + c.Rc + Rt;
     k_setup_rules<<<blocks_for(total, 128), 128, 0, s>>>(c, gl_r, gw_r, gl_a, gw_a, rad, ang, theta, xcol, rows, Rt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tables(const Consts& c, const double* coef, const Rad* rad, const double* xcol, YTab* ytab,
                           double* phiy, XTab* xtab, double* phix, cudaStream_t s) {
-    k_tables<<<blocks_for((long long)c.nr + c.Rc, 64), 64, 0, s>>>(c, coef, rad, xcol, ytab, phiy, xtab, phix);
+    k_tables<<<blocks_for((long long)rad_entries(c) + c.Rc, 64), 64, 0, s>>>(c, coef, rad, xcol, ytab, phiy, xtab, phix);
     return cudaGetLastError();
 }
 

@@ -85,7 +85,8 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
         !isfinite(p->x_Z) || !(p->x_G >= 0.0) || !isfinite(p->x_G) || !isfinite(p->g2nc) || !isfinite(p->kappa) ||
         !isfinite(p->delta) || !isfinite(p->ginv_G) || !isfinite(p->zinv_Z))
         return DSE_ERR_ARG;
-    if (p->radial_mode != 0 || p->precision != 0 || (p->extrap_mode != 0 && p->extrap_mode != 1))
+    if (p->radial_mode != 0 || p->precision != 0 || (p->extrap_mode != 0 && p->extrap_mode != 1) ||
+        (p->angular_mode != 0 && p->angular_mode != 1))
         return DSE_ERR_UNSUPPORTED;
 
     const double kPi = 3.14159265358979323846264338327950288;
@@ -97,6 +98,10 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
     c.Rc = c.NZ == c.NG ? c.N : c.n;
     c.gofs = c.NZ == c.NG ? 0 : c.NZ;
     c.nr = p->n_radial;
+    c.nrule = p->n_radial;
+    c.radmode = 0;
+    c.angmode = p->angular_mode;
+    c.pad_ = 0;
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;
     c.eps2 = p->eps2;

@@ -36,6 +36,9 @@ struct dse_plan {
     float* As;          // row-scaled FP32 copy of J (Newton step)
     double2* rowinfo;   // row scales and row sums (Newton step)
     double* aux;        // derivative scratch: dPi rows, dressing-VJP partial sums
+    // finite-difference Newton matrix: a batch of 2n copies of the problem
+    dse_batch* fd_batch;
+    double* fd_buf;     // perturbed vectors (2n x n), then their residuals (2n x n)
     double* stats;  // 4 doubles, followed by the int status word
     int* status;
     // Schwinger-function rule (allocated on first use, per node count)
@@ -69,7 +72,9 @@ int check_problem(const dse_problem* p) {
     if (!isfinite(p->g2nc) || !isfinite(p->kappa) || !isfinite(p->delta) || !isfinite(p->ginv_G) ||
         !isfinite(p->zinv_Z))
         return DSE_ERR_ARG;
-    if (p->radial_mode != 0 || (p->precision != 0 && p->precision != 1)) return DSE_ERR_UNSUPPORTED;
+    if ((p->radial_mode != 0 && p->radial_mode != 1) || (p->precision != 0 && p->precision != 1))
+        return DSE_ERR_UNSUPPORTED;
+    if (p->angular_mode != 0 && p->angular_mode != 1) return DSE_ERR_UNSUPPORTED;
     if (p->extrap_mode != 0 && p->extrap_mode != 1) return DSE_ERR_UNSUPPORTED;
     return DSE_OK;
 }
@@ -82,7 +87,11 @@ Consts make_consts(const dse_problem* p) {
     c.n = c.NZ + c.NG;
     c.Rc = c.NZ == c.NG ? c.N : c.n;
     c.gofs = c.NZ == c.NG ? 0 : c.NZ;
-    c.nr = p->n_radial;
+    c.nrule = p->n_radial;
+    c.radmode = p->radial_mode;
+    c.angmode = p->angular_mode;
+    c.pad_ = 0;
+    c.nr = p->radial_mode == 1 ? 3 * p->n_radial : p->n_radial;
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;
     c.eps2 = p->eps2;
@@ -140,8 +149,16 @@ void release_events(dse_plan* pl) {
     pl->n_ev = 0;
 }
 
+void free_fd(dse_plan* pl) {
+    if (pl->fd_batch) dse_batch_destroy(pl->fd_batch);
+    if (pl->fd_buf) cudaFree(pl->fd_buf);
+    pl->fd_batch = nullptr;
+    pl->fd_buf = nullptr;
+}
+
 void free_plan(dse_plan* pl) {
     if (!pl) return;
+    free_fd(pl);
     release_events(pl);
     if (pl->ws) cudaFree(pl->ws);
     if (pl->sch) cudaFree(pl->sch);
@@ -255,16 +272,18 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->nch = (na + 31) / 32;
     choose_split(pl);
     const int n = pl->c.n;
-    const int gmax = nr > na ? nr : na;
+    const int nrule = pl->c.nrule;
+    const int gmax = nrule > na ? nrule : na;
+    const size_t nrad = rad_entries(pl->c);
 
     size_t off = 0;
-    size_t o_rad = off; off = align_up(off + sizeof(Rad) * nr);
+    size_t o_rad = off; off = align_up(off + sizeof(Rad) * nrad);
     size_t o_ang = off; off = align_up(off + sizeof(Ang) * na);
     size_t o_th = off; off = align_up(off + sizeof(double) * na);
     size_t o_rows = off; off = align_up(off + sizeof(Row) * pl->Rt);
     size_t o_xcol = off; off = align_up(off + sizeof(double) * Rc);
-    size_t o_ytab = off; off = align_up(off + sizeof(YTab) * nr);
-    size_t o_phiy = off; off = align_up(off + sizeof(double) * (size_t)nr * N);
+    size_t o_ytab = off; off = align_up(off + sizeof(YTab) * nrad);
+    size_t o_phiy = off; off = align_up(off + sizeof(double) * nrad * N);
     size_t o_xtab = off; off = align_up(off + sizeof(XTab) * Rc);
     size_t o_phix = off; off = align_up(off + sizeof(double) * (size_t)Rc * N);
     size_t o_U = off; off = align_up(off + sizeof(double) * (size_t)pl->Rt * nr * pl->nch * 3);
@@ -280,7 +299,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_aux = off; off = align_up(off + sizeof(double) * (n_aux_a > n_aux_b ? n_aux_a : n_aux_b));
     size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + sizeof(int));
     // Gauss-Legendre scratch (set-up only): nodes/weights for both rules and 1/k
-    size_t o_gl = off; off = align_up(off + sizeof(double) * (2 * (size_t)nr + 2 * (size_t)na + gmax + 2));
+    size_t o_gl = off; off = align_up(off + sizeof(double) * (2 * (size_t)nrule + 2 * (size_t)na + gmax + 2));
 
     cudaError_t e = cudaMalloc(&pl->ws, off);
     if (e != cudaSuccess) {
@@ -310,14 +329,14 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->status = (int*)(base + o_misc + 4 * sizeof(double));
     double* gl = (double*)(base + o_gl);
     double* glr = gl;
-    double* gwr = glr + nr;
-    double* gla = gwr + nr;
+    double* gwr = glr + nrule;
+    double* gla = gwr + nrule;
     double* gwa = gla + na;
     double* inv = gwa + na;
 
     e = cudaMallocHost(&pl->h_misc, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->ws, 0, off, pl->stream);
-    if (e == cudaSuccess) e = launch_gauss_legendre(nr, inv, glr, gwr, pl->stream);
+    if (e == cudaSuccess) e = launch_gauss_legendre(nrule, inv, glr, gwr, pl->stream);
     if (e == cudaSuccess) e = launch_gauss_legendre(na, inv, gla, gwa, pl->stream);
     if (e == cudaSuccess)
         e = launch_setup_rules(pl->c, glr, gwr, gla, gwa, pl->rad, pl->ang, pl->theta, pl->xcol, pl->rows, pl->Rt,
@@ -355,11 +374,13 @@ int dse_quadrature(dse_plan* plan, double* d_y, double* d_W, double* d_theta, do
     const int nr = plan->c.nr, na = plan->c.na, Rc = plan->c.Rc;
     cudaError_t e = cudaSuccess;
     cudaStream_t s = plan->stream;
+    // radial_mode 1: the rule of the x_Z row
+    const Rad* r0 = plan->rad + rad_offset(plan->c, Rc);
     if (d_y && e == cudaSuccess)
-        e = cudaMemcpy2DAsync(d_y, sizeof(double), &plan->rad->y, sizeof(Rad), sizeof(double), nr,
+        e = cudaMemcpy2DAsync(d_y, sizeof(double), &r0->y, sizeof(Rad), sizeof(double), nr,
                               cudaMemcpyDeviceToDevice, s);
     if (d_W && e == cudaSuccess)
-        e = cudaMemcpy2DAsync(d_W, sizeof(double), &plan->rad->W, sizeof(Rad), sizeof(double), nr,
+        e = cudaMemcpy2DAsync(d_W, sizeof(double), &r0->W, sizeof(Rad), sizeof(double), nr,
                               cudaMemcpyDeviceToDevice, s);
     if (d_wt && e == cudaSuccess)
         e = cudaMemcpy2DAsync(d_wt, sizeof(double), &plan->ang->w, sizeof(Ang), sizeof(double), na,
@@ -507,6 +528,11 @@ int dse_plan_set_couplings(dse_plan* plan, double g2nc, double ginv_G, double zi
     plan->prob = p;
     plan->c = make_consts(&p);
     plan->launches += 1;
+    if (plan->fd_batch) {
+        cudaError_t e = cudaStreamSynchronize(plan->stream);
+        free_fd(plan);
+        if (e != cudaSuccess) return DSE_ERR_CUDA;
+    }
     return cuda_status(launch_row_prefactors(plan->c, plan->rows, plan->Rt, plan->stream));
 }
 
@@ -549,6 +575,41 @@ int dse_adjoint_solve(dse_plan* plan, const double* d_coeffs, const double* d_g,
     return read_status(plan, h_stats);
 }
 
+int dse_newton_matrix_fd(dse_plan* plan, const double* d_coeffs, double rel_step, double* d_J, double* d_F) {
+    if (!plan || !d_coeffs || !d_J || !(rel_step > 0.0) || !isfinite(rel_step)) return DSE_ERR_ARG;
+    const int n = plan->c.n;
+    if (!plan->fd_batch) {
+        dse_problem q = plan->prob;
+        q.precision = 0;
+        dse_problem* probs = new (std::nothrow) dse_problem[2 * (size_t)n];
+        if (!probs) return DSE_ERR_CUDA;
+        for (int v = 0; v < 2 * n; ++v) probs[v] = q;
+        int st = batch_create_impl(probs, 2 * n, plan->stream, false, &plan->fd_batch);
+        delete[] probs;
+        if (st) {
+            plan->fd_batch = nullptr;
+            return st;
+        }
+        if (cudaMalloc(&plan->fd_buf, sizeof(double) * 4 * (size_t)n * n) != cudaSuccess) {
+            plan->fd_buf = nullptr;
+            free_fd(plan);
+            return DSE_ERR_CUDA;
+        }
+    }
+    dse_batch_set_stream(plan->fd_batch, plan->stream);
+    double* pert = plan->fd_buf;
+    double* Fall = plan->fd_buf + 2 * (size_t)n * n;
+    cudaError_t e = launch_fd_perturb(n, d_coeffs, rel_step, pert, plan->stream);
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    int st = dse_batch_residual(plan->fd_batch, pert, Fall);
+    if (st) return st;
+    e = launch_fd_columns(n, pert, Fall, d_J, plan->status, plan->stream);
+    plan->launches += 2;
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    if (d_F) return build_system(plan, d_coeffs, nullptr, d_F, false, false);
+    return DSE_OK;
+}
+
 int dse_dressing_vjp(dse_plan* plan, int n, const double* d_x, const double* d_gG, const double* d_gZ, double* d_out,
                      double* d_out_g2nc) {
     if (!plan || n < 0 || !d_out) return DSE_ERR_ARG;
@@ -585,7 +646,9 @@ int dse_plan_counters(dse_plan* plan, long long* h_launches, int* h_timed, doubl
         if (e != cudaSuccess) return DSE_ERR_CUDA;
         total += ms;
     }
-    if (h_launches) *h_launches = plan->launches;
+    long long fd_launches = 0;
+    if (plan->fd_batch) dse_batch_counters(plan->fd_batch, &fd_launches, nullptr, nullptr);
+    if (h_launches) *h_launches = plan->launches + fd_launches;
     if (h_timed) *h_timed = plan->n_ev;
     if (h_timed_ms) *h_timed_ms = total;
     return DSE_OK;

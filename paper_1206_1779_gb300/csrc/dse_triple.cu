@@ -104,8 +104,8 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
             const int l = ch * 32 + lane;
             if (l < c.na) {
                 live = true;
-                const Rad rd = A.rad[k];
-                const YTab yt = A.ytab[k];
+                const Rad rd = A.rad[rad_offset(c, rt) + k];
+                const YTab yt = A.ytab[rad_offset(c, rt) + k];
                 const Ang an = A.ang[l];
                 const double d0 = row.sx - rd.sy;
                 const double d = d0 * d0;

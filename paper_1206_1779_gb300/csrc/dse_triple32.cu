@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(BT) k_triple32(const __grid_constant__ TripleA
             const int l = ch * 32 + lane;
             if (l < c.na) {
                 live = true;
-                const Rad rd = A.rad[k];
-                const YTab yt = A.ytab[k];
+                const Rad rd = A.rad[rad_offset(c, rt) + k];
+                const YTab yt = A.ytab[rad_offset(c, rt) + k];
                 const Ang an = A.ang[l];
                 const float sy = (float)rd.sy;
                 const float sig = (float)an.sig;

@@ -31,10 +31,27 @@ def test_exports_match_header(lib):
         assert hasattr(lib, n), n
 
 
-def test_struct_layout_matches_header():
+def test_struct_layout_matches_header(tmp_path):
+    """Size and field offsets of dse_problem as a C compiler lays it out from
+    include/dse.h, against the ctypes mirror of the binding."""
+    import os
+    import subprocess
     from paper_1206_1779_gb300 import Problem
-    # 3 ints (padded to 16), 9 doubles, 3 ints (padded to 8)
-    assert ctypes.sizeof(Problem) == 16 + 9 * 8 + 16
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = [n for n, _ in Problem._fields_]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dse.h"', 'int main(void) {',
+             '    printf("size %zu\\n", sizeof(dse_problem));']
+    lines += ['    printf("' + n + ' %zu\\n", offsetof(dse_problem, ' + n + '));' for n in names]
+    lines += ['    return 0;', '}', '']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(root, "include"), "-o", str(exe), str(src)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(Problem)
+    for n in names:
+        assert int(out[n]) == getattr(Problem, n).offset, n
 
 
 def test_status_strings(lib):
@@ -58,7 +75,7 @@ def test_plan_create_rejects_bad_problem(lib, inputs, bad):
 
 def test_plan_create_rejects_unsupported_modes(lib, inputs):
     from paper_1206_1779_gb300 import DSE_ERR_UNSUPPORTED, Problem
-    for over in [dict(radial_mode=1), dict(precision=2), dict(extrap_mode=7)]:
+    for over in [dict(radial_mode=2), dict(precision=2), dict(extrap_mode=7), dict(angular_mode=3)]:
         p = inputs.problem(8, 16, 16)
         p.update(over)
         h = ctypes.c_void_p()

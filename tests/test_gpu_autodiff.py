@@ -45,6 +45,8 @@ CASES = {
     "n100": dict(n_cheb=100, n_radial=64, n_angular=32),
     "orders_24_48": dict(n_cheb=24, n_cheb_G=48, n_radial=40, n_angular=24, ginv_G=0.01),
     "orders_13_6_ghost_point": dict(n_cheb=13, n_cheb_G=6, n_radial=30, n_angular=33, x_G=3e-3, ginv_G=0.02),
+    "paper_quadrature": dict(n_cheb=9, n_cheb_G=7, n_radial=14, n_angular=24, radial_mode=1, angular_mode=1,
+                             ginv_G=0.01),
 }
 
 

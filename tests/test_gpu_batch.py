@@ -32,6 +32,8 @@ def mixed_batch(inputs):
         inputs.problem(13, 37, 45),
         inputs.problem(16, 64, 32, n_cheb_G=24, ginv_G=0.01),
         inputs.problem(8, 24, 32, extrap_mode=1, zinv_Z=2.5),
+        inputs.problem(10, 20, 30, n_cheb_G=6, angular_mode=1, ginv_G=0.005),
+        inputs.problem(6, 10, 24, n_cheb_G=9, radial_mode=1, angular_mode=1, x_G=2e-3, ginv_G=0.02),
     ]
 
 
@@ -134,6 +136,17 @@ def test_batch_isolates_failures(dse, oracle, inputs):
         its, status, _ = batch.solve(ct, tol=1e-10, max_iter=40, rho_relax=0.5, n_relax=6, check=False)
     assert status[1] in (dse.DSE_ERR_NONFINITE, dse.DSE_ERR_SINGULAR, dse.DSE_ERR_NOT_CONVERGED), status
     assert [status[0], status[2], status[3]] == [dse.DSE_OK] * 3, status
+
+
+def test_batch_residual_parity(dse, oracle, inputs):
+    probs = mixed_batch(inputs)
+    c = concat_guess(inputs, probs, seed0=40)
+    with dse.Batch(probs) as batch:
+        Fb = batch.split(to_host(batch.residual(to_dev(c))))
+        cs = batch.split(c)
+    for b, p in enumerate(probs):
+        _, AF = oracle.newton_matrix_magnitudes(p, cs[b])
+        assert entries_ok(Fb[b], oracle.residual(p, cs[b]), AF)[0], b
 
 
 def test_batch_rejects_unsupported(dse, inputs):

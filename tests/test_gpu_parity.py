@@ -40,6 +40,12 @@ CASES = {
                                     x_Z=4e4),
     "orders_64_24": dict(n_cheb=64, n_cheb_G=24, n_radial=128, n_angular=64),
     "orders_48_64_constant_extrap": dict(n_cheb=48, n_cheb_G=64, n_radial=64, n_angular=32, extrap_mode=1),
+    # the paper's own quadrature: tanh-sinh in cos theta, radial split at x with an IR piece
+    "tanh_sinh": dict(n_cheb=9, n_radial=24, n_angular=40, angular_mode=1),
+    "split_radial": dict(n_cheb=7, n_radial=16, n_angular=24, radial_mode=1),
+    "paper_quadrature_ghost_point": dict(n_cheb=12, n_cheb_G=8, n_radial=20, n_angular=32, radial_mode=1,
+                                         angular_mode=1, x_G=2e-3, ginv_G=0.02),
+    "paper_quadrature": dict(n_cheb=10, n_radial=16, n_angular=32, radial_mode=1, angular_mode=1),
 }
 
 
@@ -65,6 +71,36 @@ def test_newton_matrix_parity(dse, oracle, inputs, name):
     assert okR[0], (name, okR)
 
 
+@pytest.mark.parametrize("name", ["tiny", "ragged", "orders_11_7", "paper_quadrature_ghost_point"])
+def test_newton_matrix_fd_parity(dse, oracle, inputs, name):
+    """The paper's central-difference Newton matrix (batched perturbed residuals)
+    against the oracle's central differences with the same steps: each residual
+    is within its parity bar, so an entry is within the sum of the two bars over
+    the step."""
+    from test_oracle_jacobian import fd_jacobian
+    p = inputs.problem(**CASES[name])
+    c = inputs.starting_guess(p, seed=12)
+    rel = 1e-4
+    with dse.Plan(p) as plan:
+        ct = to_dev(c)
+        Jfd = to_host(plan.newton_matrix_fd(ct, rel_step=rel))
+        Ja, _ = plan.newton_matrix(ct)
+        Ja = to_host(Ja)
+        assert plan.status() == dse.DSE_OK
+    Jo = fd_jacobian(oracle, p, c, rel=rel)
+    _, Fo = oracle.newton_matrix(p, c)
+    _, AF = oracle.newton_matrix_magnitudes(p, c)
+    h = rel * np.maximum(np.abs(c), 1e-3)
+    barF = 1e-11 * np.abs(Fo) + 1e-13 * AF
+    bound = 1e-11 * np.abs(Jo) + 2.0 * barF[:, None] / (2.0 * h[None, :]) * 1.01
+    assert np.all(np.abs(Jfd - Jo) <= bound), (name, float(np.max(np.abs(Jfd - Jo) / bound)))
+    # how far the differences sit from the analytic matrix is the truncation and
+    # noise of the quotient itself (pinned on the oracle); reported here
+    rowmax = np.abs(Ja).max(axis=1, keepdims=True)
+    print("%s: max |J_fd - J| / rowmax = %.2e" % (name, float(np.max(np.abs(Jfd - Ja) / rowmax))))
+    assert np.max(np.abs(Jfd - Ja) / rowmax) < 1e-4
+
+
 def test_quadrature_and_collocation(dse, oracle, inputs):
     p = inputs.problem(10, 77, 41)
     y, W, th, wt = oracle.quadrature(p)
@@ -78,6 +114,22 @@ def test_quadrature_and_collocation(dse, oracle, inputs):
         rel = np.max(np.abs(a - b) / np.abs(b))
         assert rel <= tol, (name, rel)
     assert np.max(np.abs(gth - th)) <= 1e-15 * math.pi
+
+
+@pytest.mark.parametrize("over", [dict(angular_mode=1), dict(radial_mode=1), dict(radial_mode=1, angular_mode=1)])
+def test_quadrature_variants(dse, oracle, inputs, over):
+    p = inputs.problem(10, 21, 37, **over)
+    y, W, th, wt = oracle.quadrature(p)  # radial_mode 1: the rule of x = lambda2 = x_Z
+    with dse.Plan(p) as plan:
+        gy, gW, gth, gwt, gx = [to_host(t) for t in plan.quadrature()]
+    assert gy.size == y.size
+    # nodes to a few ulp; weights to 1e-13 (theta near pi rounds to pi: compare on pi)
+    assert np.max(np.abs(gy - y) / y) <= 1e-14
+    nz = W != 0  # the [x_Z, lambda2] piece has zero width when x_Z = lambda2
+    assert np.max(np.abs(gW[nz] - W[nz]) / np.abs(W[nz])) <= 1e-13
+    assert np.all(gW[~nz] == 0)
+    assert np.max(np.abs(gth - th)) <= 4e-16 * math.pi
+    assert np.max(np.abs(gwt - wt) / wt) <= 1e-13
 
 
 def test_dressing_parity_all_regions(dse, oracle, inputs):
@@ -161,6 +213,22 @@ def test_solve_parity(dse, oracle, inputs):
 
 def test_solve_parity_separate_orders(dse, oracle, inputs):
     p = inputs.problem(24, 64, 32, n_cheb_G=16)
+    c0 = inputs.starting_guess(p, seed=0)
+    co, ito, _ = oracle.solve(p, c0, tol=1e-10)
+    with dse.Plan(p) as plan:
+        ct = to_dev(c0)
+        it, st = plan.solve(ct, tol=1e-10, max_iter=30)
+        x = np.exp(np.linspace(math.log(1e-6), math.log(1e6), 97))
+        gG, gZ = plan.dressing(ct, to_dev(x))
+        gG, gZ = to_host(gG), to_host(gZ)
+    assert st[1] < 1e-10
+    assert abs(it - (ito + 1)) <= 1
+    lG, lZ = oracle.dressing(p, co, x)
+    assert np.max(np.abs(gG - lG)) < 1e-8 and np.max(np.abs(gZ - lZ)) < 1e-8
+
+
+def test_solve_parity_paper_quadrature(dse, oracle, inputs):
+    p = inputs.problem(12, 32, 32, radial_mode=1, angular_mode=1)
     c0 = inputs.starting_guess(p, seed=0)
     co, ito, _ = oracle.solve(p, c0, tol=1e-10)
     with dse.Plan(p) as plan:
