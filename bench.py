@@ -45,11 +45,19 @@ N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4.0
 
 
+SERIES_TABLE_N = (24, 128)  # the kernel reads ln G(z), ln Z(z) from the series table for these N
+SERIES_TABLE_DEGREE = 15    # degree of the table's local polynomials
+
+
 def flops_per_triple(N: int) -> float:
-    # algorithmic work of the hot kernel per (x, y, theta) triple: the T_j
-    # recurrence (N FMA), two series ln G(z), ln Z(z) (2N FMA) and three
-    # derivative sums weight * phi_j(z) (3N FMA) -> 12 N flops, plus ~50 flops
-    # of geometry, kernels and integrands (log/exp/division counted separately)
+    """Algorithmic FP64 work of the hot kernel per (x, y, theta) triple, counting an
+    FMA as 2 flops (log/exp/division counted separately, not here): the T_j
+    recurrence (N FMA) and three derivative sums weight * phi_j(z) (3N FMA), the
+    two series ln G(z), ln Z(z) -- summed per triple (2N FMA) outside
+    SERIES_TABLE_N, else read from the table (u and two Horner sums of degree
+    15: 62 flops) -- and ~50 flops of geometry, kernels and integrands."""
+    if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
+        return 8.0 * N + 2.0 + 4.0 * SERIES_TABLE_DEGREE + 50.0
     return 12.0 * N + 50.0
 
 
@@ -279,7 +287,9 @@ def run_gb300(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_triple (FP64 radial x angular quadrature)",
                          "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM at the sampled SM clock",
-                         "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms},
+                         "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms,
+                         "flops_per_triple": flops_per_triple(N), "triples_per_launch": triples,
+                         "direct_series_equivalent_tflops": triples * (12.0 * N + 50.0) / (avg_launch_ms * 1e-3) / 1e12},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(c0.nbytes + tt.nbytes),
                     "d2h_bytes_per_step": int(c0.nbytes + tt.nbytes)},
             "gpu_launches": int(launches1 - launches0),

@@ -218,7 +218,7 @@ int dse_dressing_vjp(dse_plan* plan, int n, const double* d_x, const double* d_g
  * gives the offsets (n_problems + 1 entries; problem b owns
  * [off[b], off[b+1]) = N_Z + N_G doubles, the same for F) and the offsets of
  * the concatenated Newton matrices (n_b^2 each).  One Newton step of the whole
- * batch is a CUDA graph of six launches, the quadrature of all problems in one
+ * batch is a CUDA graph of seven launches, the quadrature of all problems in one
  * persistent kernel that takes (problem, external momentum, radial block) work
  * items longest first from a device counter; the radial nodes per work item
  * come from dse_batch_tune.  The paper solves one problem at a time; the batch

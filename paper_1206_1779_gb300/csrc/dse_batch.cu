@@ -1,6 +1,6 @@
 // dse_batch.cu -- batches of independent problems (a parameter sweep): every
 // problem keeps its own orders N_Z, N_G, quadrature sizes and boundary values;
-// one Newton step of the whole batch is one CUDA graph of six launches, with the
+// one Newton step of the whole batch is one CUDA graph of seven launches, with the
 // quadrature over all problems in one persistent kernel (dse_triple.cu) that
 // takes (problem, row, radial split) items from a global counter, longest first.
 // The number of radial nodes per item is chosen by timing candidates
@@ -113,7 +113,7 @@ Consts batch_consts(const dse_problem* p) {
 
 // Per-problem workspace layout; Vpart sized for ks_cap radial splits.
 struct Slice {
-    size_t rad, ang, theta, rows, xcol, ytab, phiy, xtab, phix, U, V, D, J, F, work, As, ri, stats, gl, total;
+    size_t rad, ang, theta, rows, xcol, ytab, phiy, xtab, phix, U, V, D, J, F, work, As, ri, stats, stab, gl, total;
 };
 
 Slice slice_layout(const Consts& c, int Rt, int nch, int ks_cap) {
@@ -139,6 +139,7 @@ Slice slice_layout(const Consts& c, int Rt, int nch, int ks_cap) {
     L.As = off; off = up256(off + sizeof(float) * (size_t)n * n);
     L.ri = off; off = up256(off + sizeof(double2) * (size_t)n);
     L.stats = off; off = up256(off + 4 * sizeof(double) + sizeof(int));
+    L.stab = off; off = up256(off + (use_series_table(c.N) ? sizeof(SeriesRec) * kSeriesM : 0));
     const size_t nrule = c.nrule;
     const size_t gmax = nrule > (size_t)na ? nrule : (size_t)na;
     L.gl = off; off = up256(off + sizeof(double) * (2 * nrule + 2 * (size_t)na + gmax + 2));
@@ -226,6 +227,7 @@ int set_units(dse_batch* B, int units) {
 cudaError_t enqueue_matrix(dse_batch* B, const double* coef, double* J_base, double* F_base, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int), s);
     if (e == cudaSuccess) e = launch_tables_batched(B->d_P, B->nb, B->max_units, coef, s);
+    if (e == cudaSuccess) e = launch_series_table_batched(B->d_P, B->nb, coef, s);
     if (e == cudaSuccess)
         e = launch_triple_batched(true, B->d_P, B->d_items, B->n_items, B->d_counter, coef, B->maxN, B->grid, s);
     if (e == cudaSuccess) e = launch_rowreduce_batched(true, B->d_P, B->nb, B->max_rows, B->maxN, s);
@@ -237,6 +239,7 @@ cudaError_t enqueue_matrix(dse_batch* B, const double* coef, double* J_base, dou
 cudaError_t enqueue_residual(dse_batch* B, const double* coef, double* F_base, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int), s);
     if (e == cudaSuccess) e = launch_tables_batched(B->d_P, B->nb, B->max_units, coef, s);
+    if (e == cudaSuccess) e = launch_series_table_batched(B->d_P, B->nb, coef, s);
     if (e == cudaSuccess)
         e = launch_triple_batched(false, B->d_P, B->d_items, B->n_items, B->d_counter, coef, B->maxN, B->grid, s);
     if (e == cudaSuccess) e = launch_rowreduce_batched(false, B->d_P, B->nb, B->max_rows, B->maxN, s);
@@ -399,6 +402,8 @@ int batch_create_impl(const dse_problem* problems, int n_problems, void* cuda_st
         P.rowinfo = (double2*)(s + S.ri);
         P.stats = (double*)(s + S.stats);
         P.status = (int*)(s + S.stats + 4 * sizeof(double));
+        P.stab = use_series_table(P.t.c.N) ? (SeriesRec*)(s + S.stab) : nullptr;
+        P.t.stab = P.stab;
         const Consts& c = P.t.c;
         double* gl = (double*)(s + S.gl);
         double* glr = gl;
@@ -472,7 +477,7 @@ int dse_batch_newton_matrix(dse_batch* batch, const double* d_coeffs, double* d_
     k_batch_reset<<<(B->nb + 127) / 128, 128, 0, B->stream>>>(B->d_P, B->nb, B->d_nactive);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = enqueue_matrix(B, d_coeffs, d_J, d_F, B->stream);
-    B->launches += 5;
+    B->launches += 6;
     return cuda_status(e);
 }
 
@@ -482,7 +487,7 @@ int dse_batch_residual(dse_batch* batch, const double* d_coeffs, double* d_F) {
     k_batch_reset<<<(B->nb + 127) / 128, 128, 0, B->stream>>>(B->d_P, B->nb, B->d_nactive);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = enqueue_residual(B, d_coeffs, d_F, B->stream);
-    B->launches += 5;
+    B->launches += 6;
     return cuda_status(e);
 }
 
@@ -509,6 +514,7 @@ int dse_batch_tune(dse_batch* batch, const double* d_coeffs, int* h_units, doubl
             if (rep == 1) e = cudaEventRecord(e0, B->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counter, 0, sizeof(int), B->stream);
             if (e == cudaSuccess) e = launch_tables_batched(B->d_P, B->nb, B->max_units, d_coeffs, B->stream);
+            if (e == cudaSuccess) e = launch_series_table_batched(B->d_P, B->nb, d_coeffs, B->stream);
             if (e == cudaSuccess)
                 e = launch_triple_batched(true, B->d_P, B->d_items, B->n_items, B->d_counter, d_coeffs, B->maxN,
                                           B->grid, B->stream);
@@ -517,7 +523,7 @@ int dse_batch_tune(dse_batch* batch, const double* d_coeffs, int* h_units, doubl
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        B->launches += 9;
+        B->launches += 13;
         if (e != cudaSuccess) {
             st = DSE_ERR_CUDA;
             break;
@@ -550,7 +556,7 @@ int dse_batch_solve(dse_batch* batch, double* d_coeffs, double tol, int max_iter
     for (int it = 0; it < max_iter && e == cudaSuccess; ++it) {
         e = cudaGraphLaunch(B->exec, B->stream);
         B->graph_launches += 1;
-        B->launches += 6;
+        B->launches += 7;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(B->h_nactive, B->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, B->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);

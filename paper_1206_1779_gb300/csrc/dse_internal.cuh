@@ -61,6 +61,25 @@ struct YTab { double lG, lZ, G, Z, pq, yG, pad0, pad1; };
 // Per collocation point: ln G, ln Z, G, Z, 1/G, 1/Z.
 struct XTab { double lG, lZ, G, Z, Ginv, Zinv, pad0, pad1; };
 
+// Piecewise-polynomial table of the two Chebyshev series (ln Z: a, ln G: b) on
+// [-1, 1]: kSeriesM intervals uniform in theta = arccos s, on each a polynomial of
+// degree kSeriesP in u = (s - mid) * invhalf in [-1, 1] (monomial coefficients,
+// c[k] = (ln Z, ln G) pairs), fitted at kSeriesP + 1 Chebyshev points whose series
+// values are computed in double-double arithmetic.  With interval width
+// h = pi/kSeriesM the fit error is ~ (N h/4)^(P+1)/(P+1)! of the series' scale:
+// below 1e-19 for N <= 128, so the FP64 quadrature kernel reads the table for
+// kSeriesMinN <= N <= kSeriesMaxN in place of the per-triple series sums.
+constexpr int kSeriesM = 256;
+constexpr int kSeriesP = 15;
+constexpr int kSeriesQ = kSeriesP + 1;
+constexpr int kSeriesMinN = 24;
+constexpr int kSeriesMaxN = 128;
+struct SeriesRec {
+    double mid, invhalf;
+    double2 c[kSeriesQ];
+};
+__host__ __device__ inline bool use_series_table(int N) { return N >= kSeriesMinN && N <= kSeriesMaxN; }
+
 struct TripleArgs {
     Consts c;
     int Rt;         // rows handled by the triple kernel
@@ -74,6 +93,7 @@ struct TripleArgs {
     const double* coef;   // n: a (NZ) then b (NG)
     double* Upart;        // [Rt][nr][nch][3]   angular sums per radial node
     double* Vpart;        // [Rt][KS][3][N]     z-derivative sums per split
+    const SeriesRec* stab;  // series table (nullptr: sum the series per triple)
 };
 
 // One problem of a batch: its constants, its slice of the batch workspace and its
@@ -81,6 +101,7 @@ struct TripleArgs {
 struct BatchProblem {
     TripleArgs t;          // t.coef is unused: coefficients come from coef_base + coef_off
     YTab* ytab;            // = t.ytab, writable
+    SeriesRec* stab;       // = t.stab, writable (nullptr when N < kSeriesMinN)
     double* xcol;
     double* phiy;
     XTab* xtab;
@@ -111,6 +132,9 @@ cudaError_t launch_setup_rules(const Consts& c, const double* gl_r, const double
 cudaError_t launch_tables(const Consts& c, const double* coef, const Rad* rad, const double* xcol,
                           YTab* ytab, double* phiy, XTab* xtab, double* phix, cudaStream_t s);
 cudaError_t launch_triple(bool full, const TripleArgs& a, cudaStream_t s);
+// Series table for the coefficients coef (n: a then b), kSeriesM records.
+cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* tab, cudaStream_t s);
+cudaError_t launch_series_table_batched(const BatchProblem* P, int nb, const double* coef_base, cudaStream_t s);
 // FP32-integrand variant (mixed precision), same outputs and layouts.
 cudaError_t launch_triple32(bool full, const TripleArgs& a, cudaStream_t s);
 size_t triple_smem_bytes(bool full, int N);

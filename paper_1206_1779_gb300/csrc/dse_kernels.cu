@@ -219,6 +219,141 @@ __global__ void k_tables_batched(const BatchProblem* __restrict__ P, const doubl
 }
 
 // ------------------------------------------------------------------------
+// Series table (see SeriesRec).  Error-free transformations for the node values:
+// TwoSum (Knuth) and the FMA form of TwoProduct give exact rounding errors; a
+// double-double value is hi + lo with |lo| <= ulp(hi)/2.
+struct DD { double hi, lo; };
+
+__device__ __forceinline__ DD dd_two_sum(double a, double b) {
+    const double s = a + b;
+    const double bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ DD dd_fast_two_sum(double a, double b) {  // |a| >= |b|
+    const double s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ DD dd_add(DD x, DD y) {
+    DD s = dd_two_sum(x.hi, y.hi);
+    const DD t = dd_two_sum(x.lo, y.lo);
+    s.lo += t.hi;
+    s = dd_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_fast_two_sum(s.hi, s.lo);
+}
+
+// c_0/2 + sum_{j>=1} c_j T_j(s) at s = s_h + s_l (a double-double node) by the
+// compensated Clenshaw recurrence: b_k = c_k + 2 s b_{k+1} - b_{k+2} in FP64, the
+// exact rounding error of every step from TwoProduct / TwoSum, and those errors
+// carried through the same linear recurrence in FP64; the sum of both is the
+// series as computed in about twice the working precision, rounded once.
+// cf: the coefficients in shared memory.
+__device__ double series_comp(const double* cf, int m, double sh, double sl) {
+    const double s2h = 2.0 * sh, s2l = 2.0 * sl;
+    double b1 = 0.0, b2 = 0.0, e1 = 0.0, e2 = 0.0;
+    for (int k = m - 1; k >= 1; --k) {
+        const double p = s2h * b1;
+        const double ep = fma(s2h, b1, -p);
+        const DD q = dd_two_sum(p, -b2);
+        const DD t = dd_two_sum(q.hi, cf[k]);
+        const double local = (ep + q.lo) + fma(s2l, b1, t.lo);
+        const double ek = fma(s2h, e1, local - e2);
+        b2 = b1;
+        b1 = t.hi;
+        e2 = e1;
+        e1 = ek;
+    }
+    const double p = sh * b1;
+    const double ep = fma(sh, b1, -p);
+    const DD q = dd_two_sum(p, -b2);
+    const DD t = dd_two_sum(q.hi, 0.5 * cf[0]);
+    const double local = (ep + q.lo) + fma(sl, b1, t.lo);
+    return t.hi + fma(sh, e1, local - e2);
+}
+
+// Two intervals per block of two warps; warp f (0: ln Z, 1: ln G) evaluates its
+// series, lane (il, q) = (lane / Q, lane % Q) at the q-th Chebyshev point
+// u_q = cos(pi (q + 1/2)/Q) of interval 2 blk + il, the node s = mid + half u_q
+// held exactly as s_h + s_l.  Then thread (f, il, q) forms the Chebyshev
+// coefficient of degree q of the interpolant, c_q = (2 - [q = 0])/Q sum_r v_r
+// cos(pi q (r + 1/2)/Q), and its monomial coefficient of u^q, sum_j c_j [u^q] T_j(u),
+// with the coefficients of T_j built by the recurrence T_{j+1} = 2u T_j - T_{j-1}.
+constexpr int kSeriesIntervalsPerBlock = 2;
+static_assert(kSeriesIntervalsPerBlock * kSeriesQ == 32, "one warp holds one series of the block's intervals");
+
+__device__ __forceinline__ void series_table_block(const Consts& c, const double* __restrict__ coef,
+                                                   SeriesRec* __restrict__ tab, const int blk) {
+    __shared__ double sv[2][kSeriesIntervalsPerBlock][kSeriesQ];
+    __shared__ double sc[2][kSeriesIntervalsPerBlock][kSeriesQ];
+    __shared__ double tcoef[kSeriesQ][kSeriesQ];  // tcoef[j][k] = [u^k] T_j(u)
+    __shared__ double dct[kSeriesQ][kSeriesQ];    // dct[k][r] = cos(pi k (r + 1/2)/Q)
+    __shared__ double scf[2 * DSE_MAX_CHEB];      // a then b
+    const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int il = lane / kSeriesQ, q = lane % kSeriesQ;
+    for (int j = threadIdx.x; j < c.n; j += blockDim.x) scf[j] = coef[j];
+    for (int e = threadIdx.x; e < kSeriesQ * kSeriesQ; e += blockDim.x) {
+        const int k = e / kSeriesQ, r = e % kSeriesQ;
+        dct[k][r] = cos(kPi * k * (r + 0.5) / kSeriesQ);
+    }
+    if (threadIdx.x < kSeriesQ) {
+        // column k of every T_j, by the three-term recurrence (exact integers)
+        const int k = threadIdx.x;
+        double tm = k == 0 ? 1.0 : 0.0;  // T_0
+        double tc = k == 1 ? 1.0 : 0.0;  // T_1
+        tcoef[0][k] = tm;
+        tcoef[1][k] = tc;
+        for (int j = 2; j < kSeriesQ; ++j) {
+            const double lower = __shfl_up_sync(0x0000ffffu, tc, 1);  // [u^{k-1}] T_{j-1}
+            const double tn = (k == 0 ? 0.0 : 2.0 * lower) - tm;
+            tcoef[j][k] = tn;
+            tm = tc;
+            tc = tn;
+        }
+    }
+    const int i = blk * kSeriesIntervalsPerBlock + il;
+    const double h = kPi / kSeriesM;
+    const double th0 = i * h, th1 = (i + 1) * h;
+    const double mid = 0.5 * (cos(th0) + cos(th1));
+    const double half = sin(0.5 * (th0 + th1)) * sin(0.5 * h);  // (cos th0 - cos th1)/2 without cancellation
+    const double uq = cos(kPi * (q + 0.5) / kSeriesQ);
+    // s = mid + half uq exactly as s_h + s_l
+    const DD p = dd_two_sum(half * uq, mid);
+    const DD sdd = dd_add(p, DD{fma(half, uq, -(half * uq)), 0.0});
+    __syncthreads();  // coefficients and tables staged
+    sv[f][il][q] = f == 0 ? series_comp(scf, c.NZ, sdd.hi, sdd.lo) : series_comp(scf + c.NZ, c.NG, sdd.hi, sdd.lo);
+    __syncthreads();
+    {
+        double acc = 0.0;
+        for (int r = 0; r < kSeriesQ; ++r) acc = fma(sv[f][il][r], dct[q][r], acc);
+        sc[f][il][q] = (q == 0 ? 1.0 : 2.0) / kSeriesQ * acc;
+    }
+    __syncthreads();
+    double mono = 0.0;
+    for (int j = q; j < kSeriesQ; ++j) mono = fma(sc[f][il][j], tcoef[j][q], mono);
+    SeriesRec& R = tab[i];
+    if (f == 0) R.c[q].x = mono;
+    else R.c[q].y = mono;
+    if (f == 0 && q == 0) {
+        R.mid = mid;
+        R.invhalf = 1.0 / half;
+    }
+}
+
+__global__ void __launch_bounds__(64) k_series_table(const Consts c, const double* __restrict__ coef,
+                                                      SeriesRec* __restrict__ tab) {
+    series_table_block(c, coef, tab, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(64) k_series_table_batched(const BatchProblem* __restrict__ P,
+                                                              const double* __restrict__ coef_base) {
+    const BatchProblem& B = P[blockIdx.y];
+    if (!B.active || !B.stab) return;
+    series_table_block(B.t.c, coef_base + B.coef_off, B.stab, blockIdx.x);
+}
+
+// ------------------------------------------------------------------------
 // Per external momentum r (rows 0..Rc-1: collocation points, Rc: x_Z, Rc+1: x_G):
 //   y-only contraction  Y_c[j] = sum_k U_c(r,k) phi_j(y_k),  c in {Q, M, G}
 //   z-part              V_c[j] = sum over radial splits of Vpart
@@ -1561,9 +1696,20 @@ cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* tab, cudaStream_t s) {
+    k_series_table<<<kSeriesM / kSeriesIntervalsPerBlock, 64, 0, s>>>(c, coef, tab);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------
 // Batched launchers: grid dimension y (z for the row contraction) runs over the
 // problems of the batch.
+cudaError_t launch_series_table_batched(const BatchProblem* P, int nb, const double* coef_base, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    k_series_table_batched<<<dim3(kSeriesM / kSeriesIntervalsPerBlock, nb), 64, 0, s>>>(P, coef_base);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tables_batched(const BatchProblem* P, int nb, int max_units, const double* coef_base,
                                   cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;

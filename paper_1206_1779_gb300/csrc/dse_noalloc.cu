@@ -180,6 +180,7 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
         a.coef = d_coeffs;
         a.Upart = U;
         a.Vpart = nullptr;  // not used by the residual-only kernel
+        a.stab = nullptr;   // series summed per triple (no table in the static scratch)
         e = launch_triple(false, a, s);
     }
     if (e == cudaSuccess) e = launch_rowreduce(false, c, Rt, KS, nch, rad, ang, rows, ytab, phiy, U, nullptr, D, s);

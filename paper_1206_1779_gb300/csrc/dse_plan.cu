@@ -33,6 +33,7 @@ struct dse_plan {
     double* J;
     double* F;
     double* work;
+    SeriesRec* stab;    // series table (read by the FP64 quadrature kernel when use_series_table(N))
     float* As;          // row-scaled FP32 copy of J (Newton step)
     double2* rowinfo;   // row scales and row sums (Newton step)
     double* aux;        // derivative scratch: dPi rows, dressing-VJP partial sums
@@ -181,6 +182,7 @@ TripleArgs triple_args(const dse_plan* pl, const double* coef) {
     a.coef = coef;
     a.Upart = pl->Upart;
     a.Vpart = pl->Vpart;
+    a.stab = use_series_table(pl->c.N) ? pl->stab : nullptr;
     return a;
 }
 
@@ -188,6 +190,10 @@ TripleArgs triple_args(const dse_plan* pl, const double* coef) {
 // FP32-integrand kernel (mixed precision) instead of the FP64 one.
 cudaError_t build_rows(dse_plan* pl, const double* coef, bool full, bool fp32) {
     cudaError_t e = launch_tables(pl->c, coef, pl->rad, pl->xcol, pl->ytab, pl->phiy, pl->xtab, pl->phix, pl->stream);
+    if (e == cudaSuccess && use_series_table(pl->c.N)) {
+        e = launch_series_table(pl->c, coef, pl->stab, pl->stream);
+        pl->launches += 1;
+    }
     const bool timed = pl->profiling && pl->n_ev < 4096 && !fp32;
     if (timed && e == cudaSuccess) {
         e = cudaEventCreate(&pl->ev[2 * pl->n_ev]);
@@ -292,6 +298,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_J = off; off = align_up(off + sizeof(double) * (size_t)n * n);
     size_t o_F = off; off = align_up(off + sizeof(double) * n);
     size_t o_work = off; off = align_up(off + sizeof(double) * 2 * n);
+    size_t o_stab = off; off = align_up(off + sizeof(SeriesRec) * kSeriesM);
     size_t o_As = off; off = align_up(off + sizeof(float) * (size_t)n * n);
     size_t o_ri = off; off = align_up(off + sizeof(double2) * n);
     const size_t n_aux_a = 2 * (size_t)(Rc + 2) + (size_t)n + 3;
@@ -322,6 +329,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->J = (double*)(base + o_J);
     pl->F = (double*)(base + o_F);
     pl->work = (double*)(base + o_work);
+    pl->stab = (SeriesRec*)(base + o_stab);
     pl->As = (float*)(base + o_As);
     pl->rowinfo = (double2*)(base + o_ri);
     pl->aux = (double*)(base + o_aux);

@@ -28,6 +28,7 @@ namespace dse {
 namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
+constexpr double kPi = 3.14159265358979323846264338327950288;
 
 __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 : 64; }
 
@@ -114,23 +115,57 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                 const double lz = log(z);
                 double s = (lz - c.L0) * c.invL1;
                 s = fmin(1.0, fmax(-1.0, s));
-                double lg = 0.5 * sb[0];
-                double lzz = 0.5 * sa[0];
-                if (FULL) Trow[0] = 0.5;
-                if (N > 1) {
-                    lg = fma(sb[1], s, lg);
-                    lzz = fma(sa[1], s, lzz);
-                    if (FULL) Trow[1] = s;
-                }
-                double t0 = 1.0, t1 = s;
-                const double s2x = 2.0 * s;
-                for (int j = 2; j < N; ++j) {
-                    const double t2 = fma(s2x, t1, -t0);
-                    t0 = t1;
-                    t1 = t2;
-                    lg = fma(sb[j], t2, lg);
-                    lzz = fma(sa[j], t2, lzz);
-                    if (FULL) Trow[j] = t2;
+                double lg, lzz;
+                if (A.stab) {
+                    // series from the table: the interval by arccos in FP32, the
+                    // polynomial in u = (s - mid) / half in FP64 (Horner)
+                    int it = (int)(acosf((float)s) * (float)(kSeriesM / kPi));
+                    it = min(max(it, 0), kSeriesM - 1);
+                    const SeriesRec* R = A.stab + it;
+                    const double2 mh = __ldg(reinterpret_cast<const double2*>(R));
+                    const double uu = (s - mh.x) * mh.y;
+                    const double2 top = __ldg(&R->c[kSeriesP]);
+                    double gz = top.x, gg = top.y;
+#pragma unroll
+                    for (int k = kSeriesP - 1; k >= 0; --k) {
+                        const double2 ck = __ldg(&R->c[k]);
+                        gz = fma(gz, uu, ck.x);
+                        gg = fma(gg, uu, ck.y);
+                    }
+                    lzz = gz;
+                    lg = gg;
+                    if (FULL) {
+                        // T_j(z) for the derivative sums: the recurrence alone
+                        Trow[0] = 0.5;
+                        if (N > 1) Trow[1] = s;
+                        double t0 = 1.0, t1 = s;
+                        const double s2x = 2.0 * s;
+                        for (int j = 2; j < N; ++j) {
+                            const double t2 = fma(s2x, t1, -t0);
+                            t0 = t1;
+                            t1 = t2;
+                            Trow[j] = t2;
+                        }
+                    }
+                } else {
+                    lg = 0.5 * sb[0];
+                    lzz = 0.5 * sa[0];
+                    if (FULL) Trow[0] = 0.5;
+                    if (N > 1) {
+                        lg = fma(sb[1], s, lg);
+                        lzz = fma(sa[1], s, lzz);
+                        if (FULL) Trow[1] = s;
+                    }
+                    double t0 = 1.0, t1 = s;
+                    const double s2x = 2.0 * s;
+                    for (int j = 2; j < N; ++j) {
+                        const double t2 = fma(s2x, t1, -t0);
+                        t0 = t1;
+                        t1 = t2;
+                        lg = fma(sb[j], t2, lg);
+                        lzz = fma(sa[j], t2, lzz);
+                        if (FULL) Trow[j] = t2;
+                    }
                 }
                 if (c.extrap == 0) {
                     if (z < c.eps2) {
