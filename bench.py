@@ -51,13 +51,14 @@ SERIES_TABLE_DEGREE = 15    # degree of the table's local polynomials
 
 def flops_per_triple(N: int) -> float:
     """Algorithmic FP64 work of the hot kernel per (x, y, theta) triple, counting an
-    FMA as 2 flops (log/exp/division counted separately, not here): the T_j
-    recurrence (N FMA) and three derivative sums weight * phi_j(z) (3N FMA), the
-    two series ln G(z), ln Z(z) -- summed per triple (2N FMA) outside
-    SERIES_TABLE_N, else read from the table (u and two Horner sums of degree
-    15: 62 flops) -- and ~50 flops of geometry, kernels and integrands."""
+    FMA as 2 flops (log, exp and division counted separately, not here): the T_j
+    recurrence (N FMA) and three derivative sums weight * phi_j(z) (3N FMA), and
+    ~50 flops of geometry, kernels and integrands.  The dressing functions at z:
+    for N in SERIES_TABLE_N read from the table (u, then Horner sums of degree 15
+    for Z, G and W: 93 flops, no exponential), else the two series summed per
+    triple (2N FMA) and three exponentials."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
-        return 8.0 * N + 2.0 + 4.0 * SERIES_TABLE_DEGREE + 50.0
+        return 8.0 * N + 3.0 + 6.0 * SERIES_TABLE_DEGREE + 50.0
     return 12.0 * N + 50.0
 
 

@@ -56,19 +56,20 @@ struct Ang { double w, sig, s2, s4; };
 struct Row { double x, sx, pre; int flags, pad; };
 enum : int { kRowGluon = 1, kRowGhost = 2 };
 // Per radial node, per coefficient vector: ln G(y), ln Z(y), G(y), Z(y),
-// p ln G(y) + q ln Z(y), y G(y).
-struct YTab { double lG, lZ, G, Z, pq, yG, pad0, pad1; };
+// p ln G(y) + q ln Z(y), y G(y), exp(p ln G(y) + q ln Z(y)).
+struct YTab { double lG, lZ, G, Z, pq, yG, Wy, pad1; };
 // Per collocation point: ln G, ln Z, G, Z, 1/G, 1/Z.
 struct XTab { double lG, lZ, G, Z, Ginv, Zinv, pad0, pad1; };
 
-// Piecewise-polynomial table of the two Chebyshev series (ln Z: a, ln G: b) on
-// [-1, 1]: kSeriesM intervals uniform in theta = arccos s, on each a polynomial of
-// degree kSeriesP in u = (s - mid) * invhalf in [-1, 1] (monomial coefficients,
-// c[k] = (ln Z, ln G) pairs), fitted at kSeriesP + 1 Chebyshev points whose series
-// values are computed in double-double arithmetic.  With interval width
-// h = pi/kSeriesM the fit error is ~ (N h/4)^(P+1)/(P+1)! of the series' scale:
-// below 1e-19 for N <= 128, so the FP64 quadrature kernel reads the table for
-// kSeriesMinN <= N <= kSeriesMaxN in place of the per-triple series sums.
+// Piecewise-polynomial table of the dressing functions on s in [-1, 1] (inside
+// [eps2, lambda2]): kSeriesM intervals uniform in theta = arccos s, on each a
+// polynomial of degree kSeriesP in u = (s - mid) * invhalf in [-1, 1] (monomial
+// coefficients) for Z(s), G(s) (pairs e[k]) and W(s) = G^p Z^q (w[k]), fitted at
+// kSeriesP + 1 Chebyshev points where ln Z, ln G come from a compensated Clenshaw
+// recurrence.  With interval width h = pi/kSeriesM the fit error is
+// ~ (N h/4)^(P+1)/(P+1)! relative: below 1e-19 for N <= 128, so the FP64
+// quadrature kernel reads the table for kSeriesMinN <= N <= kSeriesMaxN in place
+// of the per-triple series sums and exponentials.
 constexpr int kSeriesM = 256;
 constexpr int kSeriesP = 15;
 constexpr int kSeriesQ = kSeriesP + 1;
@@ -76,7 +77,8 @@ constexpr int kSeriesMinN = 24;
 constexpr int kSeriesMaxN = 128;
 struct SeriesRec {
     double mid, invhalf;
-    double2 c[kSeriesQ];
+    double2 e[kSeriesQ];  // (Z, G)
+    double w[kSeriesQ];   // W = G^p Z^q
 };
 __host__ __device__ inline bool use_series_table(int N) { return N >= kSeriesMinN && N <= kSeriesMaxN; }
 

@@ -184,7 +184,8 @@ __device__ __forceinline__ void tables_unit(const Consts& c, const double* __res
         t.Z = exp(lZ);
         t.pq = c.pG * lG + c.qZ * lZ;
         t.yG = y * t.G;
-        t.pad0 = t.pad1 = 0.0;
+        t.Wy = exp(t.pq);
+        t.pad1 = 0.0;
         ytab[m] = t;
         return;
     }
@@ -273,20 +274,24 @@ __device__ double series_comp(const double* cf, int m, double sh, double sl) {
     return t.hi + fma(sh, e1, local - e2);
 }
 
-// Two intervals per block of two warps; warp f (0: ln Z, 1: ln G) evaluates its
-// series, lane (il, q) = (lane / Q, lane % Q) at the q-th Chebyshev point
-// u_q = cos(pi (q + 1/2)/Q) of interval 2 blk + il, the node s = mid + half u_q
-// held exactly as s_h + s_l.  Then thread (f, il, q) forms the Chebyshev
-// coefficient of degree q of the interpolant, c_q = (2 - [q = 0])/Q sum_r v_r
-// cos(pi q (r + 1/2)/Q), and its monomial coefficient of u^q, sum_j c_j [u^q] T_j(u),
-// with the coefficients of T_j built by the recurrence T_{j+1} = 2u T_j - T_{j-1}.
+// Two intervals per block of three warps.  Warp f < 2 (0: ln Z, 1: ln G)
+// evaluates its series, lane (il, q) = (lane / Q, lane % Q) at the q-th Chebyshev
+// point u_q = cos(pi (q + 1/2)/Q) of interval 2 blk + il, the node s = mid + half u_q
+// held exactly as s_h + s_l.  Lane (il, q) of warp 0 then forms the node values
+// Z = e^{ln Z}, G = e^{ln G}, W = e^{p ln G + q ln Z}.  Thread (F, il, q) of warp F
+// (0: Z, 1: G, 2: W) forms the Chebyshev coefficient of degree q of the
+// interpolant, c_q = (2 - [q = 0])/Q sum_r v_r cos(pi q (r + 1/2)/Q), and its
+// monomial coefficient of u^q, sum_j c_j [u^q] T_j(u), with the coefficients of
+// T_j built by the recurrence T_{j+1} = 2u T_j - T_{j-1}.
 constexpr int kSeriesIntervalsPerBlock = 2;
-static_assert(kSeriesIntervalsPerBlock * kSeriesQ == 32, "one warp holds one series of the block's intervals");
+constexpr int kSeriesThreads = 96;
+static_assert(kSeriesIntervalsPerBlock * kSeriesQ == 32, "one warp holds one function of the block's intervals");
 
 __device__ __forceinline__ void series_table_block(const Consts& c, const double* __restrict__ coef,
                                                    SeriesRec* __restrict__ tab, const int blk) {
-    __shared__ double sv[2][kSeriesIntervalsPerBlock][kSeriesQ];
-    __shared__ double sc[2][kSeriesIntervalsPerBlock][kSeriesQ];
+    __shared__ double sv[2][kSeriesIntervalsPerBlock][kSeriesQ];  // ln Z, ln G
+    __shared__ double sf[3][kSeriesIntervalsPerBlock][kSeriesQ];  // Z, G, W
+    __shared__ double sc[3][kSeriesIntervalsPerBlock][kSeriesQ];
     __shared__ double tcoef[kSeriesQ][kSeriesQ];  // tcoef[j][k] = [u^k] T_j(u)
     __shared__ double dct[kSeriesQ][kSeriesQ];    // dct[k][r] = cos(pi k (r + 1/2)/Q)
     __shared__ double scf[2 * DSE_MAX_CHEB];      // a then b
@@ -317,36 +322,46 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     const double th0 = i * h, th1 = (i + 1) * h;
     const double mid = 0.5 * (cos(th0) + cos(th1));
     const double half = sin(0.5 * (th0 + th1)) * sin(0.5 * h);  // (cos th0 - cos th1)/2 without cancellation
-    const double uq = cos(kPi * (q + 0.5) / kSeriesQ);
-    // s = mid + half uq exactly as s_h + s_l
-    const DD p = dd_two_sum(half * uq, mid);
-    const DD sdd = dd_add(p, DD{fma(half, uq, -(half * uq)), 0.0});
     __syncthreads();  // coefficients and tables staged
-    sv[f][il][q] = f == 0 ? series_comp(scf, c.NZ, sdd.hi, sdd.lo) : series_comp(scf + c.NZ, c.NG, sdd.hi, sdd.lo);
+    if (f < 2) {
+        const double uq = cos(kPi * (q + 0.5) / kSeriesQ);
+        // s = mid + half uq exactly as s_h + s_l
+        const DD p = dd_two_sum(half * uq, mid);
+        const DD sdd = dd_add(p, DD{fma(half, uq, -(half * uq)), 0.0});
+        sv[f][il][q] = f == 0 ? series_comp(scf, c.NZ, sdd.hi, sdd.lo) : series_comp(scf + c.NZ, c.NG, sdd.hi, sdd.lo);
+    }
+    __syncthreads();
+    if (f == 0) {
+        const double lz = sv[0][il][q], lg = sv[1][il][q];
+        sf[0][il][q] = exp(lz);
+        sf[1][il][q] = exp(lg);
+        sf[2][il][q] = exp(fma(c.pG, lg, c.qZ * lz));
+    }
     __syncthreads();
     {
         double acc = 0.0;
-        for (int r = 0; r < kSeriesQ; ++r) acc = fma(sv[f][il][r], dct[q][r], acc);
+        for (int r = 0; r < kSeriesQ; ++r) acc = fma(sf[f][il][r], dct[q][r], acc);
         sc[f][il][q] = (q == 0 ? 1.0 : 2.0) / kSeriesQ * acc;
     }
     __syncthreads();
     double mono = 0.0;
     for (int j = q; j < kSeriesQ; ++j) mono = fma(sc[f][il][j], tcoef[j][q], mono);
     SeriesRec& R = tab[i];
-    if (f == 0) R.c[q].x = mono;
-    else R.c[q].y = mono;
+    if (f == 0) R.e[q].x = mono;
+    else if (f == 1) R.e[q].y = mono;
+    else R.w[q] = mono;
     if (f == 0 && q == 0) {
         R.mid = mid;
         R.invhalf = 1.0 / half;
     }
 }
 
-__global__ void __launch_bounds__(64) k_series_table(const Consts c, const double* __restrict__ coef,
+__global__ void __launch_bounds__(kSeriesThreads) k_series_table(const Consts c, const double* __restrict__ coef,
                                                       SeriesRec* __restrict__ tab) {
     series_table_block(c, coef, tab, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(64) k_series_table_batched(const BatchProblem* __restrict__ P,
+__global__ void __launch_bounds__(kSeriesThreads) k_series_table_batched(const BatchProblem* __restrict__ P,
                                                               const double* __restrict__ coef_base) {
     const BatchProblem& B = P[blockIdx.y];
     if (!B.active || !B.stab) return;
@@ -1697,7 +1712,7 @@ cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, c
 }
 
 cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* tab, cudaStream_t s) {
-    k_series_table<<<kSeriesM / kSeriesIntervalsPerBlock, 64, 0, s>>>(c, coef, tab);
+    k_series_table<<<kSeriesM / kSeriesIntervalsPerBlock, kSeriesThreads, 0, s>>>(c, coef, tab);
     return cudaGetLastError();
 }
 
@@ -1706,7 +1721,7 @@ cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* 
 // problems of the batch.
 cudaError_t launch_series_table_batched(const BatchProblem* P, int nb, const double* coef_base, cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;
-    k_series_table_batched<<<dim3(kSeriesM / kSeriesIntervalsPerBlock, nb), 64, 0, s>>>(P, coef_base);
+    k_series_table_batched<<<dim3(kSeriesM / kSeriesIntervalsPerBlock, nb), kSeriesThreads, 0, s>>>(P, coef_base);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ __host__ __device__ inline size_t tile_doubles(bool full, int N, int BT) {
 }
 
 __host__ __device__ inline size_t smem_doubles(bool full, int N, int BT) {
-    return tile_doubles(full, N, BT) + 3u * (size_t)BT + 2u * (size_t)N;
+    return tile_doubles(full, N, BT) + 3u * (size_t)BT + 2u * (size_t)N + 4u;
 }
 
 // One block's work: row rt, radial split ks of the problem in A.  smem holds
@@ -59,6 +59,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     double* sh = smem + tile_doubles(FULL, N, BT);
     double* sa = sh + 3 * BT;
     double* sb = sa + N;
+    double* sbnd = sb + N;  // ln Z(s=1), ln G(s=1), ln Z(s=-1), ln G(s=-1) (table path)
     constexpr int WARPS = BT / 32;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -91,6 +92,22 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     for (int jj = 0; jj < NJ; ++jj) acc[0][jj] = acc[1][jj] = acc[2][jj] = 0.0;
 
     __syncthreads();
+    if (A.stab) {
+        // the series at s = +-1 (T_j(1) = 1, T_j(-1) = (-1)^j), summed in the order
+        // of the per-triple recurrence
+        if (tid < 4) {
+            const double* cf = (tid & 1) ? sb : sa;
+            const double sgn = tid < 2 ? 1.0 : -1.0;
+            double v = 0.5 * cf[0];
+            double t = 1.0;
+            for (int j = 1; j < N; ++j) {
+                t *= sgn;
+                v = fma(cf[j], t, v);
+            }
+            sbnd[tid] = v;
+        }
+        __syncthreads();
+    }
 
     for (int base = 0; base < nunits; base += WARPS) {
         const int u = base + warp;
@@ -115,29 +132,83 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                 const double lz = log(z);
                 double s = (lz - c.L0) * c.invL1;
                 s = fmin(1.0, fmax(-1.0, s));
-                double lg, lzz;
-                if (A.stab) {
-                    // series from the table: the interval by arccos in FP32, the
-                    // polynomial in u = (s - mid) / half in FP64 (Horner)
+                const double wgt = rd.W * an.w;
+                const double iz = 1.0 / z;
+                const double iz2 = iz * iz;
+                double Zz = 0.0, Gz = 0.0, Wv = 0.0;  // Z(z), G(z), W = (G(y)G(z))^p (Z(y)Z(z))^q
+                const bool outside = c.extrap == 0 && (z < c.eps2 || z > c.lam2);
+                if (A.stab && !outside) {
+                    // Z(z), G(z), W(z) from the table: the interval by arccos in
+                    // FP32, the polynomials in u = (s - mid) / half in FP64 (Horner)
                     int it = (int)(acosf((float)s) * (float)(kSeriesM / kPi));
                     it = min(max(it, 0), kSeriesM - 1);
                     const SeriesRec* R = A.stab + it;
                     const double2 mh = __ldg(reinterpret_cast<const double2*>(R));
                     const double uu = (s - mh.x) * mh.y;
-                    const double2 top = __ldg(&R->c[kSeriesP]);
-                    double gz = top.x, gg = top.y;
+                    if (ghost || gluon) {
+                        const double2 top = __ldg(&R->e[kSeriesP]);
+                        double ez = top.x, eg = top.y;
 #pragma unroll
-                    for (int k = kSeriesP - 1; k >= 0; --k) {
-                        const double2 ck = __ldg(&R->c[k]);
-                        gz = fma(gz, uu, ck.x);
-                        gg = fma(gg, uu, ck.y);
+                        for (int kq = kSeriesP - 1; kq >= 0; --kq) {
+                            const double2 ck = __ldg(&R->e[kq]);
+                            ez = fma(ez, uu, ck.x);
+                            eg = fma(eg, uu, ck.y);
+                        }
+                        Zz = ez;
+                        Gz = eg;
                     }
-                    lzz = gz;
-                    lg = gg;
-                    if (FULL) {
-                        // T_j(z) for the derivative sums: the recurrence alone
-                        Trow[0] = 0.5;
-                        if (N > 1) Trow[1] = s;
+                    if (gluon) {
+                        double ew = __ldg(&R->w[kSeriesP]);
+#pragma unroll
+                        for (int kq = kSeriesP - 1; kq >= 0; --kq) ew = fma(ew, uu, __ldg(&R->w[kq]));
+                        Wv = yt.Wy * ew;
+                    }
+                } else {
+                    double lg, lzz;
+                    if (A.stab) {
+                        // outside [eps2, lambda2]: the series at s = +-1 (block sums)
+                        lzz = s > 0.0 ? sbnd[0] : sbnd[2];
+                        lg = s > 0.0 ? sbnd[1] : sbnd[3];
+                    } else {
+                        lg = 0.5 * sb[0];
+                        lzz = 0.5 * sa[0];
+                        if (N > 1) {
+                            lg = fma(sb[1], s, lg);
+                            lzz = fma(sa[1], s, lzz);
+                        }
+                        double t0 = 1.0, t1 = s;
+                        const double s2x = 2.0 * s;
+                        for (int j = 2; j < N; ++j) {
+                            const double t2 = fma(s2x, t1, -t0);
+                            t0 = t1;
+                            t1 = t2;
+                            lg = fma(sb[j], t2, lg);
+                            lzz = fma(sa[j], t2, lzz);
+                            if (FULL) Trow[j] = t2;
+                        }
+                    }
+                    if (outside) {
+                        if (z < c.eps2) {
+                            const double r = lz - c.ln_eps2;
+                            lg = fma(-c.kappa, r, lg);
+                            lzz = fma(2.0 * c.kappa, r, lzz);
+                        } else {
+                            const double L = log1p(c.omega * (lz - c.ln_lam2));
+                            lg = fma(c.delta, L, lg);
+                            lzz = fma(c.gam, L, lzz);
+                        }
+                    }
+                    if (ghost) Zz = exp(lzz);
+                    if (gluon) {
+                        Gz = exp(lg);
+                        Wv = exp(yt.pq + c.pG * lg + c.qZ * lzz);
+                    }
+                }
+                if (FULL) {
+                    Trow[0] = 0.5;
+                    if (N > 1) Trow[1] = s;
+                    if (A.stab) {
+                        // T_j(z) for the derivative sums (the direct path stored them above)
                         double t0 = 1.0, t1 = s;
                         const double s2x = 2.0 * s;
                         for (int j = 2; j < N; ++j) {
@@ -147,47 +218,9 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                             Trow[j] = t2;
                         }
                     }
-                } else {
-                    lg = 0.5 * sb[0];
-                    lzz = 0.5 * sa[0];
-                    if (FULL) Trow[0] = 0.5;
-                    if (N > 1) {
-                        lg = fma(sb[1], s, lg);
-                        lzz = fma(sa[1], s, lzz);
-                        if (FULL) Trow[1] = s;
-                    }
-                    double t0 = 1.0, t1 = s;
-                    const double s2x = 2.0 * s;
-                    for (int j = 2; j < N; ++j) {
-                        const double t2 = fma(s2x, t1, -t0);
-                        t0 = t1;
-                        t1 = t2;
-                        lg = fma(sb[j], t2, lg);
-                        lzz = fma(sa[j], t2, lzz);
-                        if (FULL) Trow[j] = t2;
-                    }
                 }
-                if (c.extrap == 0) {
-                    if (z < c.eps2) {
-                        const double r = lz - c.ln_eps2;
-                        lg = fma(-c.kappa, r, lg);
-                        lzz = fma(2.0 * c.kappa, r, lzz);
-                    } else if (z > c.lam2) {
-                        const double L = log1p(c.omega * (lz - c.ln_lam2));
-                        lg = fma(c.delta, L, lg);
-                        lzz = fma(c.gam, L, lzz);
-                    }
-                }
-                const double wgt = rd.W * an.w;
-                const double iz = 1.0 / z;
-                const double iz2 = iz * iz;
-                if (ghost) {
-                    const double Zz = exp(lzz);
-                    hG = wgt * yt.yG * an.s4 * Zz * iz2;
-                }
+                if (ghost) hG = wgt * yt.yG * an.s4 * Zz * iz2;
                 if (gluon) {
-                    const double Gz = exp(lg);
-                    const double Wv = exp(yt.pq + c.pG * lg + c.qZ * lzz);
                     const double dd = d * d, db = d * b, bb = b * b;
                     const double n0 = 7.5 * dd;
                     const double n1 = -(48.0 * dd + 18.0 * db + 12.0 * bb);
