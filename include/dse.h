@@ -145,7 +145,9 @@ int dse_newton_matrix_fd(dse_plan* plan, const double* d_coeffs, double rel_step
  * h_stats (host, 4 doubles, nullable): ||F||_inf, ||diag(Z(x_i), G(x_i)) F||_inf
  * (the dimensionless residual used as the stopping test), ||Delta||_inf, all for
  * the coefficients on entry, and the number of FP64 refinement sweeps (-1 when
- * the FP64 LU solved the system).
+ * the FP64 LU solved the system).  For n <= 128 the FP32 inverse of the last
+ * eliminated step is kept and tried first (a few refinement sweeps; the
+ * elimination runs only if they do not converge): dse_plan_solver_counters.
  * Waits for the stream.  On DSE_ERR_SINGULAR / DSE_ERR_NONFINITE the
  * coefficients are left unchanged. */
 int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stats);
@@ -302,6 +304,14 @@ int dse_residual_static(const dse_problem* problem, const double* d_coeffs, doub
  * pointer may be NULL. */
 int dse_plan_profile(dse_plan* plan, int enable);
 int dse_plan_counters(dse_plan* plan, long long* h_launches, int* h_timed, double* h_timed_ms);
+
+/* How the plan's Newton steps with n <= 128 solved J Delta = F since creation:
+ * h_eliminations counts steps that inverted their own row-scaled matrix
+ * (Gauss-Jordan in FP32), h_reused the steps whose FP64 refinement converged
+ * with the inverse kept from an earlier step of the same dse_solve (or of the
+ * preceding dse_newton_step calls), so that no elimination ran.  Both solve to
+ * the same backward-error bound.  Waits for the stream; either pointer may be NULL. */
+int dse_plan_solver_counters(dse_plan* plan, int* h_eliminations, int* h_reused);
 
 /* Human-readable name of a status code (static storage). */
 const char* dse_status_string(int status);

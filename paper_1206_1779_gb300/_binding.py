@@ -25,7 +25,7 @@ EXPORTS = ["dse_plan_create", "dse_plan_destroy", "dse_plan_set_stream", "dse_pl
            "dse_plan_set_couplings", "dse_vjp", "dse_param_derivatives", "dse_adjoint_solve", "dse_dressing_vjp",
            "dse_batch_create", "dse_batch_destroy", "dse_batch_set_stream", "dse_batch_offsets", "dse_batch_tune",
            "dse_batch_newton_matrix", "dse_batch_solve", "dse_batch_counters", "dse_newton_matrix_fd",
-           "dse_batch_residual"]
+           "dse_batch_residual", "dse_plan_solver_counters"]
 
 
 class DseError(RuntimeError):
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = False):
         "dse_residual_static": [PP, _VP, _VP, _VP],
         "dse_plan_counters": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_double)],
+        "dse_plan_solver_counters": [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "dse_plan_set_couplings": [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double],
         "dse_vjp": [_VP, _VP, _VP, _VP, _VP],
         "dse_param_derivatives": [_VP, _VP, _VP, _VP, _VP],
@@ -330,6 +331,14 @@ class Plan:
         _check(self._L.dse_plan_counters(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(ms)),
                "dse_plan_counters")
         return n.value, k.value, ms.value
+
+    def solver_counters(self):
+        """(Newton steps that eliminated, steps solved with a kept inverse) since creation (n <= 128)."""
+        e = ctypes.c_int(0)
+        r = ctypes.c_int(0)
+        _check(self._L.dse_plan_solver_counters(self._h, ctypes.byref(e), ctypes.byref(r)),
+               "dse_plan_solver_counters")
+        return e.value, r.value
 
 
 class Batch:

@@ -113,7 +113,8 @@ Consts batch_consts(const dse_problem* p) {
 
 // Per-problem workspace layout; Vpart sized for ks_cap radial splits.
 struct Slice {
-    size_t rad, ang, theta, rows, xcol, ytab, phiy, xtab, phix, U, V, D, J, F, work, As, ri, stats, stab, gl, total;
+    size_t rad, ang, theta, rows, xcol, ytab, phiy, xtab, phix, U, V, D, J, F, work, As, ri, X, S, stats, stab, gl,
+        total;
 };
 
 Slice slice_layout(const Consts& c, int Rt, int nch, int ks_cap) {
@@ -138,6 +139,8 @@ Slice slice_layout(const Consts& c, int Rt, int nch, int ks_cap) {
     L.work = off; off = up256(off + sizeof(double) * 2 * (size_t)n);
     L.As = off; off = up256(off + sizeof(float) * (size_t)n * n);
     L.ri = off; off = up256(off + sizeof(double2) * (size_t)n);
+    L.X = off; off = up256(off + (n <= 128 ? sizeof(float) * (size_t)n * n : 0));
+    L.S = off; off = up256(off + sizeof(double) * (size_t)n);
     L.stats = off; off = up256(off + 4 * sizeof(double) + sizeof(int));
     L.stab = off; off = up256(off + (use_series_table(c.N) ? sizeof(SeriesRec) * kSeriesM : 0));
     const size_t nrule = c.nrule;
@@ -154,6 +157,7 @@ __global__ void k_batch_reset(BatchProblem* __restrict__ P, int nb, int* __restr
         P[b].iter = 0;
         P[b].active = 1;
         P[b].result = 0;
+        P[b].xstate = 0;
         *P[b].status = 0;
     }
     if (b == 0) *n_active = nb;
@@ -400,6 +404,8 @@ int batch_create_impl(const dse_problem* problems, int n_problems, void* cuda_st
         P.work = (double*)(s + S.work);
         P.As = (float*)(s + S.As);
         P.rowinfo = (double2*)(s + S.ri);
+        P.Xinv = P.t.c.n <= 128 ? (float*)(s + S.X) : nullptr;
+        P.Sinv = (double*)(s + S.S);
         P.stats = (double*)(s + S.stats);
         P.status = (int*)(s + S.stats + 4 * sizeof(double));
         P.stab = use_series_table(P.t.c.N) ? (SeriesRec*)(s + S.stab) : nullptr;

@@ -114,6 +114,8 @@ struct BatchProblem {
     double* work;
     float* As;
     double2* rowinfo;
+    float* Xinv;           // FP32 inverse kept from the last eliminated Newton step (n <= 128)
+    double* Sinv;          // its row scales
     double* stats;         // 4 doubles of the last Newton step
     int* status;
     long long coef_off;    // offset of the problem's c (and F) in the concatenated vectors
@@ -121,7 +123,7 @@ struct BatchProblem {
     int iter;              // Newton steps taken
     int active;            // 1 while the problem still iterates
     int result;            // 0 running, 1 converged, -1 non-finite, -2 singular
-    int pad;
+    int xstate;            // 1 while Xinv holds a usable inverse
 };
 // One work item of the persistent quadrature kernel.
 struct BatchItem { int b, rt, ks, pad; };
@@ -148,10 +150,13 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
 cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix,
                             const double* D, double* J, double* F, int* status, cudaStream_t s);
 // Newton step: J Delta = F, c <- c - rho Delta (n = NZ + NG).  As (n*n floats)
-// and rowinfo (n double2) are scratch for the row-scaled FP32 copy of J.
+// and rowinfo (n double2) are scratch for the row-scaled FP32 copy of J.  For
+// n <= 128, Xinv (n*n floats), Sinv (n doubles) and *xstate keep the inverse of
+// an eliminated step for the next one (all three nullptr: no reuse).
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab,
                              double* coef, double rho, double* work, float* As, double2* rowinfo,
-                             double* stats, int* status, cudaStream_t s);
+                             double* stats, int* status, cudaStream_t s, float* Xinv = nullptr,
+                             double* Sinv = nullptr, int* xstate = nullptr);
 cudaError_t launch_dressing(const Consts& c, const double* coef, int n, const double* x, double* lG,
                             double* lZ, int* status, cudaStream_t s);
 cudaError_t launch_schwinger_map(const Consts& c, int n, const double* gx, const double* gw, double* pn,

@@ -1176,6 +1176,81 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale_rows_batched(const Batc
     scale_row(B.t.c.n, B.J, B.As, B.rowinfo, B.status, blockIdx.x);
 }
 
+// FP64 iterative refinement for J x = F with an approximate inverse X of the
+// row-scaled matrix diag(Sc) J: x <- x + X (Sc (F - J x)), with the residual in FP64
+// (J in shared memory, one thread per row) and the products X r in FP32, until
+// max |Sn (F - J x)| <= tolfac max |x| (a backward-stable solution for the
+// row scaling Sn).  Returns 1 (converged) or 2 (gave up: not finite, maxit sweeps,
+// or -- with early_abort -- a sweep that did not halve the residual).  Called by
+// every thread of the block; s_x holds x (zero on entry).
+constexpr int kReuseMax = 6;
+
+__device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, const float* Xs, const double* Sc,
+                                           const double* Sn, const double* __restrict__ F, double* s_x, float* s_rf,
+                                           double (*s_red)[4], int* s_conv, double tolfac, int maxit,
+                                           bool early_abort, int* sweeps) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double prev = INFINITY;  // thread 0 only
+    int st = 0;
+    for (int it = 0; it <= maxit; ++it) {
+        if (tid < 128) {
+            double rm = 0.0, xm = 0.0;
+            if (tid < n) {
+                const double* Jr = Js + (size_t)tid * ldj;
+                double a0 = 0.0, a1 = 0.0;
+                int jj = 0;
+                for (; jj + 1 < n; jj += 2) {
+                    a0 = fma(Jr[jj], s_x[jj], a0);
+                    a1 = fma(Jr[jj + 1], s_x[jj + 1], a1);
+                }
+                if (jj < n) a0 = fma(Jr[jj], s_x[jj], a0);
+                const double r = F[tid] - (a0 + a1);
+                s_rf[tid] = (float)(Sc[tid] * r);
+                const double rn = Sn[tid] * r;
+                rm = isfinite(rn) ? fabs(rn) : INFINITY;
+                xm = fabs(s_x[tid]);
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                rm = fmax(rm, __shfl_xor_sync(kFullMask, rm, off));
+                xm = fmax(xm, __shfl_xor_sync(kFullMask, xm, off));
+            }
+            if (lane == 0) {
+                s_red[0][warp] = rm;
+                s_red[1][warp] = xm;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double RM = fmax(fmax(s_red[0][0], s_red[0][1]), fmax(s_red[0][2], s_red[0][3]));
+            const double XM = fmax(fmax(s_red[1][0], s_red[1][1]), fmax(s_red[1][2], s_red[1][3]));
+            int v = 0;  // 0: continue, 1: converged, 2: give up
+            if (!isfinite(RM)) v = 2;
+            else if (RM <= tolfac * XM) v = 1;
+            else if (it == maxit) v = 2;
+            else if (early_abort && it > 0 && RM > 0.5 * prev) v = 2;
+            prev = RM;
+            *s_conv = v;
+        }
+        __syncthreads();
+        st = *s_conv;
+        if (st) break;
+        ++*sweeps;
+        // x += X r  (FP32 products, 8 threads per row)
+        {
+            const int i = tid >> 3, part = tid & 7;
+            float acc = 0.0f;
+            if (i < n)
+                for (int jj = part; jj < n; jj += 8) acc = fmaf(Xs[i * n + jj], s_rf[jj], acc);
+            acc += __shfl_xor_sync(kFullMask, acc, 4);
+            acc += __shfl_xor_sync(kFullMask, acc, 2);
+            acc += __shfl_xor_sync(kFullMask, acc, 1);
+            if (part == 0 && i < n) s_x[i] += (double)acc;
+        }
+        __syncthreads();
+    }
+    return st;
+}
+
 // ------------------------------------------------------------------------
 // Newton step for n = NZ + NG <= 128 on one SM, FP64 work kept to O(n^2):
 //   - the row-scaled FP32 matrix A = diag(s) J (k_scale_rows) is inverted in
@@ -1189,13 +1264,20 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale_rows_batched(const Batc
 //   - with pivot column q_k at step k the inverse is X[q_k][m] = a[k][q_m];
 //   - x <- x + X (b - A x) with the residual in FP64 (J copied to shared
 //     memory, one thread per row) until max|r| <= 4 sqrt(n) 2^-53 ||A|| ||x||;
+//   - with Xg given, the inverse that solved the previous Newton step (and its
+//     row scales) is kept in global memory and tried first: late Newton steps
+//     change J little, so a few refinement sweeps with the old X reach the same
+//     backward error and the elimination is skipped; if a sweep fails to halve
+//     the residual (or kReuseMax sweeps do not suffice) the step eliminates afresh;
 //   - FP64 LU fallback if the sweeps stall.
 template <int R>
 __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __restrict__ J,
                                                  const float* __restrict__ As, const double2* __restrict__ rowinfo,
                                                  const double* __restrict__ F, const XTab* __restrict__ xtab,
                                                  double* __restrict__ coef, const double rho, double* __restrict__ work,
-                                                 double* __restrict__ stats, int* __restrict__ status) {
+                                                 double* __restrict__ stats, int* __restrict__ status,
+                                                 float* __restrict__ Xg, double* __restrict__ Sg,
+                                                 int* __restrict__ xstate, const bool xcount) {
     extern __shared__ __align__(16) double dsm[];
     __shared__ __align__(16) float s_colq[2][kColPad];
     __shared__ float s_rowk[2][128];
@@ -1207,9 +1289,10 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     __shared__ int si[kGjThreads / 32];
     __shared__ double s_x[128];
     __shared__ double s_scale[128];
+    __shared__ double s_sold[128];
     __shared__ float s_rf[128];
     __shared__ double s_red[2][4];
-    __shared__ int s_piv, s_fail, s_done, s_conv;
+    __shared__ int s_piv, s_fail, s_done, s_conv, s_reuse;
     __shared__ double s_anorm;
     const int n = c.n;
     const int ldj = n + 1;
@@ -1255,180 +1338,155 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     for (int i = tid; i < n; i += kGjThreads) s_scale[i] = rowinfo[i].x;
     for (int i = n + tid; i < kColPad; i += kGjThreads) s_colq[0][i] = s_colq[1][i] = 0.0f;  // rows past n
     for (int idx = tid; idx < n * n; idx += kGjThreads) Js[(idx / n) * ldj + (idx % n)] = J[idx];
-    float v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = i0 + r;
-        v[r] = (owner && i < n) ? As[(size_t)i * n + j] : 0.0f;
-    }
-    bool used = false;  // this thread's column has been a pivot column
+    if (tid == 0) s_reuse = (Xg != nullptr && *xstate == 1) ? 1 : 0;
+    if (tid < n) s_x[tid] = 0.0;
     __syncthreads();
     if (s_fail) {
         if (tid == 0) atomicOr(status, s_fail);
         return;
     }
-
-    for (int gs = 0; gs < G; ++gs) {
-        // warps that hold threads of group gs
-        const int w0 = (gs * n) >> 5;
-        const int w1 = (gs * n + n - 1) >> 5;
-        const bool in_group_warp = warp >= w0 && warp <= w1;
-#pragma unroll
-        for (int rs = 0; rs < R; ++rs) {
-            const int k = gs * R + rs;
-            if (k >= n) break;  // uniform
-            const int b = k & 1;
-            // [A] group gs publishes row k and per-warp candidates over its unused columns
-            if (in_group_warp) {
-                const bool mine = owner && g == gs;
-                float a = -1.0f;
-                int idx = 1 << 30;
-                if (mine) {
-                    s_rowk[b][j] = v[rs];
-                    if (!used) {
-                        a = fabsf(v[rs]);
-                        idx = j;
-                    }
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const float oa = __shfl_xor_sync(kFullMask, a, off);
-                    const int oi = __shfl_xor_sync(kFullMask, idx, off);
-                    if (oa > a || (oa == a && oi < idx)) {
-                        a = oa;
-                        idx = oi;
-                    }
-                }
-                if (lane == 0) {
-                    s_wc[b][warp - w0] = a;
-                    s_wi[b][warp - w0] = idx;
-                }
-            }
-            __syncthreads();
-            // [B] pivot column q; its owners publish it
-            float best = s_wc[b][0];
-            int q = s_wi[b][0];
-            for (int w = 1; w <= w1 - w0; ++w) {
-                const float a = s_wc[b][w];
-                const int qi = s_wi[b][w];
-                if (a > best || (a == best && qi < q)) {
-                    best = a;
-                    q = qi;
-                }
-            }
-            if (!(best > 1e-30f)) {
-                if (tid == 0) s_done = -1;
-                goto elimination_done;  // uniform: every thread read the same candidates
-            }
-            if (tid == 0) s_q[k] = q;
-            if (owner && j == q) {
-                used = true;
-#pragma unroll
-                for (int r = 0; r < R; ++r) s_colq[b][i0 + r] = v[r];
-            }
-            __syncthreads();
-            // [C] eliminate column q from every row but k, scale row k
-            if (owner) {
-                const float inv = 1.0f / s_rowk[b][q];
-                const float nk = (j == q) ? inv : s_rowk[b][j] * inv;
-                if (j == q) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = 0.0f;
-                }
-                if (R >= 4) {
-                    const float4* col4 = reinterpret_cast<const float4*>(&s_colq[b][i0]);
-#pragma unroll
-                    for (int qq = 0; qq < R / 4; ++qq) {
-                        const float4 m = col4[qq];
-                        v[4 * qq + 0] = fmaf(-m.x, nk, v[4 * qq + 0]);
-                        v[4 * qq + 1] = fmaf(-m.y, nk, v[4 * qq + 1]);
-                        v[4 * qq + 2] = fmaf(-m.z, nk, v[4 * qq + 2]);
-                        v[4 * qq + 3] = fmaf(-m.w, nk, v[4 * qq + 3]);
-                    }
-                } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = fmaf(-s_colq[b][i0 + r], nk, v[r]);
-                }
-                if (g == gs) v[rs] = nk;
-            }
-        }
+    const double tolfac = 4.0 * sqrt((double)n) * 0x1p-53 * s_anorm;
+    int sweeps = 0;
+    bool converged = false;
+    if (s_reuse) {
+        // the previous Newton step's inverse (of its row-scaled matrix) as the
+        // approximate inverse; J changes little between late Newton steps
+        for (int idx = tid; idx < n * n; idx += kGjThreads) Xs[idx] = Xg[idx];
+        for (int i = tid; i < n; i += kGjThreads) s_sold[i] = Sg[i];
+        __syncthreads();
+        converged = refine_fp64(n, ldj, Js, Xs, s_sold, s_scale, F, s_x, s_rf, s_red, &s_conv, tolfac, kReuseMax,
+                                true, &sweeps) == 1;
+        if (xcount && converged && tid == 0) xstate[2] += 1;  // counter of steps that reused the inverse
     }
-elimination_done:
-    __syncthreads();
-    // X[q_k][m] = a[k][q_m]
-    if (tid < n && s_done == 0) s_qinv[s_q[tid]] = tid;
-    __syncthreads();
-    if (owner && s_done == 0) {
-        const int m = s_qinv[j];
+    if (!converged) {
+        sweeps = 0;  // the reported sweeps are those of the solve that is kept
+        if (tid < n) s_x[tid] = 0.0;
+        if (tid == 0) s_done = 0;
+        float v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = i0 + r;
-            if (i < n) Xs[s_q[i] * n + m] = v[r];
+            v[r] = (owner && i < n) ? As[(size_t)i * n + j] : 0.0f;
         }
-    }
-    if (tid < n) s_x[tid] = 0.0;
-    if (tid == 0) s_conv = 0;
-    __syncthreads();
-
-    int sweeps = 0;
-    if (s_done == 0) {
-        const double tolfac = 4.0 * sqrt((double)n) * 0x1p-53 * s_anorm;
-        for (int it = 0; it <= kRefineMax; ++it) {
-            // FP64 residual, one thread per row (4 warps)
-            if (tid < 128) {
-                double rm = 0.0, xm = 0.0;
-                if (tid < n) {
-                    const double* Jr = Js + (size_t)tid * ldj;
-                    double a0 = 0.0, a1 = 0.0;
-                    int jj = 0;
-                    for (; jj + 1 < n; jj += 2) {
-                        a0 = fma(Jr[jj], s_x[jj], a0);
-                        a1 = fma(Jr[jj + 1], s_x[jj + 1], a1);
+        bool used = false;  // this thread's column has been a pivot column
+        __syncthreads();
+        for (int gs = 0; gs < G; ++gs) {
+            // warps that hold threads of group gs
+            const int w0 = (gs * n) >> 5;
+            const int w1 = (gs * n + n - 1) >> 5;
+            const bool in_group_warp = warp >= w0 && warp <= w1;
+    #pragma unroll
+            for (int rs = 0; rs < R; ++rs) {
+                const int k = gs * R + rs;
+                if (k >= n) break;  // uniform
+                const int b = k & 1;
+                // [A] group gs publishes row k and per-warp candidates over its unused columns
+                if (in_group_warp) {
+                    const bool mine = owner && g == gs;
+                    float a = -1.0f;
+                    int idx = 1 << 30;
+                    if (mine) {
+                        s_rowk[b][j] = v[rs];
+                        if (!used) {
+                            a = fabsf(v[rs]);
+                            idx = j;
+                        }
                     }
-                    if (jj < n) a0 = fma(Jr[jj], s_x[jj], a0);
-                    const double r = s_scale[tid] * (F[tid] - (a0 + a1));
-                    s_rf[tid] = (float)r;
-                    rm = isfinite(r) ? fabs(r) : INFINITY;
-                    xm = fabs(s_x[tid]);
+    #pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const float oa = __shfl_xor_sync(kFullMask, a, off);
+                        const int oi = __shfl_xor_sync(kFullMask, idx, off);
+                        if (oa > a || (oa == a && oi < idx)) {
+                            a = oa;
+                            idx = oi;
+                        }
+                    }
+                    if (lane == 0) {
+                        s_wc[b][warp - w0] = a;
+                        s_wi[b][warp - w0] = idx;
+                    }
                 }
-                for (int off = 16; off > 0; off >>= 1) {
-                    rm = fmax(rm, __shfl_xor_sync(kFullMask, rm, off));
-                    xm = fmax(xm, __shfl_xor_sync(kFullMask, xm, off));
+                __syncthreads();
+                // [B] pivot column q; its owners publish it
+                float best = s_wc[b][0];
+                int q = s_wi[b][0];
+                for (int w = 1; w <= w1 - w0; ++w) {
+                    const float a = s_wc[b][w];
+                    const int qi = s_wi[b][w];
+                    if (a > best || (a == best && qi < q)) {
+                        best = a;
+                        q = qi;
+                    }
                 }
-                if (lane == 0) {
-                    s_red[0][warp] = rm;
-                    s_red[1][warp] = xm;
+                if (!(best > 1e-30f)) {
+                    if (tid == 0) s_done = -1;
+                    goto elimination_done;  // uniform: every thread read the same candidates
+                }
+                if (tid == 0) s_q[k] = q;
+                if (owner && j == q) {
+                    used = true;
+    #pragma unroll
+                    for (int r = 0; r < R; ++r) s_colq[b][i0 + r] = v[r];
+                }
+                __syncthreads();
+                // [C] eliminate column q from every row but k, scale row k
+                if (owner) {
+                    const float inv = 1.0f / s_rowk[b][q];
+                    const float nk = (j == q) ? inv : s_rowk[b][j] * inv;
+                    if (j == q) {
+    #pragma unroll
+                        for (int r = 0; r < R; ++r) v[r] = 0.0f;
+                    }
+                    if (R >= 4) {
+                        const float4* col4 = reinterpret_cast<const float4*>(&s_colq[b][i0]);
+    #pragma unroll
+                        for (int qq = 0; qq < R / 4; ++qq) {
+                            const float4 m = col4[qq];
+                            v[4 * qq + 0] = fmaf(-m.x, nk, v[4 * qq + 0]);
+                            v[4 * qq + 1] = fmaf(-m.y, nk, v[4 * qq + 1]);
+                            v[4 * qq + 2] = fmaf(-m.z, nk, v[4 * qq + 2]);
+                            v[4 * qq + 3] = fmaf(-m.w, nk, v[4 * qq + 3]);
+                        }
+                    } else {
+    #pragma unroll
+                        for (int r = 0; r < R; ++r) v[r] = fmaf(-s_colq[b][i0 + r], nk, v[r]);
+                    }
+                    if (g == gs) v[rs] = nk;
                 }
             }
-            __syncthreads();
-            if (tid == 0) {
-                const double RM = fmax(fmax(s_red[0][0], s_red[0][1]), fmax(s_red[0][2], s_red[0][3]));
-                const double XM = fmax(fmax(s_red[1][0], s_red[1][1]), fmax(s_red[1][2], s_red[1][3]));
-                int st = 0;                      // 0: continue, 1: converged, 2: give up
-                if (!isfinite(RM)) st = 2;
-                else if (RM <= tolfac * XM) st = 1;
-                else if (it == kRefineMax) st = 2;
-                s_conv = st;
+        }
+    elimination_done:
+        __syncthreads();
+        // X[q_k][m] = a[k][q_m]
+        if (tid < n && s_done == 0) s_qinv[s_q[tid]] = tid;
+        __syncthreads();
+        if (owner && s_done == 0) {
+            const int m = s_qinv[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = i0 + r;
+                if (i < n) Xs[s_q[i] * n + m] = v[r];
             }
-            __syncthreads();
-            const int st = s_conv;
-            if (st) break;
-            ++sweeps;
-            // x += X r  (FP32 products, 8 threads per row)
-            {
-                const int i = tid >> 3, part = tid & 7;
-                float acc = 0.0f;
-                if (i < n)
-                    for (int jj = part; jj < n; jj += 8) acc = fmaf(Xs[i * n + jj], s_rf[jj], acc);
-                acc += __shfl_xor_sync(kFullMask, acc, 4);
-                acc += __shfl_xor_sync(kFullMask, acc, 2);
-                acc += __shfl_xor_sync(kFullMask, acc, 1);
-                if (part == 0 && i < n) s_x[i] += (double)acc;
+        }
+        __syncthreads();
+        if (s_done == 0) {
+            converged = refine_fp64(n, ldj, Js, Xs, s_scale, s_scale, F, s_x, s_rf, s_red, &s_conv, tolfac,
+                                    kRefineMax, false, &sweeps) == 1;
+            // keep an inverse that worked for the next Newton step
+            if (Xg != nullptr) {
+                if (converged) {
+                    for (int idx = tid; idx < n * n; idx += kGjThreads) Xg[idx] = Xs[idx];
+                    for (int i = tid; i < n; i += kGjThreads) Sg[i] = s_scale[i];
+                }
+                if (tid == 0) {
+                    *xstate = converged ? 1 : 0;
+                    if (xcount) xstate[1] += 1;  // counter of eliminations
+                }
             }
-            __syncthreads();
+        } else if (Xg != nullptr && tid == 0) {
+            *xstate = 0;
         }
     }
-    const bool converged = (s_done == 0) && (s_conv == 1);
     double* xres = work + n;
     if (converged) {
         if (tid < n) xres[tid] = s_x[tid];
@@ -1473,8 +1531,11 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, doubl
                                                            const double* __restrict__ F,
                                                            const XTab* __restrict__ xtab, double* __restrict__ coef,
                                                            double rho, double* __restrict__ work,
-                                                           double* __restrict__ stats, int* __restrict__ status) {
-    newton_reg_block<R>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status);
+                                                           double* __restrict__ stats, int* __restrict__ status,
+                                                           float* __restrict__ Xinv, double* __restrict__ Sinv,
+                                                           int* __restrict__ xstate) {
+    // a plan's xstate word is followed by its two solver counters
+    newton_reg_block<R>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status, Xinv, Sinv, xstate, true);
 }
 
 // One block per problem of a batch; afterwards thread 0 advances the problem's
@@ -1490,7 +1551,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg_batched(BatchProblem*
     if (!B.active) return;
     const double rho = B.iter < n_relax ? rho_relax : 1.0;
     newton_reg_block<R>(B.t.c, B.J, B.As, B.rowinfo, B.F, B.xtab, coef_base + B.coef_off, rho, B.work, B.stats,
-                        B.status);
+                        B.status, B.Xinv, B.Sinv, &B.xstate, false);
     __syncthreads();
     if (threadIdx.x == 0) {
         B.iter += 1;
@@ -1647,7 +1708,9 @@ cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const 
 }
 
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
-                             double* work, float* As, double2* rowinfo, double* stats, int* status, cudaStream_t s) {
+                             double* work, float* As, double2* rowinfo, double* stats, int* status, cudaStream_t s,
+                             float* Xinv, double* Sinv, int* xstate) {
+    if (!Xinv || !Sinv || !xstate) Xinv = nullptr, Sinv = nullptr, xstate = nullptr;
     const int n = c.n;
     cudaError_t e = cudaSuccess;
     if (n <= 128) {
@@ -1660,7 +1723,8 @@ cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const 
 #define DSE_LAUNCH_REG(RR)                                                                                   \
     e = cudaFuncSetAttribute(k_newton_reg<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
     if (e != cudaSuccess) return e;                                                                          \
-    k_newton_reg<RR><<<1, kGjThreads, smem, s>>>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status);
+    k_newton_reg<RR><<<1, kGjThreads, smem, s>>>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status, Xinv, \
+                                                 Sinv, xstate);
         if (R <= 1) { DSE_LAUNCH_REG(1) }
         else if (R <= 2) { DSE_LAUNCH_REG(2) }
         else if (R <= 4) { DSE_LAUNCH_REG(4) }

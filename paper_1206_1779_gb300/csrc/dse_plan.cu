@@ -36,6 +36,9 @@ struct dse_plan {
     SeriesRec* stab;    // series table (read by the FP64 quadrature kernel when use_series_table(N))
     float* As;          // row-scaled FP32 copy of J (Newton step)
     double2* rowinfo;   // row scales and row sums (Newton step)
+    float* Xinv;        // FP32 inverse of the last eliminated Newton step, reused while it suffices
+    double* Sinv;       // its row scales
+    int* xstate;        // 1 while Xinv is usable, then 2 counters: eliminations, reuses (after the status word)
     double* aux;        // derivative scratch: dPi rows, dressing-VJP partial sums
     // finite-difference Newton matrix: a batch of 2n copies of the problem
     dse_batch* fd_batch;
@@ -301,10 +304,12 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_stab = off; off = align_up(off + sizeof(SeriesRec) * kSeriesM);
     size_t o_As = off; off = align_up(off + sizeof(float) * (size_t)n * n);
     size_t o_ri = off; off = align_up(off + sizeof(double2) * n);
+    size_t o_X = off; off = align_up(off + (n <= 128 ? sizeof(float) * (size_t)n * n : 0));
+    size_t o_S = off; off = align_up(off + sizeof(double) * n);
     const size_t n_aux_a = 2 * (size_t)(Rc + 2) + (size_t)n + 3;
     const size_t n_aux_b = (size_t)kDressingVjpMaxSplits * ((size_t)n + 1);
     size_t o_aux = off; off = align_up(off + sizeof(double) * (n_aux_a > n_aux_b ? n_aux_a : n_aux_b));
-    size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + sizeof(int));
+    size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + 4 * sizeof(int));
     // Gauss-Legendre scratch (set-up only): nodes/weights for both rules and 1/k
     size_t o_gl = off; off = align_up(off + sizeof(double) * (2 * (size_t)nrule + 2 * (size_t)na + gmax + 2));
 
@@ -332,9 +337,12 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->stab = (SeriesRec*)(base + o_stab);
     pl->As = (float*)(base + o_As);
     pl->rowinfo = (double2*)(base + o_ri);
+    pl->Xinv = n <= 128 ? (float*)(base + o_X) : nullptr;
+    pl->Sinv = (double*)(base + o_S);
     pl->aux = (double*)(base + o_aux);
     pl->stats = (double*)(base + o_misc);
     pl->status = (int*)(base + o_misc + 4 * sizeof(double));
+    pl->xstate = pl->status + 1;
     double* gl = (double*)(base + o_gl);
     double* glr = gl;
     double* gwr = glr + nrule;
@@ -424,7 +432,8 @@ int newton_step_impl(dse_plan* plan, double* d_coeffs, double rho, double* h_sta
     int st = build_newton(plan, d_coeffs, plan->J, plan->F, f64_residual);
     if (st) return st;
     cudaError_t e = launch_lu_newton(plan->c, plan->J, plan->F, plan->xtab, d_coeffs, rho, plan->work, plan->As,
-                                     plan->rowinfo, plan->stats, plan->status, plan->stream);
+                                     plan->rowinfo, plan->stats, plan->status, plan->stream, plan->Xinv, plan->Sinv,
+                                     plan->xstate);
     plan->launches += plan->c.n <= 128 ? 2 : 1;
     if (e != cudaSuccess) return DSE_ERR_CUDA;
     return read_status(plan, h_stats);
@@ -448,6 +457,8 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
     const double kSwitch = 1e-5;
     bool f64_res = plan->prob.precision == 0;
     double prev = INFINITY;
+    // every solve starts without a kept inverse, so its steps depend on its input alone
+    if (cudaMemsetAsync(plan->xstate, 0, sizeof(int), plan->stream) != cudaSuccess) return DSE_ERR_CUDA;
     for (; it < max_iter; ++it) {
         const double rho = it < n_relax ? rho_relax : 1.0;
         const int s = newton_step_impl(plan, d_coeffs, rho, st3, f64_res);
@@ -659,6 +670,17 @@ int dse_plan_counters(dse_plan* plan, long long* h_launches, int* h_timed, doubl
     if (h_launches) *h_launches = plan->launches + fd_launches;
     if (h_timed) *h_timed = plan->n_ev;
     if (h_timed_ms) *h_timed_ms = total;
+    return DSE_OK;
+}
+
+int dse_plan_solver_counters(dse_plan* plan, int* h_eliminations, int* h_reused) {
+    if (!plan) return DSE_ERR_ARG;
+    int v[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(v, plan->xstate + 1, sizeof(v), cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    if (h_eliminations) *h_eliminations = v[0];
+    if (h_reused) *h_reused = v[1];
     return DSE_OK;
 }
 

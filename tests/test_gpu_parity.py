@@ -193,6 +193,47 @@ def test_newton_step_parity(dse, oracle, inputs, name):
         assert sg[3] == -1
 
 
+def step_residual_ok(J, F, d, c0, c1, tol=1e-13):
+    """Row-equilibrated residual of J d = F (extended precision) within tol of a
+    backward-stable solve, allowing for the rounding of the update: d = c0 - c1 is
+    read back from the updated coefficients, so it carries up to 2^-52 max(|c0|, |c1|)
+    per component.  Returns (ok, worst ratio)."""
+    Jl, Fl, dl = (np.asarray(a, dtype=np.longdouble) for a in (J, F, d))
+    s = 1.0 / np.sum(np.abs(Jl), axis=1)
+    r = np.abs(s * (Fl - Jl @ dl))
+    ulp = np.asarray(np.maximum(np.abs(c0), np.abs(c1)) * 2.0 ** -52, dtype=np.longdouble)
+    bound = tol * np.max(np.abs(dl)) + s * (np.abs(Jl) @ ulp)
+    ratio = float(np.max(r / bound))
+    return ratio <= 1.0, ratio
+
+
+@pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64"])
+def test_newton_steps_with_kept_inverse(dse, inputs, name):
+    # every step of a Newton iteration solves the step's own J, F to a backward-stable
+    # residual: the steps that reuse the inverse kept from an earlier elimination as
+    # well as the eliminating ones, and late steps do reuse it
+    p = inputs.workload_problem(name)
+    c = inputs.starting_guess(p, seed=0)
+    steps = 0
+    with dse.Plan(p) as plan:
+        ct = to_dev(c)
+        for _ in range(30):
+            J, F = plan.newton_matrix(ct)
+            J, F = to_host(J), to_host(F)
+            c0 = to_host(ct)
+            sg = plan.newton_step(ct)
+            steps += 1
+            c1 = to_host(ct)
+            ok, ratio = step_residual_ok(J, F, c0 - c1, c0, c1)
+            assert ok, (steps, ratio)
+            assert 1 <= sg[3] <= 12, sg
+            if sg[1] < 1e-11:
+                break
+        elim, reused = plan.solver_counters()
+    assert sg[1] < 1e-11
+    assert elim + reused == steps and elim >= 1 and reused >= 1, (elim, reused, steps)
+
+
 def test_solve_parity(dse, oracle, inputs):
     p = inputs.workload_problem("newton_step_n16")
     c0 = inputs.starting_guess(p, seed=0)
