@@ -42,24 +42,44 @@ L2_FLUSH_BYTES = 256 << 20
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes per
 # clock per SM (1.25 TFLOP/s nominal) at the sampled SM clock under load.
 N_SM = 152
-FP64_FLOP_PER_CLK_SM = 4.0
+FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA lanes per SM per clock
+FP32_INST_PER_CLK_SM = 128.0   # 128 FP32 lanes per SM per clock
+DF_FMA_FP32_INST = 12          # one double-float multiply-add: exact product (2), cross terms (2), exact sum (6), lower part (2)
+DF_MULSUB_FP32_INST = 15       # one double-float a b - d with renormalisation
 
 
 SERIES_TABLE_N = (24, 128)  # the kernel reads ln G(z), ln Z(z) from the series table for these N
 SERIES_TABLE_DEGREE = 15    # degree of the table's local polynomials
 
 
-def flops_per_triple(N: int) -> float:
-    """Algorithmic FP64 work of the hot kernel per (x, y, theta) triple, counting an
-    FMA as 2 flops (log, exp and division counted separately, not here): the T_j
-    recurrence (N FMA) and three derivative sums weight * phi_j(z) (3N FMA), and
-    ~50 flops of geometry, kernels and integrands.  The dressing functions at z:
+def work_per_triple(N: int):
+    """Algorithmic work of the hot kernel per (x, y, theta) triple in the Newton-matrix
+    mode: (FP64 flops, double-float multiply-adds, double-float multiply-subtracts),
+    an FMA counted as 2 flops.
+
+    FP64: ~50 flops of geometry, kernels, integrands, ln z and 1/z; 9 for adding the
+    double-float tile sums to the FP64 accumulators.  The dressing functions at z:
     for N in SERIES_TABLE_N read from the table (u, then Horner sums of degree 15
-    for Z, G and W: 93 flops, no exponential), else the two series summed per
-    triple (2N FMA) and three exponentials."""
+    for Z, G and W: 93 flops) with T_j(z) from the stride-4 FP64 recurrence (N/4
+    steps of two FMAs: N flops, plus 8 for T_2, T_3, T_4); else the two series and
+    the recurrence summed per triple (3N FMA: 6N flops).
+    Double-float: the three derivative sums weight * phi_j(z) (3N multiply-adds) and,
+    on the table path, T_4i+2 and T_4i+3 from the anchors (N/2 multiply-subtracts)."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
-        return 8.0 * N + 3.0 + 6.0 * SERIES_TABLE_DEGREE + 50.0
-    return 12.0 * N + 50.0
+        return N + 8.0 + 3.0 + 6.0 * SERIES_TABLE_DEGREE + 50.0 + 9.0, 3.0 * N, N / 2.0
+    return 6.0 * N + 50.0 + 9.0, 3.0 * N, 0.0
+
+
+def roofline_model(N: int, triples: int, sm_mhz: float):
+    """Lower bound on one launch's duration (s) with the FP64 and FP32 pipes each at
+    their peak and not overlapped, and the FP64-equivalent flops of the launch
+    (a double-float multiply-add or -subtract counted as one FP64 FMA)."""
+    f64, dfma, dms = work_per_triple(N)
+    clk = sm_mhz * 1e6
+    t_fp64 = triples * f64 / (N_SM * FP64_FLOP_PER_CLK_SM * clk)
+    t_fp32 = triples * (dfma * DF_FMA_FP32_INST + dms * DF_MULSUB_FP32_INST) / (N_SM * FP32_INST_PER_CLK_SM * clk)
+    flops = triples * (f64 + 2.0 * (dfma + dms))
+    return t_fp64 + t_fp32, flops, t_fp64, t_fp32
 
 
 class ClockSampler:
@@ -220,14 +240,16 @@ def run_gb300(args):
     value = units / (total_ms * 1e-3)
     solves_per_s = world * args.steps / (total_ms * 1e-3)
 
-    # roofline of the hot kernel: algorithmic FP64 flops per launch / event time
+    # roofline of the hot kernel: FP64-equivalent algorithmic flops per launch /
+    # event time, against the rate at the model's lower bound on the duration
     Rt = N + 1 + (1 if p["x_G"] > 0 else 0)
     triples = Rt * nr * na
-    flops_launch = triples * flops_per_triple(N)
     avg_launch_ms = timed_ms / max(n_timed, 1)
-    achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    t_min, flops_launch, t_fp64, t_fp32 = roofline_model(N, triples, sm_mhz)
+    achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
+    peak = flops_launch / t_min / 1e12
+    f64_pt, dfma_pt, dms_pt = work_per_triple(N)
     traffic = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
 
     # mixed precision (FP32 integrands for the Newton matrix, FP64 residual)
@@ -286,11 +308,16 @@ def run_gb300(args):
             "plan_create_s": t_plan,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_triple (FP64 radial x angular quadrature)",
-                         "peak_source": "derived: 152 SMs x 4 FP64 flop/clk/SM at the sampled SM clock",
-                         "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms,
-                         "flops_per_triple": flops_per_triple(N), "triples_per_launch": triples,
-                         "direct_series_equivalent_tflops": triples * (12.0 * N + 50.0) / (avg_launch_ms * 1e-3) / 1e12},
+                         "kernel": "k_triple (radial x angular quadrature: FP64 integrands, double-float derivative sums)",
+                         "peak_source": ("derived: FP64-equivalent flops of a launch over its lower-bound duration "
+                                         "t_fp64 + t_fp32, with 152 SMs x 4 FP64 flop/clk and 152 SMs x 128 FP32 "
+                                         "inst/clk at the sampled SM clock"),
+                         "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms, "triples_per_launch": triples,
+                         "fp64_flops_per_triple": f64_pt, "double_float_fma_per_triple": dfma_pt,
+                         "double_float_mulsub_per_triple": dms_pt,
+                         "t_fp64_bound_ms": t_fp64 * 1e3, "t_fp32_bound_ms": t_fp32 * 1e3,
+                         "fp64_achieved_tflops": triples * f64_pt / (avg_launch_ms * 1e-3) / 1e12,
+                         "fp64_peak_tflops": N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(c0.nbytes + tt.nbytes),
                     "d2h_bytes_per_step": int(c0.nbytes + tt.nbytes)},
             "gpu_launches": int(launches1 - launches0),

@@ -16,10 +16,18 @@
 // alone and is contracted from Upart afterwards.
 //
 // Data flow per tile of BT triples (one warp = 32 angular nodes of one radial node):
-//   phase A: each thread builds its triple, stores phi_j(z) (j < N) into a
-//            shared-memory row and its three weights;
+//   phase A: each thread builds its triple in FP64, stores phi_j(z) (j < N) into
+//            a shared-memory row and its three weights;
 //   phase B: thread (group g, coefficient j) accumulates weight * phi_j(z) over
-//            its group's rows: three FP64 FMAs per (triple, j).
+//            its group's rows: three multiply-adds per (triple, j).
+// Phase B runs in double-float arithmetic (a value is an unevaluated sum hi + lo
+// of two FP32 numbers, 48 significant bits; Dekker's exact product and Knuth's
+// exact sum), because this GPU issues FP32 at 64 times its FP64 rate: the FP64
+// recurrence values and weights are split exactly into (hi, lo) pairs (the
+// weights scaled by a power of two per tile, so that no tile over- or
+// underflows FP32), each group sums at most one tile's rows in double-float,
+// and the tile sums are added to FP64 accumulators.  The residual (the angular
+// sums of the weights) stays in FP64 throughout.
 // The block's coefficient vector lives in shared memory (broadcast reads).
 #include "dse_internal.cuh"
 
@@ -31,6 +39,58 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 : 64; }
+
+// ---- double-float helpers (phase B) ----
+// x 2^-sh as hi + lo: hi keeps the leading 24 significant bits of x (by
+// truncation, so x - hi is exact), lo the next 24 (rounded).  Values below the
+// FP32 normal range after scaling are flushed to zero; Inf/NaN give NaN.
+__device__ __forceinline__ float2 df_split(double x, int sh) {
+    const unsigned hb = (unsigned)__double2hiint(x), lb = (unsigned)__double2loint(x);
+    const int e = (int)((hb >> 20) & 0x7ffu);
+    if (e == 0x7ff) return make_float2(__int_as_float(0x7fc00000), 0.0f);
+    const int ef = e - sh - 896;  // biased FP32 exponent of x 2^-sh
+    if (e == 0 || ef < 1) return make_float2(0.0f, 0.0f);  // zero, subnormal or flushed
+    const unsigned sign = hb & 0x80000000u;
+    const float hi = __int_as_float((int)(sign | ((unsigned)ef << 23) | ((hb & 0xfffffu) << 3) | (lb >> 29)));
+    // the 29 bits below hi: r 2^(ef - 127 - 52)
+    const float lo = __uint2float_rn(lb & 0x1fffffffu) * 0x1p-52f * __int_as_float(ef << 23);
+    return make_float2(hi, __int_as_float(__float_as_int(lo) | (int)sign));
+}
+
+// c += a b in double-float: exact product of the leading parts (FMA), the cross
+// terms in FP32, the exact sum of c.x and the product's leading part; the lower
+// parts are collected in c.y (renormalised by df_renorm).
+__device__ __forceinline__ void df_fma(float2& c, const float2 a, const float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float sm = c.x + p;
+    const float bb = sm - c.x;
+    const float err = (c.x - (sm - bb)) + (p - bb);
+    c.y += err + e;
+    c.x = sm;
+}
+
+// a b - d in double-float (renormalised)
+__device__ __forceinline__ float2 df_mulsub(const float2 a, const float2 b, const float2 d) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float sm = p - d.x;
+    const float bb = sm - p;
+    const float err = (p - (sm - bb)) + (-d.x - bb);
+    const float lo = (e + err) - d.y;
+    const float hi = sm + lo;
+    return make_float2(hi, lo - (hi - sm));
+}
+
+__device__ __forceinline__ void df_renorm(float2& c) {
+    const float sm = c.x + c.y;
+    c.y = c.y - (sm - c.x);
+    c.x = sm;
+}
 
 __host__ __device__ inline int groups_for(int N, int BT) {
     const int nact = N < BT ? N : BT;
@@ -45,7 +105,9 @@ __host__ __device__ inline size_t tile_doubles(bool full, int N, int BT) {
 }
 
 __host__ __device__ inline size_t smem_doubles(bool full, int N, int BT) {
-    return tile_doubles(full, N, BT) + 3u * (size_t)BT + 2u * (size_t)N + 4u;
+    // tile rows, 3 BT weights (FP64, then their double-float pairs), 2 N
+    // coefficients, 4 boundary sums, 3 x 8 per-warp exponent maxima
+    return tile_doubles(full, N, BT) + 6u * (size_t)BT + 2u * (size_t)N + 4u + 12u;
 }
 
 // One block's work: row rt, radial split ks of the problem in A.  smem holds
@@ -56,10 +118,13 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     const int N = c.N;
     const int ldT = N + 1;
     double* sT = smem;
+    float2* sT2 = reinterpret_cast<float2*>(smem);  // phi_j(z) rows as double-float pairs
     double* sh = smem + tile_doubles(FULL, N, BT);
-    double* sa = sh + 3 * BT;
+    float2* sh2 = reinterpret_cast<float2*>(sh + 3 * BT);  // the weights as pairs
+    double* sa = sh + 6 * BT;
     double* sb = sa + N;
     double* sbnd = sb + N;  // ln Z(s=1), ln G(s=1), ln Z(s=-1), ln G(s=-1) (table path)
+    int* sex = reinterpret_cast<int*>(sbnd + 4);  // [3][8] per-warp maxima of the weights' exponents
     constexpr int WARPS = BT / 32;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -90,6 +155,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     double acc[3][NJ];
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) acc[0][jj] = acc[1][jj] = acc[2][jj] = 0.0;
+    static_assert(WARPS <= 8, "per-warp exponent maxima hold 8 warps");
 
     __syncthreads();
     if (A.stab) {
@@ -112,7 +178,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     for (int base = 0; base < nunits; base += WARPS) {
         const int u = base + warp;
         double hQ = 0.0, hM = 0.0, hG = 0.0;
-        double* Trow = sT + (size_t)tid * ldT;
+        float2* Trow = sT2 + (size_t)tid * ldT;
         bool live = false;
         int k = 0, ch = 0;
         if (u < nunits) {
@@ -184,7 +250,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                             t1 = t2;
                             lg = fma(sb[j], t2, lg);
                             lzz = fma(sa[j], t2, lzz);
-                            if (FULL) Trow[j] = t2;
+                            if (FULL) Trow[j] = df_split(t2, 0);
                         }
                     }
                     if (outside) {
@@ -205,17 +271,40 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     }
                 }
                 if (FULL) {
-                    Trow[0] = 0.5;
-                    if (N > 1) Trow[1] = s;
+                    Trow[0] = make_float2(0.5f, 0.0f);
+                    if (N > 1) Trow[1] = df_split(s, 0);
                     if (A.stab) {
-                        // T_j(z) for the derivative sums (the direct path stored them above)
-                        double t0 = 1.0, t1 = s;
-                        const double s2x = 2.0 * s;
-                        for (int j = 2; j < N; ++j) {
-                            const double t2 = fma(s2x, t1, -t0);
-                            t0 = t1;
-                            t1 = t2;
-                            Trow[j] = t2;
+                        // T_j(z) for the derivative sums (the direct path stored them
+                        // above): T_4i and T_4i+1 by the FP64 recurrence of stride 4,
+                        // X_(i+1) = 2 T_4 X_i - X_(i-1) (from T_(m+4) + T_(m-4) = 2 T_4 T_m),
+                        // and T_4i+2, T_4i+3 by two steps of T_(j+1) = 2 s T_j - T_(j-1) in
+                        // double-float from them
+                        const double T2 = fma(2.0 * s, s, -1.0);
+                        const double T3 = fma(2.0 * s, T2, -s);
+                        const double T4 = fma(2.0 * T2, T2, -1.0);
+                        const double c4 = 2.0 * T4;
+                        const float2 fs = df_split(s, 0);
+                        const float2 s2 = make_float2(2.0f * fs.x, 2.0f * fs.y);
+                        double a0 = T4, a1 = 1.0;  // T_(4i-4), T_4i
+                        double b0 = T3, b1 = s;    // T_(4i-3), T_(4i+1)
+                        for (int j0 = 0; j0 < N; j0 += 4) {
+                            const float2 fa = df_split(a1, 0);
+                            const float2 fb = df_split(b1, 0);
+                            if (j0 > 0) {
+                                Trow[j0] = fa;
+                                if (j0 + 1 < N) Trow[j0 + 1] = fb;
+                            }
+                            if (j0 + 2 < N) {
+                                const float2 t2 = df_mulsub(s2, fb, fa);
+                                Trow[j0 + 2] = t2;
+                                if (j0 + 3 < N) Trow[j0 + 3] = df_mulsub(s2, t2, fb);
+                            }
+                            const double an = fma(c4, a1, -a0);
+                            a0 = a1;
+                            a1 = an;
+                            const double bn = fma(c4, b1, -b0);
+                            b0 = b1;
+                            b1 = bn;
                         }
                     }
                 }
@@ -237,7 +326,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
             }
         }
         if (FULL && !live) {
-            for (int j = 0; j < N; ++j) Trow[j] = 0.0;
+            for (int j = 0; j < N; ++j) Trow[j] = make_float2(0.0f, 0.0f);
         }
         // angular sums over the warp's 32 nodes (same radial node for the whole warp)
         double rQ = hQ, rM = hM, rG = hG;
@@ -254,26 +343,71 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
             up[2] = rG;
         }
         if (FULL) {
-            sh[tid] = hQ;
-            sh[BT + tid] = hM;
-            sh[2 * BT + tid] = hG;
+            // per-tile power-of-two scale of each weight kind: the largest exponent
+            {
+                const unsigned eq = ((unsigned)__double2hiint(hQ) >> 20) & 0x7ffu;
+                const unsigned em = ((unsigned)__double2hiint(hM) >> 20) & 0x7ffu;
+                const unsigned eg = ((unsigned)__double2hiint(hG) >> 20) & 0x7ffu;
+                const unsigned mq = __reduce_max_sync(kFullMask, eq);
+                const unsigned mm = __reduce_max_sync(kFullMask, em);
+                const unsigned mg = __reduce_max_sync(kFullMask, eg);
+                if (lane == 0) {
+                    sex[warp] = (int)mq;
+                    sex[8 + warp] = (int)mm;
+                    sex[16 + warp] = (int)mg;
+                }
+            }
+            __syncthreads();
+            int Eq = sex[0], Em = sex[8], Eg = sex[16];
+#pragma unroll
+            for (int w = 1; w < WARPS; ++w) {
+                Eq = max(Eq, sex[w]);
+                Em = max(Em, sex[8 + w]);
+                Eg = max(Eg, sex[16 + w]);
+            }
+            // weights w 2^-(E - 1023): the largest lands in [1, 2)
+            sh2[tid] = df_split(hQ, Eq - 1023);
+            sh2[BT + tid] = df_split(hM, Em - 1023);
+            sh2[2 * BT + tid] = df_split(hG, Eg - 1023);
             __syncthreads();
             if (bact) {
-                for (int m = mlo; m < mhi; ++m) {
-                    const double q = sh[m];
-                    const double mm = sh[BT + m];
-                    const double gg = sh[2 * BT + m];
-                    const double* Tm = sT + (size_t)m * ldT;
+                float2 ca[3][NJ];
 #pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) {
-                        const int j = jb + jj * nact;
-                        if (j < N) {
-                            const double t = Tm[j];
-                            acc[0][jj] = fma(q, t, acc[0][jj]);
-                            acc[1][jj] = fma(mm, t, acc[1][jj]);
-                            acc[2][jj] = fma(gg, t, acc[2][jj]);
+                for (int jj = 0; jj < NJ; ++jj) ca[0][jj] = ca[1][jj] = ca[2][jj] = make_float2(0.0f, 0.0f);
+                for (int m0 = mlo; m0 < mhi; m0 += 8) {
+                    const int m1 = min(mhi, m0 + 8);
+                    for (int m = m0; m < m1; ++m) {
+                        const float2 q = sh2[m];
+                        const float2 mm = sh2[BT + m];
+                        const float2 gg = sh2[2 * BT + m];
+                        const float2* Tm = sT2 + (size_t)m * ldT;
+#pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) {
+                            const int j = jb + jj * nact;
+                            if (j < N) {
+                                const float2 t = Tm[j];
+                                df_fma(ca[0][jj], q, t);
+                                df_fma(ca[1][jj], mm, t);
+                                df_fma(ca[2][jj], gg, t);
+                            }
                         }
                     }
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        df_renorm(ca[0][jj]);
+                        df_renorm(ca[1][jj]);
+                        df_renorm(ca[2][jj]);
+                    }
+                }
+                // tile sums into the FP64 accumulators, scaled back by 2^(E - 1023)
+                const double scq = __hiloint2double(Eq << 20, 0);
+                const double scm = __hiloint2double(Em << 20, 0);
+                const double scg = __hiloint2double(Eg << 20, 0);
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) {
+                    acc[0][jj] = fma((double)ca[0][jj].x + (double)ca[0][jj].y, scq, acc[0][jj]);
+                    acc[1][jj] = fma((double)ca[1][jj].x + (double)ca[1][jj].y, scm, acc[1][jj]);
+                    acc[2][jj] = fma((double)ca[2][jj].x + (double)ca[2][jj].y, scg, acc[2][jj]);
                 }
             }
             __syncthreads();
