@@ -72,6 +72,21 @@ __device__ __forceinline__ void df_fma(float2& c, const float2 a, const float2 b
     c.x = sm;
 }
 
+// f 2^(E - 1023) as a double, from the bits of f: the tile scale of phase B
+// folded into the exponent (zero and FP32 subnormals give 0, Inf/NaN or an
+// overflow give Inf/NaN).
+__device__ __forceinline__ double df_widen(float f, int E) {
+    const unsigned b = (unsigned)__float_as_int(f);
+    const int e8 = (int)((b >> 23) & 0xffu);
+    if (e8 == 0) return 0.0;
+    int e11 = e8 + E - 127;
+    if (e8 == 0xff || E == 0x7ff) e11 = 0x7ff;
+    if (e11 <= 0) return 0.0;
+    if (e11 > 0x7ff) e11 = 0x7ff;
+    const unsigned m = b & 0x7fffffu;
+    return __hiloint2double((int)((b & 0x80000000u) | ((unsigned)e11 << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // a b - d in double-float (renormalised)
 __device__ __forceinline__ float2 df_mulsub(const float2 a, const float2 b, const float2 d) {
     const float p = a.x * b.x;
@@ -104,10 +119,17 @@ __host__ __device__ inline size_t tile_doubles(bool full, int N, int BT) {
     return t > red ? t : red;
 }
 
+// Radial nodes whose per-node factors are formed together (by one warp) and
+// kept in shared memory, and the factors per node.
+constexpr int kRadGroup = 32;
+constexpr int kRadFactors = 8;
+
 __host__ __device__ inline size_t smem_doubles(bool full, int N, int BT) {
     // tile rows, 3 BT weights (FP64, then their double-float pairs), 2 N
-    // coefficients, 4 boundary sums, 3 x 8 per-warp exponent maxima
-    return tile_doubles(full, N, BT) + 6u * (size_t)BT + 2u * (size_t)N + 4u + 12u;
+    // coefficients, 4 boundary sums, 3 x 8 per-warp exponent maxima, the factors
+    // of a group of radial nodes
+    return tile_doubles(full, N, BT) + 6u * (size_t)BT + 2u * (size_t)N + 4u + 12u +
+           (size_t)kRadGroup * kRadFactors;
 }
 
 // One block's work: row rt, radial split ks of the problem in A.  smem holds
@@ -125,6 +147,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     double* sb = sa + N;
     double* sbnd = sb + N;  // ln Z(s=1), ln G(s=1), ln Z(s=-1), ln G(s=-1) (table path)
     int* sex = reinterpret_cast<int*>(sbnd + 4);  // [3][8] per-warp maxima of the weights' exponents
+    double* srad = sbnd + 16;                     // [kRadGroup][kRadFactors] radial-node factors
     constexpr int WARPS = BT / 32;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -175,7 +198,38 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
         __syncthreads();
     }
 
+    // (x, y) factors of the integrands, formed once per radial node instead of per
+    // triple: z = d + b2 sigma with d = (sqrt x - sqrt y)^2, b2 = 4 sqrt(xy);
+    // K = W_k y G(y) (hM = K w s4 G(z)/z, hG = K w s4 Z(z)/z^2); the quartic of the
+    // gluon-loop kernel times W_k W(y)/2 (hQ = w s2 W(z)/z^2 sum_i kQ_i sigma^i).
+    // A group of kRadGroup nodes spans whole tiles: kRadGroup nch is a multiple of WARPS.
+    const int group_units = kRadGroup * nch;
     for (int base = 0; base < nunits; base += WARPS) {
+        if (base % group_units == 0) {
+            __syncthreads();  // the previous group's factors are no longer read
+            if (warp == 0) {
+                const int kq = k0 + base / nch + lane;
+                if (kq < k1) {
+                    const Rad rd = A.rad[rad_offset(c, rt) + kq];
+                    const YTab yt = A.ytab[rad_offset(c, rt) + kq];
+                    const double d0 = row.sx - rd.sy;
+                    const double d = d0 * d0;
+                    const double b = 2.0 * row.sx * rd.sy;
+                    double* f = srad + lane * kRadFactors;
+                    f[0] = d;
+                    f[1] = 2.0 * b;
+                    f[2] = rd.W * yt.yG;
+                    const double dd = d * d, db = d * b, bb = b * b;
+                    const double h = 0.5 * rd.W * yt.Wy;
+                    f[3] = h * (7.5 * dd);
+                    f[4] = h * -(48.0 * dd + 18.0 * db + 12.0 * bb);
+                    f[5] = h * (48.0 * dd - 48.0 * db - 38.0 * bb);
+                    f[6] = h * (96.0 * db + 64.0 * bb);
+                    f[7] = h * (16.0 * bb);
+                }
+            }
+            __syncthreads();
+        }
         const int u = base + warp;
         double hQ = 0.0, hM = 0.0, hG = 0.0;
         float2* Trow = sT2 + (size_t)tid * ldT;
@@ -188,21 +242,19 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
             const int l = ch * 32 + lane;
             if (l < c.na) {
                 live = true;
-                const Rad rd = A.rad[rad_offset(c, rt) + k];
-                const YTab yt = A.ytab[rad_offset(c, rt) + k];
+                const double* f = srad + (kk % kRadGroup) * kRadFactors;
                 const Ang an = A.ang[l];
-                const double d0 = row.sx - rd.sy;
-                const double d = d0 * d0;
-                const double b = 2.0 * row.sx * rd.sy;
-                const double z = fma(2.0 * b, an.sig, d);
+                const double z = fma(f[1], an.sig, f[0]);
                 const double lz = log(z);
                 double s = (lz - c.L0) * c.invL1;
                 s = fmin(1.0, fmax(-1.0, s));
-                const double wgt = rd.W * an.w;
                 const double iz = 1.0 / z;
                 const double iz2 = iz * iz;
-                double Zz = 0.0, Gz = 0.0, Wv = 0.0;  // Z(z), G(z), W = (G(y)G(z))^p (Z(y)Z(z))^q
-                const bool outside = c.extrap == 0 && (z < c.eps2 || z > c.lam2);
+                double Zz = 0.0, Gz = 0.0, Wz = 0.0;  // Z(z), G(z), W(z) = G(z)^p Z(z)^q
+                // z > 0: the comparisons with eps2, lambda2 on the bit patterns
+                const long long zb = __double_as_longlong(z);
+                const bool outside =
+                    c.extrap == 0 && (zb < __double_as_longlong(c.eps2) || zb > __double_as_longlong(c.lam2));
                 if (A.stab && !outside) {
                     // Z(z), G(z), W(z) from the table: the interval by arccos in
                     // FP32, the polynomials in u = (s - mid) / half in FP64 (Horner)
@@ -227,7 +279,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         double ew = __ldg(&R->w[kSeriesP]);
 #pragma unroll
                         for (int kq = kSeriesP - 1; kq >= 0; --kq) ew = fma(ew, uu, __ldg(&R->w[kq]));
-                        Wv = yt.Wy * ew;
+                        Wz = ew;
                     }
                 } else {
                     double lg, lzz;
@@ -267,7 +319,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     if (ghost) Zz = exp(lzz);
                     if (gluon) {
                         Gz = exp(lg);
-                        Wv = exp(yt.pq + c.pG * lg + c.qZ * lzz);
+                        Wz = exp(c.pG * lg + c.qZ * lzz);
                     }
                 }
                 if (FULL) {
@@ -299,48 +351,45 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                                 Trow[j0 + 2] = t2;
                                 if (j0 + 3 < N) Trow[j0 + 3] = df_mulsub(s2, t2, fb);
                             }
-                            const double an = fma(c4, a1, -a0);
+                            const double an4 = fma(c4, a1, -a0);
                             a0 = a1;
-                            a1 = an;
+                            a1 = an4;
                             const double bn = fma(c4, b1, -b0);
                             b0 = b1;
                             b1 = bn;
                         }
                     }
                 }
-                if (ghost) hG = wgt * yt.yG * an.s4 * Zz * iz2;
+                const double Kw = f[2] * (an.w * an.s4);
+                if (ghost) hG = Kw * Zz * iz2;
                 if (gluon) {
-                    const double dd = d * d, db = d * b, bb = b * b;
-                    const double n0 = 7.5 * dd;
-                    const double n1 = -(48.0 * dd + 18.0 * db + 12.0 * bb);
-                    const double n2 = 48.0 * dd - 48.0 * db - 38.0 * bb;
-                    const double n3 = 96.0 * db + 64.0 * bb;
-                    const double n4 = 16.0 * bb;
                     const double sg = an.sig;
-                    const double num = fma(sg, fma(sg, fma(sg, fma(sg, n4, n3), n2), n1), n0);
-                    const double Q = 0.5 * num * iz2;
-                    const double M = rd.y * an.s2 * iz;
-                    hQ = wgt * an.s2 * Q * Wv;
-                    hM = wgt * an.s2 * M * yt.G * Gz;
+                    const double num = fma(sg, fma(sg, fma(sg, fma(sg, f[7], f[6]), f[5]), f[4]), f[3]);
+                    hQ = (an.w * an.s2) * iz2 * Wz * num;
+                    hM = Kw * iz * Gz;
                 }
             }
         }
         if (FULL && !live) {
             for (int j = 0; j < N; ++j) Trow[j] = make_float2(0.0f, 0.0f);
         }
-        // angular sums over the warp's 32 nodes (same radial node for the whole warp)
-        double rQ = hQ, rM = hM, rG = hG;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            rQ += __shfl_xor_sync(kFullMask, rQ, off);
-            rM += __shfl_xor_sync(kFullMask, rM, off);
-            rG += __shfl_xor_sync(kFullMask, rG, off);
-        }
-        if (u < nunits && lane == 0) {
-            double* up = A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3;
-            up[0] = rQ;
-            up[1] = rM;
-            up[2] = rG;
+        // angular sums over the warp's 32 nodes (same radial node for the whole
+        // warp) of (hQ, hM, hG) by halving exchanges, 6 FP64 additions per lane:
+        // lanes 0-15 go on with (hQ, hM), lanes 16-31 with (hG, 0); then lanes with
+        // bit 3 set with the second of the two; then three butterfly steps.  The
+        // sums end in lanes 0 (hQ), 8 (hM) and 16 (hG).
+        {
+            const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+            const double k0 = (h16 ? hG : hQ) + __shfl_xor_sync(kFullMask, h16 ? hQ : hG, 16);
+            const double k1 = (h16 ? 0.0 : hM) + __shfl_xor_sync(kFullMask, h16 ? hM : 0.0, 16);
+            double v = (h8 ? k1 : k0) + __shfl_xor_sync(kFullMask, h8 ? k0 : k1, 8);
+            v += __shfl_xor_sync(kFullMask, v, 4);
+            v += __shfl_xor_sync(kFullMask, v, 2);
+            v += __shfl_xor_sync(kFullMask, v, 1);
+            if (u < nunits && (lane & 7) == 0 && lane < 24) {
+                double* up = A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3;
+                up[lane >> 3] = v;
+            }
         }
         if (FULL) {
             // per-tile power-of-two scale of each weight kind: the largest exponent
@@ -400,14 +449,11 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     }
                 }
                 // tile sums into the FP64 accumulators, scaled back by 2^(E - 1023)
-                const double scq = __hiloint2double(Eq << 20, 0);
-                const double scm = __hiloint2double(Em << 20, 0);
-                const double scg = __hiloint2double(Eg << 20, 0);
 #pragma unroll
                 for (int jj = 0; jj < NJ; ++jj) {
-                    acc[0][jj] = fma((double)ca[0][jj].x + (double)ca[0][jj].y, scq, acc[0][jj]);
-                    acc[1][jj] = fma((double)ca[1][jj].x + (double)ca[1][jj].y, scm, acc[1][jj]);
-                    acc[2][jj] = fma((double)ca[2][jj].x + (double)ca[2][jj].y, scg, acc[2][jj]);
+                    acc[0][jj] += df_widen(ca[0][jj].x, Eq) + df_widen(ca[0][jj].y, Eq);
+                    acc[1][jj] += df_widen(ca[1][jj].x, Em) + df_widen(ca[1][jj].y, Em);
+                    acc[2][jj] += df_widen(ca[2][jj].x, Eg) + df_widen(ca[2][jj].y, Eg);
                 }
             }
             __syncthreads();
