@@ -69,16 +69,23 @@ struct XTab { double lG, lZ, G, Z, Ginv, Zinv, pad0, pad1; };
 // recurrence.  With interval width h = pi/kSeriesM the fit error is
 // ~ (N h/4)^(P+1)/(P+1)! relative: below 1e-19 for N <= 128, so the FP64
 // quadrature kernel reads the table for kSeriesMinN <= N <= kSeriesMaxN in place
-// of the per-triple series sums and exponentials.
+// of the per-triple series sums and exponentials.  The leading kSeriesLead
+// coefficients are FP64; the rest, whose terms are small next to the leading ones
+// on an interval (~(N h/4)^k/k! relative for a smooth function), are stored as
+// double-float pairs and summed on the FP32 pipe.
 constexpr int kSeriesM = 256;
 constexpr int kSeriesP = 15;
 constexpr int kSeriesQ = kSeriesP + 1;
+constexpr int kSeriesLead = 4;
+constexpr int kSeriesTail = kSeriesQ - kSeriesLead;
 constexpr int kSeriesMinN = 24;
 constexpr int kSeriesMaxN = 128;
 struct SeriesRec {
     double mid, invhalf;
-    double2 e[kSeriesQ];  // (Z, G)
-    double w[kSeriesQ];   // W = G^p Z^q
+    double2 e[kSeriesLead];     // (Z, G), coefficients 0 .. kSeriesLead - 1
+    double w[kSeriesLead];      // W = G^p Z^q
+    float4 et[kSeriesTail];     // (Z hi, Z lo, G hi, G lo), coefficients kSeriesLead .. kSeriesP
+    float2 wt[kSeriesTail];     // (W hi, W lo)
 };
 __host__ __device__ inline bool use_series_table(int N) { return N >= kSeriesMinN && N <= kSeriesMaxN; }
 

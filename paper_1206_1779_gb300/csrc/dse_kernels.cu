@@ -347,9 +347,18 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     double mono = 0.0;
     for (int j = q; j < kSeriesQ; ++j) mono = fma(sc[f][il][j], tcoef[j][q], mono);
     SeriesRec& R = tab[i];
-    if (f == 0) R.e[q].x = mono;
-    else if (f == 1) R.e[q].y = mono;
-    else R.w[q] = mono;
+    if (q < kSeriesLead) {
+        if (f == 0) R.e[q].x = mono;
+        else if (f == 1) R.e[q].y = mono;
+        else R.w[q] = mono;
+    } else {
+        // double-float pair: hi rounded to FP32, lo the rounded remainder
+        const float hi = (float)mono;
+        const float lo = (float)(mono - (double)hi);
+        float* t = f < 2 ? &R.et[q - kSeriesLead].x + 2 * f : &R.wt[q - kSeriesLead].x;
+        t[0] = hi;
+        t[1] = lo;
+    }
     if (f == 0 && q == 0) {
         R.mid = mid;
         R.invhalf = 1.0 / half;

@@ -87,6 +87,20 @@ __device__ __forceinline__ double df_widen(float f, int E) {
     return __hiloint2double((int)((b & 0x80000000u) | ((unsigned)e11 << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// a b + d in double-float (renormalised)
+__device__ __forceinline__ float2 df_muladd(const float2 a, const float2 b, const float2 d) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float sm = p + d.x;
+    const float bb = sm - p;
+    const float err = (p - (sm - bb)) + (d.x - bb);
+    const float lo = (e + err) + d.y;
+    const float hi = sm + lo;
+    return make_float2(hi, lo - (hi - sm));
+}
+
 // a b - d in double-float (renormalised)
 __device__ __forceinline__ float2 df_mulsub(const float2 a, const float2 b, const float2 d) {
     const float p = a.x * b.x;
@@ -263,11 +277,22 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     const SeriesRec* R = A.stab + it;
                     const double2 mh = __ldg(reinterpret_cast<const double2*>(R));
                     const double uu = (s - mh.x) * mh.y;
+                    // Horner: the tail (degree kSeriesLead .. kSeriesP) in double-float,
+                    // the leading coefficients in FP64
+                    const float2 uf = df_split(uu, 0);
                     if (ghost || gluon) {
-                        const double2 top = __ldg(&R->e[kSeriesP]);
-                        double ez = top.x, eg = top.y;
+                        const float4 top = __ldg(&R->et[kSeriesTail - 1]);
+                        float2 tz = make_float2(top.x, top.y), tg = make_float2(top.z, top.w);
 #pragma unroll
-                        for (int kq = kSeriesP - 1; kq >= 0; --kq) {
+                        for (int kq = kSeriesTail - 2; kq >= 0; --kq) {
+                            const float4 ck = __ldg(&R->et[kq]);
+                            tz = df_muladd(tz, uf, make_float2(ck.x, ck.y));
+                            tg = df_muladd(tg, uf, make_float2(ck.z, ck.w));
+                        }
+                        double ez = df_widen(tz.x, 1023) + df_widen(tz.y, 1023);
+                        double eg = df_widen(tg.x, 1023) + df_widen(tg.y, 1023);
+#pragma unroll
+                        for (int kq = kSeriesLead - 1; kq >= 0; --kq) {
                             const double2 ck = __ldg(&R->e[kq]);
                             ez = fma(ez, uu, ck.x);
                             eg = fma(eg, uu, ck.y);
@@ -276,9 +301,12 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         Gz = eg;
                     }
                     if (gluon) {
-                        double ew = __ldg(&R->w[kSeriesP]);
+                        float2 tw = __ldg(&R->wt[kSeriesTail - 1]);
 #pragma unroll
-                        for (int kq = kSeriesP - 1; kq >= 0; --kq) ew = fma(ew, uu, __ldg(&R->w[kq]));
+                        for (int kq = kSeriesTail - 2; kq >= 0; --kq) tw = df_muladd(tw, uf, __ldg(&R->wt[kq]));
+                        double ew = df_widen(tw.x, 1023) + df_widen(tw.y, 1023);
+#pragma unroll
+                        for (int kq = kSeriesLead - 1; kq >= 0; --kq) ew = fma(ew, uu, __ldg(&R->w[kq]));
                         Wz = ew;
                     }
                 } else {
