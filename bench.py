@@ -50,6 +50,7 @@ DF_MULSUB_FP32_INST = 15       # one double-float a b - d with renormalisation
 
 SERIES_TABLE_N = (24, 128)  # the kernel reads ln G(z), ln Z(z) from the series table for these N
 SERIES_TABLE_DEGREE = 15    # degree of the table's local polynomials
+SERIES_TABLE_LEAD = 4       # leading coefficients summed in FP64 (the rest in double-float)
 
 
 def work_per_triple(N: int):
@@ -59,14 +60,18 @@ def work_per_triple(N: int):
 
     FP64: ~50 flops of geometry, kernels, integrands, ln z and 1/z; 9 for adding the
     double-float tile sums to the FP64 accumulators.  The dressing functions at z:
-    for N in SERIES_TABLE_N read from the table (u, then Horner sums of degree 15
-    for Z, G and W: 93 flops) with T_j(z) from the stride-4 FP64 recurrence (N/4
-    steps of two FMAs: N flops, plus 8 for T_2, T_3, T_4); else the two series and
-    the recurrence summed per triple (3N FMA: 6N flops).
+    for N in SERIES_TABLE_N read from the table (u: 3 flops; for Z, G and W the
+    SERIES_TABLE_LEAD leading Horner steps in FP64, 2 flops each, and the widened
+    tail, 1) with T_j(z) from the stride-4 FP64 recurrence (N/4 steps of two FMAs:
+    N flops, plus 8 for T_2, T_3, T_4); else the two series and the recurrence summed
+    per triple (3N FMA: 6N flops).
     Double-float: the three derivative sums weight * phi_j(z) (3N multiply-adds) and,
-    on the table path, T_4i+2 and T_4i+3 from the anchors (N/2 multiply-subtracts)."""
+    on the table path, T_4i+2 and T_4i+3 from the anchors (N/2 multiply-subtracts) and
+    the three table tails (3 (SERIES_TABLE_DEGREE - SERIES_TABLE_LEAD) multiply-adds,
+    counted with the multiply-subtracts: 15 FP32 instructions each)."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
-        return N + 8.0 + 3.0 + 6.0 * SERIES_TABLE_DEGREE + 50.0 + 9.0, 3.0 * N, N / 2.0
+        tail = 3.0 * (SERIES_TABLE_DEGREE - SERIES_TABLE_LEAD)
+        return (N + 8.0 + 3.0 + 3.0 * (2.0 * SERIES_TABLE_LEAD + 1.0) + 50.0 + 9.0, 3.0 * N, N / 2.0 + tail)
     return 6.0 * N + 50.0 + 9.0, 3.0 * N, 0.0
 
 

@@ -1,5 +1,6 @@
 // dse_kernels.cu -- set-up, table, contraction, assembly, Newton-step and
 // Schwinger-function kernels of the sm_103a solver (arXiv:1206.1779).
+#include "dse_df.cuh"
 #include "dse_internal.cuh"
 #include "dse_series.cuh"
 
@@ -1619,6 +1620,65 @@ __global__ void k_schwinger_weights(const Consts c, const double* __restrict__ c
     sigw[i] = wn[i] * exp(z) / x / kPi;
 }
 
+// cos x for |x| < 2^50, FP64-accurate (a few units in the last place) with most of
+// the arithmetic on the FP32 pipe.  Cody-Waite reduction (Cody & Waite 1980):
+// k = nearest integer to 2x/pi (the 1.5 2^52 shifter), r = x - k pi/2 with pi/2 in
+// three FP64 parts (FMA; P1 = pi/2 rounded to FP64, P2 = pi/2 - P1 rounded,
+// P3 = pi/2 - P1 - P2 rounded), |r| <= pi/4.  Then by the quadrant k mod 4
+// cos x = +-cos r or -+sin r, with the Taylor series split as
+//   cos r = (1 - r^2/2) + r^4 (1/4! - r^2/6! + ... + r^14/18!)
+//   sin r = (r - r^3/6) + r^5 (1/5! - r^2/7! + ... + r^14/19!)
+// (truncation below 4e-21 for |r| <= pi/4): the leading terms in FP64, the tails
+// (at most 0.016) in double-float, both tails for every lane so that the quadrant
+// selects without divergence.
+constexpr double kPio2_1 = 1.5707963267948966;
+constexpr double kPio2_2 = 6.123233995736766e-17;
+constexpr double kPio2_3 = -1.4973849048591698e-33;
+constexpr double kTwoOverPi = 0.6366197723675814;
+constexpr double kRoundShifter = 6755399441055744.0;  // 1.5 2^52
+
+struct CosTail { float2 c[8], s[8]; };
+
+// Taylor tail coefficients (-1)^k / (2k + 4)! and (-1)^k / (2k + 5)!, k = 0..7, as
+// double-float pairs of the FP64 quotients
+__device__ __forceinline__ CosTail cos_tail_coefficients() {
+    CosTail t;
+    double fc = 24.0, fs = 120.0;  // (2k + 4)!, (2k + 5)!
+    for (int k = 0; k < 8; ++k) {
+        const double sg = (k & 1) ? -1.0 : 1.0;
+        t.c[k] = df_split(sg / fc, 0);
+        t.s[k] = df_split(sg / fs, 0);
+        fc *= (double)((2 * k + 5) * (2 * k + 6));
+        fs *= (double)((2 * k + 6) * (2 * k + 7));
+    }
+    return t;
+}
+
+__device__ __forceinline__ double cos_df(double x, const CosTail& T) {
+    double kd = fma(x, kTwoOverPi, kRoundShifter);
+    const int q = __double2loint(kd) & 3;
+    kd -= kRoundShifter;
+    double r = fma(-kd, kPio2_1, x);
+    r = fma(-kd, kPio2_2, r);
+    r = fma(-kd, kPio2_3, r);
+    const double r2 = r * r;
+    const float2 rd = df_split(r, 0);
+    const float2 r2d = df_mul(rd, rd);
+    const float2 r4d = df_mul(r2d, r2d);
+    float2 pc = T.c[7], ps = T.s[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) {
+        pc = df_muladd(pc, r2d, T.c[k]);
+        ps = df_muladd(ps, r2d, T.s[k]);
+    }
+    const bool odd = (q & 1) != 0;
+    float2 t = df_mul(odd ? ps : pc, r4d);
+    t = df_mul(t, odd ? rd : make_float2(1.0f, 0.0f));
+    const double lead = fma(odd ? r * r2 : r2, odd ? -1.0 / 6.0 : -0.5, odd ? r : 1.0);
+    const double v = lead + (df_widen(t.x, 1023) + df_widen(t.y, 1023));
+    return (q == 1 || q == 2) ? -v : v;
+}
+
 // partial[s][m] = sum over nodes of split s of sigw_n cos(t_m p_n).
 // Block: kSchT times x kSchPh phases; nodes staged through shared memory.
 constexpr int kSchT = 32;
@@ -1640,6 +1700,7 @@ __global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, c
     const int n0 = s * per;
     const int n1 = min(n_nodes, n0 + per);
     const double tm = m < n_t ? t[m] : 0.0;
+    const CosTail T = cos_tail_coefficients();
     double acc = 0.0;
     for (int base = n0; base < n1; base += kSchTile) {
         const int cnt = min(kSchTile, n1 - base);
@@ -1648,7 +1709,7 @@ __global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, c
             sw[q] = sigw[base + q];
         }
         __syncthreads();
-        for (int q = ph; q < cnt; q += kSchPh) acc = fma(sw[q], cos(tm * sp[q]), acc);
+        for (int q = ph; q < cnt; q += kSchPh) acc = fma(sw[q], cos_df(tm * sp[q], T), acc);
         __syncthreads();
     }
     sred[ph][tl] = acc;

@@ -29,6 +29,7 @@
 // and the tile sums are added to FP64 accumulators.  The residual (the angular
 // sums of the weights) stays in FP64 throughout.
 // The block's coefficient vector lives in shared memory (broadcast reads).
+#include "dse_df.cuh"
 #include "dse_internal.cuh"
 
 namespace dse {
@@ -39,87 +40,6 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 : 64; }
-
-// ---- double-float helpers (phase B) ----
-// x 2^-sh as hi + lo: hi keeps the leading 24 significant bits of x (by
-// truncation, so x - hi is exact), lo the next 24 (rounded).  Values below the
-// FP32 normal range after scaling are flushed to zero; Inf/NaN give NaN.
-__device__ __forceinline__ float2 df_split(double x, int sh) {
-    const unsigned hb = (unsigned)__double2hiint(x), lb = (unsigned)__double2loint(x);
-    const int e = (int)((hb >> 20) & 0x7ffu);
-    if (e == 0x7ff) return make_float2(__int_as_float(0x7fc00000), 0.0f);
-    const int ef = e - sh - 896;  // biased FP32 exponent of x 2^-sh
-    if (e == 0 || ef < 1) return make_float2(0.0f, 0.0f);  // zero, subnormal or flushed
-    const unsigned sign = hb & 0x80000000u;
-    const float hi = __int_as_float((int)(sign | ((unsigned)ef << 23) | ((hb & 0xfffffu) << 3) | (lb >> 29)));
-    // the 29 bits below hi: r 2^(ef - 127 - 52)
-    const float lo = __uint2float_rn(lb & 0x1fffffffu) * 0x1p-52f * __int_as_float(ef << 23);
-    return make_float2(hi, __int_as_float(__float_as_int(lo) | (int)sign));
-}
-
-// c += a b in double-float: exact product of the leading parts (FMA), the cross
-// terms in FP32, the exact sum of c.x and the product's leading part; the lower
-// parts are collected in c.y (renormalised by df_renorm).
-__device__ __forceinline__ void df_fma(float2& c, const float2 a, const float2 b) {
-    const float p = a.x * b.x;
-    float e = fmaf(a.x, b.x, -p);
-    e = fmaf(a.x, b.y, e);
-    e = fmaf(a.y, b.x, e);
-    const float sm = c.x + p;
-    const float bb = sm - c.x;
-    const float err = (c.x - (sm - bb)) + (p - bb);
-    c.y += err + e;
-    c.x = sm;
-}
-
-// f 2^(E - 1023) as a double, from the bits of f: the tile scale of phase B
-// folded into the exponent (zero and FP32 subnormals give 0, Inf/NaN or an
-// overflow give Inf/NaN).
-__device__ __forceinline__ double df_widen(float f, int E) {
-    const unsigned b = (unsigned)__float_as_int(f);
-    const int e8 = (int)((b >> 23) & 0xffu);
-    if (e8 == 0) return 0.0;
-    int e11 = e8 + E - 127;
-    if (e8 == 0xff || E == 0x7ff) e11 = 0x7ff;
-    if (e11 <= 0) return 0.0;
-    if (e11 > 0x7ff) e11 = 0x7ff;
-    const unsigned m = b & 0x7fffffu;
-    return __hiloint2double((int)((b & 0x80000000u) | ((unsigned)e11 << 20) | (m >> 3)), (int)(m << 29));
-}
-
-// a b + d in double-float (renormalised)
-__device__ __forceinline__ float2 df_muladd(const float2 a, const float2 b, const float2 d) {
-    const float p = a.x * b.x;
-    float e = fmaf(a.x, b.x, -p);
-    e = fmaf(a.x, b.y, e);
-    e = fmaf(a.y, b.x, e);
-    const float sm = p + d.x;
-    const float bb = sm - p;
-    const float err = (p - (sm - bb)) + (d.x - bb);
-    const float lo = (e + err) + d.y;
-    const float hi = sm + lo;
-    return make_float2(hi, lo - (hi - sm));
-}
-
-// a b - d in double-float (renormalised)
-__device__ __forceinline__ float2 df_mulsub(const float2 a, const float2 b, const float2 d) {
-    const float p = a.x * b.x;
-    float e = fmaf(a.x, b.x, -p);
-    e = fmaf(a.x, b.y, e);
-    e = fmaf(a.y, b.x, e);
-    const float sm = p - d.x;
-    const float bb = sm - p;
-    const float err = (p - (sm - bb)) + (-d.x - bb);
-    const float lo = (e + err) - d.y;
-    const float hi = sm + lo;
-    return make_float2(hi, lo - (hi - sm));
-}
-
-__device__ __forceinline__ void df_renorm(float2& c) {
-    const float sm = c.x + c.y;
-    c.y = c.y - (sm - c.x);
-    c.x = sm;
-}
 
 __host__ __device__ inline int groups_for(int N, int BT) {
     const int nact = N < BT ? N : BT;
