@@ -1188,12 +1188,17 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale_rows_batched(const Batc
 
 // FP64 iterative refinement for J x = F with an approximate inverse X of the
 // row-scaled matrix diag(Sc) J: x <- x + X (Sc (F - J x)), with the residual in FP64
-// (J in shared memory, one thread per row) and the products X r in FP32, until
-// max |Sn (F - J x)| <= tolfac max |x| (a backward-stable solution for the
-// row scaling Sn).  Returns 1 (converged) or 2 (gave up: not finite, maxit sweeps,
-// or -- with early_abort -- a sweep that did not halve the residual).  Called by
-// every thread of the block; s_x holds x (zero on entry).
-constexpr int kReuseMax = 6;
+// (J in shared memory, one thread per row; F itself for the starting x = 0) and the
+// products X r in FP32, until max |Sn (F - J x)| <= tolfac max |x| (a
+// backward-stable solution for the row scaling Sn).  Returns 1 (converged) or 2
+// (gave up: not finite or maxit sweeps; with early_abort also when a sweep reduces
+// the residual by less than kReuseRate or the observed rate predicts more than
+// maxit sweeps in all).  Called by every thread of the block; s_x holds x (zero
+// on entry).  A sweep costs one FP64 matrix-vector product on this SM (~4 us at
+// n = 128) against ~190 us for an elimination, so a kept inverse that contracts
+// by 0.1 per sweep still pays.
+constexpr int kReuseMax = 24;
+constexpr double kReuseRate = 0.5;
 
 __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, const float* Xs, const double* Sc,
                                            const double* Sn, const double* __restrict__ F, double* s_x, float* s_rf,
@@ -1208,7 +1213,7 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
             if (tid < n) {
                 const double* Jr = Js + (size_t)tid * ldj;
                 double a0 = 0.0, a1 = 0.0;
-                int jj = 0;
+                int jj = it == 0 ? n : 0;  // x = 0 at the start: r = F
                 for (; jj + 1 < n; jj += 2) {
                     a0 = fma(Jr[jj], s_x[jj], a0);
                     a1 = fma(Jr[jj + 1], s_x[jj + 1], a1);
@@ -1237,7 +1242,12 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
             if (!isfinite(RM)) v = 2;
             else if (RM <= tolfac * XM) v = 1;
             else if (it == maxit) v = 2;
-            else if (early_abort && it > 0 && RM > 0.5 * prev) v = 2;
+            else if (early_abort && it > 0) {
+                // observed contraction; sweeps still needed at that rate
+                const double rate = RM / prev;
+                if (!(rate <= kReuseRate)) v = 2;
+                else if (it + log(tolfac * XM / RM) / log(rate) > maxit) v = 2;
+            }
             prev = RM;
             *s_conv = v;
         }
@@ -1276,9 +1286,10 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
 //     memory, one thread per row) until max|r| <= 4 sqrt(n) 2^-53 ||A|| ||x||;
 //   - with Xg given, the inverse that solved the previous Newton step (and its
 //     row scales) is kept in global memory and tried first: late Newton steps
-//     change J little, so a few refinement sweeps with the old X reach the same
-//     backward error and the elimination is skipped; if a sweep fails to halve
-//     the residual (or kReuseMax sweeps do not suffice) the step eliminates afresh;
+//     change J little, so refinement sweeps with the old X reach the same
+//     backward error and the elimination is skipped; if the observed contraction
+//     per sweep is above kReuseRate, or predicts more than kReuseMax sweeps in
+//     all, the step eliminates afresh;
 //   - FP64 LU fallback if the sweeps stall.
 template <int R>
 __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __restrict__ J,

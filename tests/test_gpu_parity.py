@@ -226,7 +226,7 @@ def test_newton_steps_with_kept_inverse(dse, inputs, name):
             c1 = to_host(ct)
             ok, ratio = step_residual_ok(J, F, c0 - c1, c0, c1)
             assert ok, (steps, ratio)
-            assert 1 <= sg[3] <= 12, sg
+            assert 1 <= sg[3] <= 24, sg  # up to 12 sweeps after an elimination, 24 with a kept inverse
             if sg[1] < 1e-11:
                 break
         elim, reused = plan.solver_counters()
