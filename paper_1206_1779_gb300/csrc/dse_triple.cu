@@ -41,14 +41,26 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 
 __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 : 64; }
 
+// The shared-memory row of a triple holds 2s and the anchors T_4i, T_4i+1
+// (i < nq = ceil(N/4)) as double-float pairs; phase B forms T_4i+2 = 2s T_4i+1 - T_4i
+// and T_4i+3 = 2s T_4i+2 - T_4i+1 from them.  Its 4 nq derivative columns c map to
+// j = 4 (c mod nq) + c div nq, so that a warp's threads share c div nq (the same
+// number of recurrence steps) when nq is a multiple of 16.
+__host__ __device__ inline int anchors_for(int N) { return (N + 3) / 4; }
+__host__ __device__ inline int row_len_for(int N) {
+    const int l = 1 + 2 * anchors_for(N);
+    return l | 1;  // odd: conflict-free rows
+}
+
 __host__ __device__ inline int groups_for(int N, int BT) {
-    const int nact = N < BT ? N : BT;
+    const int nc = 4 * anchors_for(N);
+    const int nact = nc < BT ? nc : BT;
     return BT / nact;
 }
 
 __host__ __device__ inline size_t tile_doubles(bool full, int N, int BT) {
     if (!full) return 0;
-    const size_t t = (size_t)BT * (size_t)(N + 1);
+    const size_t t = (size_t)BT * (size_t)row_len_for(N);
     const size_t red = (size_t)groups_for(N, BT) * 3u * (size_t)N;
     return t > red ? t : red;
 }
@@ -72,9 +84,10 @@ template <int BT, int NJ, bool FULL>
 __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, const int ks, double* smem) {
     const Consts& c = A.c;
     const int N = c.N;
-    const int ldT = N + 1;
+    const int nq = anchors_for(N);
+    const int ldT = row_len_for(N);
     double* sT = smem;
-    float2* sT2 = reinterpret_cast<float2*>(smem);  // phi_j(z) rows as double-float pairs
+    float2* sT2 = reinterpret_cast<float2*>(smem);  // rows [2s][T_4i][T_4i+1] as double-float pairs
     double* sh = smem + tile_doubles(FULL, N, BT);
     float2* sh2 = reinterpret_cast<float2*>(sh + 3 * BT);  // the weights as pairs
     double* sa = sh + 6 * BT;
@@ -100,14 +113,24 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     const int nch = A.nch;
     const int nunits = k1 > k0 ? (k1 - k0) * nch : 0;
 
-    // phase-B mapping: NG groups of nact threads, thread owns j = jb + jj*nact
-    const int nact = N < BT ? N : BT;
+    // phase-B mapping: NG groups of nact threads, thread owns the columns
+    // c = jb + jj*nact of 4 nq: T_j with j = 4 (c mod nq) + c div nq
+    const int ncol = 4 * nq;
+    const int nact = ncol < BT ? ncol : BT;
     const int NG = BT / nact;
     const int g = tid / nact;
     const int jb = tid - g * nact;
     const bool bact = g < NG;
     const int mlo = (g * BT) / NG;
     const int mhi = ((g + 1) * BT) / NG;
+    int colj[NJ], coli[NJ], colr[NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+        const int cc = jb + jj * nact;
+        colr[jj] = cc / nq;
+        coli[jj] = cc - colr[jj] * nq;
+        colj[jj] = cc < ncol ? 4 * coli[jj] + colr[jj] : N;  // j >= N: inactive
+    }
 
     double acc[3][NJ];
 #pragma unroll
@@ -250,7 +273,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                             t1 = t2;
                             lg = fma(sb[j], t2, lg);
                             lzz = fma(sa[j], t2, lzz);
-                            if (FULL) Trow[j] = df_split(t2, 0);
+                            if (FULL && (j & 3) < 2) Trow[1 + (j & 1) * nq + (j >> 2)] = df_split(t2, 0);
                         }
                     }
                     if (outside) {
@@ -271,34 +294,23 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     }
                 }
                 if (FULL) {
-                    Trow[0] = make_float2(0.5f, 0.0f);
-                    if (N > 1) Trow[1] = df_split(s, 0);
+                    const float2 fs = df_split(s, 0);
+                    Trow[0] = make_float2(2.0f * fs.x, 2.0f * fs.y);  // 2s
+                    Trow[1] = make_float2(1.0f, 0.0f);                // T_0
+                    Trow[1 + nq] = fs;                                // T_1
                     if (A.stab) {
-                        // T_j(z) for the derivative sums (the direct path stored them
-                        // above): T_4i and T_4i+1 by the FP64 recurrence of stride 4,
-                        // X_(i+1) = 2 T_4 X_i - X_(i-1) (from T_(m+4) + T_(m-4) = 2 T_4 T_m),
-                        // and T_4i+2, T_4i+3 by two steps of T_(j+1) = 2 s T_j - T_(j-1) in
-                        // double-float from them
+                        // T_4i and T_4i+1 (the direct path stored them above) by the FP64
+                        // recurrence of stride 4, X_(i+1) = 2 T_4 X_i - X_(i-1) (from
+                        // T_(m+4) + T_(m-4) = 2 T_4 T_m)
                         const double T2 = fma(2.0 * s, s, -1.0);
                         const double T3 = fma(2.0 * s, T2, -s);
                         const double T4 = fma(2.0 * T2, T2, -1.0);
                         const double c4 = 2.0 * T4;
-                        const float2 fs = df_split(s, 0);
-                        const float2 s2 = make_float2(2.0f * fs.x, 2.0f * fs.y);
-                        double a0 = T4, a1 = 1.0;  // T_(4i-4), T_4i
-                        double b0 = T3, b1 = s;    // T_(4i-3), T_(4i+1)
-                        for (int j0 = 0; j0 < N; j0 += 4) {
-                            const float2 fa = df_split(a1, 0);
-                            const float2 fb = df_split(b1, 0);
-                            if (j0 > 0) {
-                                Trow[j0] = fa;
-                                if (j0 + 1 < N) Trow[j0 + 1] = fb;
-                            }
-                            if (j0 + 2 < N) {
-                                const float2 t2 = df_mulsub(s2, fb, fa);
-                                Trow[j0 + 2] = t2;
-                                if (j0 + 3 < N) Trow[j0 + 3] = df_mulsub(s2, t2, fb);
-                            }
+                        double a0 = 1.0, a1 = T4;  // T_(4i-4), T_4i
+                        double b0 = s, b1 = fma(2.0 * s, T4, -T3);  // T_(4i-3), T_(4i+1)
+                        for (int i = 1; i < nq; ++i) {
+                            Trow[1 + i] = df_split(a1, 0);
+                            Trow[1 + nq + i] = df_split(b1, 0);
                             const double an4 = fma(c4, a1, -a0);
                             a0 = a1;
                             a1 = an4;
@@ -319,7 +331,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
             }
         }
         if (FULL && !live) {
-            for (int j = 0; j < N; ++j) Trow[j] = make_float2(0.0f, 0.0f);
+            for (int j = 0; j < ldT; ++j) Trow[j] = make_float2(0.0f, 0.0f);
         }
         // angular sums over the warp's 32 nodes (same radial node for the whole
         // warp) of (hQ, hM, hG) by halving exchanges, 6 FP64 additions per lane:
@@ -378,11 +390,18 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         const float2 mm = sh2[BT + m];
                         const float2 gg = sh2[2 * BT + m];
                         const float2* Tm = sT2 + (size_t)m * ldT;
+                        const float2 s2 = Tm[0];
 #pragma unroll
                         for (int jj = 0; jj < NJ; ++jj) {
-                            const int j = jb + jj * nact;
-                            if (j < N) {
-                                const float2 t = Tm[j];
+                            if (colj[jj] < N) {
+                                const float2 a = Tm[1 + coli[jj]];
+                                const float2 b = Tm[1 + nq + coli[jj]];
+                                float2 t = (colr[jj] & 1) ? b : a;
+                                if (colr[jj] >= 2) {
+                                    const float2 t2 = df_mulsub(s2, b, a);
+                                    t = colr[jj] == 2 ? t2 : df_mulsub(s2, t2, b);
+                                }
+                                if (colj[jj] == 0) t = make_float2(0.5f, 0.0f);  // T_0 enters as 1/2
                                 df_fma(ca[0][jj], q, t);
                                 df_fma(ca[1][jj], mm, t);
                                 df_fma(ca[2][jj], gg, t);
@@ -414,7 +433,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
         if (bact) {
 #pragma unroll
             for (int jj = 0; jj < NJ; ++jj) {
-                const int j = jb + jj * nact;
+                const int j = colj[jj];
                 if (j < N) {
                     red[(g * 3 + 0) * N + j] = acc[0][jj];
                     red[(g * 3 + 1) * N + j] = acc[1][jj];
