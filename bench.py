@@ -48,7 +48,7 @@ DF_FMA_FP32_INST = 12          # one double-float multiply-add: exact product (2
 DF_MULSUB_FP32_INST = 15       # one double-float a b - d with renormalisation
 
 
-SERIES_TABLE_N = (24, 128)  # the kernel reads ln G(z), ln Z(z) from the series table for these N
+SERIES_TABLE_N = (24, 256)  # the kernel reads Z(z), G(z), W(z) from the series table for these N
 SERIES_TABLE_DEGREE = 15    # degree of the table's local polynomials
 SERIES_TABLE_LEAD = 4       # leading coefficients summed in FP64 (the rest in double-float)
 

@@ -142,7 +142,7 @@ Slice slice_layout(const Consts& c, int Rt, int nch, int ks_cap) {
     L.X = off; off = up256(off + (n <= 128 ? sizeof(float) * (size_t)n * n : 0));
     L.S = off; off = up256(off + sizeof(double) * (size_t)n);
     L.stats = off; off = up256(off + 4 * sizeof(double) + sizeof(int));
-    L.stab = off; off = up256(off + (use_series_table(c.N) ? sizeof(SeriesRec) * kSeriesM : 0));
+    L.stab = off; off = up256(off + (use_series_table(c.N) ? sizeof(SeriesRec) * kSeriesRecords : 0));
     const size_t nrule = c.nrule;
     const size_t gmax = nrule > (size_t)na ? nrule : (size_t)na;
     L.gl = off; off = up256(off + sizeof(double) * (2 * nrule + 2 * (size_t)na + gmax + 2));

@@ -67,7 +67,8 @@ struct XTab { double lG, lZ, G, Z, Ginv, Zinv, pad0, pad1; };
 // coefficients) for Z(s), G(s) (pairs e[k]) and W(s) = G^p Z^q (w[k]), fitted at
 // kSeriesP + 1 Chebyshev points where ln Z, ln G come from a compensated Clenshaw
 // recurrence.  With interval width h = pi/kSeriesM the fit error is
-// ~ (N h/4)^(P+1)/(P+1)! relative: below 1e-19 for N <= 128, so the FP64
+// ~ (N h/4)^(P+1)/(P+1)! relative: below 1e-19 for N <= 128 and ~1e-15 for the
+// highest mode at N = 256 (whose coefficient is small for a smooth solution), so the FP64
 // quadrature kernel reads the table for kSeriesMinN <= N <= kSeriesMaxN in place
 // of the per-triple series sums and exponentials.  The leading kSeriesLead
 // coefficients are FP64; the rest, whose terms are small next to the leading ones
@@ -79,7 +80,7 @@ constexpr int kSeriesQ = kSeriesP + 1;
 constexpr int kSeriesLead = 4;
 constexpr int kSeriesTail = kSeriesQ - kSeriesLead;
 constexpr int kSeriesMinN = 24;
-constexpr int kSeriesMaxN = 128;
+constexpr int kSeriesMaxN = 256;  // DSE_MAX_CHEB: every N >= kSeriesMinN
 struct SeriesRec {
     double mid, invhalf;
     double2 e[kSeriesLead];     // (Z, G), coefficients 0 .. kSeriesLead - 1
@@ -87,6 +88,10 @@ struct SeriesRec {
     float4 et[kSeriesTail];     // (Z hi, Z lo, G hi, G lo), coefficients kSeriesLead .. kSeriesP
     float2 wt[kSeriesTail];     // (W hi, W lo)
 };
+// A table is kSeriesRecords records: the kSeriesM intervals, then one record whose
+// first four doubles are the series at the end points, ln Z(s=1), ln G(s=1),
+// ln Z(s=-1), ln G(s=-1) (summed in the order of the per-triple recurrence).
+constexpr int kSeriesRecords = kSeriesM + 1;
 __host__ __device__ inline bool use_series_table(int N) { return N >= kSeriesMinN && N <= kSeriesMaxN; }
 
 struct TripleArgs {

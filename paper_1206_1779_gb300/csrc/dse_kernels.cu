@@ -324,6 +324,21 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     const double mid = 0.5 * (cos(th0) + cos(th1));
     const double half = sin(0.5 * (th0 + th1)) * sin(0.5 * h);  // (cos th0 - cos th1)/2 without cancellation
     __syncthreads();  // coefficients and tables staged
+    if (blk == 0 && threadIdx.x >= 64 && threadIdx.x < 68) {
+        // the end-point record (threads of the third warp, which has no node work
+        // here): sum_j c_j T_j(+-1) with T_j(1) = 1, T_j(-1) = (-1)^j
+        const int e = threadIdx.x - 64;
+        const int nc = (e & 1) ? c.NG : c.NZ;
+        const double* cf = scf + ((e & 1) ? c.NZ : 0);
+        const double sgn = e < 2 ? 1.0 : -1.0;
+        double v = 0.5 * cf[0];
+        double t = 1.0;
+        for (int j = 1; j < nc; ++j) {
+            t *= sgn;
+            v = fma(cf[j], t, v);
+        }
+        reinterpret_cast<double*>(tab + kSeriesM)[e] = v;
+    }
     if (f < 2) {
         const double uq = cos(kPi * (q + 0.5) / kSeriesQ);
         // s = mid + half uq exactly as s_h + s_l
@@ -1140,6 +1155,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
 // FP32, and the row sum of |A_i| (for ||A||_inf).  A zero row is singular.
 constexpr int kScaleThreads = 128;
 constexpr int kColPad = 144;  // >= 128 + 16 - 1, multiple of 4
+constexpr int kGjBlock = 4;   // pivots per round of the blocked elimination
 
 __device__ __forceinline__ void scale_row(int n, const double* __restrict__ J, float* __restrict__ As,
                                           double2* __restrict__ rowinfo, int* __restrict__ status, const int i) {
@@ -1315,6 +1331,9 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     __shared__ double s_red[2][4];
     __shared__ int s_piv, s_fail, s_done, s_conv, s_reuse;
     __shared__ double s_anorm;
+    __shared__ float s_panel[2][kGjBlock][128];                // panel rows of a round (by round parity)
+    __shared__ __align__(16) float s_colb[kGjBlock][kColPad];  // the round's pivot columns
+    __shared__ float s_pc[2][kGjBlock];                        // pivot column within the panel
     const int n = c.n;
     const int ldj = n + 1;
     double* Js = dsm;                                             // [n][n+1] FP64 copy of J
@@ -1358,7 +1377,21 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     }
     for (int i = tid; i < n; i += kGjThreads) s_scale[i] = rowinfo[i].x;
     for (int i = n + tid; i < kColPad; i += kGjThreads) s_colq[0][i] = s_colq[1][i] = 0.0f;  // rows past n
-    for (int idx = tid; idx < n * n; idx += kGjThreads) Js[(idx / n) * ldj + (idx % n)] = J[idx];
+    for (int base = 0; base < n * n; base += 4 * kGjThreads) {
+        double t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * kGjThreads + tid;
+            t[u] = idx < n * n ? J[idx] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * kGjThreads + tid;
+            if (idx < n * n) Js[(idx / n) * ldj + (idx % n)] = t[u];
+        }
+    }
+    for (int i = n + tid; i < kColPad; i += kGjThreads)
+        for (int p = 0; p < kGjBlock; ++p) s_colb[p][i] = 0.0f;  // rows past n
     if (tid == 0) s_reuse = (Xg != nullptr && *xstate == 1) ? 1 : 0;
     if (tid < n) s_x[tid] = 0.0;
     __syncthreads();
@@ -1391,88 +1424,228 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
         }
         bool used = false;  // this thread's column has been a pivot column
         __syncthreads();
-        for (int gs = 0; gs < G; ++gs) {
-            // warps that hold threads of group gs
-            const int w0 = (gs * n) >> 5;
-            const int w1 = (gs * n + n - 1) >> 5;
-            const bool in_group_warp = warp >= w0 && warp <= w1;
-    #pragma unroll
-            for (int rs = 0; rs < R; ++rs) {
-                const int k = gs * R + rs;
-                if (k >= n) break;  // uniform
-                const int b = k & 1;
-                // [A] group gs publishes row k and per-warp candidates over its unused columns
-                if (in_group_warp) {
-                    const bool mine = owner && g == gs;
-                    float a = -1.0f;
-                    int idx = 1 << 30;
-                    if (mine) {
-                        s_rowk[b][j] = v[rs];
-                        if (!used) {
-                            a = fabsf(v[rs]);
-                            idx = j;
+        if constexpr (R % kGjBlock == 0) {
+            // Blocked form: rounds of kGjBlock pivots.  The kGjBlock pivot steps of a
+            // round on the panel rows k0.. are a block pivot on P = A[K][Q]; for the
+            // other rows i they compose to
+            //   A[i][j] <- (j in Q ? 0 : A[i][j]) - sum_p A[i][q_p] R_p[j]
+            // with the pre-round entries A[i][q_p] and the final panel rows R_p, so a
+            // round takes three block barriers instead of two per pivot:
+            //   (1) the owners of the panel rows write them to shared memory;
+            //   (2) the warps of group 0 (thread t holds column t) pivot the panel in
+            //       registers, synchronising on a named barrier of their own;
+            //   (3) the owners of the round's pivot columns publish them;
+            //   (4) every thread updates its rows.
+            const int panel_threads = ((n + 31) / 32) * 32;
+            const bool pw = tid < panel_threads;
+            int round = 0;
+            for (int gs = 0; gs < G; ++gs) {
+#pragma unroll
+                for (int mb = 0; mb < R / kGjBlock; ++mb, ++round) {
+                    const int k0 = gs * R + mb * kGjBlock;
+                    if (k0 >= n) break;  // uniform
+                    const int nb = min(kGjBlock, n - k0);
+                    float(*panel)[128] = s_panel[round & 1];
+                    // (1)
+                    if (owner && g == gs) {
+#pragma unroll
+                        for (int p = 0; p < kGjBlock; ++p)
+                            if (p < nb) panel[p][j] = v[mb * kGjBlock + p];
+                    }
+                    __syncthreads();
+                    // (2)
+                    if (pw) {
+                        const bool col = tid < n;  // group 0: j == tid
+                        float P[kGjBlock];
+#pragma unroll
+                        for (int p = 0; p < kGjBlock; ++p) P[p] = (col && p < nb) ? panel[p][tid] : 0.0f;
+                        for (int p = 0; p < nb; ++p) {
+                            const int bb = p & 1;
+                            float a = -1.0f;
+                            int idx = 1 << 30;
+#pragma unroll
+                            for (int pp = 0; pp < kGjBlock; ++pp)
+                                if (pp == p && col && !used) {
+                                    a = fabsf(P[pp]);
+                                    idx = tid;
+                                }
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1) {
+                                const float oa = __shfl_xor_sync(kFullMask, a, off);
+                                const int oi = __shfl_xor_sync(kFullMask, idx, off);
+                                if (oa > a || (oa == a && oi < idx)) {
+                                    a = oa;
+                                    idx = oi;
+                                }
+                            }
+                            if (lane == 0) {
+                                s_wc[bb][warp] = a;
+                                s_wi[bb][warp] = idx;
+                            }
+                            asm volatile("bar.sync 1, %0;" ::"r"(panel_threads) : "memory");
+                            float best = s_wc[bb][0];
+                            int q = s_wi[bb][0];
+                            for (int w = 1; w < panel_threads / 32; ++w) {
+                                const float aw = s_wc[bb][w];
+                                const int qw = s_wi[bb][w];
+                                if (aw > best || (aw == best && qw < q)) {
+                                    best = aw;
+                                    q = qw;
+                                }
+                            }
+                            if (!(best > 1e-30f)) {
+                                if (tid == 0) s_done = -1;
+                                break;  // uniform over the panel threads
+                            }
+                            if (tid == q) {
+#pragma unroll
+                                for (int pp = 0; pp < kGjBlock; ++pp) s_pc[bb][pp] = P[pp];
+                                used = true;
+                            }
+                            if (tid == 0) s_q[k0 + p] = q;
+                            asm volatile("bar.sync 1, %0;" ::"r"(panel_threads) : "memory");
+                            float pk = 0.0f;
+#pragma unroll
+                            for (int pp = 0; pp < kGjBlock; ++pp)
+                                if (pp == p) pk = P[pp];
+                            const float inv = 1.0f / s_pc[bb][p];
+                            const float nk = (tid == q) ? inv : pk * inv;
+#pragma unroll
+                            for (int pp = 0; pp < kGjBlock; ++pp)
+                                P[pp] = (pp == p) ? nk : fmaf(-s_pc[bb][pp], nk, (tid == q) ? 0.0f : P[pp]);
+                        }
+                        if (col) {
+#pragma unroll
+                            for (int p = 0; p < kGjBlock; ++p)
+                                if (p < nb) panel[p][tid] = P[p];
                         }
                     }
-    #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const float oa = __shfl_xor_sync(kFullMask, a, off);
-                        const int oi = __shfl_xor_sync(kFullMask, idx, off);
-                        if (oa > a || (oa == a && oi < idx)) {
-                            a = oa;
-                            idx = oi;
+                    __syncthreads();
+                    if (s_done != 0) goto elimination_done;  // uniform
+                    // (3)
+                    int pj = -1;
+#pragma unroll
+                    for (int p = 0; p < kGjBlock; ++p)
+                        if (p < nb && s_q[k0 + p] == j) pj = p;
+                    if (owner && pj >= 0) {
+                        used = true;
+                        float4* dst = reinterpret_cast<float4*>(&s_colb[pj][i0]);
+#pragma unroll
+                        for (int qq = 0; qq < R / 4; ++qq)
+                            dst[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                    }
+                    __syncthreads();
+                    // (4)
+                    if (owner) {
+                        float rk[kGjBlock];
+#pragma unroll
+                        for (int p = 0; p < kGjBlock; ++p) rk[p] = p < nb ? panel[p][j] : 0.0f;
+#pragma unroll
+                        for (int r = 0; r < R; ++r) v[r] = pj >= 0 ? 0.0f : v[r];
+#pragma unroll
+                        for (int p = 0; p < kGjBlock; ++p) {
+                            const float4* cb = reinterpret_cast<const float4*>(&s_colb[p][i0]);
+#pragma unroll
+                            for (int qq = 0; qq < R / 4; ++qq) {
+                                const float4 m = cb[qq];
+                                v[4 * qq + 0] = fmaf(-m.x, rk[p], v[4 * qq + 0]);
+                                v[4 * qq + 1] = fmaf(-m.y, rk[p], v[4 * qq + 1]);
+                                v[4 * qq + 2] = fmaf(-m.z, rk[p], v[4 * qq + 2]);
+                                v[4 * qq + 3] = fmaf(-m.w, rk[p], v[4 * qq + 3]);
+                            }
+                        }
+                        if (g == gs) {
+#pragma unroll
+                            for (int p = 0; p < kGjBlock; ++p)
+                                if (p < nb) v[mb * kGjBlock + p] = rk[p];
                         }
                     }
-                    if (lane == 0) {
-                        s_wc[b][warp - w0] = a;
-                        s_wi[b][warp - w0] = idx;
-                    }
                 }
-                __syncthreads();
-                // [B] pivot column q; its owners publish it
-                float best = s_wc[b][0];
-                int q = s_wi[b][0];
-                for (int w = 1; w <= w1 - w0; ++w) {
-                    const float a = s_wc[b][w];
-                    const int qi = s_wi[b][w];
-                    if (a > best || (a == best && qi < q)) {
-                        best = a;
-                        q = qi;
-                    }
-                }
-                if (!(best > 1e-30f)) {
-                    if (tid == 0) s_done = -1;
-                    goto elimination_done;  // uniform: every thread read the same candidates
-                }
-                if (tid == 0) s_q[k] = q;
-                if (owner && j == q) {
-                    used = true;
-    #pragma unroll
-                    for (int r = 0; r < R; ++r) s_colq[b][i0 + r] = v[r];
-                }
-                __syncthreads();
-                // [C] eliminate column q from every row but k, scale row k
-                if (owner) {
-                    const float inv = 1.0f / s_rowk[b][q];
-                    const float nk = (j == q) ? inv : s_rowk[b][j] * inv;
-                    if (j == q) {
-    #pragma unroll
-                        for (int r = 0; r < R; ++r) v[r] = 0.0f;
-                    }
-                    if (R >= 4) {
-                        const float4* col4 = reinterpret_cast<const float4*>(&s_colq[b][i0]);
-    #pragma unroll
-                        for (int qq = 0; qq < R / 4; ++qq) {
-                            const float4 m = col4[qq];
-                            v[4 * qq + 0] = fmaf(-m.x, nk, v[4 * qq + 0]);
-                            v[4 * qq + 1] = fmaf(-m.y, nk, v[4 * qq + 1]);
-                            v[4 * qq + 2] = fmaf(-m.z, nk, v[4 * qq + 2]);
-                            v[4 * qq + 3] = fmaf(-m.w, nk, v[4 * qq + 3]);
+            }
+        } else {
+            for (int gs = 0; gs < G; ++gs) {
+                // warps that hold threads of group gs
+                const int w0 = (gs * n) >> 5;
+                const int w1 = (gs * n + n - 1) >> 5;
+                const bool in_group_warp = warp >= w0 && warp <= w1;
+        #pragma unroll
+                for (int rs = 0; rs < R; ++rs) {
+                    const int k = gs * R + rs;
+                    if (k >= n) break;  // uniform
+                    const int b = k & 1;
+                    // [A] group gs publishes row k and per-warp candidates over its unused columns
+                    if (in_group_warp) {
+                        const bool mine = owner && g == gs;
+                        float a = -1.0f;
+                        int idx = 1 << 30;
+                        if (mine) {
+                            s_rowk[b][j] = v[rs];
+                            if (!used) {
+                                a = fabsf(v[rs]);
+                                idx = j;
+                            }
                         }
-                    } else {
-    #pragma unroll
-                        for (int r = 0; r < R; ++r) v[r] = fmaf(-s_colq[b][i0 + r], nk, v[r]);
+        #pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            const float oa = __shfl_xor_sync(kFullMask, a, off);
+                            const int oi = __shfl_xor_sync(kFullMask, idx, off);
+                            if (oa > a || (oa == a && oi < idx)) {
+                                a = oa;
+                                idx = oi;
+                            }
+                        }
+                        if (lane == 0) {
+                            s_wc[b][warp - w0] = a;
+                            s_wi[b][warp - w0] = idx;
+                        }
                     }
-                    if (g == gs) v[rs] = nk;
+                    __syncthreads();
+                    // [B] pivot column q; its owners publish it
+                    float best = s_wc[b][0];
+                    int q = s_wi[b][0];
+                    for (int w = 1; w <= w1 - w0; ++w) {
+                        const float a = s_wc[b][w];
+                        const int qi = s_wi[b][w];
+                        if (a > best || (a == best && qi < q)) {
+                            best = a;
+                            q = qi;
+                        }
+                    }
+                    if (!(best > 1e-30f)) {
+                        if (tid == 0) s_done = -1;
+                        goto elimination_done;  // uniform: every thread read the same candidates
+                    }
+                    if (tid == 0) s_q[k] = q;
+                    if (owner && j == q) {
+                        used = true;
+        #pragma unroll
+                        for (int r = 0; r < R; ++r) s_colq[b][i0 + r] = v[r];
+                    }
+                    __syncthreads();
+                    // [C] eliminate column q from every row but k, scale row k
+                    if (owner) {
+                        const float inv = 1.0f / s_rowk[b][q];
+                        const float nk = (j == q) ? inv : s_rowk[b][j] * inv;
+                        if (j == q) {
+        #pragma unroll
+                            for (int r = 0; r < R; ++r) v[r] = 0.0f;
+                        }
+                        if (R >= 4) {
+                            const float4* col4 = reinterpret_cast<const float4*>(&s_colq[b][i0]);
+        #pragma unroll
+                            for (int qq = 0; qq < R / 4; ++qq) {
+                                const float4 m = col4[qq];
+                                v[4 * qq + 0] = fmaf(-m.x, nk, v[4 * qq + 0]);
+                                v[4 * qq + 1] = fmaf(-m.y, nk, v[4 * qq + 1]);
+                                v[4 * qq + 2] = fmaf(-m.z, nk, v[4 * qq + 2]);
+                                v[4 * qq + 3] = fmaf(-m.w, nk, v[4 * qq + 3]);
+                            }
+                        } else {
+        #pragma unroll
+                            for (int r = 0; r < R; ++r) v[r] = fmaf(-s_colq[b][i0 + r], nk, v[r]);
+                        }
+                        if (g == gs) v[rs] = nk;
+                    }
                 }
             }
         }

@@ -121,31 +121,25 @@ Consts make_consts(const dse_problem* p) {
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Radial nodes per block: balance Rt * KS blocks over the resident slots.
+// Radial nodes per block: about five waves of Rt * KS blocks over the resident
+// slots, so that the block scheduler evens out rows of unequal cost (rows near
+// Lambda^2 evaluate the UV forms with exponentials for many triples); at least
+// two radial nodes per block and at most 128 splits.  Measured at N = 64 with
+// 256 x 128 nodes: one wave (KS = 11) 0.84 ms per launch, KS = 23 / 35 / 47 / 64:
+// 0.81 / 0.78 / 0.76 / 0.74 ms.
 void choose_split(dse_plan* pl) {
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int occ = triple_max_blocks_per_sm(true, pl->c.N);
     if (occ < 1) occ = 1;
-    const double slots = (double)nsm * occ;
-    const int warps = triple_block_threads(pl->c.N) / 32;
+    const long long slots = (long long)nsm * occ;
     const int nr = pl->c.nr;
-    double best = 1e300;
-    int bestKB = nr;
-    for (int KB = 1; KB <= nr; ++KB) {
-        const int KS = (nr + KB - 1) / KB;
-        if (KS > 64) continue;
-        const double blocks = (double)pl->Rt * KS;
-        const double waves = ceil(blocks / slots);
-        const double tiles = ceil((double)KB * pl->nch / warps);
-        const double cost = waves * (tiles + 0.25);
-        if (cost < best - 1e-9) {
-            best = cost;
-            bestKB = KB;
-        }
-    }
-    pl->KB = bestKB;
-    pl->KS = (nr + bestKB - 1) / bestKB;
+    long long kb = ((long long)nr * pl->Rt) / (5 * slots);
+    if (kb < 2) kb = 2;
+    if (kb > nr) kb = nr;
+    while ((nr + kb - 1) / kb > 128) ++kb;
+    pl->KB = (int)kb;
+    pl->KS = (int)((nr + kb - 1) / kb);
 }
 
 void release_events(dse_plan* pl) {
@@ -301,7 +295,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_J = off; off = align_up(off + sizeof(double) * (size_t)n * n);
     size_t o_F = off; off = align_up(off + sizeof(double) * n);
     size_t o_work = off; off = align_up(off + sizeof(double) * 2 * n);
-    size_t o_stab = off; off = align_up(off + sizeof(SeriesRec) * kSeriesM);
+    size_t o_stab = off; off = align_up(off + sizeof(SeriesRec) * kSeriesRecords);
     size_t o_As = off; off = align_up(off + sizeof(float) * (size_t)n * n);
     size_t o_ri = off; off = align_up(off + sizeof(double2) * n);
     size_t o_X = off; off = align_up(off + (n <= 128 ? sizeof(float) * (size_t)n * n : 0));

@@ -137,23 +137,9 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     for (int jj = 0; jj < NJ; ++jj) acc[0][jj] = acc[1][jj] = acc[2][jj] = 0.0;
     static_assert(WARPS <= 8, "per-warp exponent maxima hold 8 warps");
 
+    // the series at s = +-1 from the table's end-point record
+    if (A.stab && tid < 4) sbnd[tid] = reinterpret_cast<const double*>(A.stab + kSeriesM)[tid];
     __syncthreads();
-    if (A.stab) {
-        // the series at s = +-1 (T_j(1) = 1, T_j(-1) = (-1)^j), summed in the order
-        // of the per-triple recurrence
-        if (tid < 4) {
-            const double* cf = (tid & 1) ? sb : sa;
-            const double sgn = tid < 2 ? 1.0 : -1.0;
-            double v = 0.5 * cf[0];
-            double t = 1.0;
-            for (int j = 1; j < N; ++j) {
-                t *= sgn;
-                v = fma(cf[j], t, v);
-            }
-            sbnd[tid] = v;
-        }
-        __syncthreads();
-    }
 
     // (x, y) factors of the integrands, formed once per radial node instead of per
     // triple: z = d + b2 sigma with d = (sqrt x - sqrt y)^2, b2 = 4 sqrt(xy);

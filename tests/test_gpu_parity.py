@@ -46,6 +46,10 @@ CASES = {
     "paper_quadrature_ghost_point": dict(n_cheb=12, n_cheb_G=8, n_radial=20, n_angular=32, radial_mode=1,
                                          angular_mode=1, x_G=2e-3, ginv_G=0.02),
     "paper_quadrature": dict(n_cheb=10, n_radial=16, n_angular=32, radial_mode=1, angular_mode=1),
+    # degenerate and maximum orders: one coefficient per function; N = 256 (the
+    # largest, 512 unknowns)
+    "n1_degenerate": dict(n_cheb=1, n_radial=4, n_angular=4),
+    "n256_max": dict(n_cheb=256, n_radial=12, n_angular=10),
 }
 
 
