@@ -1156,6 +1156,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_mixed(const Consts c, dou
 constexpr int kScaleThreads = 128;
 constexpr int kColPad = 144;  // >= 128 + 16 - 1, multiple of 4
 constexpr int kGjBlock = 4;   // pivots per round of the blocked elimination
+constexpr int kGjCols = 4;    // columns per lane of the panel warp (n <= 128)
 
 __device__ __forceinline__ void scale_row(int n, const double* __restrict__ J, float* __restrict__ As,
                                           double2* __restrict__ rowinfo, int* __restrict__ status, const int i) {
@@ -1218,28 +1219,36 @@ constexpr double kReuseRate = 0.5;
 
 __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, const float* Xs, const double* Sc,
                                            const double* Sn, const double* __restrict__ F, double* s_x, float* s_rf,
-                                           double (*s_red)[4], int* s_conv, double tolfac, int maxit,
+                                           double (*s_red)[8], int* s_conv, double tolfac, int maxit,
                                            bool early_abort, int* sweeps) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double prev = INFINITY;  // thread 0 only
     int st = 0;
     for (int it = 0; it <= maxit; ++it) {
-        if (tid < 128) {
+        // residual: two threads per row (8 warps), each over half of the row
+        if (tid < 256) {
             double rm = 0.0, xm = 0.0;
-            if (tid < n) {
-                const double* Jr = Js + (size_t)tid * ldj;
+            const int row = tid >> 1, hf = tid & 1;
+            double acc = 0.0;
+            if (row < n && it > 0) {  // x = 0 at the start: r = F
+                const double* Jr = Js + (size_t)row * ldj;
+                const int j0 = hf ? n / 2 : 0, j1 = hf ? n : n / 2;
                 double a0 = 0.0, a1 = 0.0;
-                int jj = it == 0 ? n : 0;  // x = 0 at the start: r = F
-                for (; jj + 1 < n; jj += 2) {
+                int jj = j0;
+                for (; jj + 1 < j1; jj += 2) {
                     a0 = fma(Jr[jj], s_x[jj], a0);
                     a1 = fma(Jr[jj + 1], s_x[jj + 1], a1);
                 }
-                if (jj < n) a0 = fma(Jr[jj], s_x[jj], a0);
-                const double r = F[tid] - (a0 + a1);
-                s_rf[tid] = (float)(Sc[tid] * r);
-                const double rn = Sn[tid] * r;
+                if (jj < j1) a0 = fma(Jr[jj], s_x[jj], a0);
+                acc = a0 + a1;
+            }
+            acc += __shfl_xor_sync(kFullMask, acc, 1);
+            if (row < n && hf == 0) {
+                const double r = F[row] - acc;
+                s_rf[row] = (float)(Sc[row] * r);
+                const double rn = Sn[row] * r;
                 rm = isfinite(rn) ? fabs(rn) : INFINITY;
-                xm = fabs(s_x[tid]);
+                xm = fabs(s_x[row]);
             }
             for (int off = 16; off > 0; off >>= 1) {
                 rm = fmax(rm, __shfl_xor_sync(kFullMask, rm, off));
@@ -1252,8 +1261,11 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
         }
         __syncthreads();
         if (tid == 0) {
-            const double RM = fmax(fmax(s_red[0][0], s_red[0][1]), fmax(s_red[0][2], s_red[0][3]));
-            const double XM = fmax(fmax(s_red[1][0], s_red[1][1]), fmax(s_red[1][2], s_red[1][3]));
+            double RM = s_red[0][0], XM = s_red[1][0];
+            for (int w = 1; w < 8; ++w) {
+                RM = fmax(RM, s_red[0][w]);
+                XM = fmax(XM, s_red[1][w]);
+            }
             int v = 0;  // 0: continue, 1: converged, 2: give up
             if (!isfinite(RM)) v = 2;
             else if (RM <= tolfac * XM) v = 1;
@@ -1271,12 +1283,19 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
         st = *s_conv;
         if (st) break;
         ++*sweeps;
-        // x += X r  (FP32 products, 8 threads per row)
+        // x += X r  (FP32 products, 8 threads per row; the four rows of a warp start
+        // at columns 8 apart, so that their shared-memory reads use distinct banks)
         {
             const int i = tid >> 3, part = tid & 7;
+            const int n8 = (n + 7) & ~7;
+            const int rot = 8 * (i & 3);
             float acc = 0.0f;
             if (i < n)
-                for (int jj = part; jj < n; jj += 8) acc = fmaf(Xs[i * n + jj], s_rf[jj], acc);
+                for (int t = part; t < n8; t += 8) {
+                    int jj = t + rot;
+                    if (jj >= n8) jj -= n8;
+                    if (jj < n) acc = fmaf(Xs[i * n + jj], s_rf[jj], acc);
+                }
             acc += __shfl_xor_sync(kFullMask, acc, 4);
             acc += __shfl_xor_sync(kFullMask, acc, 2);
             acc += __shfl_xor_sync(kFullMask, acc, 1);
@@ -1328,12 +1347,12 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     __shared__ double s_scale[128];
     __shared__ double s_sold[128];
     __shared__ float s_rf[128];
-    __shared__ double s_red[2][4];
+    __shared__ double s_red[2][8];
     __shared__ int s_piv, s_fail, s_done, s_conv, s_reuse;
     __shared__ double s_anorm;
     __shared__ float s_panel[2][kGjBlock][128];                // panel rows of a round (by round parity)
     __shared__ __align__(16) float s_colb[kGjBlock][kColPad];  // the round's pivot columns
-    __shared__ float s_pc[2][kGjBlock];                        // pivot column within the panel
+    __shared__ unsigned char s_used[128];                      // columns pivoted so far
     const int n = c.n;
     const int ldj = n + 1;
     double* Js = dsm;                                             // [n][n+1] FP64 copy of J
@@ -1432,12 +1451,12 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
             // with the pre-round entries A[i][q_p] and the final panel rows R_p, so a
             // round takes three block barriers instead of two per pivot:
             //   (1) the owners of the panel rows write them to shared memory;
-            //   (2) the warps of group 0 (thread t holds column t) pivot the panel in
-            //       registers, synchronising on a named barrier of their own;
+            //   (2) one warp pivots the panel in registers (lane L holds columns
+            //       L + 32 c), with shuffles only;
             //   (3) the owners of the round's pivot columns publish them;
             //   (4) every thread updates its rows.
-            const int panel_threads = ((n + 31) / 32) * 32;
-            const bool pw = tid < panel_threads;
+            for (int i = tid; i < 128; i += kGjThreads) s_used[i] = 0;
+            __syncthreads();
             int round = 0;
             for (int gs = 0; gs < G; ++gs) {
 #pragma unroll
@@ -1453,71 +1472,81 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
                             if (p < nb) panel[p][j] = v[mb * kGjBlock + p];
                     }
                     __syncthreads();
-                    // (2)
-                    if (pw) {
-                        const bool col = tid < n;  // group 0: j == tid
-                        float P[kGjBlock];
+                    // (2) warp 0 pivots the panel: lane L holds columns L + 32 c
+                    if (warp == 0) {
+                        float P[kGjBlock][kGjCols];
+                        bool ucol[kGjCols];
 #pragma unroll
-                        for (int p = 0; p < kGjBlock; ++p) P[p] = (col && p < nb) ? panel[p][tid] : 0.0f;
-                        for (int p = 0; p < nb; ++p) {
-                            const int bb = p & 1;
-                            float a = -1.0f;
-                            int idx = 1 << 30;
+                        for (int cc = 0; cc < kGjCols; ++cc) {
+                            const int col = lane + 32 * cc;
+                            ucol[cc] = col >= n || s_used[col] != 0;
 #pragma unroll
-                            for (int pp = 0; pp < kGjBlock; ++pp)
-                                if (pp == p && col && !used) {
-                                    a = fabsf(P[pp]);
-                                    idx = tid;
-                                }
-#pragma unroll
-                            for (int off = 16; off > 0; off >>= 1) {
-                                const float oa = __shfl_xor_sync(kFullMask, a, off);
-                                const int oi = __shfl_xor_sync(kFullMask, idx, off);
-                                if (oa > a || (oa == a && oi < idx)) {
-                                    a = oa;
-                                    idx = oi;
-                                }
-                            }
-                            if (lane == 0) {
-                                s_wc[bb][warp] = a;
-                                s_wi[bb][warp] = idx;
-                            }
-                            asm volatile("bar.sync 1, %0;" ::"r"(panel_threads) : "memory");
-                            float best = s_wc[bb][0];
-                            int q = s_wi[bb][0];
-                            for (int w = 1; w < panel_threads / 32; ++w) {
-                                const float aw = s_wc[bb][w];
-                                const int qw = s_wi[bb][w];
-                                if (aw > best || (aw == best && qw < q)) {
-                                    best = aw;
-                                    q = qw;
-                                }
-                            }
-                            if (!(best > 1e-30f)) {
-                                if (tid == 0) s_done = -1;
-                                break;  // uniform over the panel threads
-                            }
-                            if (tid == q) {
-#pragma unroll
-                                for (int pp = 0; pp < kGjBlock; ++pp) s_pc[bb][pp] = P[pp];
-                                used = true;
-                            }
-                            if (tid == 0) s_q[k0 + p] = q;
-                            asm volatile("bar.sync 1, %0;" ::"r"(panel_threads) : "memory");
-                            float pk = 0.0f;
-#pragma unroll
-                            for (int pp = 0; pp < kGjBlock; ++pp)
-                                if (pp == p) pk = P[pp];
-                            const float inv = 1.0f / s_pc[bb][p];
-                            const float nk = (tid == q) ? inv : pk * inv;
-#pragma unroll
-                            for (int pp = 0; pp < kGjBlock; ++pp)
-                                P[pp] = (pp == p) ? nk : fmaf(-s_pc[bb][pp], nk, (tid == q) ? 0.0f : P[pp]);
+                            for (int p = 0; p < kGjBlock; ++p) P[p][cc] = (col < n && p < nb) ? panel[p][col] : 0.0f;
                         }
-                        if (col) {
+                        bool sing = false;
 #pragma unroll
-                            for (int p = 0; p < kGjBlock; ++p)
-                                if (p < nb) panel[p][tid] = P[p];
+                        for (int p = 0; p < kGjBlock; ++p) {
+                            if (p < nb && !sing) {  // uniform over the warp
+                                // pivot column: the largest unused entry of panel row p
+                                float a = -1.0f;
+                                int idx = 1 << 30;
+#pragma unroll
+                                for (int cc = 0; cc < kGjCols; ++cc) {
+                                    const float av = ucol[cc] ? -1.0f : fabsf(P[p][cc]);
+                                    if (av > a) {
+                                        a = av;
+                                        idx = lane + 32 * cc;
+                                    }
+                                }
+#pragma unroll
+                                for (int off = 16; off > 0; off >>= 1) {
+                                    const float oa = __shfl_xor_sync(kFullMask, a, off);
+                                    const int oi = __shfl_xor_sync(kFullMask, idx, off);
+                                    if (oa > a || (oa == a && oi < idx)) {
+                                        a = oa;
+                                        idx = oi;
+                                    }
+                                }
+                                if (!(a > 1e-30f)) {
+                                    if (lane == 0) s_done = -1;
+                                    sing = true;
+                                } else {
+                                    const int q = idx;
+                                    const int ql = q & 31, qc = q >> 5;
+                                    // the pivot column's panel entries, from the lane that holds it
+                                    float pc[kGjBlock];
+#pragma unroll
+                                    for (int pp = 0; pp < kGjBlock; ++pp) {
+                                        float mine = P[pp][0];
+#pragma unroll
+                                        for (int cc = 1; cc < kGjCols; ++cc)
+                                            if (cc == qc) mine = P[pp][cc];
+                                        pc[pp] = __shfl_sync(kFullMask, mine, ql);
+                                    }
+                                    const float inv = 1.0f / pc[p];
+#pragma unroll
+                                    for (int cc = 0; cc < kGjCols; ++cc) {
+                                        const bool isq = (lane + 32 * cc) == q;
+                                        if (isq) ucol[cc] = true;
+                                        const float nk = isq ? inv : P[p][cc] * inv;
+#pragma unroll
+                                        for (int pp = 0; pp < kGjBlock; ++pp)
+                                            if (pp != p) P[pp][cc] = fmaf(-pc[pp], nk, isq ? 0.0f : P[pp][cc]);
+                                        P[p][cc] = nk;
+                                    }
+                                    if (lane == 0) s_q[k0 + p] = q;
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < kGjCols; ++cc) {
+                            const int col = lane + 32 * cc;
+                            if (col < n) {
+                                s_used[col] = ucol[cc] ? 1 : 0;
+#pragma unroll
+                                for (int p = 0; p < kGjBlock; ++p)
+                                    if (p < nb) panel[p][col] = P[p][cc];
+                            }
                         }
                     }
                     __syncthreads();

@@ -189,19 +189,23 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                 const Ang an = A.ang[l];
                 const double z = fma(f[1], an.sig, f[0]);
                 const double lz = log(z);
+                // s(z), clamped to [-1, 1] for z outside [eps2, lambda2] (inside, it can
+                // leave the interval only by a rounding)
                 double s = (lz - c.L0) * c.invL1;
-                s = fmin(1.0, fmax(-1.0, s));
                 const double iz = 1.0 / z;
                 const double iz2 = iz * iz;
                 double Zz = 0.0, Gz = 0.0, Wz = 0.0;  // Z(z), G(z), W(z) = G(z)^p Z(z)^q
                 // z > 0: the comparisons with eps2, lambda2 on the bit patterns
                 const long long zb = __double_as_longlong(z);
-                const bool outside =
-                    c.extrap == 0 && (zb < __double_as_longlong(c.eps2) || zb > __double_as_longlong(c.lam2));
+                const bool beyond = zb < __double_as_longlong(c.eps2) || zb > __double_as_longlong(c.lam2);
+                const bool outside = c.extrap == 0 && beyond;
+                if (beyond) s = fmin(1.0, fmax(-1.0, s));
                 if (A.stab && !outside) {
                     // Z(z), G(z), W(z) from the table: the interval by arccos in
                     // FP32, the polynomials in u = (s - mid) / half in FP64 (Horner)
-                    int it = (int)(acosf((float)s) * (float)(kSeriesM / kPi));
+                    // (FP32 s from the bits of s, truncated: the interval only)
+                    const float sf = fminf(1.0f, fmaxf(-1.0f, df_split(s, 0).x));
+                    int it = (int)(acosf(sf) * (float)(kSeriesM / kPi));
                     it = min(max(it, 0), kSeriesM - 1);
                     const SeriesRec* R = A.stab + it;
                     const double2 mh = __ldg(reinterpret_cast<const double2*>(R));
