@@ -1222,7 +1222,7 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
                                            double (*s_red)[8], int* s_conv, double tolfac, int maxit,
                                            bool early_abort, int* sweeps) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double prev = INFINITY;  // thread 0 only
+    double prev = INFINITY;  // lane 0 of warp 0 only
     int st = 0;
     for (int it = 0; it <= maxit; ++it) {
         // residual: two threads per row (8 warps), each over half of the row
@@ -1235,6 +1235,7 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
                 const int j0 = hf ? n / 2 : 0, j1 = hf ? n : n / 2;
                 double a0 = 0.0, a1 = 0.0;
                 int jj = j0;
+#pragma unroll 4
                 for (; jj + 1 < j1; jj += 2) {
                     a0 = fma(Jr[jj], s_x[jj], a0);
                     a1 = fma(Jr[jj + 1], s_x[jj + 1], a1);
@@ -1260,24 +1261,29 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            double RM = s_red[0][0], XM = s_red[1][0];
-            for (int w = 1; w < 8; ++w) {
-                RM = fmax(RM, s_red[0][w]);
-                XM = fmax(XM, s_red[1][w]);
+        if (warp == 0) {
+            // the maxima over the eight warps by shuffles (a single thread's FP64
+            // chain is slow here), the decision by lane 0
+            double RM = s_red[0][lane & 7], XM = s_red[1][lane & 7];
+            for (int off = 4; off > 0; off >>= 1) {
+                RM = fmax(RM, __shfl_xor_sync(kFullMask, RM, off));
+                XM = fmax(XM, __shfl_xor_sync(kFullMask, XM, off));
             }
-            int v = 0;  // 0: continue, 1: converged, 2: give up
-            if (!isfinite(RM)) v = 2;
-            else if (RM <= tolfac * XM) v = 1;
-            else if (it == maxit) v = 2;
-            else if (early_abort && it > 0) {
-                // observed contraction; sweeps still needed at that rate
-                const double rate = RM / prev;
-                if (!(rate <= kReuseRate)) v = 2;
-                else if (it + log(tolfac * XM / RM) / log(rate) > maxit) v = 2;
+            if (lane == 0) {
+                int v = 0;  // 0: continue, 1: converged, 2: give up
+                if (!isfinite(RM)) v = 2;
+                else if (RM <= tolfac * XM) v = 1;
+                else if (it == maxit) v = 2;
+                else if (early_abort && it > 0) {
+                    // observed contraction; sweeps still needed at that rate (FP32
+                    // logarithms: an estimate of a count)
+                    const float rate = (float)(RM / prev);
+                    if (!(rate <= (float)kReuseRate)) v = 2;
+                    else if ((float)it + __log2f((float)(tolfac * XM / RM)) / __log2f(rate) > (float)maxit) v = 2;
+                }
+                prev = RM;
+                *s_conv = v;
             }
-            prev = RM;
-            *s_conv = v;
         }
         __syncthreads();
         st = *s_conv;
@@ -1290,12 +1296,14 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
             const int n8 = (n + 7) & ~7;
             const int rot = 8 * (i & 3);
             float acc = 0.0f;
-            if (i < n)
+            if (i < n) {
+#pragma unroll 4
                 for (int t = part; t < n8; t += 8) {
                     int jj = t + rot;
                     if (jj >= n8) jj -= n8;
                     if (jj < n) acc = fmaf(Xs[i * n + jj], s_rf[jj], acc);
                 }
+            }
             acc += __shfl_xor_sync(kFullMask, acc, 4);
             acc += __shfl_xor_sync(kFullMask, acc, 2);
             acc += __shfl_xor_sync(kFullMask, acc, 1);
@@ -1922,6 +1930,7 @@ __global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, c
             sw[q] = sigw[base + q];
         }
         __syncthreads();
+#pragma unroll 2
         for (int q = ph; q < cnt; q += kSchPh) acc = fma(sw[q], cos_df(tm * sp[q], T), acc);
         __syncthreads();
     }

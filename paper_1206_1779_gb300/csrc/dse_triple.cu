@@ -31,6 +31,7 @@
 // The block's coefficient vector lives in shared memory (broadcast reads).
 #include "dse_df.cuh"
 #include "dse_internal.cuh"
+#include "dse_lntab.cuh"
 
 namespace dse {
 
@@ -40,6 +41,54 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 : 64; }
+
+// ---- ln z and 1/z (table-driven, Tang 1990) ----
+// z = 2^e m with m in [1, 2); for the leading 7 fraction bits j of m, c_j =
+// 1 + (j + 1/2)/128, inv_j = 1/c_j rounded to FP64 and L_j = -ln(inv_j) as a
+// double-double (dse_lntab.cuh, written by gen_lntab.py with 60-digit arithmetic).  With r = m inv_j - 1
+// (one FMA, |r| < 2^-7.9):
+//   ln z = e ln2 + L_j + ln(1 + r),  ln(1 + r) = r - r^2/2 + r^3/3 (FP64)
+//          - r^4 (1/4 - r/5 + r^2/6 - r^3/7) (FP32, below 2.4e-10);
+//   1/z = 2^-e inv_j / (1 + r),  1/(1 + r) = ((1 - r) + r^2) - r^3 (FP64) + r^4 (1 - r + r^2) (FP32).
+// ln2 = ln2_hi + ln2_lo with ln2_hi holding 42 significant bits, so e ln2_hi is exact.
+// Accuracy (emulated against 40-digit arithmetic over z in [1e-14, 1e8]): ln z within
+// 2 units of 2^-53 max(1, |ln z|), 1/z within 4 units in the last place.  Zero,
+// subnormal, very large, infinite and NaN arguments take the library routines.
+constexpr int kLnTab = 128;  // g_lntab: inv_j, L_j hi, L_j lo (kLnTab each), ln2_hi, ln2_lo
+
+struct LnRcp { double ln, rcp; };
+
+__device__ __forceinline__ LnRcp ln_rcp(double z) {
+    LnRcp o;
+    if (!(z >= 0x1p-1020 && z <= 0x1p+1020)) {
+        o.ln = log(z);
+        o.rcp = 1.0 / z;
+        return o;
+    }
+    const int hz = __double2hiint(z);
+    const int e = ((hz >> 20) & 0x7ff) - 1023;
+    const int j = (hz >> 13) & (kLnTab - 1);
+    const double m = __hiloint2double((hz & 0x000fffff) | 0x3ff00000, __double2loint(z));
+    const double inv = __ldg(&g_lntab[j]);
+    const double Lh = __ldg(&g_lntab[kLnTab + j]), Ll = __ldg(&g_lntab[2 * kLnTab + j]);
+    const double ln2h = __ldg(&g_lntab[3 * kLnTab]), ln2l = __ldg(&g_lntab[3 * kLnTab + 1]);
+    const double r = fma(m, inv, -1.0);
+    const double r2 = r * r;
+    const double r3 = r2 * r;
+    const float rf = df_split(r, 0).x;  // r to FP32 precision (truncated)
+    const float r4f = (rf * rf) * (rf * rf);
+    const float tl = r4f * fmaf(fmaf(fmaf(-1.0f / 7.0f, rf, 1.0f / 6.0f), rf, -0.2f), rf, 0.25f);
+    const float tq = r4f * fmaf(rf, rf - 1.0f, 1.0f);
+    // e as a double without a conversion instruction: 1.5 2^52 + (e + 2^31) - (1.5 2^52 + 2^31)
+    const double ed = __hiloint2double(0x43380000, (int)((unsigned)e ^ 0x80000000u)) - 6755401588539392.0;
+    const double lead = fma(r3, 1.0 / 3.0, fma(r2, -0.5, r));
+    const double hi = fma(ed, ln2h, Lh);
+    const double lo = fma(ed, ln2l, Ll);
+    o.ln = hi + ((lead - df_widen(tl, 1023)) + lo);
+    const double q = (((1.0 - r) + r2) - r3) + df_widen(tq, 1023);
+    o.rcp = (q * inv) * __hiloint2double((1023 - e) << 20, 0);
+    return o;
+}
 
 // The shared-memory row of a triple holds 2s and the anchors T_4i, T_4i+1
 // (i < nq = ceil(N/4)) as double-float pairs; phase B forms T_4i+2 = 2s T_4i+1 - T_4i
@@ -188,11 +237,12 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                 const double* f = srad + (kk % kRadGroup) * kRadFactors;
                 const Ang an = A.ang[l];
                 const double z = fma(f[1], an.sig, f[0]);
-                const double lz = log(z);
+                const LnRcp lr = ln_rcp(z);
+                const double lz = lr.ln;
                 // s(z), clamped to [-1, 1] for z outside [eps2, lambda2] (inside, it can
                 // leave the interval only by a rounding)
                 double s = (lz - c.L0) * c.invL1;
-                const double iz = 1.0 / z;
+                const double iz = lr.rcp;
                 const double iz2 = iz * iz;
                 double Zz = 0.0, Gz = 0.0, Wz = 0.0;  // Z(z), G(z), W(z) = G(z)^p Z(z)^q
                 // z > 0: the comparisons with eps2, lambda2 on the bit patterns
