@@ -419,6 +419,7 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
                                                 const int jb) {
     __shared__ double sU[kChunkK][3];
     __shared__ double sY[kRowKG][3][kRowJ];
+    __shared__ double sV[kRowKG][3][kRowJ];
     __shared__ double sS4;
     const int N = c.N;
     const int NZ = c.NZ, NG = c.NG, n = c.n, Rc = c.Rc;
@@ -495,6 +496,21 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
         sY[kg][1][lane] = Y1;
         sY[kg][2][lane] = Y2;
     }
+    // the z-derivative sums of the radial splits: warp kg adds the splits
+    // kg, kg + kRowKG, ... (independent loads in flight), warp 0 the warps' sums
+    // in a fixed order
+    if (FULL && !special && j < N) {
+        const double* vp = Vpart + (size_t)rt * KS * 3 * N;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+        for (int sp = kg; sp < KS; sp += kRowKG) {
+            v0 += vp[(size_t)sp * 3 * N + j];
+            v1 += vp[(size_t)sp * 3 * N + N + j];
+            v2 += vp[(size_t)sp * 3 * N + 2 * N + j];
+        }
+        sV[kg][0][lane] = v0;
+        sV[kg][1][lane] = v1;
+        sV[kg][2][lane] = v2;
+    }
     __syncthreads();
     const Row rw = rows[rt >= 0 ? rt : 0];
     const double pre = gluon ? rw.pre : 0.0;
@@ -508,11 +524,10 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
         }
         double VQ = 0.0, VM = 0.0, VG = 0.0;
         if (!special) {
-            const double* vp = Vpart + (size_t)rt * KS * 3 * N;
-            for (int sp = 0; sp < KS; ++sp) {
-                VQ += vp[(size_t)sp * 3 * N + j];
-                VM += vp[(size_t)sp * 3 * N + N + j];
-                VG += vp[(size_t)sp * 3 * N + 2 * N + j];
+            for (int q = 0; q < kRowKG; ++q) {
+                VQ += sV[q][0][lane];
+                VM += sV[q][1][lane];
+                VG += sV[q][2][lane];
             }
         } else {
             VG = y2;
@@ -2047,9 +2062,20 @@ cudaError_t launch_schwinger_map(const Consts& c, int n, const double* gx, const
     return cudaGetLastError();
 }
 
+// Node splits of the Schwinger sum: as many as fill one wave of resident blocks
+// (tb time blocks x splits <= SMs x blocks per SM), so that no SM runs a block
+// more than another; at least one split and at least one tile of nodes per split.
+// When the time blocks alone exceed a wave: about four blocks per SM.
 int schwinger_splits(int n_t, int n_nodes) {
     const int tb = (n_t + kSchT - 1) / kSchT;
-    int ns = (4 * 152 + tb - 1) / (tb > 0 ? tb : 1);
+    int dev = 0, nsm = 152, occ = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_schwinger_sum, kSchT * kSchPh, 0) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const int slots = nsm * occ;
+    int ns = tb > 0 ? slots / tb : 1;
+    if (ns < 1) ns = (4 * nsm + tb - 1) / (tb > 0 ? tb : 1);
     const int maxs = (n_nodes + kSchTile - 1) / kSchTile;
     if (ns > maxs) ns = maxs;
     if (ns < 1) ns = 1;
