@@ -95,49 +95,59 @@ __device__ __forceinline__ LnRcp ln_rcp(double z) {
 // and T_4i+3 = 2s T_4i+2 - T_4i+1 from them.  Its 4 nq derivative columns c map to
 // j = 4 (c mod nq) + c div nq, so that a warp's threads share c div nq (the same
 // number of recurrence steps) when nq is a multiple of 16.
+// With AR false (full rows) the row holds T_0 .. T_N-1 (T_0 as 1/2) and column c
+// is j = c: twice the shared memory, no recurrence steps in phase B.
 __host__ __device__ inline int anchors_for(int N) { return (N + 3) / 4; }
-__host__ __device__ inline int row_len_for(int N) {
+__host__ __device__ inline int row_len_for(int N, bool ar) {
+    if (!ar) return N + 1;
     const int l = 1 + 2 * anchors_for(N);
     return l | 1;  // odd: conflict-free rows
 }
 
-__host__ __device__ inline int groups_for(int N, int BT) {
-    const int nc = 4 * anchors_for(N);
+__host__ __device__ inline int ncols_for(int N, bool ar) { return ar ? 4 * anchors_for(N) : N; }
+
+__host__ __device__ inline int groups_for(int N, int BT, bool ar) {
+    const int nc = ncols_for(N, ar);
     const int nact = nc < BT ? nc : BT;
     return BT / nact;
 }
 
-__host__ __device__ inline size_t tile_doubles(bool full, int N, int BT) {
+__host__ __device__ inline size_t tile_doubles(bool full, int N, int BT, bool ar) {
     if (!full) return 0;
-    const size_t t = (size_t)BT * (size_t)row_len_for(N);
-    const size_t red = (size_t)groups_for(N, BT) * 3u * (size_t)N;
+    const size_t t = (size_t)BT * (size_t)row_len_for(N, ar);
+    const size_t red = (size_t)groups_for(N, BT, ar) * 3u * (size_t)N;
     return t > red ? t : red;
 }
+
+// Row layout of each kernel: the single-problem kernel keeps anchor rows (more
+// blocks per SM); the persistent batched kernel, limited by its registers, full rows.
+constexpr bool kAnchorRowsSingle = true;
+constexpr bool kAnchorRowsBatched = false;
 
 // Radial nodes whose per-node factors are formed together (by one warp) and
 // kept in shared memory, and the factors per node.
 constexpr int kRadGroup = 32;
 constexpr int kRadFactors = 8;
 
-__host__ __device__ inline size_t smem_doubles(bool full, int N, int BT) {
+__host__ __device__ inline size_t smem_doubles(bool full, int N, int BT, bool ar) {
     // tile rows, 3 BT weights (FP64, then their double-float pairs), 2 N
     // coefficients, 4 boundary sums, 3 x 8 per-warp exponent maxima, the factors
     // of a group of radial nodes
-    return tile_doubles(full, N, BT) + 6u * (size_t)BT + 2u * (size_t)N + 4u + 12u +
+    return tile_doubles(full, N, BT, ar) + 6u * (size_t)BT + 2u * (size_t)N + 4u + 12u +
            (size_t)kRadGroup * kRadFactors;
 }
 
 // One block's work: row rt, radial split ks of the problem in A.  smem holds
-// smem_doubles(FULL, N, BT) doubles.
-template <int BT, int NJ, bool FULL>
+// smem_doubles(FULL, N, BT, AR) doubles.
+template <int BT, int NJ, bool FULL, bool AR>
 __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, const int ks, double* smem) {
     const Consts& c = A.c;
     const int N = c.N;
     const int nq = anchors_for(N);
-    const int ldT = row_len_for(N);
+    const int ldT = row_len_for(N, AR);
     double* sT = smem;
     float2* sT2 = reinterpret_cast<float2*>(smem);  // rows [2s][T_4i][T_4i+1] as double-float pairs
-    double* sh = smem + tile_doubles(FULL, N, BT);
+    double* sh = smem + tile_doubles(FULL, N, BT, AR);
     float2* sh2 = reinterpret_cast<float2*>(sh + 3 * BT);  // the weights as pairs
     double* sa = sh + 6 * BT;
     double* sb = sa + N;
@@ -164,7 +174,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
 
     // phase-B mapping: NG groups of nact threads, thread owns the columns
     // c = jb + jj*nact of 4 nq: T_j with j = 4 (c mod nq) + c div nq
-    const int ncol = 4 * nq;
+    const int ncol = ncols_for(N, AR);
     const int nact = ncol < BT ? ncol : BT;
     const int NG = BT / nact;
     const int g = tid / nact;
@@ -176,9 +186,10 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
         const int cc = jb + jj * nact;
-        colr[jj] = cc / nq;
-        coli[jj] = cc - colr[jj] * nq;
-        colj[jj] = cc < ncol ? 4 * coli[jj] + colr[jj] : N;  // j >= N: inactive
+        colr[jj] = AR ? cc / nq : 0;
+        coli[jj] = AR ? cc - colr[jj] * nq : 0;
+        if (AR) colj[jj] = cc < ncol ? 4 * coli[jj] + colr[jj] : N;  // j >= N: inactive
+        else colj[jj] = cc < N ? cc : N;
     }
 
     double acc[3][NJ];
@@ -313,7 +324,8 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                             t1 = t2;
                             lg = fma(sb[j], t2, lg);
                             lzz = fma(sa[j], t2, lzz);
-                            if (FULL && (j & 3) < 2) Trow[1 + (j & 1) * nq + (j >> 2)] = df_split(t2, 0);
+                            if (FULL && AR && (j & 3) < 2) Trow[1 + (j & 1) * nq + (j >> 2)] = df_split(t2, 0);
+                            if (FULL && !AR) Trow[j] = df_split(t2, 0);
                         }
                     }
                     if (outside) {
@@ -333,7 +345,42 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         Wz = exp(c.pG * lg + c.qZ * lzz);
                     }
                 }
-                if (FULL) {
+                if (FULL && !AR) {
+                    const float2 fs = df_split(s, 0);
+                    Trow[0] = make_float2(0.5f, 0.0f);  // T_0 enters as 1/2
+                    if (N > 1) Trow[1] = fs;
+                    if (A.stab) {
+                        // T_4i, T_4i+1 by the FP64 recurrence of stride 4 (see below), T_4i+2
+                        // and T_4i+3 by two double-float steps (the direct path stored all)
+                        const double T2 = fma(2.0 * s, s, -1.0);
+                        const double T3 = fma(2.0 * s, T2, -s);
+                        const double T4 = fma(2.0 * T2, T2, -1.0);
+                        const double c4 = 2.0 * T4;
+                        const float2 s2 = make_float2(2.0f * fs.x, 2.0f * fs.y);
+                        double a0 = T4, a1 = 1.0;  // T_(4i-4), T_4i
+                        double b0 = T3, b1 = s;    // T_(4i-3), T_(4i+1)
+                        for (int j0 = 0; j0 < N; j0 += 4) {
+                            const float2 fa = j0 == 0 ? make_float2(1.0f, 0.0f) : df_split(a1, 0);
+                            const float2 fb = df_split(b1, 0);
+                            if (j0 > 0) {
+                                Trow[j0] = fa;
+                                if (j0 + 1 < N) Trow[j0 + 1] = fb;
+                            }
+                            if (j0 + 2 < N) {
+                                const float2 t2 = df_mulsub(s2, fb, fa);
+                                Trow[j0 + 2] = t2;
+                                if (j0 + 3 < N) Trow[j0 + 3] = df_mulsub(s2, t2, fb);
+                            }
+                            const double an4 = fma(c4, a1, -a0);
+                            a0 = a1;
+                            a1 = an4;
+                            const double bn = fma(c4, b1, -b0);
+                            b0 = b1;
+                            b1 = bn;
+                        }
+                    }
+                }
+                if (FULL && AR) {
                     const float2 fs = df_split(s, 0);
                     Trow[0] = make_float2(2.0f * fs.x, 2.0f * fs.y);  // 2s
                     Trow[1] = make_float2(1.0f, 0.0f);                // T_0
@@ -430,18 +477,23 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         const float2 mm = sh2[BT + m];
                         const float2 gg = sh2[2 * BT + m];
                         const float2* Tm = sT2 + (size_t)m * ldT;
-                        const float2 s2 = Tm[0];
+                        const float2 s2 = AR ? Tm[0] : make_float2(0.0f, 0.0f);
 #pragma unroll
                         for (int jj = 0; jj < NJ; ++jj) {
                             if (colj[jj] < N) {
-                                const float2 a = Tm[1 + coli[jj]];
-                                const float2 b = Tm[1 + nq + coli[jj]];
-                                float2 t = (colr[jj] & 1) ? b : a;
-                                if (colr[jj] >= 2) {
-                                    const float2 t2 = df_mulsub(s2, b, a);
-                                    t = colr[jj] == 2 ? t2 : df_mulsub(s2, t2, b);
+                                float2 t;
+                                if (AR) {
+                                    const float2 a = Tm[1 + coli[jj]];
+                                    const float2 b = Tm[1 + nq + coli[jj]];
+                                    t = (colr[jj] & 1) ? b : a;
+                                    if (colr[jj] >= 2) {
+                                        const float2 t2 = df_mulsub(s2, b, a);
+                                        t = colr[jj] == 2 ? t2 : df_mulsub(s2, t2, b);
+                                    }
+                                    if (colj[jj] == 0) t = make_float2(0.5f, 0.0f);  // T_0 enters as 1/2
+                                } else {
+                                    t = Tm[colj[jj]];
                                 }
-                                if (colj[jj] == 0) t = make_float2(0.5f, 0.0f);  // T_0 enters as 1/2
                                 df_fma(ca[0][jj], q, t);
                                 df_fma(ca[1][jj], mm, t);
                                 df_fma(ca[2][jj], gg, t);
@@ -494,7 +546,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
 template <int BT, int NJ, bool FULL>
 __global__ void __launch_bounds__(BT) k_triple(const __grid_constant__ TripleArgs A) {
     extern __shared__ __align__(16) double smem[];
-    triple_tile<BT, NJ, FULL>(A, blockIdx.y, blockIdx.x, smem);
+    triple_tile<BT, NJ, FULL, kAnchorRowsSingle>(A, blockIdx.y, blockIdx.x, smem);
 }
 
 // Persistent form for a batch of independent problems: each block takes work
@@ -518,14 +570,14 @@ __global__ void __launch_bounds__(BT) k_triple_batched(const BatchProblem* __res
         if (!P[w.b].active) continue;
         TripleArgs A = P[w.b].t;
         A.coef = coef_base + P[w.b].coef_off;
-        triple_tile<BT, NJ, FULL>(A, w.rt, w.ks, smem);
+        triple_tile<BT, NJ, FULL, kAnchorRowsBatched>(A, w.rt, w.ks, smem);
     }
 }
 
 template <int BT, bool FULL>
 cudaError_t launch_bt(const TripleArgs& a, cudaStream_t s) {
     const int N = a.c.N;
-    const size_t smem = smem_doubles(FULL, N, BT) * sizeof(double);
+    const size_t smem = smem_doubles(FULL, N, BT, kAnchorRowsSingle) * sizeof(double);
     const dim3 grid(a.KS, a.Rt);
     const int nj = (N + BT - 1) / BT;
     cudaError_t e = cudaSuccess;
@@ -549,7 +601,7 @@ cudaError_t launch_bt(const TripleArgs& a, cudaStream_t s) {
 
 template <int BT, bool FULL>
 int occupancy_bt(int N) {
-    const size_t smem = smem_doubles(FULL, N, BT) * sizeof(double);
+    const size_t smem = smem_doubles(FULL, N, BT, kAnchorRowsSingle) * sizeof(double);
     const int nj = (N + BT - 1) / BT;
     int nb = 0;
     cudaError_t e;
@@ -571,7 +623,7 @@ int occupancy_bt(int N) {
 int triple_block_threads(int N) { return block_threads_for(N); }
 
 size_t triple_smem_bytes(bool full, int N) {
-    return smem_doubles(full, N, block_threads_for(N)) * sizeof(double);
+    return smem_doubles(full, N, block_threads_for(N), kAnchorRowsSingle) * sizeof(double);
 }
 
 int triple_max_blocks_per_sm(bool full, int N) {
@@ -583,7 +635,7 @@ namespace {
 template <int BT, bool FULL>
 cudaError_t launch_batched_bt(const BatchProblem* P, const BatchItem* items, int n_items, int* counter,
                               const double* coef_base, int maxN, int grid, cudaStream_t s) {
-    const size_t smem = smem_doubles(FULL, maxN, BT) * sizeof(double);
+    const size_t smem = smem_doubles(FULL, maxN, BT, kAnchorRowsBatched) * sizeof(double);
     const int nj = (maxN + BT - 1) / BT;
     // the shared-memory limit was set by triple_batched_blocks_per_sm (no attribute
     // change here: this launch may be captured into a graph)
@@ -598,7 +650,7 @@ cudaError_t launch_batched_bt(const BatchProblem* P, const BatchItem* items, int
 
 template <int BT, bool FULL>
 int batched_occupancy_bt(int maxN) {
-    const size_t smem = smem_doubles(FULL, maxN, BT) * sizeof(double);
+    const size_t smem = smem_doubles(FULL, maxN, BT, kAnchorRowsBatched) * sizeof(double);
     const int nj = (maxN + BT - 1) / BT;
     int nb = 0;
     cudaError_t e;
