@@ -15,6 +15,9 @@ struct dse_plan {
     dse_problem prob;
     Consts c;
     cudaStream_t stream;
+    // the series table is built on side while the tables kernel runs on stream
+    cudaStream_t side;
+    cudaEvent_t fork, join;
     int Rt, KB, KS, nch;
     // fixed workspace (one allocation)
     void* ws;
@@ -158,6 +161,9 @@ void free_plan(dse_plan* pl) {
     if (!pl) return;
     free_fd(pl);
     release_events(pl);
+    if (pl->fork) cudaEventDestroy(pl->fork);
+    if (pl->join) cudaEventDestroy(pl->join);
+    if (pl->side) cudaStreamDestroy(pl->side);
     if (pl->ws) cudaFree(pl->ws);
     if (pl->sch) cudaFree(pl->sch);
     if (pl->sch_partial) cudaFree(pl->sch_partial);
@@ -186,11 +192,19 @@ TripleArgs triple_args(const dse_plan* pl, const double* coef) {
 // tables -> quadrature kernel -> per-row contraction (the D vectors).  fp32: the
 // FP32-integrand kernel (mixed precision) instead of the FP64 one.
 cudaError_t build_rows(dse_plan* pl, const double* coef, bool full, bool fp32) {
-    cudaError_t e = launch_tables(pl->c, coef, pl->rad, pl->xcol, pl->ytab, pl->phiy, pl->xtab, pl->phix, pl->stream);
-    if (e == cudaSuccess && use_series_table(pl->c.N)) {
-        e = launch_series_table(pl->c, coef, pl->stab, pl->stream);
+    cudaError_t e = cudaSuccess;
+    const bool table = use_series_table(pl->c.N);
+    if (table) {
+        // the series table (independent of the tables kernel) on the side stream
+        e = cudaEventRecord(pl->fork, pl->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->side, pl->fork, 0);
+        if (e == cudaSuccess) e = launch_series_table(pl->c, coef, pl->stab, pl->side);
+        if (e == cudaSuccess) e = cudaEventRecord(pl->join, pl->side);
         pl->launches += 1;
     }
+    if (e == cudaSuccess)
+        e = launch_tables(pl->c, coef, pl->rad, pl->xcol, pl->ytab, pl->phiy, pl->xtab, pl->phix, pl->stream);
+    if (e == cudaSuccess && table) e = cudaStreamWaitEvent(pl->stream, pl->join, 0);
     const bool timed = pl->profiling && pl->n_ev < 4096 && !fp32;
     if (timed && e == cudaSuccess) {
         e = cudaEventCreate(&pl->ev[2 * pl->n_ev]);
@@ -273,6 +287,12 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     const int N = pl->c.N, nr = pl->c.nr, na = pl->c.na, Rc = pl->c.Rc;
     pl->Rt = Rc + 1 + (problem->x_G > 0.0 ? 1 : 0);
     pl->nch = (na + 31) / 32;
+    if (cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->join, cudaEventDisableTiming) != cudaSuccess) {
+        free_plan(pl);
+        return DSE_ERR_CUDA;
+    }
     choose_split(pl);
     const int n = pl->c.n;
     const int nrule = pl->c.nrule;
