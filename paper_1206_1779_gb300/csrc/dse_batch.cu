@@ -87,7 +87,7 @@ Consts batch_consts(const dse_problem* p) {
     c.radmode = p->radial_mode;
     c.angmode = p->angular_mode;
     c.nr = p->radial_mode == 1 ? 3 * p->n_radial : p->n_radial;
-    c.pad_ = 0;
+    c.sM = series_intervals(c.N);
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;
     c.eps2 = p->eps2;

@@ -28,7 +28,7 @@ enum : int { kStatusNonfinite = 1, kStatusSingular = 2 };
 struct Consts {
     int N, nr, na, extrap;
     int NZ, NG, n, Rc, gofs;
-    int nrule, radmode, angmode, pad_;
+    int nrule, radmode, angmode, sM;  // sM: series-table intervals (0: no table)
     double eps2, lam2, ln_eps2, ln_lam2;
     double L0, L1, invL1;          // ln x = L0 + L1 s
     double K;                      // g^2 Nc / (2 pi)^3
@@ -62,12 +62,12 @@ struct YTab { double lG, lZ, G, Z, pq, yG, Wy, pad1; };
 struct XTab { double lG, lZ, G, Z, Ginv, Zinv, pad0, pad1; };
 
 // Piecewise-polynomial table of the dressing functions on s in [-1, 1] (inside
-// [eps2, lambda2]): kSeriesM intervals uniform in theta = arccos s, on each a
-// polynomial of degree kSeriesP in u = (s - mid) * invhalf in [-1, 1] (monomial
-// coefficients) for Z(s), G(s) (pairs e[k]) and W(s) = G^p Z^q (w[k]), fitted at
-// kSeriesP + 1 Chebyshev points where ln Z, ln G come from a compensated Clenshaw
-// recurrence.  With interval width h = pi/kSeriesM the fit error is
-// ~ (N h/4)^(P+1)/(P+1)! relative: below 1e-19 for N <= 128 and ~1e-15 for the
+// [eps2, lambda2]): M = series_intervals(N) = kSeriesM intervals uniform in
+// theta = arccos s, on each a polynomial of degree kSeriesP in u = (s - mid) * invhalf
+// in [-1, 1] (monomial coefficients) for Z(s), G(s) (pairs e[k]) and W(s) = G^p Z^q
+// (w[k]), fitted at kSeriesP + 1 Chebyshev points where ln Z, ln G come from a
+// compensated Clenshaw recurrence.  With interval width h = pi/M the fit error is
+// ~ (N h/4)^(P+1)/(P+1)! relative: below 2e-20 for M >= 2N and ~1e-15 for the
 // highest mode at N = 256 (whose coefficient is small for a smooth solution), so the FP64
 // quadrature kernel reads the table for kSeriesMinN <= N <= kSeriesMaxN in place
 // of the per-triple series sums and exponentials.  The leading kSeriesLead
@@ -93,6 +93,11 @@ struct SeriesRec {
 // ln Z(s=-1), ln G(s=-1) (summed in the order of the per-triple recurrence).
 constexpr int kSeriesRecords = kSeriesM + 1;
 __host__ __device__ inline bool use_series_table(int N) { return N >= kSeriesMinN && N <= kSeriesMaxN; }
+// Intervals of a problem's table (the end-point record stays at index kSeriesM).
+// Fewer intervals would not shorten the build, whose time is the length of one
+// lane's compensated Clenshaw chain (N steps), and at N = 64 the hot kernel ran
+// 4 % slower with 128 intervals than with 256.
+__host__ __device__ inline int series_intervals(int N) { return use_series_table(N) ? kSeriesM : 0; }
 
 struct TripleArgs {
     Consts c;

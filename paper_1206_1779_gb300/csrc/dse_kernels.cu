@@ -296,6 +296,7 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     __shared__ double tcoef[kSeriesQ][kSeriesQ];  // tcoef[j][k] = [u^k] T_j(u)
     __shared__ double dct[kSeriesQ][kSeriesQ];    // dct[k][r] = cos(pi k (r + 1/2)/Q)
     __shared__ double scf[2 * DSE_MAX_CHEB];      // a then b
+    if (blk * kSeriesIntervalsPerBlock >= c.sM) return;  // (batched grids span the largest table)
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int il = lane / kSeriesQ, q = lane % kSeriesQ;
     for (int j = threadIdx.x; j < c.n; j += blockDim.x) scf[j] = coef[j];
@@ -319,7 +320,7 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
         }
     }
     const int i = blk * kSeriesIntervalsPerBlock + il;
-    const double h = kPi / kSeriesM;
+    const double h = kPi / c.sM;
     const double th0 = i * h, th1 = (i + 1) * h;
     const double mid = 0.5 * (cos(th0) + cos(th1));
     const double half = sin(0.5 * (th0 + th1)) * sin(0.5 * h);  // (cos th0 - cos th1)/2 without cancellation
@@ -2094,7 +2095,7 @@ cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, c
 }
 
 cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* tab, cudaStream_t s) {
-    k_series_table<<<kSeriesM / kSeriesIntervalsPerBlock, kSeriesThreads, 0, s>>>(c, coef, tab);
+    k_series_table<<<c.sM / kSeriesIntervalsPerBlock, kSeriesThreads, 0, s>>>(c, coef, tab);
     return cudaGetLastError();
 }
 

@@ -101,7 +101,7 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
     c.nrule = p->n_radial;
     c.radmode = 0;
     c.angmode = p->angular_mode;
-    c.pad_ = 0;
+    c.sM = 0;  // no series table here
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;
     c.eps2 = p->eps2;

@@ -97,7 +97,7 @@ Consts make_consts(const dse_problem* p) {
     c.nrule = p->n_radial;
     c.radmode = p->radial_mode;
     c.angmode = p->angular_mode;
-    c.pad_ = 0;
+    c.sM = series_intervals(c.N);
     c.nr = p->radial_mode == 1 ? 3 * p->n_radial : p->n_radial;
     c.na = p->n_angular;
     c.extrap = p->extrap_mode;

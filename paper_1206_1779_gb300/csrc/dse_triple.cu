@@ -197,6 +197,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     for (int jj = 0; jj < NJ; ++jj) acc[0][jj] = acc[1][jj] = acc[2][jj] = 0.0;
     static_assert(WARPS <= 8, "per-warp exponent maxima hold 8 warps");
 
+    const float ith_scale = (float)c.sM * (float)(1.0 / kPi);  // theta -> interval index
     // the series at s = +-1 from the table's end-point record
     if (A.stab && tid < 4) sbnd[tid] = reinterpret_cast<const double*>(A.stab + kSeriesM)[tid];
     __syncthreads();
@@ -266,8 +267,8 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     // FP32, the polynomials in u = (s - mid) / half in FP64 (Horner)
                     // (FP32 s from the bits of s, truncated: the interval only)
                     const float sf = fminf(1.0f, fmaxf(-1.0f, df_split(s, 0).x));
-                    int it = (int)(acosf(sf) * (float)(kSeriesM / kPi));
-                    it = min(max(it, 0), kSeriesM - 1);
+                    int it = (int)(acosf(sf) * ith_scale);
+                    it = min(max(it, 0), c.sM - 1);
                     const SeriesRec* R = A.stab + it;
                     const double2 mh = __ldg(reinterpret_cast<const double2*>(R));
                     const double uu = (s - mh.x) * mh.y;
