@@ -1512,25 +1512,22 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
                         for (int p = 0; p < kGjBlock; ++p) {
                             if (p < nb && !sing) {  // uniform over the warp
                                 // pivot column: the largest unused entry of panel row p
-                                float a = -1.0f;
-                                int idx = 1 << 30;
+                                // |a| as bits (monotonic for non-negative floats; pivoted
+                                // columns 0): the warp maximum by one reduction, then the
+                                // lowest column holding it by another
+                                unsigned ab = 0u;
+                                int idx = 0x7fffffff;
 #pragma unroll
                                 for (int cc = 0; cc < kGjCols; ++cc) {
-                                    const float av = ucol[cc] ? -1.0f : fabsf(P[p][cc]);
-                                    if (av > a) {
-                                        a = av;
+                                    const unsigned bv = ucol[cc] ? 0u : (unsigned)__float_as_int(fabsf(P[p][cc]));
+                                    if (bv > ab) {  // the first of equal maxima
+                                        ab = bv;
                                         idx = lane + 32 * cc;
                                     }
                                 }
-#pragma unroll
-                                for (int off = 16; off > 0; off >>= 1) {
-                                    const float oa = __shfl_xor_sync(kFullMask, a, off);
-                                    const int oi = __shfl_xor_sync(kFullMask, idx, off);
-                                    if (oa > a || (oa == a && oi < idx)) {
-                                        a = oa;
-                                        idx = oi;
-                                    }
-                                }
+                                const unsigned mb = __reduce_max_sync(kFullMask, ab);
+                                idx = (int)__reduce_min_sync(kFullMask, ab == mb ? (unsigned)idx : 0x7fffffffu);
+                                const float a = __int_as_float((int)mb);
                                 if (!(a > 1e-30f)) {
                                     if (lane == 0) s_done = -1;
                                     sing = true;
@@ -1860,17 +1857,18 @@ __global__ void k_schwinger_weights(const Consts c, const double* __restrict__ c
 // cos x for |x| < 2^50, FP64-accurate (a few units in the last place) with most of
 // the arithmetic on the FP32 pipe.  Cody-Waite reduction (Cody & Waite 1980):
 // k = nearest integer to 2x/pi (the 1.5 2^52 shifter), r = x - k pi/2 with pi/2 in
-// three FP64 parts (FMA; P1 = pi/2 rounded to FP64, P2 = pi/2 - P1 rounded,
-// P3 = pi/2 - P1 - P2 rounded), |r| <= pi/4.  Then by the quadrant k mod 4
+// two FP64 parts (FMA; P1 = pi/2 rounded to FP64, P2 = pi/2 - P1 rounded; the
+// remainder |pi/2 - P1 - P2| < 1.5e-33 leaves k below 2^50 an error under 2e-18,
+// below an ulp of r), |r| <= pi/4.  Then by the quadrant k mod 4
 // cos x = +-cos r or -+sin r, with the Taylor series split as
 //   cos r = (1 - r^2/2) + r^4 (1/4! - r^2/6! + ... + r^14/18!)
 //   sin r = (r - r^3/6) + r^5 (1/5! - r^2/7! + ... + r^14/19!)
 // (truncation below 4e-21 for |r| <= pi/4): the leading terms in FP64, the tails
 // (at most 0.016) in double-float, both tails for every lane so that the quadrant
-// selects without divergence.
+// selects without divergence.  The caller keeps the two parts apart (an FP64 sum of
+// w lead, a double-float sum of w tail) and adds them once at the end.
 constexpr double kPio2_1 = 1.5707963267948966;
 constexpr double kPio2_2 = 6.123233995736766e-17;
-constexpr double kPio2_3 = -1.4973849048591698e-33;
 constexpr double kTwoOverPi = 0.6366197723675814;
 constexpr double kRoundShifter = 6755399441055744.0;  // 1.5 2^52
 
@@ -1891,13 +1889,14 @@ __device__ __forceinline__ CosTail cos_tail_coefficients() {
     return t;
 }
 
-__device__ __forceinline__ double cos_df(double x, const CosTail& T) {
+struct CosParts { double lead; float2 tail; };
+
+__device__ __forceinline__ CosParts cos_df(double x, const CosTail& T) {
     double kd = fma(x, kTwoOverPi, kRoundShifter);
     const int q = __double2loint(kd) & 3;
     kd -= kRoundShifter;
     double r = fma(-kd, kPio2_1, x);
     r = fma(-kd, kPio2_2, r);
-    r = fma(-kd, kPio2_3, r);
     const double r2 = r * r;
     const float2 rd = df_split(r, 0);
     const float2 r2d = df_mul(rd, rd);
@@ -1912,8 +1911,11 @@ __device__ __forceinline__ double cos_df(double x, const CosTail& T) {
     float2 t = df_mul(odd ? ps : pc, r4d);
     t = df_mul(t, odd ? rd : make_float2(1.0f, 0.0f));
     const double lead = fma(odd ? r * r2 : r2, odd ? -1.0 / 6.0 : -0.5, odd ? r : 1.0);
-    const double v = lead + (df_widen(t.x, 1023) + df_widen(t.y, 1023));
-    return (q == 1 || q == 2) ? -v : v;
+    const bool neg = (q == 1 || q == 2);
+    CosParts o;
+    o.lead = neg ? -lead : lead;
+    o.tail = neg ? make_float2(-t.x, -t.y) : t;
+    return o;
 }
 
 // partial[s][m] = sum over nodes of split s of sigw_n cos(t_m p_n).
@@ -1928,6 +1930,7 @@ __global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, c
                                                                   int nsplit, double* __restrict__ partial) {
     __shared__ double sp[kSchTile];
     __shared__ double sw[kSchTile];
+    __shared__ float2 swd[kSchTile];  // the weights as double-float pairs
     __shared__ double sred[kSchPh][kSchT];
     const int tl = threadIdx.x % kSchT;
     const int ph = threadIdx.x / kSchT;
@@ -1938,18 +1941,27 @@ __global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, c
     const int n1 = min(n_nodes, n0 + per);
     const double tm = m < n_t ? t[m] : 0.0;
     const CosTail T = cos_tail_coefficients();
-    double acc = 0.0;
+    double acc = 0.0;                   // sum of w lead (FP64)
+    float2 acct = make_float2(0.f, 0.f);  // sum of w tail (double-float)
     for (int base = n0; base < n1; base += kSchTile) {
         const int cnt = min(kSchTile, n1 - base);
         for (int q = threadIdx.x; q < cnt; q += kSchT * kSchPh) {
             sp[q] = pn[base + q];
-            sw[q] = sigw[base + q];
+            const double w = sigw[base + q];
+            sw[q] = w;
+            swd[q] = df_split(w, 0);
         }
         __syncthreads();
 #pragma unroll 2
-        for (int q = ph; q < cnt; q += kSchPh) acc = fma(sw[q], cos_df(tm * sp[q], T), acc);
+        for (int q = ph; q < cnt; q += kSchPh) {
+            const CosParts cp = cos_df(tm * sp[q], T);
+            acc = fma(sw[q], cp.lead, acc);
+            df_fma(acct, swd[q], cp.tail);
+            df_renorm(acct);
+        }
         __syncthreads();
     }
+    acc += df_widen(acct.x, 1023) + df_widen(acct.y, 1023);
     sred[ph][tl] = acc;
     __syncthreads();
     if (ph == 0 && m < n_t) {

@@ -1,5 +1,5 @@
 """Host-side pins for the constants of the Schwinger-function cosine
-(dse_kernels.cu): the three-part pi/2 of the Cody-Waite reduction, 2/pi and the
+(dse_kernels.cu): the two-part pi/2 of the Cody-Waite reduction, 2/pi and the
 rounding shifter, checked against 50-digit arithmetic; and the tail-coefficient
 recurrence of the kernel (the factorials (2k+4)!, (2k+5)! it builds by products)."""
 import math
@@ -22,12 +22,12 @@ def test_reduction_constants():
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 50
     half_pi = mpmath.pi / 2
-    p1, p2, p3 = constant("kPio2_1"), constant("kPio2_2"), constant("kPio2_3")
+    p1, p2 = constant("kPio2_1"), constant("kPio2_2")
     assert p1 == float(half_pi)
     assert p2 == float(half_pi - mpmath.mpf(p1))
-    assert p3 == float(half_pi - mpmath.mpf(p1) - mpmath.mpf(p2))
-    # the three parts carry pi/2 to ~1e-49
-    assert abs(mpmath.mpf(p1) + mpmath.mpf(p2) + mpmath.mpf(p3) - half_pi) < 1e-48
+    # the two parts carry pi/2 to 1.5e-33: k below 2^50 leaves an error under 2e-18
+    rem = abs(mpmath.mpf(p1) + mpmath.mpf(p2) - half_pi)
+    assert rem < 1.5e-33 and rem * 2 ** 50 < 2e-18
     assert constant("kTwoOverPi") == float(2 / mpmath.pi)
     assert constant("kRoundShifter") == 1.5 * 2.0 ** 52
 
