@@ -62,16 +62,16 @@ def work_per_triple(N: int):
     double-float tile sums to the FP64 accumulators.  The dressing functions at z:
     for N in SERIES_TABLE_N read from the table (u: 3 flops; for Z, G and W the
     SERIES_TABLE_LEAD leading Horner steps in FP64, 2 flops each, and the widened
-    tail, 1) with T_j(z) from the stride-4 FP64 recurrence (N/4 steps of two FMAs:
-    N flops, plus 8 for T_2, T_3, T_4); else the two series and the recurrence summed
-    per triple (3N FMA: 6N flops).
+    tail, 1) with T_2 .. T_5 in FP64 (8 flops); else the two series and the
+    recurrence summed per triple (3N FMA: 6N flops).
     Double-float: the three derivative sums weight * phi_j(z) (3N multiply-adds) and,
-    on the table path, T_4i+2 and T_4i+3 from the anchors (N/2 multiply-subtracts) and
-    the three table tails (3 (SERIES_TABLE_DEGREE - SERIES_TABLE_LEAD) multiply-adds,
-    counted with the multiply-subtracts: 15 FP32 instructions each)."""
+    on the table path, the anchors T_4i, T_4i+1 by the stride-4 recurrence (N/2
+    multiply-subtracts), T_4i+2 and T_4i+3 from them (N/2) and the three table tails
+    (3 (SERIES_TABLE_DEGREE - SERIES_TABLE_LEAD) multiply-adds, counted with the
+    multiply-subtracts: 15 FP32 instructions each)."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
         tail = 3.0 * (SERIES_TABLE_DEGREE - SERIES_TABLE_LEAD)
-        return (N + 8.0 + 3.0 + 3.0 * (2.0 * SERIES_TABLE_LEAD + 1.0) + 50.0 + 9.0, 3.0 * N, N / 2.0 + tail)
+        return (8.0 + 3.0 + 3.0 * (2.0 * SERIES_TABLE_LEAD + 1.0) + 50.0 + 9.0, 3.0 * N, float(N) + tail)
     return 6.0 * N + 50.0 + 9.0, 3.0 * N, 0.0
 
 

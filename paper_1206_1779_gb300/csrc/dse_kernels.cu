@@ -1854,8 +1854,8 @@ __global__ void k_schwinger_weights(const Consts c, const double* __restrict__ c
     sigw[i] = wn[i] * exp(z) / x / kPi;
 }
 
-// cos x for |x| < 2^50, FP64-accurate (a few units in the last place) with most of
-// the arithmetic on the FP32 pipe.  Cody-Waite reduction (Cody & Waite 1980):
+// cos x for |x| < 2^49 (the caller takes the library cos beyond), FP64-accurate (a
+// few units in the last place) with most of the arithmetic on the FP32 pipe.  Cody-Waite reduction (Cody & Waite 1980):
 // k = nearest integer to 2x/pi (the 1.5 2^52 shifter), r = x - k pi/2 with pi/2 in
 // two FP64 parts (FMA; P1 = pi/2 rounded to FP64, P2 = pi/2 - P1 rounded; the
 // remainder |pi/2 - P1 - P2| < 1.5e-33 leaves k below 2^50 an error under 2e-18,
@@ -1871,6 +1871,7 @@ constexpr double kPio2_1 = 1.5707963267948966;
 constexpr double kPio2_2 = 6.123233995736766e-17;
 constexpr double kTwoOverPi = 0.6366197723675814;
 constexpr double kRoundShifter = 6755399441055744.0;  // 1.5 2^52
+constexpr double kCosReduceMax = 0x1p49;  // |x| from which the library cos is used
 
 struct CosTail { float2 c[8], s[8]; };
 
@@ -1940,28 +1941,48 @@ __global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, c
     const int n0 = s * per;
     const int n1 = min(n_nodes, n0 + per);
     const double tm = m < n_t ? t[m] : 0.0;
+    // Scale of the double-float tail sum: the largest |w| of the split maps to
+    // about 2^100, so that w tail (|tail| <= 0.016) summed over up to 2^20 nodes
+    // stays inside the FP32 range, and weights more than 2^-226 below the largest
+    // (whose tail terms are below 2^-232 of it) are the only ones flushed.
+    __shared__ int semax[kSchPh];
+    int em = 0;
+    for (int q = n0 + (int)threadIdx.x; q < n1; q += kSchT * kSchPh)
+        em = max(em, (int)(((unsigned)__double2hiint(sigw[q]) >> 20) & 0x7ffu));
+    em = (int)__reduce_max_sync(kFullMask, (unsigned)em);
+    if (tl == 0) semax[ph] = em;
+    __syncthreads();
+    em = semax[0];
+#pragma unroll
+    for (int q = 1; q < kSchPh; ++q) em = max(em, semax[q]);
+    const int sh = em - 1123;  // biased FP32 exponent of (largest |w|) 2^-sh is 227
     const CosTail T = cos_tail_coefficients();
     double acc = 0.0;                   // sum of w lead (FP64)
-    float2 acct = make_float2(0.f, 0.f);  // sum of w tail (double-float)
+    float2 acct = make_float2(0.f, 0.f);  // sum of w tail 2^-sh (double-float)
     for (int base = n0; base < n1; base += kSchTile) {
         const int cnt = min(kSchTile, n1 - base);
         for (int q = threadIdx.x; q < cnt; q += kSchT * kSchPh) {
             sp[q] = pn[base + q];
             const double w = sigw[base + q];
             sw[q] = w;
-            swd[q] = df_split(w, 0);
+            swd[q] = df_split(w, sh);
         }
         __syncthreads();
 #pragma unroll 2
         for (int q = ph; q < cnt; q += kSchPh) {
-            const CosParts cp = cos_df(tm * sp[q], T);
+            const double x = tm * sp[q];
+            CosParts cp = cos_df(x, T);
+            if (fabs(x) >= kCosReduceMax) {  // beyond the two-part reduction
+                cp.lead = cos(x);
+                cp.tail = make_float2(0.f, 0.f);
+            }
             acc = fma(sw[q], cp.lead, acc);
             df_fma(acct, swd[q], cp.tail);
             df_renorm(acct);
         }
         __syncthreads();
     }
-    acc += df_widen(acct.x, 1023) + df_widen(acct.y, 1023);
+    acc += df_widen(acct.x, 1023 + sh) + df_widen(acct.y, 1023 + sh);
     sred[ph][tl] = acc;
     __syncthreads();
     if (ph == 0 && m < n_t) {

@@ -351,31 +351,30 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     Trow[0] = make_float2(0.5f, 0.0f);  // T_0 enters as 1/2
                     if (N > 1) Trow[1] = fs;
                     if (A.stab) {
-                        // T_4i, T_4i+1 by the FP64 recurrence of stride 4 (see below), T_4i+2
-                        // and T_4i+3 by two double-float steps (the direct path stored all)
+                        // T_4i, T_4i+1 by the double-float recurrence of stride 4 (see
+                        // below), T_4i+2 and T_4i+3 by two double-float steps (the direct
+                        // path stored all)
                         const double T2 = fma(2.0 * s, s, -1.0);
                         const double T3 = fma(2.0 * s, T2, -s);
                         const double T4 = fma(2.0 * T2, T2, -1.0);
-                        const double c4 = 2.0 * T4;
+                        const float2 c4 = df_split(2.0 * T4, 0);
                         const float2 s2 = make_float2(2.0f * fs.x, 2.0f * fs.y);
-                        double a0 = T4, a1 = 1.0;  // T_(4i-4), T_4i
-                        double b0 = T3, b1 = s;    // T_(4i-3), T_(4i+1)
+                        float2 a0 = df_split(T4, 0), a1 = make_float2(1.0f, 0.0f);  // T_(4i-4), T_4i
+                        float2 b0 = df_split(T3, 0), b1 = fs;                       // T_(4i-3), T_(4i+1)
                         for (int j0 = 0; j0 < N; j0 += 4) {
-                            const float2 fa = j0 == 0 ? make_float2(1.0f, 0.0f) : df_split(a1, 0);
-                            const float2 fb = df_split(b1, 0);
                             if (j0 > 0) {
-                                Trow[j0] = fa;
-                                if (j0 + 1 < N) Trow[j0 + 1] = fb;
+                                Trow[j0] = a1;
+                                if (j0 + 1 < N) Trow[j0 + 1] = b1;
                             }
                             if (j0 + 2 < N) {
-                                const float2 t2 = df_mulsub(s2, fb, fa);
+                                const float2 t2 = df_mulsub(s2, b1, a1);
                                 Trow[j0 + 2] = t2;
-                                if (j0 + 3 < N) Trow[j0 + 3] = df_mulsub(s2, t2, fb);
+                                if (j0 + 3 < N) Trow[j0 + 3] = df_mulsub(s2, t2, b1);
                             }
-                            const double an4 = fma(c4, a1, -a0);
+                            const float2 an4 = df_mulsub(c4, a1, a0);
                             a0 = a1;
                             a1 = an4;
-                            const double bn = fma(c4, b1, -b0);
+                            const float2 bn = df_mulsub(c4, b1, b0);
                             b0 = b1;
                             b1 = bn;
                         }
@@ -387,22 +386,24 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     Trow[1] = make_float2(1.0f, 0.0f);                // T_0
                     Trow[1 + nq] = fs;                                // T_1
                     if (A.stab) {
-                        // T_4i and T_4i+1 (the direct path stored them above) by the FP64
+                        // T_4i and T_4i+1 (the direct path stored them above) by the
                         // recurrence of stride 4, X_(i+1) = 2 T_4 X_i - X_(i-1) (from
-                        // T_(m+4) + T_(m-4) = 2 T_4 T_m)
+                        // T_(m+4) + T_(m-4) = 2 T_4 T_m), in double-float from T_4 and T_5
+                        // formed in FP64: the rounding errors (2^-48 per step) grow at most
+                        // like i^2 over i steps, below 2 i^2 2^-48 for |s| <= 1
                         const double T2 = fma(2.0 * s, s, -1.0);
                         const double T3 = fma(2.0 * s, T2, -s);
                         const double T4 = fma(2.0 * T2, T2, -1.0);
-                        const double c4 = 2.0 * T4;
-                        double a0 = 1.0, a1 = T4;  // T_(4i-4), T_4i
-                        double b0 = s, b1 = fma(2.0 * s, T4, -T3);  // T_(4i-3), T_(4i+1)
+                        const float2 c4 = df_split(2.0 * T4, 0);
+                        float2 a0 = make_float2(1.0f, 0.0f), a1 = df_split(T4, 0);  // T_(4i-4), T_4i
+                        float2 b0 = fs, b1 = df_split(fma(2.0 * s, T4, -T3), 0);    // T_(4i-3), T_(4i+1)
                         for (int i = 1; i < nq; ++i) {
-                            Trow[1 + i] = df_split(a1, 0);
-                            Trow[1 + nq + i] = df_split(b1, 0);
-                            const double an4 = fma(c4, a1, -a0);
+                            Trow[1 + i] = a1;
+                            Trow[1 + nq + i] = b1;
+                            const float2 an4 = df_mulsub(c4, a1, a0);
                             a0 = a1;
                             a1 = an4;
-                            const double bn = fma(c4, b1, -b0);
+                            const float2 bn = df_mulsub(c4, b1, b0);
                             b0 = b1;
                             b1 = bn;
                         }

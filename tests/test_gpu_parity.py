@@ -302,6 +302,42 @@ def test_schwinger_parity(dse, oracle, inputs, n_t, n_nodes):
     assert np.all(np.abs(dg - do) <= 1e-11 * np.abs(do) + 1e-14 * scale)
 
 
+def _schwinger_check(dse, oracle, p, c, t, n_nodes):
+    do = oracle.schwinger(p, c, t, n_nodes)
+    pn, wn = oracle.schwinger_nodes(p, n_nodes)
+    lG, lZ = oracle.dressing(p, c, pn * pn)
+    scale = np.sum(np.abs(wn * np.exp(lZ) / (pn * pn))) / math.pi
+    with dse.Plan(p) as plan:
+        dg = to_host(plan.schwinger(to_dev(c), to_dev(t), n_nodes))
+    assert np.all(np.isfinite(dg))
+    assert np.all(np.abs(dg - do) <= 1e-11 * np.abs(do) + 1e-14 * scale)
+
+
+@pytest.mark.parametrize("shift", [-240.0, 240.0])
+def test_schwinger_weight_range(dse, oracle, inputs, shift):
+    # Z scaled by e^(-+120) (the T_0 coefficient enters ln Z with weight 1/2): the
+    # weights Z/(pi p^2) lie far outside the FP32 range on both sides, which the
+    # double-float part of the sum must follow by its scale.
+    p = inputs.problem(12, 8, 8)
+    c = inputs.starting_guess(p, seed=2).copy()
+    c[0] += shift
+    _schwinger_check(dse, oracle, p, c, inputs.schwinger_times(37, seed=4), 1000)
+
+
+def test_schwinger_large_arguments(dse, oracle, inputs):
+    # cos(t p) for t up to 1e300 at the one node p = 1: with eps2 lambda2 = 1 the
+    # one-point rule sits at u = ln p^2 = 0 on both sides, so the two evaluate the
+    # cosine at the same argument t (with several nodes a one-ulp difference of
+    # the nodes moves t p by t p 2^-53).  Beyond 2^49 the argument reduction hands
+    # over to the library cosine.
+    p = inputs.problem(12, 8, 8, eps2=0.25, lambda2=4.0)
+    c = inputs.starting_guess(p, seed=2)
+    pn, _ = oracle.schwinger_nodes(p, 1)
+    assert pn[0] == 1.0
+    t = np.array([0.0, 1.0, 1e5, 2.0**47, 2.0**49 - 1.0, -(2.0**49), 2.0**50 + 3.0, 1e16, 1e18, 1e300])
+    _schwinger_check(dse, oracle, p, c, t, 1)
+
+
 def test_schwinger_full_size(dse, oracle, inputs):
     p = inputs.workload_problem("full_solve_n64")
     c = inputs.starting_guess(p, seed=0)
