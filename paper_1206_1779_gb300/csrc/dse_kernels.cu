@@ -1871,7 +1871,7 @@ constexpr double kPio2_1 = 1.5707963267948966;
 constexpr double kPio2_2 = 6.123233995736766e-17;
 constexpr double kTwoOverPi = 0.6366197723675814;
 constexpr double kRoundShifter = 6755399441055744.0;  // 1.5 2^52
-constexpr double kCosReduceMax = 0x1p49;  // |x| from which the library cos is used
+constexpr unsigned kCosReduceMaxHi = 0x43000000u;  // high word of 2^49: from there the library cos
 
 struct CosTail { float2 c[8], s[8]; };
 
@@ -1911,10 +1911,13 @@ __device__ __forceinline__ CosParts cos_df(double x, const CosTail& T) {
     const bool odd = (q & 1) != 0;
     float2 t = df_mul(odd ? ps : pc, r4d);
     t = df_mul(t, odd ? rd : make_float2(1.0f, 0.0f));
-    const double lead = fma(odd ? r * r2 : r2, odd ? -1.0 / 6.0 : -0.5, odd ? r : 1.0);
+    // leading terms as one FMA, P + P k with P = +-r (odd) or +-1 (even) and
+    // k = -r^2/6 or -r^2/2; the sign of the quadrant goes into P's sign bit
     const bool neg = (q == 1 || q == 2);
+    const double base = odd ? r : 1.0;
+    const double P = __hiloint2double(__double2hiint(base) ^ (neg ? (int)0x80000000 : 0), __double2loint(base));
     CosParts o;
-    o.lead = neg ? -lead : lead;
+    o.lead = fma(P, r2 * (odd ? -1.0 / 6.0 : -0.5), P);
     o.tail = neg ? make_float2(-t.x, -t.y) : t;
     return o;
 }
@@ -1972,7 +1975,8 @@ __global__ void __launch_bounds__(kSchT * kSchPh) k_schwinger_sum(int n_nodes, c
         for (int q = ph; q < cnt; q += kSchPh) {
             const double x = tm * sp[q];
             CosParts cp = cos_df(x, T);
-            if (fabs(x) >= kCosReduceMax) {  // beyond the two-part reduction
+            // |x| >= 2^49 (or not finite), from the exponent field: beyond the two-part reduction
+            if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= kCosReduceMaxHi) {
                 cp.lead = cos(x);
                 cp.tail = make_float2(0.f, 0.f);
             }
