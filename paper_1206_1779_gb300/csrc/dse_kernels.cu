@@ -278,12 +278,13 @@ __device__ double series_comp(const double* cf, int m, double sh, double sl) {
 // Two intervals per block of three warps.  Warp f < 2 (0: ln Z, 1: ln G)
 // evaluates its series, lane (il, q) = (lane / Q, lane % Q) at the q-th Chebyshev
 // point u_q = cos(pi (q + 1/2)/Q) of interval 2 blk + il, the node s = mid + half u_q
-// held exactly as s_h + s_l.  Lane (il, q) of warp 0 then forms the node values
-// Z = e^{ln Z}, G = e^{ln G}, W = e^{p ln G + q ln Z}.  Thread (F, il, q) of warp F
-// (0: Z, 1: G, 2: W) forms the Chebyshev coefficient of degree q of the
-// interpolant, c_q = (2 - [q = 0])/Q sum_r v_r cos(pi q (r + 1/2)/Q), and its
-// monomial coefficient of u^q, sum_j c_j [u^q] T_j(u), with the coefficients of
-// T_j built by the recurrence T_{j+1} = 2u T_j - T_{j-1}.
+// held exactly as s_h + s_l; meanwhile warp 2 builds the end-point record and the
+// interpolation and monomial tables.  Lane (il, q) of warp F then forms the node
+// value F (0: Z = e^{ln Z}, 1: G = e^{ln G}, 2: W = e^{p ln G + q ln Z}), and thread
+// (F, il, q) forms the Chebyshev coefficient of degree q of F's interpolant,
+// c_q = (2 - [q = 0])/Q sum_r v_r cos(pi q (r + 1/2)/Q), and its monomial
+// coefficient of u^q, sum_j c_j [u^q] T_j(u), with the coefficients of T_j built by
+// the recurrence T_{j+1} = 2u T_j - T_{j-1}.
 constexpr int kSeriesIntervalsPerBlock = 2;
 constexpr int kSeriesThreads = 96;
 static_assert(kSeriesIntervalsPerBlock * kSeriesQ == 32, "one warp holds one function of the block's intervals");
@@ -296,63 +297,75 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     __shared__ double tcoef[kSeriesQ][kSeriesQ];  // tcoef[j][k] = [u^k] T_j(u)
     __shared__ double dct[kSeriesQ][kSeriesQ];    // dct[k][r] = cos(pi k (r + 1/2)/Q)
     __shared__ double scf[2 * DSE_MAX_CHEB];      // a then b
+    __shared__ double smh[kSeriesIntervalsPerBlock][4];  // cos th0, cos th1, sin((th0 + th1)/2), sin(h/2)
+    __shared__ double suq[kSeriesQ];                     // the Chebyshev points u_q
     if (blk * kSeriesIntervalsPerBlock >= c.sM) return;  // (batched grids span the largest table)
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int il = lane / kSeriesQ, q = lane % kSeriesQ;
     for (int j = threadIdx.x; j < c.n; j += blockDim.x) scf[j] = coef[j];
-    for (int e = threadIdx.x; e < kSeriesQ * kSeriesQ; e += blockDim.x) {
-        const int k = e / kSeriesQ, r = e % kSeriesQ;
-        dct[k][r] = cos(kPi * k * (r + 0.5) / kSeriesQ);
-    }
-    if (threadIdx.x < kSeriesQ) {
-        // column k of every T_j, by the three-term recurrence (exact integers)
-        const int k = threadIdx.x;
-        double tm = k == 0 ? 1.0 : 0.0;  // T_0
-        double tc = k == 1 ? 1.0 : 0.0;  // T_1
-        tcoef[0][k] = tm;
-        tcoef[1][k] = tc;
-        for (int j = 2; j < kSeriesQ; ++j) {
-            const double lower = __shfl_up_sync(0x0000ffffu, tc, 1);  // [u^{k-1}] T_{j-1}
-            const double tn = (k == 0 ? 0.0 : 2.0 * lower) - tm;
-            tcoef[j][k] = tn;
-            tm = tc;
-            tc = tn;
-        }
+    const double h = kPi / c.sM;
+    if (f == 0 && lane < 4 * kSeriesIntervalsPerBlock) {
+        // the intervals' end points and half-widths: one sincos per lane
+        const int ii = blk * kSeriesIntervalsPerBlock + (lane >> 2), w = lane & 3;
+        const double th0 = ii * h, th1 = (ii + 1) * h;
+        const double x = w == 0 ? th0 : w == 1 ? th1 : w == 2 ? 0.5 * (th0 + th1) : 0.5 * h;
+        double sn, cs;
+        sincos(x, &sn, &cs);
+        smh[lane >> 2][w] = w < 2 ? cs : sn;
+    } else if (f == 1 && lane < kSeriesQ) {
+        suq[lane] = cos(kPi * (lane + 0.5) / kSeriesQ);
     }
     const int i = blk * kSeriesIntervalsPerBlock + il;
-    const double h = kPi / c.sM;
-    const double th0 = i * h, th1 = (i + 1) * h;
-    const double mid = 0.5 * (cos(th0) + cos(th1));
-    const double half = sin(0.5 * (th0 + th1)) * sin(0.5 * h);  // (cos th0 - cos th1)/2 without cancellation
-    __syncthreads();  // coefficients and tables staged
-    if (blk == 0 && threadIdx.x >= 64 && threadIdx.x < 68) {
-        // the end-point record (threads of the third warp, which has no node work
-        // here): sum_j c_j T_j(+-1) with T_j(1) = 1, T_j(-1) = (-1)^j
-        const int e = threadIdx.x - 64;
-        const int nc = (e & 1) ? c.NG : c.NZ;
-        const double* cf = scf + ((e & 1) ? c.NZ : 0);
-        const double sgn = e < 2 ? 1.0 : -1.0;
-        double v = 0.5 * cf[0];
-        double t = 1.0;
-        for (int j = 1; j < nc; ++j) {
-            t *= sgn;
-            v = fma(cf[j], t, v);
-        }
-        reinterpret_cast<double*>(tab + kSeriesM)[e] = v;
-    }
+    __syncthreads();  // coefficients, end points and nodes staged
+    const double mid = 0.5 * (smh[il][0] + smh[il][1]);
+    const double half = smh[il][2] * smh[il][3];  // (cos th0 - cos th1)/2 without cancellation
     if (f < 2) {
-        const double uq = cos(kPi * (q + 0.5) / kSeriesQ);
+        const double uq = suq[q];
         // s = mid + half uq exactly as s_h + s_l
         const DD p = dd_two_sum(half * uq, mid);
         const DD sdd = dd_add(p, DD{fma(half, uq, -(half * uq)), 0.0});
         sv[f][il][q] = f == 0 ? series_comp(scf, c.NZ, sdd.hi, sdd.lo) : series_comp(scf + c.NZ, c.NG, sdd.hi, sdd.lo);
+    } else {
+        // the third warp, while the other two sum the series: the end-point record,
+        // the interpolation table and the monomial coefficients of the T_j
+        if (blk == 0 && lane < 4) {
+            // sum_j c_j T_j(+-1) with T_j(1) = 1, T_j(-1) = (-1)^j
+            const int e = lane;
+            const int nc = (e & 1) ? c.NG : c.NZ;
+            const double* cf = scf + ((e & 1) ? c.NZ : 0);
+            const double sgn = e < 2 ? 1.0 : -1.0;
+            double v = 0.5 * cf[0];
+            double t = 1.0;
+            for (int j = 1; j < nc; ++j) {
+                t *= sgn;
+                v = fma(cf[j], t, v);
+            }
+            reinterpret_cast<double*>(tab + kSeriesM)[e] = v;
+        }
+        for (int e = lane; e < kSeriesQ * kSeriesQ; e += 32) {
+            const int k = e / kSeriesQ, r = e % kSeriesQ;
+            dct[k][r] = cos(kPi * k * (r + 0.5) / kSeriesQ);
+        }
+        if (lane < kSeriesQ) {
+            // column k of every T_j, by the three-term recurrence (exact integers)
+            const int k = lane;
+            double tm = k == 0 ? 1.0 : 0.0;  // T_0
+            double tc = k == 1 ? 1.0 : 0.0;  // T_1
+            tcoef[0][k] = tm;
+            tcoef[1][k] = tc;
+            for (int j = 2; j < kSeriesQ; ++j) {
+                const double lower = __shfl_up_sync(0x0000ffffu, tc, 1);  // [u^{k-1}] T_{j-1}
+                const double tn = (k == 0 ? 0.0 : 2.0 * lower) - tm;
+                tcoef[j][k] = tn;
+                tm = tc;
+                tc = tn;
+            }
+        }
     }
     __syncthreads();
-    if (f == 0) {
+    {
         const double lz = sv[0][il][q], lg = sv[1][il][q];
-        sf[0][il][q] = exp(lz);
-        sf[1][il][q] = exp(lg);
-        sf[2][il][q] = exp(fma(c.pG, lg, c.qZ * lz));
+        sf[f][il][q] = exp(f == 0 ? lz : f == 1 ? lg : fma(c.pG, lg, c.qZ * lz));
     }
     __syncthreads();
     {
