@@ -1186,6 +1186,7 @@ constexpr int kScaleThreads = 128;
 constexpr int kColPad = 144;  // >= 128 + 16 - 1, multiple of 4
 constexpr int kGjBlock = 4;   // pivots per round of the blocked elimination
 constexpr int kGjCols = 4;    // columns per lane of the panel warp (n <= 128)
+static_assert(kGjCols * 32 <= 128, "the pivot keys hold the column in 7 bits");
 
 __device__ __forceinline__ void scale_row(int n, const double* __restrict__ J, float* __restrict__ As,
                                           double2* __restrict__ rowinfo, int* __restrict__ status, const int i) {
@@ -1524,23 +1525,21 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
 #pragma unroll
                         for (int p = 0; p < kGjBlock; ++p) {
                             if (p < nb && !sing) {  // uniform over the warp
-                                // pivot column: the largest unused entry of panel row p
-                                // |a| as bits (monotonic for non-negative floats; pivoted
-                                // columns 0): the warp maximum by one reduction, then the
-                                // lowest column holding it by another
-                                unsigned ab = 0u;
-                                int idx = 0x7fffffff;
+                                // pivot column: the largest unused entry of panel row p,
+                                // by one warp reduction over keys that hold |a| as bits
+                                // (monotonic for non-negative floats) cut to 16 fraction
+                                // bits, and 127 - column in the 7 bits below: of entries
+                                // equal to 2^-16 the lowest column wins (pivoted columns: 0)
+                                unsigned key = 0u;
 #pragma unroll
                                 for (int cc = 0; cc < kGjCols; ++cc) {
-                                    const unsigned bv = ucol[cc] ? 0u : (unsigned)__float_as_int(fabsf(P[p][cc]));
-                                    if (bv > ab) {  // the first of equal maxima
-                                        ab = bv;
-                                        idx = lane + 32 * cc;
-                                    }
+                                    const unsigned ab = (unsigned)__float_as_int(fabsf(P[p][cc])) & 0xffffff80u;
+                                    const unsigned bv = ucol[cc] ? 0u : (ab | (unsigned)(127 - (lane + 32 * cc)));
+                                    key = max(key, bv);
                                 }
-                                const unsigned mb = __reduce_max_sync(kFullMask, ab);
-                                idx = (int)__reduce_min_sync(kFullMask, ab == mb ? (unsigned)idx : 0x7fffffffu);
-                                const float a = __int_as_float((int)mb);
+                                const unsigned mk = __reduce_max_sync(kFullMask, key);
+                                const int idx = 127 - (int)(mk & 0x7fu);
+                                const float a = __int_as_float((int)(mk & 0xffffff80u));
                                 if (!(a > 1e-30f)) {
                                     if (lane == 0) s_done = -1;
                                     sing = true;
@@ -1557,7 +1556,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
                                             if (cc == qc) mine = P[pp][cc];
                                         pc[pp] = __shfl_sync(kFullMask, mine, ql);
                                     }
-                                    const float inv = 1.0f / pc[p];
+                                    const float inv = __frcp_rn(pc[p]);
 #pragma unroll
                                     for (int cc = 0; cc < kGjCols; ++cc) {
                                         const bool isq = (lane + 32 * cc) == q;
