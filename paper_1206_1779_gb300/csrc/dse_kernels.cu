@@ -496,7 +496,8 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
             }
         }
         if (FULL && j < N) {
-            for (int kk = kg; kk < kn; kk += kRowKG) {
+#pragma unroll 8
+            for (int kk = kg; kk < kn; kk += kRowKG) {  // (unrolled: loads in flight, same order)
                 const double ph = phiy[(size_t)(kb + kk) * N + j];
                 Y0 = fma(sU[kk][0], ph, Y0);
                 Y1 = fma(sU[kk][1], ph, Y1);
@@ -516,6 +517,7 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
     if (FULL && !special && j < N) {
         const double* vp = Vpart + (size_t)rt * KS * 3 * N;
         double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+#pragma unroll 4
         for (int sp = kg; sp < KS; sp += kRowKG) {
             v0 += vp[(size_t)sp * 3 * N + j];
             v1 += vp[(size_t)sp * 3 * N + N + j];
