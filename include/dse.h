@@ -165,7 +165,10 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
  *   Delta(t_m) = (1/pi) int_0^inf d|p| cos(t_m |p|) Z(p^2)/p^2,
  * with n_nodes Gauss-Legendre nodes in u = ln p^2 over [ln eps2, ln lambda2]
  * (tails outside the range are left out).  The nodes for a given n_nodes are
- * generated on the device on first use and kept in the plan. */
+ * generated on the device on first use and kept in the plan.  cos(t p) is taken
+ * at the FP64 product t p to a few units in the last place for any finite t p;
+ * weights Z/(pi p^2) of any FP64 magnitude.  A non-finite Delta sets the
+ * sticky DSE_ERR_NONFINITE flag (dse_plan_status). */
 int dse_schwinger(dse_plan* plan, const double* d_coeffs, const double* d_t, int n_t,
                   int n_nodes, double* d_delta);
 
