@@ -130,10 +130,9 @@ constexpr int kRadGroup = 32;
 constexpr int kRadFactors = 8;
 
 __host__ __device__ inline size_t smem_doubles(bool full, int N, int BT, bool ar) {
-    // tile rows, 3 BT weights (FP64, then their double-float pairs), 2 N
-    // coefficients, 4 boundary sums, 3 x 8 per-warp exponent maxima, the factors
-    // of a group of radial nodes
-    return tile_doubles(full, N, BT, ar) + 6u * (size_t)BT + 2u * (size_t)N + 4u + 12u +
+    // tile rows, 3 BT weights as double-float pairs, 2 N coefficients, 4 boundary
+    // sums, 3 x 8 per-warp exponent maxima, the factors of a group of radial nodes
+    return tile_doubles(full, N, BT, ar) + 3u * (size_t)BT + 2u * (size_t)N + 4u + 12u +
            (size_t)kRadGroup * kRadFactors;
 }
 
@@ -147,9 +146,8 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     const int ldT = row_len_for(N, AR);
     double* sT = smem;
     float2* sT2 = reinterpret_cast<float2*>(smem);  // rows [2s][T_4i][T_4i+1] as double-float pairs
-    double* sh = smem + tile_doubles(FULL, N, BT, AR);
-    float2* sh2 = reinterpret_cast<float2*>(sh + 3 * BT);  // the weights as pairs
-    double* sa = sh + 6 * BT;
+    float2* sh2 = reinterpret_cast<float2*>(smem + tile_doubles(FULL, N, BT, AR));  // [3][BT] weight pairs
+    double* sa = smem + tile_doubles(FULL, N, BT, AR) + 3 * BT;
     double* sb = sa + N;
     double* sbnd = sb + N;  // ln Z(s=1), ln G(s=1), ln Z(s=-1), ln G(s=-1) (table path)
     int* sex = reinterpret_cast<int*>(sbnd + 4);  // [3][8] per-warp maxima of the weights' exponents
