@@ -22,12 +22,13 @@
 //            its group's rows: three multiply-adds per (triple, j).
 // Phase B runs in double-float arithmetic (a value is an unevaluated sum hi + lo
 // of two FP32 numbers, 48 significant bits; Dekker's exact product and Knuth's
-// exact sum), because this GPU issues FP32 at 64 times its FP64 rate: the FP64
-// recurrence values and weights are split exactly into (hi, lo) pairs (the
-// weights scaled by a power of two per tile, so that no tile over- or
-// underflows FP32), each group sums at most one tile's rows in double-float,
-// and the tile sums are added to FP64 accumulators.  The residual (the angular
-// sums of the weights) stays in FP64 throughout.
+// exact sum), because this GPU issues FP32 at 64 times its FP64 rate: the
+// Chebyshev values phi_j(z) come from double-float recurrences started from FP64
+// values, the FP64 weights are split exactly into (hi, lo) pairs (scaled by a
+// power of two per tile, so that no tile over- or underflows FP32), each group
+// sums at most one tile's rows in double-float, and the tile sums are added to
+// FP64 accumulators.  The residual (the angular sums of the weights) stays in
+// FP64 throughout.
 // The block's coefficient vector lives in shared memory (broadcast reads).
 #include "dse_df.cuh"
 #include "dse_internal.cuh"
