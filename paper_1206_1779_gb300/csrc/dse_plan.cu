@@ -124,12 +124,13 @@ Consts make_consts(const dse_problem* p) {
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Radial nodes per block: about five waves of Rt * KS blocks over the resident
+// Radial nodes per block: about eight waves of Rt * KS blocks over the resident
 // slots, so that the block scheduler evens out rows of unequal cost (rows near
 // Lambda^2 evaluate the UV forms with exponentials for many triples); at least
 // two radial nodes per block and at most 128 splits.  Measured at N = 64 with
-// 256 x 128 nodes: one wave (KS = 11) 0.84 ms per launch, KS = 23 / 35 / 47 / 64:
-// 0.81 / 0.78 / 0.76 / 0.74 ms.
+// 256 x 128 nodes on an earlier version of the kernel: one wave (KS = 11) 0.84 ms
+// per launch, KS = 23 / 35 / 47 / 64: 0.81 / 0.78 / 0.76 / 0.74 ms; on the current
+// one KS = 64 / 128: 0.617 / 0.608 ms.
 void choose_split(dse_plan* pl) {
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -137,7 +138,7 @@ void choose_split(dse_plan* pl) {
     if (occ < 1) occ = 1;
     const long long slots = (long long)nsm * occ;
     const int nr = pl->c.nr;
-    long long kb = ((long long)nr * pl->Rt) / (5 * slots);
+    long long kb = ((long long)nr * pl->Rt) / (8 * slots);
     if (kb < 2) kb = 2;
     if (kb > nr) kb = nr;
     while ((nr + kb - 1) / kb > 128) ++kb;
