@@ -39,11 +39,13 @@ N_T = 4096
 N_NODES = 8192
 TOL = 1e-10
 L2_FLUSH_BYTES = 256 << 20
-# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes per
-# clock per SM (1.25 TFLOP/s nominal) at the sampled SM clock under load.
+# Nominal unit counts (context only; the roofline divides by the rates that
+# dse_alu_peak measures on this GPU): 152 SMs, 2 FP64 FMA lanes and 128 FP32
+# lanes per SM per clock, 4 schedulers per SM issuing one warp instruction per clock.
 N_SM = 152
-FP64_FLOP_PER_CLK_SM = 4.0     # 2 FP64 FMA lanes per SM per clock
-FP32_INST_PER_CLK_SM = 128.0   # 128 FP32 lanes per SM per clock
+FP64_FLOP_PER_CLK_SM = 4.0
+FP32_INST_PER_CLK_SM = 128.0
+WARP_ISSUE_PER_CLK_SM = 4.0
 DF_FMA_FP32_INST = 12          # one double-float multiply-add: exact product (2), cross terms (2), exact sum (6), lower part (2)
 DF_MULSUB_FP32_INST = 15       # one double-float a b - d with renormalisation
 
@@ -75,16 +77,38 @@ def work_per_triple(N: int):
     return 6.0 * N + 50.0 + 9.0, 3.0 * N, 0.0
 
 
-def roofline_model(N: int, triples: int, sm_mhz: float):
-    """Lower bound on one launch's duration (s) with the FP64 and FP32 pipes each at
-    their peak and not overlapped, and the FP64-equivalent flops of the launch
-    (a double-float multiply-add or -subtract counted as one FP64 FMA)."""
+def roofline_model(N: int, triples: int, fp64_flops_per_s: float, fp32_inst_per_s: float):
+    """Lower bound on one launch's duration (s): the FP64 and FP32 pipes issue
+    independently, so the bound is the larger of the two pipes' times at their
+    measured rates; and the FP64-equivalent flops of the launch (a double-float
+    multiply-add or -subtract counted as one FP64 FMA)."""
     f64, dfma, dms = work_per_triple(N)
-    clk = sm_mhz * 1e6
-    t_fp64 = triples * f64 / (N_SM * FP64_FLOP_PER_CLK_SM * clk)
-    t_fp32 = triples * (dfma * DF_FMA_FP32_INST + dms * DF_MULSUB_FP32_INST) / (N_SM * FP32_INST_PER_CLK_SM * clk)
+    t_fp64 = triples * f64 / fp64_flops_per_s
+    t_fp32 = triples * (dfma * DF_FMA_FP32_INST + dms * DF_MULSUB_FP32_INST) / fp32_inst_per_s
     flops = triples * (f64 + 2.0 * (dfma + dms))
-    return t_fp64 + t_fp32, flops, t_fp64, t_fp32
+    return max(t_fp64, t_fp32), flops, t_fp64, t_fp32
+
+
+def measure_alu_peaks(dse, local: int):
+    """FP64 FMA, FP32 FMA and special-function (exp2, log2) rates of this GPU by
+    the library's microbenchmark, with the SM clock sampled meanwhile."""
+    clocks = ClockSampler(local)
+    clocks.start()
+    out = {}
+    for name, kind in (("fp64_fma", dse.DSE_PEAK_FP64_FMA), ("fp32_fma", dse.DSE_PEAK_FP32_FMA),
+                       ("mufu_ex2", dse.DSE_PEAK_MUFU_EX2), ("mufu_lg2", dse.DSE_PEAK_MUFU_LG2)):
+        best = 0.0
+        for _ in range(2):
+            rate, _ms = dse.alu_peak(kind, 150.0)
+            best = max(best, rate)
+        out[name + "_per_s"] = best
+    clk = clocks.stop()
+    out["fp64_tflops"] = 2.0 * out["fp64_fma_per_s"] / 1e12
+    out["fp32_tflops"] = 2.0 * out["fp32_fma_per_s"] / 1e12
+    out["clocks"] = clk
+    out["how"] = ("dse_alu_peak: eight independent FMA (or exp2/log2) chains per thread, SM count x resident "
+                  "blocks of 256 threads, ~150 ms per launch, CUDA events, best of 2")
+    return out
 
 
 class ClockSampler:
@@ -142,8 +166,8 @@ class ClockSampler:
 
 
 def traffic_record(kernel_src: str):
-    """DRAM bytes per hot-kernel launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """ncu record of the hot kernel (DRAM bytes and warp instructions per launch at
+    the benchmark's size), if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "triple_kernel_traffic.json")
     try:
         rec = json.load(open(path))
@@ -152,7 +176,7 @@ def traffic_record(kernel_src: str):
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
     if rec.get("kernel_sha256") != h:
         return None
-    return rec.get("dram_bytes_per_launch_full_size")
+    return rec
 
 
 def dist_setup(args):
@@ -193,6 +217,7 @@ def run_gb300(args):
     c0 = inputs.starting_guess(p, seed=0)
     tt = inputs.schwinger_times(N_T, seed=0)
     stream = torch.cuda.current_stream()
+    peaks = measure_alu_peaks(dse, local)
 
     t_plan0 = time.perf_counter()
     plan = dse.Plan(p)
@@ -246,16 +271,25 @@ def run_gb300(args):
     solves_per_s = world * args.steps / (total_ms * 1e-3)
 
     # roofline of the hot kernel: FP64-equivalent algorithmic flops per launch /
-    # event time, against the rate at the model's lower bound on the duration
+    # event time, against the rate at the lower bound on the duration that the
+    # measured FP64 and FP32 pipe rates give (the pipes overlapped)
     Rt = N + 1 + (1 if p["x_G"] > 0 else 0)
     triples = Rt * nr * na
     avg_launch_ms = timed_ms / max(n_timed, 1)
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    t_min, flops_launch, t_fp64, t_fp32 = roofline_model(N, triples, sm_mhz)
+    t_min, flops_launch, t_fp64, t_fp32 = roofline_model(N, triples, 2.0 * peaks["fp64_fma_per_s"],
+                                                         peaks["fp32_fma_per_s"])
     achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = flops_launch / t_min / 1e12
     f64_pt, dfma_pt, dms_pt = work_per_triple(N)
-    traffic = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
+    rec = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
+    traffic = rec.get("dram_bytes_per_launch_full_size") if rec else None
+    issue = None
+    if rec and rec.get("warp_instructions_per_launch"):
+        # every scheduler issues at most one warp instruction per clock
+        t_issue = rec["warp_instructions_per_launch"] / (N_SM * WARP_ISSUE_PER_CLK_SM * sm_mhz * 1e6)
+        issue = {"warp_instructions_per_launch": rec["warp_instructions_per_launch"],
+                 "t_issue_bound_ms": t_issue * 1e3, "frac_of_issue_bound": t_issue / (avg_launch_ms * 1e-3)}
 
     # mixed precision (FP32 integrands for the Newton matrix, FP64 residual)
     mixed = None
@@ -314,15 +348,18 @@ def run_gb300(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_triple (radial x angular quadrature: FP64 integrands, double-float derivative sums)",
-                         "peak_source": ("derived: FP64-equivalent flops of a launch over its lower-bound duration "
-                                         "t_fp64 + t_fp32, with 152 SMs x 4 FP64 flop/clk and 152 SMs x 128 FP32 "
-                                         "inst/clk at the sampled SM clock"),
+                         "peak_source": ("measured (dse_alu_peak on this GPU): FP64-equivalent flops of a launch over "
+                                         "max(t_fp64, t_fp32), the FP64 work at the measured FP64 FMA rate and the "
+                                         "FP32 instructions at the measured FP32 FMA rate, the two pipes overlapped"),
                          "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms, "triples_per_launch": triples,
                          "fp64_flops_per_triple": f64_pt, "double_float_fma_per_triple": dfma_pt,
                          "double_float_mulsub_per_triple": dms_pt,
                          "t_fp64_bound_ms": t_fp64 * 1e3, "t_fp32_bound_ms": t_fp32 * 1e3,
                          "fp64_achieved_tflops": triples * f64_pt / (avg_launch_ms * 1e-3) / 1e12,
-                         "fp64_peak_tflops": N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12},
+                         "fp64_measured_peak_tflops": peaks["fp64_tflops"],
+                         "fp32_measured_peak_tflops": peaks["fp32_tflops"],
+                         "issue": issue},
+            "alu_peaks": peaks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(c0.nbytes + tt.nbytes),
                     "d2h_bytes_per_step": int(c0.nbytes + tt.nbytes)},
             "gpu_launches": int(launches1 - launches0),

@@ -25,7 +25,13 @@ EXPORTS = ["dse_plan_create", "dse_plan_destroy", "dse_plan_set_stream", "dse_pl
            "dse_plan_set_couplings", "dse_vjp", "dse_param_derivatives", "dse_adjoint_solve", "dse_dressing_vjp",
            "dse_batch_create", "dse_batch_destroy", "dse_batch_set_stream", "dse_batch_offsets", "dse_batch_tune",
            "dse_batch_newton_matrix", "dse_batch_solve", "dse_batch_counters", "dse_newton_matrix_fd",
-           "dse_batch_residual", "dse_plan_solver_counters"]
+           "dse_batch_residual", "dse_plan_solver_counters", "dse_alu_peak"]
+
+# pipes of dse_alu_peak (include/dse_peaks.h)
+DSE_PEAK_FP64_FMA = 0
+DSE_PEAK_FP32_FMA = 1
+DSE_PEAK_MUFU_EX2 = 2
+DSE_PEAK_MUFU_LG2 = 3
 
 
 class DseError(RuntimeError):
@@ -110,6 +116,7 @@ def load(build_if_missing: bool = False):
                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D],
         "dse_batch_counters": [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_int)],
+        "dse_alu_peak": [ctypes.c_int, ctypes.c_double, _VP, _D, _D],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -119,6 +126,17 @@ def load(build_if_missing: bool = False):
     L.dse_status_string.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+def alu_peak(kind: int, target_ms: float = 100.0):
+    """(operations per second, ms) of one arithmetic pipe on the current device,
+    on torch's current stream (dse_alu_peak)."""
+    import torch
+    L = load()
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(L.dse_alu_peak(int(kind), float(target_ms), _VP(torch.cuda.current_stream().cuda_stream),
+                          ctypes.byref(rate), ctypes.byref(ms)), "dse_alu_peak")
+    return rate.value, ms.value
 
 
 def status_string(code: int) -> str:

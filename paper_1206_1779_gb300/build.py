@@ -15,7 +15,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libdse_gb300.so")
-SOURCES = ["dse_triple.cu", "dse_triple32.cu", "dse_kernels.cu", "dse_plan.cu", "dse_noalloc.cu", "dse_adjoint.cu", "dse_batch.cu"]
+SOURCES = ["dse_triple.cu", "dse_triple32.cu", "dse_kernels.cu", "dse_plan.cu", "dse_noalloc.cu", "dse_adjoint.cu", "dse_batch.cu",
+           "dse_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -28,7 +29,8 @@ def nvcc() -> str:
 
 
 def _inputs_newest() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "dse.h"), __file__]
+    files = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] +
+             [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__])
     return max(os.path.getmtime(f) for f in files)
 
 

@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI (no GPU work): the library loads, exports every
-entry point declared in include/dse.h, and rejects bad arguments before
+entry point declared in include/*.h, and rejects bad arguments before
 touching the device."""
 import ctypes
 import os
@@ -18,7 +18,8 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "dse.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(dse_[a-z_]+)\s*\(", src)))
 
@@ -99,3 +100,13 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_binding._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _binding.load()
+
+
+def test_alu_peak_rejects_bad_arguments(lib):
+    import ctypes as C
+    rate = C.c_double()
+    # checked before any device work
+    assert lib.dse_alu_peak(9, 100.0, None, C.byref(rate), None) == -1
+    assert lib.dse_alu_peak(0, 0.5, None, C.byref(rate), None) == -1
+    assert lib.dse_alu_peak(0, float("nan"), None, C.byref(rate), None) == -1
+    assert lib.dse_alu_peak(0, 100.0, None, None, None) == -1
