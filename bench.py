@@ -46,46 +46,49 @@ N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4.0
 FP32_INST_PER_CLK_SM = 128.0
 WARP_ISSUE_PER_CLK_SM = 4.0
-DF_FMA_FP32_INST = 12          # one double-float multiply-add: exact product (2), cross terms (2), exact sum (6), lower part (2)
-DF_MULSUB_FP32_INST = 15       # one double-float a b - d with renormalisation
 
 
 SERIES_TABLE_N = (24, 256)  # the kernel reads Z(z), G(z), W(z) from the series table for these N
 SERIES_TABLE_DEGREE = 15    # degree of the table's local polynomials
-SERIES_TABLE_LEAD = 4       # leading coefficients summed in FP64 (the rest in double-float)
+SERIES_TABLE_DF_STEPS = 7   # Horner steps in double-float per polynomial (the rest in FP32; 7 at N = 64)
 
 
 def work_per_triple(N: int):
     """Algorithmic work of the hot kernel per (x, y, theta) triple in the Newton-matrix
-    mode: (FP64 flops, double-float multiply-adds, double-float multiply-subtracts),
-    an FMA counted as 2 flops.
+    mode: (FP64 flops, FP32 instructions, double-float multiply-adds), an FMA counted
+    as 2 flops.
 
-    FP64: ~50 flops of geometry, kernels, integrands, ln z and 1/z; 9 for adding the
-    double-float tile sums to the FP64 accumulators.  The dressing functions at z:
-    for N in SERIES_TABLE_N read from the table (u: 3 flops; for Z, G and W the
-    SERIES_TABLE_LEAD leading Horner steps in FP64, 2 flops each, and the widened
-    tail, 1) with T_2 .. T_5 in FP64 (8 flops); else the two series and the
-    recurrence summed per triple (3N FMA: 6N flops).
-    Double-float: the three derivative sums weight * phi_j(z) (3N multiply-adds) and,
-    on the table path, the anchors T_4i, T_4i+1 by the stride-4 recurrence (N/2
-    multiply-subtracts), T_4i+2 and T_4i+3 from them (N/2) and the three table tails
-    (3 (SERIES_TABLE_DEGREE - SERIES_TABLE_LEAD) multiply-adds, counted with the
-    multiply-subtracts: 15 FP32 instructions each)."""
+    FP64 (54 flops on the table path): z (2); ln z and 1/z (11: the FMAs of r and of
+    e ln2_hi, the leading sums, the product by inv_j); s and u (4); the widened table
+    values (3); T_2 .. T_5 for the anchors (11); the integrands (17); the angular sums
+    (6).  Without the table (N < 24) the two series and the recurrence add 6N and the
+    exponentials replace the table lookup.
+    FP32 (double-float, on the FP32 pipe): the derivative sums weight * T_j (3N
+    double-float multiply-adds, 12 instructions each), the T_j recurrences (N
+    multiply-subtracts, 15 each: the stride-4 anchors and the steps to T_4i+2, T_4i+3),
+    the three table polynomials (3 x SERIES_TABLE_DF_STEPS double-float steps of 15,
+    the others one FFMA each) and the small terms of ln z and 1/z (40)."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
-        tail = 3.0 * (SERIES_TABLE_DEGREE - SERIES_TABLE_LEAD)
-        return (8.0 + 3.0 + 3.0 * (2.0 * SERIES_TABLE_LEAD + 1.0) + 50.0 + 9.0, 3.0 * N, float(N) + tail)
-    return 6.0 * N + 50.0 + 9.0, 3.0 * N, 0.0
+        f64 = 54.0
+        horner = 3.0 * (SERIES_TABLE_DF_STEPS * 15.0 + (SERIES_TABLE_DEGREE - SERIES_TABLE_DF_STEPS))
+        df_ops = 3.0 * N + N + 3.0 * SERIES_TABLE_DF_STEPS
+    else:
+        f64 = 54.0 + 6.0 * N
+        horner = 0.0
+        df_ops = 3.0 * N + N
+    f32 = 12.0 * 3 * N + 15.0 * N + horner + 40.0
+    return f64, f32, df_ops
 
 
 def roofline_model(N: int, triples: int, fp64_flops_per_s: float, fp32_inst_per_s: float):
     """Lower bound on one launch's duration (s): the FP64 and FP32 pipes issue
     independently, so the bound is the larger of the two pipes' times at their
     measured rates; and the FP64-equivalent flops of the launch (a double-float
-    multiply-add or -subtract counted as one FP64 FMA)."""
-    f64, dfma, dms = work_per_triple(N)
+    multiply-add or -subtract counted as one FP64 FMA, 2 flops)."""
+    f64, f32, df_ops = work_per_triple(N)
     t_fp64 = triples * f64 / fp64_flops_per_s
-    t_fp32 = triples * (dfma * DF_FMA_FP32_INST + dms * DF_MULSUB_FP32_INST) / fp32_inst_per_s
-    flops = triples * (f64 + 2.0 * (dfma + dms))
+    t_fp32 = triples * f32 / fp32_inst_per_s
+    flops = triples * (f64 + 2.0 * df_ops)
     return max(t_fp64, t_fp32), flops, t_fp64, t_fp32
 
 
@@ -281,7 +284,7 @@ def run_gb300(args):
                                                          peaks["fp32_fma_per_s"])
     achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = flops_launch / t_min / 1e12
-    f64_pt, dfma_pt, dms_pt = work_per_triple(N)
+    f64_pt, f32_pt, dfops_pt = work_per_triple(N)
     rec = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
     traffic = rec.get("dram_bytes_per_launch_full_size") if rec else None
     issue = None
@@ -352,8 +355,8 @@ def run_gb300(args):
                                          "max(t_fp64, t_fp32), the FP64 work at the measured FP64 FMA rate and the "
                                          "FP32 instructions at the measured FP32 FMA rate, the two pipes overlapped"),
                          "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms, "triples_per_launch": triples,
-                         "fp64_flops_per_triple": f64_pt, "double_float_fma_per_triple": dfma_pt,
-                         "double_float_mulsub_per_triple": dms_pt,
+                         "fp64_flops_per_triple": f64_pt, "fp32_instructions_per_triple": f32_pt,
+                         "double_float_ops_per_triple": dfops_pt,
                          "t_fp64_bound_ms": t_fp64 * 1e3, "t_fp32_bound_ms": t_fp32 * 1e3,
                          "fp64_achieved_tflops": triples * f64_pt / (avg_launch_ms * 1e-3) / 1e12,
                          "fp64_measured_peak_tflops": peaks["fp64_tflops"],

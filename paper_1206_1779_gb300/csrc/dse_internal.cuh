@@ -50,8 +50,9 @@ __host__ __device__ inline size_t rad_entries(const Consts& c) {
 
 // Per radial node: y_k, quadrature weight W_k (Jacobian y_k included), sqrt(y_k).
 struct Rad { double y, W, sy, pad; };
-// Per angular node: weight w_l, sigma_l = sin^2(theta_l/2), sin^2 theta_l, sin^4 theta_l.
-struct Ang { double w, sig, s2, s4; };
+// Per angular node: weight w_l, sigma_l = sin^2(theta_l/2), sin^2 theta_l, sin^4 theta_l,
+// and the products w_l sin^2 theta_l, w_l sin^4 theta_l.
+struct Ang { double w, sig, s2, s4, ws2, ws4; };
 // Per triple-kernel row (external momentum): x, sqrt(x), K/(3x), flags.
 struct Row { double x, sx, pre; int flags, pad; };
 enum : int { kRowGluon = 1, kRowGhost = 2 };
@@ -66,27 +67,27 @@ struct XTab { double lG, lZ, G, Z, Ginv, Zinv, pad0, pad1; };
 // theta = arccos s, on each a polynomial of degree kSeriesP in u = (s - mid) * invhalf
 // in [-1, 1] (monomial coefficients) for Z(s), G(s) (pairs e[k]) and W(s) = G^p Z^q
 // (w[k]), fitted at kSeriesP + 1 Chebyshev points where ln Z, ln G come from a
-// compensated Clenshaw recurrence.  With interval width h = pi/M the fit error is
-// ~ (N h/4)^(P+1)/(P+1)! relative: below 2e-20 for M >= 2N and ~1e-15 for the
-// highest mode at N = 256 (whose coefficient is small for a smooth solution), so the FP64
-// quadrature kernel reads the table for kSeriesMinN <= N <= kSeriesMaxN in place
-// of the per-triple series sums and exponentials.  The leading kSeriesLead
-// coefficients are FP64; the rest, whose terms are small next to the leading ones
-// on an interval (~(N h/4)^k/k! relative for a smooth function), are stored as
-// double-float pairs and summed on the FP32 pipe.
+// compensated Clenshaw recurrence.  With interval width h = pi/M the interpolation
+// error of a mode T_j is at most 4 (j h/4)^(P+1)/(P+1)! (modes j <= P exactly), so
+// for ln Z = sum a_j T_j the relative error of the table's Z is below
+// 4 (N h/4)^16/16! sum_{j>=16} |a_j|: 3.8e-15 times that sum at N = 256, 1e-24 at
+// N = 64.  The FP64 quadrature kernel therefore reads the table for
+// kSeriesMinN <= N <= kSeriesMaxN in place of the per-triple series sums and
+// exponentials.  Every coefficient is a double-float pair (hi, lo) of the
+// coefficient times 2^-E, E the record's exponent of that function (ex[F]: the
+// largest coefficient lands in [1, 2), so no value leaves the FP32 range); the
+// polynomials are summed on the FP32 pipe and widened with E folded in.
 constexpr int kSeriesM = 256;
 constexpr int kSeriesP = 15;
 constexpr int kSeriesQ = kSeriesP + 1;
-constexpr int kSeriesLead = 4;
-constexpr int kSeriesTail = kSeriesQ - kSeriesLead;
 constexpr int kSeriesMinN = 24;
 constexpr int kSeriesMaxN = 256;  // DSE_MAX_CHEB: every N >= kSeriesMinN
 struct SeriesRec {
     double mid, invhalf;
-    double2 e[kSeriesLead];     // (Z, G), coefficients 0 .. kSeriesLead - 1
-    double w[kSeriesLead];      // W = G^p Z^q
-    float4 et[kSeriesTail];     // (Z hi, Z lo, G hi, G lo), coefficients kSeriesLead .. kSeriesP
-    float2 wt[kSeriesTail];     // (W hi, W lo)
+    int ex[4];                  // biased FP64 exponents E of Z, G, W; ex[3]: the degree kf from
+                                // which on the coefficients (hi parts) are summed in FP32 alone
+    float4 e[kSeriesQ];         // (Z hi, Z lo, G hi, G lo) 2^-E, coefficients 0 .. kSeriesP
+    float2 w[kSeriesQ];         // (W hi, W lo) 2^-E
 };
 // A table is kSeriesRecords records: the kSeriesM intervals, then one record whose
 // first four doubles are the series at the end points, ln Z(s=1), ln G(s=1),
@@ -158,7 +159,7 @@ cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* 
 cudaError_t launch_series_table_batched(const BatchProblem* P, int nb, const double* coef_base, cudaStream_t s);
 // FP32-integrand variant (mixed precision), same outputs and layouts.
 cudaError_t launch_triple32(bool full, const TripleArgs& a, cudaStream_t s);
-size_t triple_smem_bytes(bool full, int N);
+size_t triple_smem_bytes(bool full, int N, int KB);
 int triple_block_threads(int N);
 int triple_max_blocks_per_sm(bool full, int N);
 cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch, const Rad* rad,

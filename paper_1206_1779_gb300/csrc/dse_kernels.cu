@@ -133,6 +133,8 @@ __global__ void k_setup_rules(const Consts c, const double* __restrict__ gr, con
             a.s2 = 1.0 / (cu * cu);
         }
         a.s4 = a.s2 * a.s2;
+        a.ws2 = a.w * a.s2;
+        a.ws4 = a.w * a.s4;
         ang[q] = a;
         theta[q] = th;
         return;
@@ -299,6 +301,7 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     __shared__ double scf[2 * DSE_MAX_CHEB];      // a then b
     __shared__ double smh[kSeriesIntervalsPerBlock][4];  // cos th0, cos th1, sin((th0 + th1)/2), sin(h/2)
     __shared__ double suq[kSeriesQ];                     // the Chebyshev points u_q
+    __shared__ int skf[3][kSeriesIntervalsPerBlock];     // FP32-tail degree per function
     if (blk * kSeriesIntervalsPerBlock >= c.sM) return;  // (batched grids span the largest table)
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int il = lane / kSeriesQ, q = lane % kSeriesQ;
@@ -376,22 +379,40 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     __syncthreads();
     double mono = 0.0;
     for (int j = q; j < kSeriesQ; ++j) mono = fma(sc[f][il][j], tcoef[j][q], mono);
+    // the record's exponent of this function: the largest biased exponent of its
+    // coefficients (the 16 lanes of the interval)
+    int E = (int)(((unsigned)__double2hiint(mono) >> 20) & 0x7ffu);
+    for (int off = kSeriesQ / 2; off > 0; off >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, off));
+    // double-float pair of mono 2^-(E - 1023): hi rounded to FP32, lo the rounded remainder
+    const double ms = ldexp(mono, 1023 - E);
+    const float hi = (float)ms;
+    const float lo = (float)(ms - (double)hi);
     SeriesRec& R = tab[i];
-    if (q < kSeriesLead) {
-        if (f == 0) R.e[q].x = mono;
-        else if (f == 1) R.e[q].y = mono;
-        else R.w[q] = mono;
-    } else {
-        // double-float pair: hi rounded to FP32, lo the rounded remainder
-        const float hi = (float)mono;
-        const float lo = (float)(mono - (double)hi);
-        float* t = f < 2 ? &R.et[q - kSeriesLead].x + 2 * f : &R.wt[q - kSeriesLead].x;
-        t[0] = hi;
-        t[1] = lo;
+    float* t = f < 2 ? &R.e[q].x + 2 * f : &R.w[q].x;
+    t[0] = hi;
+    t[1] = lo;
+    if (q == 0) R.ex[f] = E;
+    // the degree from which on the polynomial's tail is summed in FP32 alone: the
+    // smallest k >= 1 with sum_{k' >= k} |c_k'| <= 2^-30 |c_0| for all three
+    // functions (c_0, the value at the interval's middle, is positive), so that
+    // the FP32 rounding of the tail (16 roundings of 2^-24 at most) stays below
+    // 2^-50 of the value
+    {
+        double tail = fabs(ms);
+        for (int off = 1; off < kSeriesQ; off <<= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, tail, off);
+            if (q + off < kSeriesQ) tail += o;
+        }
+        const double c0 = __shfl_sync(0xffffffffu, ms, lane & ~(kSeriesQ - 1));
+        int kq = (q >= 1 && tail <= 0x1p-30 * fabs(c0)) ? q : kSeriesQ;
+        for (int off = kSeriesQ / 2; off > 0; off >>= 1) kq = min(kq, __shfl_xor_sync(0xffffffffu, kq, off));
+        if (q == 0) skf[f][il] = kq;
     }
+    __syncthreads();
     if (f == 0 && q == 0) {
         R.mid = mid;
         R.invhalf = 1.0 / half;
+        R.ex[3] = max(skf[0][il], max(skf[1][il], skf[2][il]));
     }
 }
 

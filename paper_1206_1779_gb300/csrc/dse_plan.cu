@@ -131,6 +131,13 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // 256 x 128 nodes on an earlier version of the kernel: one wave (KS = 11) 0.84 ms
 // per launch, KS = 23 / 35 / 47 / 64: 0.81 / 0.78 / 0.76 / 0.74 ms; on the current
 // one KS = 64 / 128: 0.617 / 0.608 ms.
+// Radial splits of the quadrature kernel: about kSplitWaves waves of blocks over the
+// resident slots, at least two radial nodes per block, at most 128 splits.
+#ifndef DSE_SPLIT_WAVES
+#define DSE_SPLIT_WAVES 8
+#endif
+constexpr int kSplitWaves = DSE_SPLIT_WAVES;
+
 void choose_split(dse_plan* pl) {
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -138,7 +145,7 @@ void choose_split(dse_plan* pl) {
     if (occ < 1) occ = 1;
     const long long slots = (long long)nsm * occ;
     const int nr = pl->c.nr;
-    long long kb = ((long long)nr * pl->Rt) / (8 * slots);
+    long long kb = ((long long)nr * pl->Rt) / (kSplitWaves * slots);
     if (kb < 2) kb = 2;
     if (kb > nr) kb = nr;
     while ((nr + kb - 1) / kb > 128) ++kb;

@@ -46,113 +46,622 @@ __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 :
 // ---- ln z and 1/z (table-driven, Tang 1990) ----
 // z = 2^e m with m in [1, 2); for the leading 7 fraction bits j of m, c_j =
 // 1 + (j + 1/2)/128, inv_j = 1/c_j rounded to FP64 and L_j = -ln(inv_j) as a
-// double-double (dse_lntab.cuh, written by gen_lntab.py with 60-digit arithmetic).  With r = m inv_j - 1
-// (one FMA, |r| < 2^-7.9):
-//   ln z = e ln2 + L_j + ln(1 + r),  ln(1 + r) = r - r^2/2 + r^3/3 (FP64)
-//          - r^4 (1/4 - r/5 + r^2/6 - r^3/7) (FP32, below 2.4e-10);
-//   1/z = 2^-e inv_j / (1 + r),  1/(1 + r) = ((1 - r) + r^2) - r^3 (FP64) + r^4 (1 - r + r^2) (FP32).
-// ln2 = ln2_hi + ln2_lo with ln2_hi holding 42 significant bits, so e ln2_hi is exact.
-// Accuracy (emulated against 40-digit arithmetic over z in [1e-14, 1e8]): ln z within
-// 2 units of 2^-53 max(1, |ln z|), 1/z within 4 units in the last place.  Zero,
-// subnormal, very large, infinite and NaN arguments take the library routines.
+// double-double (dse_lntab.cuh, written by gen_lntab.py with 60-digit arithmetic).
+// With r = m inv_j - 1 (one FMA, |r| < 2^-7.9):
+//   ln z = (e ln2_hi + L_j,hi) + r + [c + e ln2_lo + L_j,lo],
+//          c = ln(1 + r) - r = -r^2 (1/2 - r/3 + r^2/4 - r^3/5 + r^4/6) (|c| < 2^-16.8);
+//   1/z = 2^-e inv_j ((1 - r) + [d]),  d = 1/(1 + r) - (1 - r) = r^2 (1 - r + r^2 - r^3 + r^4);
+// where the bracketed small terms are formed in double-float on the FP32 pipe (they
+// need about 40 significant bits) and only the leading sums, the product by inv_j and
+// the FMAs of r and of e ln2_hi take the FP64 pipe (10 FP64 operations).  ln2 = ln2_hi
+// + ln2_lo with ln2_hi holding 42 significant bits, so e ln2_hi is exact.  Accuracy
+// (tests/test_ln_rcp.py, an emulation of these operations against 40-digit values over
+// z in [1e-14, 1e8]): ln z within 2 units of 2^-53 max(1, |ln z|), 1/z within 3 units in
+// the last place.  Zero, subnormal, negative, very large, infinite and NaN arguments
+// take the library routines.
 constexpr int kLnTab = 128;  // g_lntab: inv_j, L_j hi, L_j lo (kLnTab each), ln2_hi, ln2_lo
+constexpr float kLn2LoF = 0x1.ef357ap-45f;   // ln2_lo of g_lntab rounded to FP32
+constexpr float kThirdHi = 0x1.555556p-2f;   // 1/3 = kThirdHi + kThirdLo to 2^-50
+constexpr float kThirdLo = -0x1.555556p-27f;
 
 struct LnRcp { double ln, rcp; };
 
 __device__ __forceinline__ LnRcp ln_rcp(double z) {
     LnRcp o;
-    if (!(z >= 0x1p-1020 && z <= 0x1p+1020)) {
+    const int hz = __double2hiint(z);
+    if (hz < 0x00300000 || hz >= 0x7fc00000) {  // outside [2^-1020, 2^1021), or negative
         o.ln = log(z);
         o.rcp = 1.0 / z;
         return o;
     }
-    const int hz = __double2hiint(z);
     const int e = ((hz >> 20) & 0x7ff) - 1023;
     const int j = (hz >> 13) & (kLnTab - 1);
     const double m = __hiloint2double((hz & 0x000fffff) | 0x3ff00000, __double2loint(z));
     const double inv = __ldg(&g_lntab[j]);
     const double Lh = __ldg(&g_lntab[kLnTab + j]), Ll = __ldg(&g_lntab[2 * kLnTab + j]);
-    const double ln2h = __ldg(&g_lntab[3 * kLnTab]), ln2l = __ldg(&g_lntab[3 * kLnTab + 1]);
+    const double ln2h = __ldg(&g_lntab[3 * kLnTab]);
     const double r = fma(m, inv, -1.0);
-    const double r2 = r * r;
-    const double r3 = r2 * r;
-    const float rf = df_split(r, 0).x;  // r to FP32 precision (truncated)
-    const float r4f = (rf * rf) * (rf * rf);
-    const float tl = r4f * fmaf(fmaf(fmaf(-1.0f / 7.0f, rf, 1.0f / 6.0f), rf, -0.2f), rf, 0.25f);
-    const float tq = r4f * fmaf(rf, rf - 1.0f, 1.0f);
+    const float2 rd = df_split(r, 0);
+    const float rf = rd.x;
+    // r^2 = p2 + e2: the exact product of the leading parts and the cross term
+    const float p2 = rf * rf;
+    const float e2 = fmaf(2.0f * rf, rd.y, fmaf(rf, rf, -p2));
+    // c = -r^2 P, P = (1/2 - r/3) + (r^2/4 - r^3/5 + r^4/6), the first part in double-float
+    const float2 r3 = df_mul(rd, make_float2(kThirdHi, kThirdLo));
+    const float ph = 0.5f - r3.x;
+    const float pl = (((0.5f - ph) - r3.x) - r3.y) + p2 * fmaf(fmaf(1.0f / 6.0f, rf, -0.2f), rf, 0.25f);
+    const float2 cm = df_mul(make_float2(p2, e2), make_float2(ph, pl));
+    // S = c + e ln2_lo + L_j,lo (the last two below 2^-32: FP32 suffices)
+    const float ef = __int_as_float(0x4b400000 + e) - 12582912.0f;  // e as FP32 (|e| < 2^22)
+    const float sl = fmaf(ef, kLn2LoF, (float)Ll) - cm.y;
+    // d = r^2 Q, Q = (1 - r) + (r^2 - r^3 + r^4), the first part in double-float
+    const float qh = 1.0f - rf;
+    const float ql = (((1.0f - qh) - rf) - rd.y) + p2 * (1.0f - rf + p2);
+    const float2 dm = df_mul(make_float2(p2, e2), make_float2(qh, ql));
     // e as a double without a conversion instruction: 1.5 2^52 + (e + 2^31) - (1.5 2^52 + 2^31)
     const double ed = __hiloint2double(0x43380000, (int)((unsigned)e ^ 0x80000000u)) - 6755401588539392.0;
-    const double lead = fma(r3, 1.0 / 3.0, fma(r2, -0.5, r));
     const double hi = fma(ed, ln2h, Lh);
-    const double lo = fma(ed, ln2l, Ll);
-    o.ln = hi + ((lead - df_widen(tl, 1023)) + lo);
-    const double q = (((1.0 - r) + r2) - r3) + df_widen(tq, 1023);
-    o.rcp = (q * inv) * __hiloint2double((1023 - e) << 20, 0);
+    o.ln = hi + ((r - df_widen(cm.x, 1023)) + df_widen(sl, 1023));
+    const double q = ((1.0 - r) + df_widen(dm.x, 1023)) + df_widen(dm.y, 1023);
+    const double t = q * inv;  // in (1/2, 1.004]: scaled by 2^-e in its exponent field
+    o.rcp = __hiloint2double(__double2hiint(t) - (e << 20), __double2loint(t));
     return o;
 }
 
-// The shared-memory row of a triple holds 2s and the anchors T_4i, T_4i+1
-// (i < nq = ceil(N/4)) as double-float pairs; phase B forms T_4i+2 = 2s T_4i+1 - T_4i
-// and T_4i+3 = 2s T_4i+2 - T_4i+1 from them.  Its 4 nq derivative columns c map to
-// j = 4 (c mod nq) + c div nq, so that a warp's threads share c div nq (the same
-// number of recurrence steps) when nq is a multiple of 16.
-// With AR false (full rows) the row holds T_0 .. T_N-1 (T_0 as 1/2) and column c
-// is j = c: twice the shared memory, no recurrence steps in phase B.
-__host__ __device__ inline int anchors_for(int N) { return (N + 3) / 4; }
-__host__ __device__ inline int row_len_for(int N, bool ar) {
-    if (!ar) return N + 1;
-    const int l = 1 + 2 * anchors_for(N);
-    return l | 1;  // odd: conflict-free rows
+// a + b in double-float (renormalised; exact sum of the leading parts)
+__device__ __forceinline__ float2 df_add(const float2 a, const float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
 }
 
-__host__ __device__ inline int ncols_for(int N, bool ar) { return ar ? 4 * anchors_for(N) : N; }
-
-__host__ __device__ inline int groups_for(int N, int BT, bool ar) {
-    const int nc = ncols_for(N, ar);
-    const int nact = nc < BT ? nc : BT;
-    return BT / nact;
+// Z(z), G(z) (zg) and W(z) (w) from the series-table record R at u = uf
+// (double-float): Horner over the kSeriesQ coefficients of each, the terms of
+// degree >= kf in FP32 on the leading parts (the record's tail is small enough
+// for that: kf = R->ex[3], here the largest over the lanes that evaluate together,
+// so that they take the same steps), the rest in double-float.  Results as
+// double-float mantissas Zm, Gm, Wm and exponent shifts (Z = Zm 2^Zs).
+__device__ __forceinline__ void series_eval_df(const SeriesRec* __restrict__ R, const float2 uf, const bool zg,
+                                               const bool w, float2& Zm, float2& Gm, float2& Wm, int& Zs, int& Gs,
+                                               int& Ws) {
+    const int kf = __reduce_max_sync(__activemask(), __ldg(&R->ex[3]));
+    if (zg) {
+        const float4 top = __ldg(&R->e[kSeriesP]);
+        float2 tz = make_float2(top.x, kf > kSeriesP ? top.y : 0.0f);
+        float2 tg = make_float2(top.z, kf > kSeriesP ? top.w : 0.0f);
+#pragma unroll
+        for (int k = kSeriesP - 1; k >= 0; --k) {
+            const float4 ck = __ldg(&R->e[k]);
+            if (k >= kf) {
+                tz.x = fmaf(tz.x, uf.x, ck.x);
+                tg.x = fmaf(tg.x, uf.x, ck.z);
+            } else {
+                tz = df_muladd(tz, uf, make_float2(ck.x, ck.y));
+                tg = df_muladd(tg, uf, make_float2(ck.z, ck.w));
+            }
+        }
+        const int2 ex = __ldg(reinterpret_cast<const int2*>(R->ex));
+        Zm = tz;
+        Gm = tg;
+        Zs = ex.x - 1023;
+        Gs = ex.y - 1023;
+    }
+    if (w) {
+        const float2 top = __ldg(&R->w[kSeriesP]);
+        float2 tw = make_float2(top.x, kf > kSeriesP ? top.y : 0.0f);
+#pragma unroll
+        for (int k = kSeriesP - 1; k >= 0; --k) {
+            const float2 ck = __ldg(&R->w[k]);
+            if (k >= kf) tw.x = fmaf(tw.x, uf.x, ck.x);
+            else tw = df_muladd(tw, uf, ck);
+        }
+        Wm = tw;
+        Ws = __ldg(&R->ex[2]) - 1023;
+    }
 }
 
-__host__ __device__ inline size_t tile_doubles(bool full, int N, int BT, bool ar) {
-    if (!full) return 0;
-    const size_t t = (size_t)BT * (size_t)row_len_for(N, ar);
-    const size_t red = (size_t)groups_for(N, BT, ar) * 3u * (size_t)N;
-    return t > red ? t : red;
+// The same, widened to FP64.
+__device__ __forceinline__ void series_eval(const SeriesRec* __restrict__ R, const float2 uf, const bool zg,
+                                            const bool w, double& Z, double& G, double& W) {
+    float2 Zm, Gm, Wm;
+    int Zs = 0, Gs = 0, Ws = 0;
+    series_eval_df(R, uf, zg, w, Zm, Gm, Wm, Zs, Gs, Ws);
+    if (zg) {
+        Z = df_widen(Zm.x, Zs + 1023) + df_widen(Zm.y, Zs + 1023);
+        G = df_widen(Gm.x, Gs + 1023) + df_widen(Gm.y, Gs + 1023);
+    }
+    if (w) W = df_widen(Wm.x, Ws + 1023) + df_widen(Wm.y, Ws + 1023);
 }
 
-// Row layout of each kernel: the single-problem kernel keeps anchor rows (more
-// blocks per SM); the persistent batched kernel, limited by its registers, full rows.
-constexpr bool kAnchorRowsSingle = true;
-constexpr bool kAnchorRowsBatched = false;
+// The anchors T_4i, T_4i+1 for i = 1 .. nq - 1 by the recurrence of stride 4,
+// X_(i+1) = 2 T_4 X_i - X_(i-1) (from T_(m+4) + T_(m-4) = 2 T_4 T_m), in
+// double-float from T_4 and T_5 formed in FP64 from s (their rounding to 48 bits,
+// 2^-49 relative, is the start error, which grows at most like i over i steps; the
+// steps' own rounding errors, 2^-48 each, at most like i^2); dst[i - 1] =
+// (T_4i hi, lo, T_4i+1 hi, lo).  sd is s as a double-float pair.
+__device__ __forceinline__ void store_anchors(const double s, const float2 sd, const int nq,
+                                              float4* __restrict__ dst) {
+    const double T2 = fma(2.0 * s, s, -1.0);
+    const double T3 = fma(2.0 * s, T2, -s);
+    const double T4 = fma(2.0 * T2, T2, -1.0);
+    const float2 c4 = df_split(2.0 * T4, 0);
+    float2 a0 = make_float2(1.0f, 0.0f), a1 = df_split(T4, 0);
+    float2 b0 = sd, b1 = df_split(fma(2.0 * s, T4, -T3), 0);
+    for (int i = 1; i < nq; ++i) {
+        dst[i - 1] = make_float4(a1.x, a1.y, b1.x, b1.y);
+        const float2 an = df_mulsub(c4, a1, a0);
+        a0 = a1;
+        a1 = an;
+        const float2 bn = df_mulsub(c4, b1, b0);
+        b0 = b1;
+        b1 = bn;
+    }
+}
 
-// Radial nodes whose per-node factors are formed together (by one warp) and
-// kept in shared memory, and the factors per node.
+// 2^d as FP32 for -126 <= d <= 127 (0 below, Inf above)
+__device__ __forceinline__ float pow2f(int d) {
+    return d < -126 ? 0.0f : d > 127 ? __int_as_float(0x7f800000) : __int_as_float((127 + d) << 23);
+}
+
+// ---- single-problem kernels ----
+// Radial nodes whose per-node factors are formed together (by one warp), and the
+// factors per node: d, 4 sqrt(xy), K = W_k y G(y), the five quartic coefficients
+// of the gluon-loop kernel.
 constexpr int kRadGroup = 32;
 constexpr int kRadFactors = 8;
 
-__host__ __device__ inline size_t smem_doubles(bool full, int N, int BT, bool ar) {
-    // tile rows, 3 BT weights as double-float pairs, 2 N coefficients, 4 boundary
-    // sums, 3 x 8 per-warp exponent maxima, the factors of a group of radial nodes
-    return tile_doubles(full, N, BT, ar) + 3u * (size_t)BT + 2u * (size_t)N + 4u + 12u +
-           (size_t)kRadGroup * kRadFactors;
+// (x, y) factors of the integrands of radial node kq, formed once per node instead
+// of per triple: z = d + b2 sigma with d = (sqrt x - sqrt y)^2, b2 = 4 sqrt(xy);
+// K = W_k y G(y) (hM = K w s4 G(z)/z, hG = K w s4 Z(z)/z^2); the quartic of the
+// gluon-loop kernel times W_k W(y)/2 (hQ = w s2 W(z)/z^2 sum_i kQ_i sigma^i).
+__device__ __forceinline__ void radial_factors(const TripleArgs& A, const Row& row, const int rt, const int kq,
+                                               double* __restrict__ f) {
+    const Consts& c = A.c;
+    const Rad rd = A.rad[rad_offset(c, rt) + kq];
+    const YTab yt = A.ytab[rad_offset(c, rt) + kq];
+    const double d0 = row.sx - rd.sy;
+    const double d = d0 * d0;
+    const double b = 2.0 * row.sx * rd.sy;
+    f[0] = d;
+    f[1] = 2.0 * b;
+    f[2] = rd.W * yt.yG;
+    const double dd = d * d, db = d * b, bb = b * b;
+    const double h = 0.5 * rd.W * yt.Wy;
+    f[3] = h * (7.5 * dd);
+    f[4] = h * -(48.0 * dd + 18.0 * db + 12.0 * bb);
+    f[5] = h * (48.0 * dd - 48.0 * db - 38.0 * bb);
+    f[6] = h * (96.0 * db + 64.0 * bb);
+    f[7] = h * (16.0 * bb);
 }
 
-// One block's work: row rt, radial split ks of the problem in A.  smem holds
-// smem_doubles(FULL, N, BT, AR) doubles.
-template <int BT, int NJ, bool FULL, bool AR>
-__device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, const int ks, double* smem) {
+// The three integrands (hQ, hM, hG) of the triple (x_r, y_k, theta_l) in FP64 and
+// s(z): z = d + b2 sigma_l from the node factors f, ln z and 1/z (ln_rcp), s(z)
+// (clamped outside [eps2, lambda2]), Z(z), G(z), W(z) from the series table, or by
+// the per-triple series and the IR/UV forms, and the kernels M and Q.
+struct TripleW {
+    double hQ, hM, hG, s;
+};
+
+__device__ __forceinline__ TripleW triple_weights(const TripleArgs& A, const bool gluon, const bool ghost,
+                                                  const double* __restrict__ f, const int l,
+                                                  const double* __restrict__ sa, const double* __restrict__ sb,
+                                                  const double* __restrict__ sbnd, const float ith_scale) {
     const Consts& c = A.c;
     const int N = c.N;
-    const int nq = anchors_for(N);
-    const int ldT = row_len_for(N, AR);
+    TripleW o;
+    o.hQ = o.hM = o.hG = 0.0;
+    const Ang an = A.ang[l];
+    const double z = fma(f[1], an.sig, f[0]);
+    const LnRcp lr = ln_rcp(z);
+    const double lz = lr.ln;
+    // s(z), clamped to [-1, 1] for z outside [eps2, lambda2] (inside, it can leave
+    // the interval only by a rounding)
+    double s = (lz - c.L0) * c.invL1;
+    const double iz = lr.rcp;
+    const double iz2 = iz * iz;
+    double Zz = 0.0, Gz = 0.0, Wz = 0.0;  // Z(z), G(z), W(z) = G(z)^p Z(z)^q
+    // z > 0: the comparisons with eps2, lambda2 on the bit patterns
+    const long long zb = __double_as_longlong(z);
+    const bool beyond = zb < __double_as_longlong(c.eps2) || zb > __double_as_longlong(c.lam2);
+    const bool outside = c.extrap == 0 && beyond;
+    if (beyond) s = fmin(1.0, fmax(-1.0, s));
+    if (A.stab && !outside) {
+        // from the table: the interval by arccos in FP32 (FP32 s from the bits of s,
+        // truncated: the interval only; a neighbouring interval is as good), the
+        // polynomials in double-float
+        const float sf = fminf(1.0f, fmaxf(-1.0f, df_split(s, 0).x));
+        int it = (int)(acosf(sf) * ith_scale);
+        it = min(max(it, 0), c.sM - 1);
+        const SeriesRec* Rr = A.stab + it;
+        const double2 mh = __ldg(reinterpret_cast<const double2*>(Rr));
+        series_eval(Rr, df_split((s - mh.x) * mh.y, 0), ghost || gluon, gluon, Zz, Gz, Wz);
+    } else {
+        double lg, lzz;
+        if (A.stab) {
+            // outside [eps2, lambda2]: the series at s = +-1 (block sums)
+            lzz = s > 0.0 ? sbnd[0] : sbnd[2];
+            lg = s > 0.0 ? sbnd[1] : sbnd[3];
+        } else {
+            lg = 0.5 * sb[0];
+            lzz = 0.5 * sa[0];
+            if (N > 1) {
+                lg = fma(sb[1], s, lg);
+                lzz = fma(sa[1], s, lzz);
+            }
+            double t0 = 1.0, t1 = s;
+            const double s2x = 2.0 * s;
+            for (int j = 2; j < N; ++j) {
+                const double t2 = fma(s2x, t1, -t0);
+                t0 = t1;
+                t1 = t2;
+                lg = fma(sb[j], t2, lg);
+                lzz = fma(sa[j], t2, lzz);
+            }
+        }
+        if (outside) {
+            if (z < c.eps2) {
+                const double r = lz - c.ln_eps2;
+                lg = fma(-c.kappa, r, lg);
+                lzz = fma(2.0 * c.kappa, r, lzz);
+            } else {
+                const double L = log1p(c.omega * (lz - c.ln_lam2));
+                lg = fma(c.delta, L, lg);
+                lzz = fma(c.gam, L, lzz);
+            }
+        }
+        if (ghost) Zz = exp(lzz);
+        if (gluon) {
+            Gz = exp(lg);
+            Wz = exp(c.pG * lg + c.qZ * lzz);
+        }
+    }
+    const double Kw = f[2] * an.ws4;
+    if (ghost) o.hG = Kw * Zz * iz2;
+    if (gluon) {
+        const double sg = an.sig;
+        const double num = fma(sg, fma(sg, fma(sg, fma(sg, f[7], f[6]), f[5]), f[4]), f[3]);
+        o.hQ = an.ws2 * iz2 * Wz * num;
+        o.hM = Kw * iz * Gz;
+    }
+    o.s = s;
+    return o;
+}
+
+// Angular sums over the warp's 32 nodes (same radial node for the whole warp) of
+// (hQ, hM, hG) by halving exchanges, 6 FP64 additions per lane: lanes 0-15 go on
+// with (hQ, hM), lanes 16-31 with (hG, 0); then lanes with bit 3 set with the second
+// of the two; then three butterfly steps.  The sums end in lanes 0 (hQ), 8 (hM) and
+// 16 (hG), which write them to up[0..2] (when write is set).
+__device__ __forceinline__ void angular_sums(const TripleW& w, const int lane, const bool write, double* up) {
+    const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+    const double k0s = (h16 ? w.hG : w.hQ) + __shfl_xor_sync(kFullMask, h16 ? w.hQ : w.hG, 16);
+    const double k1s = (h16 ? 0.0 : w.hM) + __shfl_xor_sync(kFullMask, h16 ? w.hM : 0.0, 16);
+    double v = (h8 ? k1s : k0s) + __shfl_xor_sync(kFullMask, h8 ? k0s : k1s, 8);
+    v += __shfl_xor_sync(kFullMask, v, 4);
+    v += __shfl_xor_sync(kFullMask, v, 2);
+    v += __shfl_xor_sync(kFullMask, v, 1);
+    if (write && (lane & 7) == 0 && lane < 24) up[lane >> 3] = v;
+}
+
+__host__ __device__ inline size_t smem_res_doubles(int N, int KB) {
+    // 2 N coefficients, 4 boundary sums, the factors of a group of radial nodes
+    const int kg = KB < kRadGroup ? KB : kRadGroup;
+    return 2u * (size_t)N + 4u + (size_t)kg * kRadFactors;
+}
+
+// Residual mode (Upart only): one block of BT threads per (row, radial split).
+template <int BT>
+__device__ __forceinline__ void triple_tile_residual(const TripleArgs& A, const int rt, const int ks, double* smem) {
+    const Consts& c = A.c;
+    const int N = c.N;
+    constexpr int WARPS = BT / 32;
+    double* sa = smem;
+    double* sb = sa + N;
+    double* sbnd = sb + N;
+    double* srad = sbnd + 4;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    for (int j = tid; j < N; j += BT) {
+        sa[j] = j < c.NZ ? A.coef[j] : 0.0;
+        sb[j] = j < c.NG ? A.coef[c.NZ + j] : 0.0;
+    }
+    const Row row = A.rows[rt];
+    const bool gluon = (row.flags & kRowGluon) != 0;
+    const bool ghost = (row.flags & kRowGhost) != 0;
+    const int k0 = ks * A.KB;
+    const int k1 = min(c.nr, k0 + A.KB);
+    const int nch = A.nch;
+    const int nunits = k1 > k0 ? (k1 - k0) * nch : 0;
+    const int kgrp = A.KB < kRadGroup ? A.KB : kRadGroup;
+    const float ith_scale = (float)c.sM * (float)(1.0 / kPi);
+    if (A.stab && tid < 4) sbnd[tid] = reinterpret_cast<const double*>(A.stab + kSeriesM)[tid];
+    // a group of kgrp nodes spans whole tiles when kgrp = kRadGroup (kRadGroup nch is
+    // a multiple of WARPS); with fewer nodes per block one group covers the block
+    const int group_units = kgrp * nch;
+    for (int base = 0; base < nunits; base += WARPS) {
+        if (base % group_units == 0) {
+            __syncthreads();  // the previous group's factors are no longer read (and the coefficients staged)
+            if (warp == 0 && lane < kgrp && k0 + base / nch + lane < k1)
+                radial_factors(A, row, rt, k0 + base / nch + lane, srad + lane * kRadFactors);
+            __syncthreads();
+        }
+        const int u = base + warp;
+        TripleW w;
+        w.hQ = w.hM = w.hG = w.s = 0.0;
+        int k = 0, ch = 0;
+        if (u < nunits) {
+            const int kk = u / nch;
+            ch = u - kk * nch;
+            k = k0 + kk;
+            const int l = ch * 32 + lane;
+            if (l < c.na)
+                w = triple_weights(A, gluon, ghost, srad + (kk % kgrp) * kRadFactors, l, sa, sb, sbnd, ith_scale);
+        }
+        angular_sums(w, lane, u < nunits, A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3);
+    }
+}
+
+// ---- Newton-matrix mode ----
+// One block of BT threads per (row, radial split); tiles of BT triples (one warp =
+// 32 angular nodes of one radial node), each in two phases separated by barriers:
+//   phase A: each thread forms its triple's FP64 weights and s(z) (triple_weights),
+//            the warp's angular sums (Upart), and its shared-memory row;
+//   phase B: the derivative sums weight * T_j(s) in double-float on the FP32 pipe.
+// Shared-memory row of triple m (float4 units, stride rs4 = quad_count(N) + 1 made
+// odd, so that the rows of eight consecutive triples fall in distinct banks):
+//   [0] (2s, hQ), [1] (hM, hG) as double-float pairs, the weights times 2^-E with E
+//       the block's running exponent of each weight kind;
+//   [1 + i] (T_4i, T_4i+1) for quads i = 1 .. nq - 1 (quad 0 is T_0 = 1, T_1 = s).
+// Phase B: thread (group g, quad i) owns the columns j = 4i .. 4i+3 and the rows of
+// group g; it forms T_4i+2, T_4i+3 by two double-float steps of the recurrence and
+// adds the twelve products weight * T_j to double-float accumulators that live for
+// the whole block, at the block's running scale.
+__host__ __device__ inline int quad_count(int N) { return (N + 3) / 4; }
+__host__ __device__ inline int row_stride4(int N) { return (quad_count(N) + 1) | 1; }
+
+__host__ __device__ inline size_t tile_full_doubles(int N, int BT) {
+    const size_t t = 2u * (size_t)BT * (size_t)row_stride4(N);  // float4 = 2 doubles
+    const size_t red = (size_t)(BT / quad_count(N)) * 3u * (size_t)N;  // groups' sums, float2 = 1 double
+    return t > red ? t : red;
+}
+
+__host__ __device__ inline size_t smem_full_doubles(int N, int BT, int KB) {
+    // tile rows, 2 N coefficients, 4 boundary sums, 8 (16 ints: per-warp exponents),
+    // the factors of a group of radial nodes
+    const int kg = KB < kRadGroup ? KB : kRadGroup;
+    return tile_full_doubles(N, BT) + 2u * (size_t)N + 4u + 8u + (size_t)kg * kRadFactors;
+}
+
+template <int BT>
+__device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int rt, const int ks, double* smem) {
+    const Consts& c = A.c;
+    const int N = c.N;
+    const int nq = quad_count(N);
+    const int rs4 = row_stride4(N);
+    constexpr int WARPS = BT / 32;
+    static_assert(WARPS <= 4, "per-warp exponents hold 4 warps");
+    float4* sT = reinterpret_cast<float4*>(smem);
+    double* sa = smem + tile_full_doubles(N, BT);
+    double* sb = sa + N;
+    double* sbnd = sb + N;  // ln Z(s=1), ln G(s=1), ln Z(s=-1), ln G(s=-1) (table path)
+    int* sE = reinterpret_cast<int*>(sbnd + 4);  // [WARPS][4] per-warp maxima of the weights' exponents
+    double* srad = sbnd + 12;                    // [min(KB, kRadGroup)][kRadFactors] radial-node factors
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+
+    for (int j = tid; j < N; j += BT) {
+        sa[j] = j < c.NZ ? A.coef[j] : 0.0;
+        sb[j] = j < c.NG ? A.coef[c.NZ + j] : 0.0;
+    }
+    if (A.stab && tid < 4) sbnd[tid] = reinterpret_cast<const double*>(A.stab + kSeriesM)[tid];
+    const Row row = A.rows[rt];
+    const bool gluon = (row.flags & kRowGluon) != 0;
+    const bool ghost = (row.flags & kRowGhost) != 0;
+    const int k0 = ks * A.KB;
+    const int k1 = min(c.nr, k0 + A.KB);
+    const int nch = A.nch;
+    const int nunits = k1 > k0 ? (k1 - k0) * nch : 0;
+    const int kgrp = A.KB < kRadGroup ? A.KB : kRadGroup;
+    const float ith_scale = (float)c.sM * (float)(1.0 / kPi);
+
+    // phase-B mapping: G groups of nq threads, rows [g R, (g + 1) R)
+    const int G = BT / nq;
+    const int R = (BT + G - 1) / G;
+    const int g = tid / nq;
+    const int qi = tid - g * nq;
+    const bool bact = g < G;
+    const int mlo = min(BT, g * R);
+    const int mhi = min(BT, mlo + R);
+    float2 acc[3][4];
+#pragma unroll
+    for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[kd][q] = make_float2(0.0f, 0.0f);
+    int Erun[3] = {0, 0, 0};  // running biased exponents of the accumulators' scale (0: nothing yet)
+
+    // a group of kgrp nodes spans whole tiles when kgrp = kRadGroup (kRadGroup nch is
+    // a multiple of WARPS); with fewer nodes per block one group covers the block
+    const int group_units = kgrp * nch;
+    for (int base = 0; base < nunits; base += WARPS) {
+        if (base % group_units == 0) {
+            __syncthreads();  // the previous group's factors are no longer read (and the coefficients staged)
+            if (warp == 0 && lane < kgrp && k0 + base / nch + lane < k1)
+                radial_factors(A, row, rt, k0 + base / nch + lane, srad + lane * kRadFactors);
+            __syncthreads();
+        }
+        const int u = base + warp;
+        TripleW w;
+        w.hQ = w.hM = w.hG = w.s = 0.0;
+        bool live = false;
+        int k = 0, ch = 0;
+        if (u < nunits) {
+            const int kk = u / nch;
+            ch = u - kk * nch;
+            k = k0 + kk;
+            const int l = ch * 32 + lane;
+            if (l < c.na) {
+                live = true;
+                w = triple_weights(A, gluon, ghost, srad + (kk % kgrp) * kRadFactors, l, sa, sb, sbnd, ith_scale);
+            }
+        }
+        angular_sums(w, lane, u < nunits, A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3);
+        float4* Trow = sT + (size_t)tid * rs4;
+        const float2 sd = df_split(w.s, 0);  // s as a double-float pair (48 bits)
+        if (live) {
+            store_anchors(w.s, sd, nq, Trow + 2);
+        } else {
+            for (int i = 1; i < nq; ++i) Trow[1 + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        // per-warp maxima of the weights' exponents
+        {
+            const unsigned eq = ((unsigned)__double2hiint(w.hQ) >> 20) & 0x7ffu;
+            const unsigned em = ((unsigned)__double2hiint(w.hM) >> 20) & 0x7ffu;
+            const unsigned eg = ((unsigned)__double2hiint(w.hG) >> 20) & 0x7ffu;
+            const unsigned mq = __reduce_max_sync(kFullMask, eq);
+            const unsigned mm = __reduce_max_sync(kFullMask, em);
+            const unsigned mg = __reduce_max_sync(kFullMask, eg);
+            if (lane == 0) {
+                sE[warp * 4 + 0] = (int)mq;
+                sE[warp * 4 + 1] = (int)mm;
+                sE[warp * 4 + 2] = (int)mg;
+            }
+        }
+        __syncthreads();
+        // the block's running scale per weight kind: the largest exponent so far;
+        // when it grows, the accumulators are rescaled (exact powers of two)
+#pragma unroll
+        for (int kd = 0; kd < 3; ++kd) {
+            int Et = sE[kd];
+#pragma unroll
+            for (int ww = 1; ww < WARPS; ++ww) Et = max(Et, sE[ww * 4 + kd]);
+            if (Et > Erun[kd]) {
+                const float f = pow2f(Erun[kd] - Et);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[kd][q] = make_float2(acc[kd][q].x * f, acc[kd][q].y * f);
+                Erun[kd] = Et;
+            }
+        }
+        {
+            const float2 wq = df_split(w.hQ, Erun[0] - 1023);
+            const float2 wm = df_split(w.hM, Erun[1] - 1023);
+            const float2 wg = df_split(w.hG, Erun[2] - 1023);
+            Trow[0] = make_float4(2.0f * sd.x, 2.0f * sd.y, wq.x, wq.y);
+            Trow[1] = make_float4(wm.x, wm.y, wg.x, wg.y);
+        }
+        __syncthreads();
+        if (bact) {
+            // rows in groups of four, the accumulators renormalised after each
+            for (int m0 = mlo; m0 < mhi; m0 += 4) {
+                const int m1 = min(mhi, m0 + 4);
+                for (int m = m0; m < m1; ++m) {
+                    const float4* Tm = sT + (size_t)m * rs4;
+                    const float4 h01 = Tm[0];
+                    const float4 h23 = Tm[1];
+                    const float4 an = Tm[1 + (qi > 0 ? qi : 1)];
+                    const float2 s2 = make_float2(h01.x, h01.y);
+                    const float2 t0 = qi > 0 ? make_float2(an.x, an.y) : make_float2(1.0f, 0.0f);
+                    const float2 t1 = qi > 0 ? make_float2(an.z, an.w) : make_float2(0.5f * h01.x, 0.5f * h01.y);
+                    const float2 t2 = df_mulsub(s2, t1, t0);
+                    const float2 t3 = df_mulsub(s2, t2, t1);
+                    const float2 w0 = make_float2(h01.z, h01.w);
+                    const float2 w1 = make_float2(h23.x, h23.y);
+                    const float2 w2 = make_float2(h23.z, h23.w);
+                    df_fma(acc[0][0], w0, t0);
+                    df_fma(acc[0][1], w0, t1);
+                    df_fma(acc[0][2], w0, t2);
+                    df_fma(acc[0][3], w0, t3);
+                    df_fma(acc[1][0], w1, t0);
+                    df_fma(acc[1][1], w1, t1);
+                    df_fma(acc[1][2], w1, t2);
+                    df_fma(acc[1][3], w1, t3);
+                    df_fma(acc[2][0], w2, t0);
+                    df_fma(acc[2][1], w2, t1);
+                    df_fma(acc[2][2], w2, t2);
+                    df_fma(acc[2][3], w2, t3);
+                }
+#pragma unroll
+                for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) df_renorm(acc[kd][q]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // combine the groups (double-float, at the common running scale) in a fixed
+    // order, widen to FP64 and write this block's split; T_0 enters as 1/2
+    float2* red = reinterpret_cast<float2*>(smem);  // [G][3][N]
+    if (bact) {
+#pragma unroll
+        for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * qi + q;
+                if (j < N) {
+                    float2 v = acc[kd][q];
+                    if (j == 0) v = make_float2(0.5f * v.x, 0.5f * v.y);
+                    red[((size_t)g * 3 + kd) * N + j] = v;
+                }
+            }
+    }
+    __syncthreads();
+    double* out = A.Vpart + ((size_t)rt * A.KS + ks) * 3 * (size_t)N;
+    for (int idx = tid; idx < 3 * N; idx += BT) {
+        float2 v = red[idx];
+        for (int gg = 1; gg < G; ++gg) v = df_add(v, red[(size_t)gg * 3 * N + idx]);
+        const int kd = idx / N;
+        const int E = kd == 0 ? Erun[0] : kd == 1 ? Erun[1] : Erun[2];
+        out[idx] = df_widen(v.x, E) + df_widen(v.y, E);
+    }
+}
+
+// factors per radial node in the batched tile (the FP64 ones of the single tile)
+constexpr int kRadFactorsBatched = 8;
+
+// Row layout of the batched tile: T_0 .. T_N-1 per triple (N + 1 pairs).
+__host__ __device__ inline int row_len_for(int N) { return N + 1; }
+
+__host__ __device__ inline int groups_for(int N, int BT) {
+    const int nact = N < BT ? N : BT;
+    return BT / nact;
+}
+
+__host__ __device__ inline size_t tile_doubles(bool full, int N, int BT) {
+    if (!full) return 0;
+    const size_t t = (size_t)BT * (size_t)row_len_for(N);
+    const size_t red = (size_t)groups_for(N, BT) * 3u * (size_t)N;
+    return t > red ? t : red;
+}
+
+__host__ __device__ inline size_t smem_doubles(bool full, int N, int BT) {
+    // tile rows, 3 BT weights as double-float pairs, 2 N coefficients, 4 boundary
+    // sums, 3 x 8 per-warp exponent maxima, the factors of a group of radial nodes
+    return tile_doubles(full, N, BT) + 3u * (size_t)BT + 2u * (size_t)N + 4u + 12u +
+           (size_t)kRadGroup * kRadFactorsBatched;
+}
+
+// One work item of the persistent batched kernel: row rt, radial split ks of the
+// problem in A.  The shared-memory row of a triple holds T_0 .. T_N-1 (T_0 as 1/2)
+// as double-float pairs; phase-B thread j accumulates column j.  smem holds
+// smem_doubles(FULL, N, BT) doubles.
+template <int BT, int NJ, bool FULL>
+__device__ __forceinline__ void triple_tile_batched(const TripleArgs& A, const int rt, const int ks, double* smem) {
+    const Consts& c = A.c;
+    const int N = c.N;
+    const int ldT = row_len_for(N);
     double* sT = smem;
-    float2* sT2 = reinterpret_cast<float2*>(smem);  // rows [2s][T_4i][T_4i+1] as double-float pairs
-    float2* sh2 = reinterpret_cast<float2*>(smem + tile_doubles(FULL, N, BT, AR));  // [3][BT] weight pairs
-    double* sa = smem + tile_doubles(FULL, N, BT, AR) + 3 * BT;
+    float2* sT2 = reinterpret_cast<float2*>(smem);  // rows T_0 .. T_N-1 as double-float pairs
+    float2* sh2 = reinterpret_cast<float2*>(smem + tile_doubles(FULL, N, BT));  // [3][BT] weight pairs
+    double* sa = smem + tile_doubles(FULL, N, BT) + 3 * BT;
     double* sb = sa + N;
     double* sbnd = sb + N;  // ln Z(s=1), ln G(s=1), ln Z(s=-1), ln G(s=-1) (table path)
     int* sex = reinterpret_cast<int*>(sbnd + 4);  // [3][8] per-warp maxima of the weights' exponents
-    double* srad = sbnd + 16;                     // [kRadGroup][kRadFactors] radial-node factors
+    double* srad = sbnd + 16;                     // [kRadGroup][kRadFactorsBatched] radial-node factors
     constexpr int WARPS = BT / 32;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -172,8 +681,8 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     const int nunits = k1 > k0 ? (k1 - k0) * nch : 0;
 
     // phase-B mapping: NG groups of nact threads, thread owns the columns
-    // c = jb + jj*nact of 4 nq: T_j with j = 4 (c mod nq) + c div nq
-    const int ncol = ncols_for(N, AR);
+    // j = jb + jj*nact
+    const int ncol = N;
     const int nact = ncol < BT ? ncol : BT;
     const int NG = BT / nact;
     const int g = tid / nact;
@@ -181,14 +690,11 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     const bool bact = g < NG;
     const int mlo = (g * BT) / NG;
     const int mhi = ((g + 1) * BT) / NG;
-    int colj[NJ], coli[NJ], colr[NJ];
+    int colj[NJ];
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
         const int cc = jb + jj * nact;
-        colr[jj] = AR ? cc / nq : 0;
-        coli[jj] = AR ? cc - colr[jj] * nq : 0;
-        if (AR) colj[jj] = cc < ncol ? 4 * coli[jj] + colr[jj] : N;  // j >= N: inactive
-        else colj[jj] = cc < N ? cc : N;
+        colj[jj] = cc < N ? cc : N;  // j >= N: inactive
     }
 
     double acc[3][NJ];
@@ -218,7 +724,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                     const double d0 = row.sx - rd.sy;
                     const double d = d0 * d0;
                     const double b = 2.0 * row.sx * rd.sy;
-                    double* f = srad + lane * kRadFactors;
+                    double* f = srad + lane * kRadFactorsBatched;
                     f[0] = d;
                     f[1] = 2.0 * b;
                     f[2] = rd.W * yt.yG;
@@ -245,7 +751,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
             const int l = ch * 32 + lane;
             if (l < c.na) {
                 live = true;
-                const double* f = srad + (kk % kRadGroup) * kRadFactors;
+                const double* f = srad + (kk % kRadGroup) * kRadFactorsBatched;
                 const Ang an = A.ang[l];
                 const double z = fma(f[1], an.sig, f[0]);
                 const LnRcp lr = ln_rcp(z);
@@ -263,46 +769,14 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                 if (beyond) s = fmin(1.0, fmax(-1.0, s));
                 if (A.stab && !outside) {
                     // Z(z), G(z), W(z) from the table: the interval by arccos in
-                    // FP32, the polynomials in u = (s - mid) / half in FP64 (Horner)
-                    // (FP32 s from the bits of s, truncated: the interval only)
+                    // FP32 (FP32 s from the bits of s, truncated: the interval only),
+                    // the polynomials in u = (s - mid) / half in double-float
                     const float sf = fminf(1.0f, fmaxf(-1.0f, df_split(s, 0).x));
                     int it = (int)(acosf(sf) * ith_scale);
                     it = min(max(it, 0), c.sM - 1);
-                    const SeriesRec* R = A.stab + it;
-                    const double2 mh = __ldg(reinterpret_cast<const double2*>(R));
-                    const double uu = (s - mh.x) * mh.y;
-                    // Horner: the tail (degree kSeriesLead .. kSeriesP) in double-float,
-                    // the leading coefficients in FP64
-                    const float2 uf = df_split(uu, 0);
-                    if (ghost || gluon) {
-                        const float4 top = __ldg(&R->et[kSeriesTail - 1]);
-                        float2 tz = make_float2(top.x, top.y), tg = make_float2(top.z, top.w);
-#pragma unroll
-                        for (int kq = kSeriesTail - 2; kq >= 0; --kq) {
-                            const float4 ck = __ldg(&R->et[kq]);
-                            tz = df_muladd(tz, uf, make_float2(ck.x, ck.y));
-                            tg = df_muladd(tg, uf, make_float2(ck.z, ck.w));
-                        }
-                        double ez = df_widen(tz.x, 1023) + df_widen(tz.y, 1023);
-                        double eg = df_widen(tg.x, 1023) + df_widen(tg.y, 1023);
-#pragma unroll
-                        for (int kq = kSeriesLead - 1; kq >= 0; --kq) {
-                            const double2 ck = __ldg(&R->e[kq]);
-                            ez = fma(ez, uu, ck.x);
-                            eg = fma(eg, uu, ck.y);
-                        }
-                        Zz = ez;
-                        Gz = eg;
-                    }
-                    if (gluon) {
-                        float2 tw = __ldg(&R->wt[kSeriesTail - 1]);
-#pragma unroll
-                        for (int kq = kSeriesTail - 2; kq >= 0; --kq) tw = df_muladd(tw, uf, __ldg(&R->wt[kq]));
-                        double ew = df_widen(tw.x, 1023) + df_widen(tw.y, 1023);
-#pragma unroll
-                        for (int kq = kSeriesLead - 1; kq >= 0; --kq) ew = fma(ew, uu, __ldg(&R->w[kq]));
-                        Wz = ew;
-                    }
+                    const SeriesRec* Rr = A.stab + it;
+                    const double2 mh = __ldg(reinterpret_cast<const double2*>(Rr));
+                    series_eval(Rr, df_split((s - mh.x) * mh.y, 0), ghost || gluon, gluon, Zz, Gz, Wz);
                 } else {
                     double lg, lzz;
                     if (A.stab) {
@@ -324,8 +798,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                             t1 = t2;
                             lg = fma(sb[j], t2, lg);
                             lzz = fma(sa[j], t2, lzz);
-                            if (FULL && AR && (j & 3) < 2) Trow[1 + (j & 1) * nq + (j >> 2)] = df_split(t2, 0);
-                            if (FULL && !AR) Trow[j] = df_split(t2, 0);
+                            if (FULL) Trow[j] = df_split(t2, 0);
                         }
                     }
                     if (outside) {
@@ -345,7 +818,7 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         Wz = exp(c.pG * lg + c.qZ * lzz);
                     }
                 }
-                if (FULL && !AR) {
+                if (FULL) {
                     const float2 fs = df_split(s, 0);
                     Trow[0] = make_float2(0.5f, 0.0f);  // T_0 enters as 1/2
                     if (N > 1) Trow[1] = fs;
@@ -379,41 +852,12 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         }
                     }
                 }
-                if (FULL && AR) {
-                    const float2 fs = df_split(s, 0);
-                    Trow[0] = make_float2(2.0f * fs.x, 2.0f * fs.y);  // 2s
-                    Trow[1] = make_float2(1.0f, 0.0f);                // T_0
-                    Trow[1 + nq] = fs;                                // T_1
-                    if (A.stab) {
-                        // T_4i and T_4i+1 (the direct path stored them above) by the
-                        // recurrence of stride 4, X_(i+1) = 2 T_4 X_i - X_(i-1) (from
-                        // T_(m+4) + T_(m-4) = 2 T_4 T_m), in double-float from T_4 and T_5
-                        // formed in FP64: the rounding errors (2^-48 per step) grow at most
-                        // like i^2 over i steps, below 2 i^2 2^-48 for |s| <= 1
-                        const double T2 = fma(2.0 * s, s, -1.0);
-                        const double T3 = fma(2.0 * s, T2, -s);
-                        const double T4 = fma(2.0 * T2, T2, -1.0);
-                        const float2 c4 = df_split(2.0 * T4, 0);
-                        float2 a0 = make_float2(1.0f, 0.0f), a1 = df_split(T4, 0);  // T_(4i-4), T_4i
-                        float2 b0 = fs, b1 = df_split(fma(2.0 * s, T4, -T3), 0);    // T_(4i-3), T_(4i+1)
-                        for (int i = 1; i < nq; ++i) {
-                            Trow[1 + i] = a1;
-                            Trow[1 + nq + i] = b1;
-                            const float2 an4 = df_mulsub(c4, a1, a0);
-                            a0 = a1;
-                            a1 = an4;
-                            const float2 bn = df_mulsub(c4, b1, b0);
-                            b0 = b1;
-                            b1 = bn;
-                        }
-                    }
-                }
-                const double Kw = f[2] * (an.w * an.s4);
+                const double Kw = f[2] * an.ws4;
                 if (ghost) hG = Kw * Zz * iz2;
                 if (gluon) {
                     const double sg = an.sig;
                     const double num = fma(sg, fma(sg, fma(sg, fma(sg, f[7], f[6]), f[5]), f[4]), f[3]);
-                    hQ = (an.w * an.s2) * iz2 * Wz * num;
+                    hQ = an.ws2 * iz2 * Wz * num;
                     hM = Kw * iz * Gz;
                 }
             }
@@ -478,23 +922,10 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
                         const float2 mm = sh2[BT + m];
                         const float2 gg = sh2[2 * BT + m];
                         const float2* Tm = sT2 + (size_t)m * ldT;
-                        const float2 s2 = AR ? Tm[0] : make_float2(0.0f, 0.0f);
 #pragma unroll
                         for (int jj = 0; jj < NJ; ++jj) {
                             if (colj[jj] < N) {
-                                float2 t;
-                                if (AR) {
-                                    const float2 a = Tm[1 + coli[jj]];
-                                    const float2 b = Tm[1 + nq + coli[jj]];
-                                    t = (colr[jj] & 1) ? b : a;
-                                    if (colr[jj] >= 2) {
-                                        const float2 t2 = df_mulsub(s2, b, a);
-                                        t = colr[jj] == 2 ? t2 : df_mulsub(s2, t2, b);
-                                    }
-                                    if (colj[jj] == 0) t = make_float2(0.5f, 0.0f);  // T_0 enters as 1/2
-                                } else {
-                                    t = Tm[colj[jj]];
-                                }
+                                const float2 t = Tm[colj[jj]];
                                 df_fma(ca[0][jj], q, t);
                                 df_fma(ca[1][jj], mm, t);
                                 df_fma(ca[2][jj], gg, t);
@@ -544,10 +975,22 @@ __device__ __forceinline__ void triple_tile(const TripleArgs& A, const int rt, c
     }
 }
 
-template <int BT, int NJ, bool FULL>
-__global__ void __launch_bounds__(BT) k_triple(const __grid_constant__ TripleArgs A) {
+// Newton-matrix mode: blocks of BT threads; with BT = 128 six blocks per SM (at
+// most 80 registers a thread)
+#ifndef DSE_TRIPLE_MIN_BLOCKS
+#define DSE_TRIPLE_MIN_BLOCKS 6
+#endif
+template <int BT>
+__global__ void __launch_bounds__(BT, BT == 128 ? DSE_TRIPLE_MIN_BLOCKS : 8) k_triple(const __grid_constant__ TripleArgs A) {
     extern __shared__ __align__(16) double smem[];
-    triple_tile<BT, NJ, FULL, kAnchorRowsSingle>(A, blockIdx.y, blockIdx.x, smem);
+    triple_tile_full<BT>(A, blockIdx.y, blockIdx.x, smem);
+}
+
+// Residual mode: blocks of BT threads
+template <int BT>
+__global__ void __launch_bounds__(BT) k_triple_res(const __grid_constant__ TripleArgs A) {
+    extern __shared__ __align__(16) double smem[];
+    triple_tile_residual<BT>(A, blockIdx.y, blockIdx.x, smem);
 }
 
 // Persistent form for a batch of independent problems: each block takes work
@@ -571,51 +1014,46 @@ __global__ void __launch_bounds__(BT) k_triple_batched(const BatchProblem* __res
         if (!P[w.b].active) continue;
         TripleArgs A = P[w.b].t;
         A.coef = coef_base + P[w.b].coef_off;
-        triple_tile<BT, NJ, FULL, kAnchorRowsBatched>(A, w.rt, w.ks, smem);
+        triple_tile_batched<BT, NJ, FULL>(A, w.rt, w.ks, smem);
     }
 }
 
-template <int BT, bool FULL>
-cudaError_t launch_bt(const TripleArgs& a, cudaStream_t s) {
-    const int N = a.c.N;
-    const size_t smem = smem_doubles(FULL, N, BT, kAnchorRowsSingle) * sizeof(double);
+template <int BT>
+cudaError_t launch_full(const TripleArgs& a, cudaStream_t s) {
+    const size_t smem = smem_full_doubles(a.c.N, BT, a.KB) * sizeof(double);
     const dim3 grid(a.KS, a.Rt);
-    const int nj = (N + BT - 1) / BT;
-    cudaError_t e = cudaSuccess;
-    if (nj <= 1) {
-        e = cudaFuncSetAttribute(k_triple<BT, 1, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_triple<BT, 1, FULL><<<grid, BT, smem, s>>>(a);
-    } else if (nj <= 2) {
-        e = cudaFuncSetAttribute(k_triple<BT, 2, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_triple<BT, 2, FULL><<<grid, BT, smem, s>>>(a);
-    } else if (nj <= 4) {
-        e = cudaFuncSetAttribute(k_triple<BT, 4, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_triple<BT, 4, FULL><<<grid, BT, smem, s>>>(a);
-    } else {
-        return cudaErrorInvalidValue;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_triple<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_triple<BT><<<grid, BT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int BT, bool FULL>
-int occupancy_bt(int N) {
-    const size_t smem = smem_doubles(FULL, N, BT, kAnchorRowsSingle) * sizeof(double);
-    const int nj = (N + BT - 1) / BT;
+template <int BT>
+cudaError_t launch_res(const TripleArgs& a, cudaStream_t s) {
+    const size_t smem = smem_res_doubles(a.c.N, a.KB) * sizeof(double);
+    const dim3 grid(a.KS, a.Rt);
+    cudaError_t e = cudaFuncSetAttribute(k_triple_res<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_triple_res<BT><<<grid, BT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// resident blocks per SM (with the radial-factor store of two nodes per block,
+// the fewest the split uses)
+template <int BT>
+int occupancy_full(int N) {
+    const size_t smem = smem_full_doubles(N, BT, 2) * sizeof(double);
     int nb = 0;
-    cudaError_t e;
-    if (nj <= 1) {
-        cudaFuncSetAttribute(k_triple<BT, 1, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple<BT, 1, FULL>, BT, smem);
-    } else if (nj <= 2) {
-        cudaFuncSetAttribute(k_triple<BT, 2, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple<BT, 2, FULL>, BT, smem);
-    } else {
-        cudaFuncSetAttribute(k_triple<BT, 4, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple<BT, 4, FULL>, BT, smem);
-    }
+    cudaFuncSetAttribute(k_triple<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple<BT>, BT, smem);
+    return e == cudaSuccess ? nb : 0;
+}
+
+int occupancy_res(int N) {
+    const size_t smem = smem_res_doubles(N, 2) * sizeof(double);
+    int nb = 0;
+    cudaFuncSetAttribute(k_triple_res<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_triple_res<128>, 128, smem);
     return e == cudaSuccess ? nb : 0;
 }
 
@@ -623,20 +1061,20 @@ int occupancy_bt(int N) {
 
 int triple_block_threads(int N) { return block_threads_for(N); }
 
-size_t triple_smem_bytes(bool full, int N) {
-    return smem_doubles(full, N, block_threads_for(N), kAnchorRowsSingle) * sizeof(double);
+size_t triple_smem_bytes(bool full, int N, int KB) {
+    return (full ? smem_full_doubles(N, block_threads_for(N), KB) : smem_res_doubles(N, KB)) * sizeof(double);
 }
 
 int triple_max_blocks_per_sm(bool full, int N) {
-    if (block_threads_for(N) == 128) return full ? occupancy_bt<128, true>(N) : occupancy_bt<128, false>(N);
-    return full ? occupancy_bt<64, true>(N) : occupancy_bt<64, false>(N);
+    if (!full) return occupancy_res(N);
+    return block_threads_for(N) == 128 ? occupancy_full<128>(N) : occupancy_full<64>(N);
 }
 
 namespace {
 template <int BT, bool FULL>
 cudaError_t launch_batched_bt(const BatchProblem* P, const BatchItem* items, int n_items, int* counter,
                               const double* coef_base, int maxN, int grid, cudaStream_t s) {
-    const size_t smem = smem_doubles(FULL, maxN, BT, kAnchorRowsBatched) * sizeof(double);
+    const size_t smem = smem_doubles(FULL, maxN, BT) * sizeof(double);
     const int nj = (maxN + BT - 1) / BT;
     // the shared-memory limit was set by triple_batched_blocks_per_sm (no attribute
     // change here: this launch may be captured into a graph)
@@ -651,7 +1089,7 @@ cudaError_t launch_batched_bt(const BatchProblem* P, const BatchItem* items, int
 
 template <int BT, bool FULL>
 int batched_occupancy_bt(int maxN) {
-    const size_t smem = smem_doubles(FULL, maxN, BT, kAnchorRowsBatched) * sizeof(double);
+    const size_t smem = smem_doubles(FULL, maxN, BT) * sizeof(double);
     const int nj = (maxN + BT - 1) / BT;
     int nb = 0;
     cudaError_t e;
@@ -687,8 +1125,8 @@ int triple_batched_blocks_per_sm(bool full, int maxN) {
 
 cudaError_t launch_triple(bool full, const TripleArgs& a, cudaStream_t s) {
     if (a.KS <= 0 || a.Rt <= 0) return cudaSuccess;
-    if (block_threads_for(a.c.N) == 128) return full ? launch_bt<128, true>(a, s) : launch_bt<128, false>(a, s);
-    return full ? launch_bt<64, true>(a, s) : launch_bt<64, false>(a, s);
+    if (!full) return launch_res<128>(a, s);
+    return block_threads_for(a.c.N) == 128 ? launch_full<128>(a, s) : launch_full<64>(a, s);
 }
 
 }  // namespace dse
