@@ -275,21 +275,26 @@ int dse_batch_counters(dse_batch* batch, long long* h_launches, long long* h_gra
  * exists for callers that cannot call cudaMalloc -- code that runs where device
  * memory is owned by another allocator (a framework's caching pool, a fixed
  * memory budget) or where the implicit device synchronisation of cudaMalloc /
- * cudaFree is not acceptable.  It computes the same F as dse_residual (Gauss-
- * Legendre rules, dressing tables, quadrature kernel, contraction, assembly),
- * but needs no plan: every intermediate buffer is carved out of one static
- * device array of DSE_STATIC_SCRATCH_BYTES compiled into the library, which
- * every GPU that loads the library holds until the process exits.
+ * cudaFree is not acceptable.  For radial_mode 0 and precision 0 it computes the
+ * same F as dse_residual (Gauss-Legendre rules, dressing tables, quadrature
+ * kernel, contraction, assembly; the dressing series summed per triple, without
+ * the plan's series table), but needs no plan: every intermediate buffer is carved
+ * out of one static device array of DSE_STATIC_SCRATCH_BYTES compiled into the
+ * library, which every GPU that loads the library holds until the process exits.
  *  - d_coeffs (n) and d_F (n) are caller-owned device buffers; cuda_stream is
  *    a cudaStream_t (NULL = legacy default stream).  Queued without waiting.
- *  - Returns DSE_ERR_ARG for bad arguments and when the problem needs more than
- *    DSE_STATIC_SCRATCH_BYTES of scratch (about 14 MB for N = 128 with
- *    512 x 256 nodes; the size grows with max(N_Z, N_G) x n_radial x n_angular / 32);
- *    nothing is queued then.  Non-finite values are not reported: they appear
- *    in d_F.
- *  - It calls no cudaMalloc, cudaFree or other allocating routine.  The first
- *    call on each device looks up the array's device address (once per device,
- *    with that device current); make that first call before any stream capture.
+ *  - Returns DSE_ERR_UNSUPPORTED for radial_mode != 0 or precision != 0,
+ *    DSE_ERR_ARG for bad arguments and when the problem needs more than
+ *    DSE_STATIC_SCRATCH_BYTES of scratch; nothing is queued then.  The largest
+ *    part is the angular sums, (R_c + 2) x n_radial x ceil(n_angular/32) x 3
+ *    doubles with R_c = N for N_Z = N_G and R_c = N_Z + N_G otherwise (about
+ *    12 MB for N = 128 with 512 x 256 nodes; N_Z = 128, N_G = 96 at that size
+ *    needs about 22 MB and is rejected).  Non-finite values are not reported:
+ *    they appear in d_F.
+ *  - It calls no cudaMalloc, cudaFree or other allocating routine.  Every call
+ *    looks up the array's device address on the current device (a host-side
+ *    lookup); the first call on a device also loads the library's device code
+ *    there, so make that first call before any stream capture.
  *  - All calls share the one array and it keeps the previous call's contents:
  *    calls that overlap on the GPU (different streams, or different host
  *    threads on the same device) race on it and must be serialised by the

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libdse_gb300.so")
 SOURCES = ["dse_triple.cu", "dse_triple32.cu", "dse_kernels.cu", "dse_plan.cu", "dse_noalloc.cu", "dse_adjoint.cu", "dse_batch.cu",
-           "dse_peaks.cu"]
+           "dse_peaks.cu", "dse_lu32.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

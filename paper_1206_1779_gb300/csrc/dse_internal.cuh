@@ -146,6 +146,11 @@ struct BatchProblem {
 // One work item of the persistent quadrature kernel.
 struct BatchItem { int b, rt, ks, pad; };
 
+// Argument checks of a dse_problem (DSE_OK, DSE_ERR_ARG or DSE_ERR_UNSUPPORTED) and
+// its derived constants (dse_plan.cu).
+int check_problem(const dse_problem* p);
+Consts make_consts(const dse_problem* p);
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_gauss_legendre(int n, double* inv, double* x, double* w, cudaStream_t s);
 cudaError_t launch_setup_rules(const Consts& c, const double* gl_r, const double* gw_r,
@@ -167,14 +172,20 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
                              const double* Upart, const double* Vpart, double* D, cudaStream_t s);
 cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix,
                             const double* D, double* J, double* F, int* status, cudaStream_t s);
-// Newton step: J Delta = F, c <- c - rho Delta (n = NZ + NG).  As (n*n floats)
+// Newton step: J Delta = F, c <- c - rho Delta (n = NZ + NG).  For n > 160 with
+// done given (an int on the device): the FP32 LU + FP64 refinement of dse_lu32.cu,
+// and the FP64 LU only where that one did not converge (*done = 0).  As (n*n floats)
 // and rowinfo (n double2) are scratch for the row-scaled FP32 copy of J.  For
 // n <= 128, Xinv (n*n floats), Sinv (n doubles) and *xstate keep the inverse of
 // an eliminated step for the next one (all three nullptr: no reuse).
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab,
                              double* coef, double rho, double* work, float* As, double2* rowinfo,
                              double* stats, int* status, cudaStream_t s, float* Xinv = nullptr,
-                             double* Sinv = nullptr, int* xstate = nullptr);
+                             double* Sinv = nullptr, int* xstate = nullptr, int* done = nullptr);
+size_t newton_lu32_smem_bytes(int n);
+cudaError_t launch_newton_lu32(const Consts& c, const double* J, float* As, const double2* rowinfo, const double* F,
+                               const XTab* xtab, double* coef, double rho, double* stats, int* status, int* done,
+                               cudaStream_t s);
 cudaError_t launch_dressing(const Consts& c, const double* coef, int n, const double* x, double* lG,
                             double* lZ, int* status, cudaStream_t s);
 cudaError_t launch_schwinger_map(const Consts& c, int n, const double* gx, const double* gw, double* pn,

@@ -698,7 +698,10 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_newton(const Consts c, double
                                                           const double* __restrict__ F,
                                                           const XTab* __restrict__ xtab, double* __restrict__ coef,
                                                           double rho, double* __restrict__ work,
-                                                          double* __restrict__ stats, int* __restrict__ status) {
+                                                          double* __restrict__ stats, int* __restrict__ status,
+                                                          const int* __restrict__ done) {
+    // the FP32 LU path already took the step (dse_lu32.cu)
+    if (done && *done) return;
     __shared__ double sv[kLuThreads / 32];
     __shared__ int si[kLuThreads / 32];
     __shared__ int s_piv;
@@ -2089,7 +2092,7 @@ cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const 
 
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
                              double* work, float* As, double2* rowinfo, double* stats, int* status, cudaStream_t s,
-                             float* Xinv, double* Sinv, int* xstate) {
+                             float* Xinv, double* Sinv, int* xstate, int* done) {
     if (!Xinv || !Sinv || !xstate) Xinv = nullptr, Sinv = nullptr, xstate = nullptr;
     const int n = c.n;
     cudaError_t e = cudaSuccess;
@@ -2117,7 +2120,15 @@ cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const 
         if (e != cudaSuccess) return e;
         k_newton_mixed<<<1, kGjThreads, smem, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
     } else {
-        k_lu_newton<<<1, kLuThreads, 0, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
+        if (done && n <= 2 * DSE_MAX_CHEB) {
+            k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = launch_newton_lu32(c, J, As, rowinfo, F, xtab, coef, rho, stats, status, done, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            done = nullptr;
+        }
+        k_lu_newton<<<1, kLuThreads, 0, s>>>(c, J, F, xtab, coef, rho, work, stats, status, done);
     }
     return cudaGetLastError();
 }

@@ -7,8 +7,6 @@
 // The kernels are the same as those of dse_residual.
 #include <math.h>
 
-#include <mutex>
-
 #include "dse_internal.cuh"
 
 using namespace dse;
@@ -19,27 +17,16 @@ namespace {
 // every GPU that loads the library holds these bytes until the process exits.
 static __device__ __align__(256) unsigned char g_dse_static_scratch[DSE_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device.  The host-side
-// name g_dse_static_scratch is only a stand-in, not a device address: it is
-// resolved once per device with cudaGetSymbolAddress while that device is
-// current.
+// Device address of the scratch array on the current device.  The host-side name
+// g_dse_static_scratch is only a stand-in, not a device address: it is looked up
+// with cudaGetSymbolAddress, with the device current, on every call (a host-side
+// lookup that allocates nothing), so that an address never outlives the context it
+// belongs to.  The first call on a device also loads the library's device code there.
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_dse_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_dse_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -76,52 +63,13 @@ Layout layout(const Consts& c, int Rt, int nch) {
 extern "C" int dse_residual_static(const dse_problem* problem, const double* d_coeffs, double* d_F,
                                    void* cuda_stream) {
     if (!problem || !d_coeffs || !d_F) return DSE_ERR_ARG;
+    const int st = check_problem(problem);
+    if (st != DSE_OK) return st;
     const dse_problem* p = problem;
-    if (p->n_cheb < 1 || p->n_cheb > DSE_MAX_CHEB || p->n_cheb_G < 0 || p->n_cheb_G > DSE_MAX_CHEB ||
-        p->n_radial < 1 || p->n_radial > DSE_MAX_NODES ||
-        p->n_angular < 1 || p->n_angular > DSE_MAX_NODES)
-        return DSE_ERR_ARG;
-    if (!(p->eps2 > 0.0) || !(p->lambda2 > p->eps2) || !isfinite(p->lambda2) || !(p->x_Z > 0.0) ||
-        !isfinite(p->x_Z) || !(p->x_G >= 0.0) || !isfinite(p->x_G) || !isfinite(p->g2nc) || !isfinite(p->kappa) ||
-        !isfinite(p->delta) || !isfinite(p->ginv_G) || !isfinite(p->zinv_Z))
-        return DSE_ERR_ARG;
-    if (p->radial_mode != 0 || p->precision != 0 || (p->extrap_mode != 0 && p->extrap_mode != 1) ||
-        (p->angular_mode != 0 && p->angular_mode != 1))
-        return DSE_ERR_UNSUPPORTED;
-
-    const double kPi = 3.14159265358979323846264338327950288;
-    Consts c;
-    c.NZ = p->n_cheb;
-    c.NG = p->n_cheb_G > 0 ? p->n_cheb_G : p->n_cheb;
-    c.N = c.NZ > c.NG ? c.NZ : c.NG;
-    c.n = c.NZ + c.NG;
-    c.Rc = c.NZ == c.NG ? c.N : c.n;
-    c.gofs = c.NZ == c.NG ? 0 : c.NZ;
-    c.nr = p->n_radial;
-    c.nrule = p->n_radial;
-    c.radmode = 0;
-    c.angmode = p->angular_mode;
-    c.sM = 0;  // no series table here
-    c.na = p->n_angular;
-    c.extrap = p->extrap_mode;
-    c.eps2 = p->eps2;
-    c.lam2 = p->lambda2;
-    c.ln_eps2 = log(p->eps2);
-    c.ln_lam2 = log(p->lambda2);
-    c.L0 = 0.5 * (c.ln_eps2 + c.ln_lam2);
-    c.L1 = 0.5 * (c.ln_lam2 - c.ln_eps2);
-    c.invL1 = 1.0 / c.L1;
-    c.K = p->g2nc / (8.0 * kPi * kPi * kPi);
-    c.kappa = p->kappa;
-    c.delta = p->delta;
-    c.gam = -1.0 - 2.0 * p->delta;
-    c.pG = -2.0 - 6.0 * p->delta;
-    c.qZ = -3.0 * p->delta;
-    c.omega = 11.0 * p->g2nc / (48.0 * kPi * kPi);
-    c.x_G = p->x_G;
-    c.x_Z = p->x_Z;
-    c.ginv_G = p->ginv_G;
-    c.zinv_Z = p->zinv_Z;
+    // the plan's single radial rule and the FP64 kernels only
+    if (p->radial_mode != 0 || p->precision != 0) return DSE_ERR_UNSUPPORTED;
+    Consts c = make_consts(p);
+    c.sM = 0;  // no series table here: the dressing series are summed per triple
 
     const int nr = c.nr, na = c.na;
     const int Rt = c.Rc + 1 + (p->x_G > 0.0 ? 1 : 0);
@@ -152,12 +100,20 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
     int* status = (int*)(b + L.status);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    // radial splits: about three blocks per SM of 152
-    int KS = (3 * 152 + Rt - 1) / Rt;
-    if (KS > nr) KS = nr;
-    if (KS < 1) KS = 1;
-    const int KB = (nr + KS - 1) / KS;
-    KS = (nr + KB - 1) / KB;
+    // radial splits: about eight waves of blocks over the resident slots (the rule
+    // of the plans); the queries allocate nothing
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+        return DSE_ERR_CUDA;
+    int occ = triple_max_blocks_per_sm(false, c.N);
+    if (occ < 1) occ = 1;
+    long long kb = ((long long)nr * Rt) / (8LL * nsm * occ);
+    if (kb < 2) kb = 2;
+    if (kb > nr) kb = nr;
+    while ((nr + kb - 1) / kb > 128) ++kb;
+    const int KB = (int)kb;
+    const int KS = (int)((nr + kb - 1) / kb);
 
     // only the status word must start at zero; every other buffer is written
     // in full before it is read

@@ -42,6 +42,7 @@ struct dse_plan {
     float* Xinv;        // FP32 inverse of the last eliminated Newton step, reused while it suffices
     double* Sinv;       // its row scales
     int* xstate;        // 1 while Xinv is usable, then 2 counters: eliminations, reuses (after the status word)
+    int* lu_done;       // 1 when the FP32 LU path took the Newton step (n > 160)
     double* aux;        // derivative scratch: dPi rows, dressing-VJP partial sums
     // finite-difference Newton matrix: a batch of 2n copies of the problem
     dse_batch* fd_batch;
@@ -62,12 +63,9 @@ struct dse_plan {
     cudaEvent_t ev[2 * 4096];
 };
 
-namespace {
+namespace dse {
 
-constexpr double kPi = 3.14159265358979323846264338327950288;
-
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? DSE_OK : DSE_ERR_CUDA; }
-
+// Argument checks shared by every entry point that takes a dse_problem.
 int check_problem(const dse_problem* p) {
     if (!p) return DSE_ERR_ARG;
     if (p->n_cheb < 1 || p->n_cheb > DSE_MAX_CHEB) return DSE_ERR_ARG;
@@ -86,7 +84,9 @@ int check_problem(const dse_problem* p) {
     return DSE_OK;
 }
 
+// Derived constants of Sec. 2 / Sec. 3 (the series table's interval count from N).
 Consts make_consts(const dse_problem* p) {
+    constexpr double kPi = 3.14159265358979323846264338327950288;
     Consts c;
     c.NZ = p->n_cheb;
     c.NG = p->n_cheb_G > 0 ? p->n_cheb_G : p->n_cheb;
@@ -121,6 +121,14 @@ Consts make_consts(const dse_problem* p) {
     c.zinv_Z = p->zinv_Z;
     return c;
 }
+
+}  // namespace dse
+
+namespace {
+
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? DSE_OK : DSE_ERR_CUDA; }
+
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -331,7 +339,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     const size_t n_aux_a = 2 * (size_t)(Rc + 2) + (size_t)n + 3;
     const size_t n_aux_b = (size_t)kDressingVjpMaxSplits * ((size_t)n + 1);
     size_t o_aux = off; off = align_up(off + sizeof(double) * (n_aux_a > n_aux_b ? n_aux_a : n_aux_b));
-    size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + 4 * sizeof(int));
+    size_t o_misc = off; off = align_up(off + 4 * sizeof(double) + 8 * sizeof(int));
     // Gauss-Legendre scratch (set-up only): nodes/weights for both rules and 1/k
     size_t o_gl = off; off = align_up(off + sizeof(double) * (2 * (size_t)nrule + 2 * (size_t)na + gmax + 2));
 
@@ -365,6 +373,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->stats = (double*)(base + o_misc);
     pl->status = (int*)(base + o_misc + 4 * sizeof(double));
     pl->xstate = pl->status + 1;
+    pl->lu_done = pl->status + 4;
     double* gl = (double*)(base + o_gl);
     double* glr = gl;
     double* gwr = glr + nrule;
@@ -455,8 +464,8 @@ int newton_step_impl(dse_plan* plan, double* d_coeffs, double rho, double* h_sta
     if (st) return st;
     cudaError_t e = launch_lu_newton(plan->c, plan->J, plan->F, plan->xtab, d_coeffs, rho, plan->work, plan->As,
                                      plan->rowinfo, plan->stats, plan->status, plan->stream, plan->Xinv, plan->Sinv,
-                                     plan->xstate);
-    plan->launches += plan->c.n <= 128 ? 2 : 1;
+                                     plan->xstate, plan->lu_done);
+    plan->launches += plan->c.n <= 128 ? 2 : plan->c.n <= 160 ? 1 : 3;
     if (e != cudaSuccess) return DSE_ERR_CUDA;
     return read_status(plan, h_stats);
 }

@@ -1,58 +1,99 @@
-// dse_triple32.cu -- FP32-integrand variant of the quadrature kernel for the
-// mixed-precision mode (precision = 1).
+// dse_triple32.cu -- the quadrature kernel of the mixed-precision Newton matrix
+// (precision = 1).
 //
-// Same data flow and outputs as k_triple in dse_triple.cu (Upart, Vpart in
-// FP64, identical layouts), but every per-triple quantity -- z, s(z), T_j(s),
-// ln G(z), ln Z(z), the exponentials, the kernels M and Q and the three
-// integrands -- is evaluated in FP32, where this GPU has 64 times the FP64
-// rate.  Accumulation is blocked: 32-term warp sums and BT-term tile sums in
-// FP32, everything beyond a tile in FP64.  T_j(s) uses the forward recurrence
-// rewritten in differences, D_{j+1} = sgn(s) (D_j - 2 (1 - |s|) T_j),
-// T_{j+1} = sgn(s) T_j + D_{j+1}, whose rounding errors grow like j rather than
-// j^2 near s = +-1.  The Jacobian built from these sums carries relative errors
-// of ~1e-6; the mixed-precision Newton iteration pairs it with an FP64 residual.
+// Same outputs and layouts as the FP64 kernel of dse_triple.cu (Upart, Vpart in
+// FP64), with the precision split of the mixed-precision Newton matrix:
+//   FP64: the Chebyshev log-momentum map s(z) = (ln z - L0)/L1 (z, ln z and the
+//         distance 1 - |s| to the ends of the interval, which the FP32 recurrence
+//         for T_j needs to full relative accuracy); the exponentials of the
+//         dressing-function series, taken at the nodes of the series table (the
+//         kernel interpolates Z, G and W = G^p Z^q from it) and, for z outside
+//         [eps2, lambda2], per triple; the angular and radial sums beyond one
+//         block of triples (Upart, Vpart, and their FP64 contraction after it).
+//   FP32: 1/z, the table polynomials, the kernels M and Q and the three
+//         integrands, T_j(s) by the forward recurrence in differences,
+//           D_(j+1) = sgn(s) (D_j - 2 (1 - |s|) T_j),  T_(j+1) = sgn(s) T_j + D_(j+1),
+//         whose rounding errors grow like j rather than j^2 near s = +-1, and the
+//         products weight * T_j;
+//   compensated (two-sum) block accumulation: each thread adds its products over
+//   blocks of 8 triples in FP32 and joins each block sum to a compensated pair
+//   (sum, error) by Knuth's two-sum, which is widened to FP64 at the end.
+// The Jacobian built from these sums carries relative errors of about 1e-7 of the
+// entries' magnitude sums; the mixed-precision Newton iteration pairs it with an
+// FP64 residual near convergence (an inexact Newton method whose fixed point is
+// the FP64 solution).
+//
+// Tile layout: one block of BT threads per (row, radial split) walks its radial
+// nodes in tiles of BT triples (one warp = 32 angular nodes of one radial node).
+// Shared-memory row of triple m (float4 units, stride rs4 = quad count + 1 made
+// odd): [0] (hQ, hM, hG, 0), [1 + i] (T_4i .. T_4i+3) with T_0 stored as 1/2.
+// Thread (group g, quad i) then sums the twelve products of its four columns over
+// the rows of group g.
 #include "dse_internal.cuh"
+#include "dse_lnrcp.cuh"
 
 namespace dse {
 
 namespace {
 
-constexpr unsigned kFullMask = 0xffffffffu;
+constexpr unsigned kFullMask32 = 0xffffffffu;
+constexpr double kPi32 = 3.14159265358979323846264338327950288;
 
-__host__ __device__ inline int bt32_for(int N) { return N <= 96 ? 128 : 64; }
+__host__ __device__ inline int bt32_for(int N) { return N <= 128 ? 128 : 64; }
+__host__ __device__ inline int quads32(int N) { return (N + 3) / 4; }
+__host__ __device__ inline int stride32(int N) { return (quads32(N) + 1) | 1; }
 
-__host__ __device__ inline size_t tile32_floats(bool full, int N, int BT) {
-    if (!full) return 0;
-    const size_t t = (size_t)BT * (size_t)(N + 1);
-    const int nact = N < BT ? N : BT;
-    const size_t red = 2u * (size_t)(BT / nact) * 3u * (size_t)N;  // doubles as float pairs
-    return t > red ? t : red;
+// radial-node factors: d, 4 sqrt(xy) (FP64, for z), K = W_k y G(y) and the five
+// quartic coefficients of the gluon-loop kernel times W_k W(y)/2 (FP32)
+constexpr int kRadGroup32 = 32;
+struct RadF32 { double d, b2; float K, q0, q1, q2, q3, q4, pad0, pad1; };
+
+__host__ __device__ inline size_t smem32_bytes(int N, int BT, int KB) {
+    const int kg = KB < kRadGroup32 ? KB : kRadGroup32;
+    const size_t tile = (size_t)BT * stride32(N) * sizeof(float4);
+    const size_t red = (size_t)(BT / quads32(N)) * 3u * (size_t)N * sizeof(double2);
+    return (tile > red ? tile : red) + 2u * (size_t)N * sizeof(float) + 4u * sizeof(double) +
+           (size_t)kg * sizeof(RadF32);
 }
 
-__host__ __device__ inline size_t smem32_bytes(bool full, int N, int BT) {
-    return tile32_floats(full, N, BT) * sizeof(float) + 3u * BT * sizeof(float) + 2u * N * sizeof(float);
+// 2^d as FP32 (0 below the normal range, Inf above it)
+__device__ __forceinline__ float pow2f32(int d) {
+    return d < -126 ? 0.0f : d > 127 ? __int_as_float(0x7f800000) : __int_as_float((127 + d) << 23);
 }
 
-template <int BT, int NJ, bool FULL>
+// c += t in the compensated pair (c.x the sum, c.y the accumulated rounding errors)
+__device__ __forceinline__ void two_sum_acc(float2& c, const float t) {
+    const float s = c.x + t;
+    const float bb = s - c.x;
+    c.y += (c.x - (s - bb)) + (t - bb);
+    c.x = s;
+}
+
+template <int BT>
 __global__ void __launch_bounds__(BT) k_triple32(const __grid_constant__ TripleArgs A) {
-    extern __shared__ __align__(16) float smem32[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Consts& c = A.c;
     const int N = c.N;
-    const int ldT = N + 1;
-    float* sT = smem32;
-    float* sh = smem32 + tile32_floats(FULL, N, BT);
-    float* sa = sh + 3 * BT;
-    float* sb = sa + N;
+    const int nq = quads32(N);
+    const int rs4 = stride32(N);
     constexpr int WARPS = BT / 32;
+    float4* sT = reinterpret_cast<float4*>(smem_raw);
+    const size_t tile_bytes = (size_t)BT * rs4 * sizeof(float4);
+    const size_t red_bytes = (size_t)(BT / nq) * 3u * (size_t)N * sizeof(double2);
+    float* sa = reinterpret_cast<float*>(smem_raw + (tile_bytes > red_bytes ? tile_bytes : red_bytes));
+    float* sb = sa + N;
+    double* sbnd = reinterpret_cast<double*>(sb + N);  // (2 N floats: 8-byte aligned)
+    RadF32* srad = reinterpret_cast<RadF32*>(sbnd + 4);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
 
-    // a (NZ) and b (NG) zero-padded to N = max(NZ, NG): one recurrence serves both series
+    // the series' coefficients (for N below the table's range), zero-padded to N
     for (int j = tid; j < N; j += BT) {
         sa[j] = j < c.NZ ? (float)A.coef[j] : 0.0f;
         sb[j] = j < c.NG ? (float)A.coef[c.NZ + j] : 0.0f;
     }
+    if (A.stab && tid < 4) sbnd[tid] = reinterpret_cast<const double*>(A.stab + kSeriesM)[tid];
     const int rt = blockIdx.y;
     const int ks = blockIdx.x;
     const Row row = A.rows[rt];
@@ -62,31 +103,53 @@ __global__ void __launch_bounds__(BT) k_triple32(const __grid_constant__ TripleA
     const int k1 = min(c.nr, k0 + A.KB);
     const int nch = A.nch;
     const int nunits = k1 > k0 ? (k1 - k0) * nch : 0;
-    const float L0 = (float)c.L0, invL1 = (float)c.invL1;
-    const float eps2 = (float)c.eps2, lam2 = (float)c.lam2;
-    const float ln_eps2 = (float)c.ln_eps2, ln_lam2 = (float)c.ln_lam2;
-    const float kappa = (float)c.kappa, delta = (float)c.delta, gam = (float)c.gam;
-    const float pG = (float)c.pG, qZ = (float)c.qZ, omega = (float)c.omega;
-    const float sx = (float)row.sx;
+    const int kgrp = A.KB < kRadGroup32 ? A.KB : kRadGroup32;
+    const float ith_scale = (float)c.sM * (float)(1.0 / kPi32);
 
-    const int nact = N < BT ? N : BT;
-    const int NG = BT / nact;
-    const int g = tid / nact;
-    const int jb = tid - g * nact;
-    const bool bact = g < NG;
-    const int mlo = (g * BT) / NG;
-    const int mhi = ((g + 1) * BT) / NG;
-
-    double acc[3][NJ];
+    // phase-B mapping: G groups of nq threads, rows [g R, (g + 1) R)
+    const int G = BT / nq;
+    const int R = (BT + G - 1) / G;
+    const int g = tid / nq;
+    const int qi = tid - g * nq;
+    const bool bact = g < G;
+    const int mlo = min(BT, g * R);
+    const int mhi = min(BT, mlo + R);
+    float2 acc[3][4];  // compensated pairs (sum, error)
 #pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) acc[0][jj] = acc[1][jj] = acc[2][jj] = 0.0;
+    for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[kd][q] = make_float2(0.0f, 0.0f);
 
-    __syncthreads();
-
+    const int group_units = kgrp * nch;
     for (int base = 0; base < nunits; base += WARPS) {
+        if (base % group_units == 0) {
+            __syncthreads();  // the previous group's factors are no longer read (and the coefficients staged)
+            const int kq = k0 + base / nch + lane;
+            if (warp == 0 && lane < kgrp && kq < k1) {
+                const Rad rd = A.rad[rad_offset(c, rt) + kq];
+                const YTab yt = A.ytab[rad_offset(c, rt) + kq];
+                const double d0 = row.sx - rd.sy;
+                const double d = d0 * d0;
+                const double b = 2.0 * row.sx * rd.sy;
+                const double dd = d * d, db = d * b, bb = b * b;
+                const double h = 0.5 * rd.W * yt.Wy;
+                RadF32 f;
+                f.d = d;
+                f.b2 = 2.0 * b;
+                f.K = (float)(rd.W * yt.yG);
+                f.q0 = (float)(h * (7.5 * dd));
+                f.q1 = (float)(h * -(48.0 * dd + 18.0 * db + 12.0 * bb));
+                f.q2 = (float)(h * (48.0 * dd - 48.0 * db - 38.0 * bb));
+                f.q3 = (float)(h * (96.0 * db + 64.0 * bb));
+                f.q4 = (float)(h * (16.0 * bb));
+                f.pad0 = f.pad1 = 0.0f;
+                srad[lane] = f;
+            }
+            __syncthreads();
+        }
         const int u = base + warp;
         float hQ = 0.0f, hM = 0.0f, hG = 0.0f;
-        float* Trow = sT + (size_t)tid * ldT;
+        float4* Trow = sT + (size_t)tid * rs4;
         bool live = false;
         int k = 0, ch = 0;
         if (u < nunits) {
@@ -96,181 +159,220 @@ __global__ void __launch_bounds__(BT) k_triple32(const __grid_constant__ TripleA
             const int l = ch * 32 + lane;
             if (l < c.na) {
                 live = true;
-                const Rad rd = A.rad[rad_offset(c, rt) + k];
-                const YTab yt = A.ytab[rad_offset(c, rt) + k];
+                const RadF32& f = srad[kk % kgrp];
                 const Ang an = A.ang[l];
-                const float sy = (float)rd.sy;
-                const float sig = (float)an.sig;
-                const float d0 = sx - sy;
-                const float d = d0 * d0;
-                const float b = 2.0f * sx * sy;
-                const float z = fmaf(2.0f * b, sig, d);
-                const float lz = logf(z);
-                float s = (lz - L0) * invL1;
-                s = fminf(1.0f, fmaxf(-1.0f, s));
-                // T_0 = 1 (phi_0 = 1/2), T_1 = s, then the difference form
-                float lg = 0.5f * sb[0];
-                float lzz = 0.5f * sa[0];
-                if (FULL) Trow[0] = 0.5f;
-                if (N > 1) {
-                    lg = fmaf(sb[1], s, lg);
-                    lzz = fmaf(sa[1], s, lzz);
-                    if (FULL) Trow[1] = s;
-                }
-                const float sg = s < 0.0f ? -1.0f : 1.0f;
-                const float m2d = -2.0f * (1.0f - fabsf(s));
-                float T = s;
-                float D = s - sg;
-                for (int j = 2; j < N; ++j) {
-                    D = sg * fmaf(m2d, T, D);
-                    T = fmaf(sg, T, D);
-                    lg = fmaf(sb[j], T, lg);
-                    lzz = fmaf(sa[j], T, lzz);
-                    if (FULL) Trow[j] = T;
-                }
-                if (c.extrap == 0) {
-                    if (z < eps2) {
-                        const float r = lz - ln_eps2;
-                        lg = fmaf(-kappa, r, lg);
-                        lzz = fmaf(2.0f * kappa, r, lzz);
-                    } else if (z > lam2) {
-                        const float L = log1pf(omega * (lz - ln_lam2));
-                        lg = fmaf(delta, L, lg);
-                        lzz = fmaf(gam, L, lzz);
+                // the map in FP64: z, ln z, s and 1 - |s|
+                const double z = fma(f.b2, an.sig, f.d);
+                const LnRcp lr = ln_rcp(z);
+                double sd = (lr.ln - c.L0) * c.invL1;
+                const long long zb = __double_as_longlong(z);
+                const bool beyond = zb < __double_as_longlong(c.eps2) || zb > __double_as_longlong(c.lam2);
+                const bool outside = c.extrap == 0 && beyond;
+                if (beyond) sd = fmin(1.0, fmax(-1.0, sd));
+                const float s = (float)sd;
+                const float m2d = (float)(-2.0 * (1.0 - fabs(sd)));  // -2 (1 - |s|), relative accuracy
+                const float sg = sd < 0.0 ? -1.0f : 1.0f;
+                // T_j(s) by the recurrence in differences, written to the row as quads
+                // (T_0 as 1/2); for N below the table's range the series as well
+                const bool series = A.stab == nullptr;
+                float lg = 0.0f, lzz = 0.0f;
+                if (series) {
+                    lg = 0.5f * sb[0];
+                    lzz = 0.5f * sa[0];
+                    if (N > 1) {
+                        lg = fmaf(sb[1], s, lg);
+                        lzz = fmaf(sa[1], s, lzz);
                     }
                 }
-                const float wgt = (float)(rd.W * an.w);
-                const float iz = 1.0f / z;
-                const float iz2 = iz * iz;
-                const float s2 = (float)an.s2;
-                if (ghost) {
-                    const float Zz = expf(lzz);
-                    hG = wgt * (float)yt.yG * (float)an.s4 * Zz * iz2;
+                {
+                    float T = s;        // T_1
+                    float D = s - sg;   // D_1 = T_1 - sgn(s) T_0
+                    float4 qv = make_float4(0.5f, s, 0.0f, 0.0f);
+                    for (int j = 2; j < 4 * nq; ++j) {
+                        D = sg * fmaf(m2d, T, D);
+                        T = fmaf(sg, T, D);
+                        if (series && j < N) {
+                            lg = fmaf(sb[j], T, lg);
+                            lzz = fmaf(sa[j], T, lzz);
+                        }
+                        const float tv = j < N ? T : 0.0f;
+                        if ((j & 3) == 2) qv.z = tv;
+                        else if ((j & 3) == 3) {
+                            qv.w = tv;
+                            Trow[1 + (j >> 2)] = qv;
+                        } else if ((j & 3) == 0) qv.x = tv;
+                        else qv.y = tv;
+                    }
                 }
-                if (gluon) {
-                    const float Gz = expf(lg);
-                    const float Wv = expf((float)yt.pq + pG * lg + qZ * lzz);
-                    const float dd = d * d, db = d * b, bb = b * b;
-                    const float n0 = 7.5f * dd;
-                    const float n1 = -(48.0f * dd + 18.0f * db + 12.0f * bb);
-                    const float n2 = 48.0f * dd - 48.0f * db - 38.0f * bb;
-                    const float n3 = 96.0f * db + 64.0f * bb;
-                    const float n4 = 16.0f * bb;
-                    const float num = fmaf(sig, fmaf(sig, fmaf(sig, fmaf(sig, n4, n3), n2), n1), n0);
-                    const float Q = 0.5f * num * iz2;
-                    const float M = (float)rd.y * s2 * iz;
-                    hQ = wgt * s2 * Q * Wv;
-                    hM = wgt * s2 * M * (float)yt.G * Gz;
-                }
-            }
-        }
-        if (FULL && !live) {
-            for (int j = 0; j < N; ++j) Trow[j] = 0.0f;
-        }
-        float rQ = hQ, rM = hM, rG = hG;
+                // the dressing functions at z
+                float Zz = 0.0f, Gz = 0.0f, Wz = 0.0f;
+                if (A.stab && !outside) {
+                    // from the series table, built from FP64 exponentials at its nodes:
+                    // the polynomials' leading parts in FP32, scaled by the records'
+                    // exponents
+                    const float sf = fminf(1.0f, fmaxf(-1.0f, s));
+                    int it = (int)(acosf(sf) * ith_scale);
+                    it = min(max(it, 0), c.sM - 1);
+                    const SeriesRec* Rr = A.stab + it;
+                    const double2 mh = __ldg(reinterpret_cast<const double2*>(Rr));
+                    const float uu = (float)((sd - mh.x) * mh.y);
+                    const int4 ex = __ldg(reinterpret_cast<const int4*>(Rr->ex));
+                    if (ghost || gluon) {
+                        const float4 top = __ldg(&Rr->e[kSeriesP]);
+                        float tz = top.x, tg = top.z;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            rQ += __shfl_xor_sync(kFullMask, rQ, off);
-            rM += __shfl_xor_sync(kFullMask, rM, off);
-            rG += __shfl_xor_sync(kFullMask, rG, off);
-        }
-        if (u < nunits && lane == 0) {
-            double* up = A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3;
-            up[0] = (double)rQ;
-            up[1] = (double)rM;
-            up[2] = (double)rG;
-        }
-        if (FULL) {
-            sh[tid] = hQ;
-            sh[BT + tid] = hM;
-            sh[2 * BT + tid] = hG;
-            __syncthreads();
-            if (bact) {
-                float t0[NJ], t1[NJ], t2[NJ];
+                        for (int q = kSeriesP - 1; q >= 0; --q) {
+                            const float4 ck = __ldg(&Rr->e[q]);
+                            tz = fmaf(tz, uu, ck.x);
+                            tg = fmaf(tg, uu, ck.z);
+                        }
+                        Zz = tz * pow2f32(ex.x - 1023);
+                        Gz = tg * pow2f32(ex.y - 1023);
+                    }
+                    if (gluon) {
+                        float tw = __ldg(&Rr->w[kSeriesP]).x;
 #pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) t0[jj] = t1[jj] = t2[jj] = 0.0f;
-                for (int m = mlo; m < mhi; ++m) {
-                    const float q = sh[m];
-                    const float mm = sh[BT + m];
-                    const float gg = sh[2 * BT + m];
-                    const float* Tm = sT + (size_t)m * ldT;
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) {
-                        const int j = jb + jj * nact;
-                        if (j < N) {
-                            const float t = Tm[j];
-                            t0[jj] = fmaf(q, t, t0[jj]);
-                            t1[jj] = fmaf(mm, t, t1[jj]);
-                            t2[jj] = fmaf(gg, t, t2[jj]);
+                        for (int q = kSeriesP - 1; q >= 0; --q) tw = fmaf(tw, uu, __ldg(&Rr->w[q]).x);
+                        Wz = tw * pow2f32(ex.z - 1023);
+                    }
+                } else {
+                    // outside [eps2, lambda2] (or no table): the series' values in FP64,
+                    // the IR/UV forms and the exponentials in FP64
+                    double lgd, lzd;
+                    if (A.stab) {
+                        lzd = sd > 0.0 ? sbnd[0] : sbnd[2];
+                        lgd = sd > 0.0 ? sbnd[1] : sbnd[3];
+                    } else {
+                        lgd = lg;
+                        lzd = lzz;
+                    }
+                    if (outside) {
+                        if (z < c.eps2) {
+                            const double r = lr.ln - c.ln_eps2;
+                            lgd = fma(-c.kappa, r, lgd);
+                            lzd = fma(2.0 * c.kappa, r, lzd);
+                        } else {
+                            const double L = log1p(c.omega * (lr.ln - c.ln_lam2));
+                            lgd = fma(c.delta, L, lgd);
+                            lzd = fma(c.gam, L, lzd);
                         }
                     }
+                    if (ghost) Zz = (float)exp(lzd);
+                    if (gluon) {
+                        Gz = (float)exp(lgd);
+                        Wz = (float)exp(c.pG * lgd + c.qZ * lzd);
+                    }
                 }
-                // tile sums join the FP64 accumulators
-#pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) {
-                    acc[0][jj] += (double)t0[jj];
-                    acc[1][jj] += (double)t1[jj];
-                    acc[2][jj] += (double)t2[jj];
+                // the integrands in FP32
+                const float zf = (float)z;
+                const float iz = 1.0f / zf;
+                const float iz2 = iz * iz;
+                const float Kw = f.K * (float)an.ws4;
+                if (ghost) hG = (Kw * iz2) * Zz;
+                if (gluon) {
+                    const float sgm = (float)an.sig;
+                    const float num = fmaf(sgm, fmaf(sgm, fmaf(sgm, fmaf(sgm, f.q4, f.q3), f.q2), f.q1), f.q0);
+                    hQ = ((float)an.ws2 * iz2) * Wz * num;
+                    hM = (Kw * iz) * Gz;
                 }
             }
-            __syncthreads();
         }
-    }
-
-    if (FULL) {
-        double* red = reinterpret_cast<double*>(sT);  // [NG][3][N]
-        if (bact) {
+        if (!live) {
+            for (int i = 1; i <= nq; ++i) Trow[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        Trow[0] = make_float4(hQ, hM, hG, 0.0f);
+        // angular sums over the warp's 32 nodes (FP32; the radial sums beyond are FP64)
+        {
+            float rQ = hQ, rM = hM, rG = hG;
 #pragma unroll
-            for (int jj = 0; jj < NJ; ++jj) {
-                const int j = jb + jj * nact;
-                if (j < N) {
-                    red[(g * 3 + 0) * N + j] = acc[0][jj];
-                    red[(g * 3 + 1) * N + j] = acc[1][jj];
-                    red[(g * 3 + 2) * N + j] = acc[2][jj];
-                }
+            for (int off = 16; off > 0; off >>= 1) {
+                rQ += __shfl_xor_sync(kFullMask32, rQ, off);
+                rM += __shfl_xor_sync(kFullMask32, rM, off);
+                rG += __shfl_xor_sync(kFullMask32, rG, off);
+            }
+            if (u < nunits && lane == 0) {
+                double* up = A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3;
+                up[0] = (double)rQ;
+                up[1] = (double)rM;
+                up[2] = (double)rG;
             }
         }
         __syncthreads();
-        double* out = A.Vpart + ((size_t)rt * A.KS + ks) * 3 * (size_t)N;
-        for (int idx = tid; idx < 3 * N; idx += BT) {
-            double s = 0.0;
-            for (int gg = 0; gg < NG; ++gg) s += red[(size_t)gg * 3 * N + idx];
-            out[idx] = s;
+        if (bact) {
+            // blocks of 8 rows summed in FP32, each block joined to the compensated pairs
+            for (int m0 = mlo; m0 < mhi; m0 += 8) {
+                const int m1 = min(mhi, m0 + 8);
+                float p[3][4];
+#pragma unroll
+                for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) p[kd][q] = 0.0f;
+                for (int m = m0; m < m1; ++m) {
+                    const float4* Tm = sT + (size_t)m * rs4;
+                    const float4 h = Tm[0];
+                    const float4 t = Tm[1 + qi];
+                    p[0][0] = fmaf(h.x, t.x, p[0][0]);
+                    p[0][1] = fmaf(h.x, t.y, p[0][1]);
+                    p[0][2] = fmaf(h.x, t.z, p[0][2]);
+                    p[0][3] = fmaf(h.x, t.w, p[0][3]);
+                    p[1][0] = fmaf(h.y, t.x, p[1][0]);
+                    p[1][1] = fmaf(h.y, t.y, p[1][1]);
+                    p[1][2] = fmaf(h.y, t.z, p[1][2]);
+                    p[1][3] = fmaf(h.y, t.w, p[1][3]);
+                    p[2][0] = fmaf(h.z, t.x, p[2][0]);
+                    p[2][1] = fmaf(h.z, t.y, p[2][1]);
+                    p[2][2] = fmaf(h.z, t.z, p[2][2]);
+                    p[2][3] = fmaf(h.z, t.w, p[2][3]);
+                }
+#pragma unroll
+                for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) two_sum_acc(acc[kd][q], p[kd][q]);
+            }
         }
+        __syncthreads();
+    }
+
+    // combine the groups in FP64 in a fixed order and write this block's split
+    double2* red = reinterpret_cast<double2*>(smem_raw);  // [G][3][N]: (sum, error) widened
+    if (bact) {
+#pragma unroll
+        for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * qi + q;
+                if (j < N) red[((size_t)g * 3 + kd) * N + j] = make_double2(acc[kd][q].x, acc[kd][q].y);
+            }
+    }
+    __syncthreads();
+    double* out = A.Vpart + ((size_t)rt * A.KS + ks) * 3 * (size_t)N;
+    for (int idx = tid; idx < 3 * N; idx += BT) {
+        double v = 0.0;
+        for (int gg = 0; gg < G; ++gg) {
+            const double2 r = red[(size_t)gg * 3 * N + idx];
+            v += r.x + r.y;
+        }
+        out[idx] = v;
     }
 }
 
-template <int BT, bool FULL>
+template <int BT>
 cudaError_t launch32_bt(const TripleArgs& a, cudaStream_t s) {
-    const int N = a.c.N;
-    const size_t smem = smem32_bytes(FULL, N, BT);
+    const size_t smem = smem32_bytes(a.c.N, BT, a.KB);
     const dim3 grid(a.KS, a.Rt);
-    const int nj = (N + BT - 1) / BT;
-    cudaError_t e = cudaSuccess;
-    if (nj <= 1) {
-        e = cudaFuncSetAttribute(k_triple32<BT, 1, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_triple32<BT, 1, FULL><<<grid, BT, smem, s>>>(a);
-    } else if (nj <= 2) {
-        e = cudaFuncSetAttribute(k_triple32<BT, 2, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_triple32<BT, 2, FULL><<<grid, BT, smem, s>>>(a);
-    } else if (nj <= 4) {
-        e = cudaFuncSetAttribute(k_triple32<BT, 4, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_triple32<BT, 4, FULL><<<grid, BT, smem, s>>>(a);
-    } else {
-        return cudaErrorInvalidValue;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_triple32<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_triple32<BT><<<grid, BT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+// Newton-matrix mode only (the mixed-precision residual is the FP64 kernel's).
 cudaError_t launch_triple32(bool full, const TripleArgs& a, cudaStream_t s) {
+    if (!full) return cudaErrorInvalidValue;
     if (a.KS <= 0 || a.Rt <= 0) return cudaSuccess;
-    if (bt32_for(a.c.N) == 128) return full ? launch32_bt<128, true>(a, s) : launch32_bt<128, false>(a, s);
-    return full ? launch32_bt<64, true>(a, s) : launch32_bt<64, false>(a, s);
+    return bt32_for(a.c.N) == 128 ? launch32_bt<128>(a, s) : launch32_bt<64>(a, s);
 }
 
 }  // namespace dse

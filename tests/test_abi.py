@@ -110,3 +110,15 @@ def test_alu_peak_rejects_bad_arguments(lib):
     assert lib.dse_alu_peak(0, 0.5, None, C.byref(rate), None) == -1
     assert lib.dse_alu_peak(0, float("nan"), None, C.byref(rate), None) == -1
     assert lib.dse_alu_peak(0, 100.0, None, None, None) == -1
+
+
+def test_static_residual_rejects_unsupported_modes(lib):
+    """The allocation-free residual refuses the split radial rule and mixed
+    precision, and oversized problems, before any device work."""
+    import ctypes as C
+    from paper_1206_1779_gb300 import Problem, inputs
+    for over, code in ((dict(radial_mode=1), -5), (dict(precision=1), -5)):
+        prob = Problem.from_params(inputs.problem(8, 16, 16, **over))
+        assert lib.dse_residual_static(C.byref(prob), C.c_void_p(16), C.c_void_p(16), None) == code
+    prob = Problem.from_params(inputs.problem(128, 512, 256, n_cheb_G=96))
+    assert lib.dse_residual_static(C.byref(prob), C.c_void_p(16), C.c_void_p(16), None) == -1

@@ -1,5 +1,5 @@
 """Error bound of ln z and 1/z in the quadrature kernel (ln_rcp in
-paper_1206_1779_gb300/csrc/dse_triple.cu), checked on the CPU by an emulation of its
+paper_1206_1779_gb300/csrc/dse_lnrcp.cuh), checked on the CPU by an emulation of its
 operations against 40-digit values.  s(z) = (ln z - L0)/L1 is the Chebyshev argument
 of the dressing functions (Sec. 3), so ln z must be good to the FP64 level; 1/z
 enters every integrand.
@@ -22,7 +22,7 @@ import pytest
 from df_emulation import _dmul, _fmaf, _fma64, _split, f32
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu")
+SRC = os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_lnrcp.cuh")
 TAB = os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_lntab.cuh")
 
 

@@ -34,10 +34,19 @@ def static_residual(dse, params, c_dev, F_dev):
                                  ctypes.c_void_p(F_dev.data_ptr()), stream)
 
 
-@pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64"])
+CASES = {
+    "newton_step_n16": None,
+    "full_solve_n64": None,
+    # separate orders (gluon rows at the N_Z roots, ghost rows at the N_G roots) with
+    # a ghost subtraction point x_G > 0 (its own row)
+    "orders_24_16_ghost_point": dict(n_cheb=24, n_cheb_G=16, n_radial=96, n_angular=64, x_G=2e-3, ginv_G=0.02),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_static_residual_matches_plan_residual(dse, oracle, inputs, name):
     import torch
-    p = inputs.workload_problem(name)
+    p = inputs.workload_problem(name) if CASES[name] is None else inputs.problem(**CASES[name])
     _, AF = oracle.newton_matrix_magnitudes(p, inputs.starting_guess(p, seed=0))
     with dse.Plan(p) as plan:
         for seed in (0, 1):  # two calls in a row, different inputs
@@ -51,10 +60,14 @@ def test_static_residual_matches_plan_residual(dse, oracle, inputs, name):
             assert r.ok, (name, seed, r)
 
 
-def test_static_residual_rejects_oversized_problem(dse, inputs):
+@pytest.mark.parametrize("orders", [(256, 0), (128, 96)])
+def test_static_residual_rejects_oversized_problem(dse, inputs, orders):
     import torch
-    # 256 coefficients with 4096 x 2048 nodes needs far more than the static scratch
-    p = inputs.problem(256, 4096, 2048)
-    c = torch.zeros(512, dtype=torch.float64, device="cuda")
-    F = torch.zeros(512, dtype=torch.float64, device="cuda")
+    # 256 coefficients with 4096 x 2048 nodes, and N_Z = 128, N_G = 96 (separate
+    # collocation rows) with 512 x 256 nodes, need more than the static scratch
+    nz, ng = orders
+    p = inputs.problem(nz, 4096, 2048) if ng == 0 else inputs.problem(nz, 512, 256, n_cheb_G=ng)
+    n = nz + (ng or nz)
+    c = torch.zeros(n, dtype=torch.float64, device="cuda")
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
     assert static_residual(dse, p, c, F) == dse.DSE_ERR_ARG
