@@ -55,38 +55,41 @@ SERIES_TABLE_DF_STEPS = 7   # Horner steps in double-float per polynomial (the r
 
 def work_per_triple(N: int):
     """Algorithmic work of the hot kernel per (x, y, theta) triple in the Newton-matrix
-    mode: (FP64 flops, FP32 instructions, double-float multiply-adds), an FMA counted
-    as 2 flops.
+    mode: (FP64 operations, FP64 flops, FP32 instructions, double-float multiply-adds).
 
-    FP64 (54 flops on the table path): z (2); ln z and 1/z (11: the FMAs of r and of
-    e ln2_hi, the leading sums, the product by inv_j); s and u (4); the widened table
-    values (3); T_2 .. T_5 for the anchors (11); the integrands (17); the angular sums
-    (6).  Without the table (N < 24) the two series and the recurrence add 6N and the
-    exponentials replace the table lookup.
+    FP64 operations are the instructions of the FP64 pipe, each of which takes one
+    slot of it whether it is an FMA, an add or a multiply; flops count an FMA as 2.
+    On the table path (44 operations, 54 flops): z (1); ln z and 1/z (10: the FMAs
+    of r and of e ln2_hi, the leading sums, the product by inv_j); s and u (4); the
+    widened table values (3); T_2 .. T_5 for the anchors (7); the integrands (13);
+    the angular sums (6).  Without the table (N < 24) the two series and the
+    recurrence add 3N FMAs and the exponentials replace the table lookup.
     FP32 (double-float, on the FP32 pipe): the derivative sums weight * T_j (3N
     double-float multiply-adds, 12 instructions each), the T_j recurrences (N
     multiply-subtracts, 15 each: the stride-4 anchors and the steps to T_4i+2, T_4i+3),
     the three table polynomials (3 x SERIES_TABLE_DF_STEPS double-float steps of 15,
     the others one FFMA each) and the small terms of ln z and 1/z (40)."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
-        f64 = 54.0
+        f64_ops, f64 = 44.0, 54.0
         horner = 3.0 * (SERIES_TABLE_DF_STEPS * 15.0 + (SERIES_TABLE_DEGREE - SERIES_TABLE_DF_STEPS))
         df_ops = 3.0 * N + N + 3.0 * SERIES_TABLE_DF_STEPS
     else:
-        f64 = 54.0 + 6.0 * N
+        f64_ops, f64 = 44.0 + 3.0 * N, 54.0 + 6.0 * N
         horner = 0.0
         df_ops = 3.0 * N + N
     f32 = 12.0 * 3 * N + 15.0 * N + horner + 40.0
-    return f64, f32, df_ops
+    return f64_ops, f64, f32, df_ops
 
 
-def roofline_model(N: int, triples: int, fp64_flops_per_s: float, fp32_inst_per_s: float):
+def roofline_model(N: int, triples: int, fp64_ops_per_s: float, fp32_inst_per_s: float):
     """Lower bound on one launch's duration (s): the FP64 and FP32 pipes issue
     independently, so the bound is the larger of the two pipes' times at their
-    measured rates; and the FP64-equivalent flops of the launch (a double-float
-    multiply-add or -subtract counted as one FP64 FMA, 2 flops)."""
-    f64, f32, df_ops = work_per_triple(N)
-    t_fp64 = triples * f64 / fp64_flops_per_s
+    measured rates (FP64 operations at the measured FP64 FMA instruction rate, FP32
+    instructions at the measured FP32 FMA rate, which is also the schedulers' issue
+    rate); and the FP64-equivalent flops of the launch (a double-float multiply-add
+    or -subtract counted as one FP64 FMA, 2 flops)."""
+    f64_ops, f64, f32, df_ops = work_per_triple(N)
+    t_fp64 = triples * f64_ops / fp64_ops_per_s
     t_fp32 = triples * f32 / fp32_inst_per_s
     flops = triples * (f64 + 2.0 * df_ops)
     return max(t_fp64, t_fp32), flops, t_fp64, t_fp32
@@ -280,11 +283,11 @@ def run_gb300(args):
     triples = Rt * nr * na
     avg_launch_ms = timed_ms / max(n_timed, 1)
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    t_min, flops_launch, t_fp64, t_fp32 = roofline_model(N, triples, 2.0 * peaks["fp64_fma_per_s"],
+    t_min, flops_launch, t_fp64, t_fp32 = roofline_model(N, triples, peaks["fp64_fma_per_s"],
                                                          peaks["fp32_fma_per_s"])
     achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = flops_launch / t_min / 1e12
-    f64_pt, f32_pt, dfops_pt = work_per_triple(N)
+    f64ops_pt, f64_pt, f32_pt, dfops_pt = work_per_triple(N)
     rec = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
     traffic = rec.get("dram_bytes_per_launch_full_size") if rec else None
     issue = None
@@ -352,9 +355,11 @@ def run_gb300(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_triple (radial x angular quadrature: FP64 integrands, double-float derivative sums)",
                          "peak_source": ("measured (dse_alu_peak on this GPU): FP64-equivalent flops of a launch over "
-                                         "max(t_fp64, t_fp32), the FP64 work at the measured FP64 FMA rate and the "
-                                         "FP32 instructions at the measured FP32 FMA rate, the two pipes overlapped"),
+                                         "max(t_fp64, t_fp32), the FP64 operations at the measured FP64 FMA "
+                                         "instruction rate and the FP32 instructions at the measured FP32 FMA rate, "
+                                         "the two pipes overlapped"),
                          "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms, "triples_per_launch": triples,
+                         "fp64_operations_per_triple": f64ops_pt,
                          "fp64_flops_per_triple": f64_pt, "fp32_instructions_per_triple": f32_pt,
                          "double_float_ops_per_triple": dfops_pt,
                          "t_fp64_bound_ms": t_fp64 * 1e3, "t_fp32_bound_ms": t_fp32 * 1e3,

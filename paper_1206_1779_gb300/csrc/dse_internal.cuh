@@ -160,7 +160,15 @@ cudaError_t launch_tables(const Consts& c, const double* coef, const Rad* rad, c
                           YTab* ytab, double* phiy, XTab* xtab, double* phix, cudaStream_t s);
 cudaError_t launch_triple(bool full, const TripleArgs& a, cudaStream_t s);
 // Series table for the coefficients coef (n: a then b), kSeriesM records.
-cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* tab, cudaStream_t s);
+// The node values of a problem's series table depend on the table's geometry alone:
+// tq (sM x kSeriesQ x N double2) holds T_j(s_q) as double-doubles, cst (2 kSeriesQ^2
+// doubles) the interpolation and monomial tables; both written once by launch_series_init,
+// which also writes the records' interval geometry.
+constexpr size_t series_node_values(int N) { return (size_t)kSeriesM * kSeriesQ * (size_t)N; }
+constexpr int kSeriesConsts = 2 * kSeriesQ * kSeriesQ;
+cudaError_t launch_series_init(const Consts& c, double2* tq, double* cst, SeriesRec* tab, cudaStream_t s);
+cudaError_t launch_series_table(const Consts& c, const double* coef, const double2* tq, const double* cst,
+                                SeriesRec* tab, cudaStream_t s);
 cudaError_t launch_series_table_batched(const BatchProblem* P, int nb, const double* coef_base, cudaStream_t s);
 // FP32-integrand variant (mixed precision), same outputs and layouts.
 cudaError_t launch_triple32(bool full, const TripleArgs& a, cudaStream_t s);

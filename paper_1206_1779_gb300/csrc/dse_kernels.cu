@@ -277,16 +277,141 @@ __device__ double series_comp(const double* cf, int m, double sh, double sl) {
     return t.hi + fma(sh, e1, local - e2);
 }
 
-// Two intervals per block of three warps.  Warp f < 2 (0: ln Z, 1: ln G)
-// evaluates its series, lane (il, q) = (lane / Q, lane % Q) at the q-th Chebyshev
-// point u_q = cos(pi (q + 1/2)/Q) of interval 2 blk + il, the node s = mid + half u_q
-// held exactly as s_h + s_l; meanwhile warp 2 builds the end-point record and the
-// interpolation and monomial tables.  Lane (il, q) of warp F then forms the node
-// value F (0: Z = e^{ln Z}, 1: G = e^{ln G}, 2: W = e^{p ln G + q ln Z}), and thread
-// (F, il, q) forms the Chebyshev coefficient of degree q of F's interpolant,
-// c_q = (2 - [q = 0])/Q sum_r v_r cos(pi q (r + 1/2)/Q), and its monomial
-// coefficient of u^q, sum_j c_j [u^q] T_j(u), with the coefficients of T_j built by
-// the recurrence T_{j+1} = 2u T_j - T_{j-1}.
+// The interval geometry of the table: mid = (cos th0 + cos th1)/2 and
+// half = (cos th0 - cos th1)/2 = sin((th0 + th1)/2) sin(h/2) (no cancellation) of
+// interval i, th0 = i h, th1 = (i + 1) h, h = pi/M; and the node
+// s = mid + half u_q at the q-th Chebyshev point u_q = cos(pi (q + 1/2)/Q), held
+// exactly as a double-double.
+__device__ __forceinline__ void series_interval(const int M, const int i, double& mid, double& half) {
+    const double h = kPi / M;
+    const double th0 = i * h, th1 = (i + 1) * h;
+    double s0, c0, s1, c1, sm, cm, sh, ch;
+    sincos(th0, &s0, &c0);
+    sincos(th1, &s1, &c1);
+    sincos(0.5 * (th0 + th1), &sm, &cm);
+    sincos(0.5 * h, &sh, &ch);
+    mid = 0.5 * (c0 + c1);
+    half = sm * sh;
+}
+
+__device__ __forceinline__ DD series_node(const double mid, const double half, const int q) {
+    const double uq = cos(kPi * (q + 0.5) / kSeriesQ);
+    const DD p = dd_two_sum(half * uq, mid);
+    return dd_add(p, DD{fma(half, uq, -(half * uq)), 0.0});
+}
+
+// The interpolation table dct[k][r] = cos(pi k (r + 1/2)/Q) (one entry per call)
+// and, by lanes 0 .. Q-1 of a warp together, the monomial coefficients
+// tcoef[j][k] = [u^k] T_j(u) by the three-term recurrence (exact integers).
+__device__ __forceinline__ void series_tcoef_column(const int k, double (*tcoef)[kSeriesQ]) {
+    double tm = k == 0 ? 1.0 : 0.0;  // T_0
+    double tc = k == 1 ? 1.0 : 0.0;  // T_1
+    tcoef[0][k] = tm;
+    tcoef[1][k] = tc;
+    for (int j = 2; j < kSeriesQ; ++j) {
+        const double lower = __shfl_up_sync(0x0000ffffu, tc, 1);  // [u^{k-1}] T_{j-1}
+        const double tn = (k == 0 ? 0.0 : 2.0 * lower) - tm;
+        tcoef[j][k] = tn;
+        tm = tc;
+        tc = tn;
+    }
+}
+
+// The end-point record: sum_j c_j T_j(+-1) with T_j(1) = 1, T_j(-1) = (-1)^j, in
+// the order of the per-triple recurrence (e: 0 ln Z(1), 1 ln G(1), 2 ln Z(-1),
+// 3 ln G(-1)).
+__device__ __forceinline__ void series_endpoint(const Consts& c, const double* cf_ab, const int e, SeriesRec* tab) {
+    const int nc = (e & 1) ? c.NG : c.NZ;
+    const double* cf = cf_ab + ((e & 1) ? c.NZ : 0);
+    const double sgn = e < 2 ? 1.0 : -1.0;
+    double v = 0.5 * cf[0];
+    double t = 1.0;
+    for (int j = 1; j < nc; ++j) {
+        t *= sgn;
+        v = fma(cf[j], t, v);
+    }
+    reinterpret_cast<double*>(tab + kSeriesM)[e] = v;
+}
+
+// From the node values ln Z, ln G of IPB intervals (sv[f][il][q]) to their records:
+// thread (f, il, q) forms the node value F (0: Z = e^{ln Z}, 1: G = e^{ln G},
+// 2: W = e^{p ln G + q ln Z}), the Chebyshev coefficient of degree q of F's
+// interpolant, c_q = (2 - [q = 0])/Q sum_r v_r cos(pi q (r + 1/2)/Q), and its
+// monomial coefficient of u^q, sum_j c_j [u^q] T_j(u), stored as a double-float
+// pair at the record's exponent of F.  Every thread of the block calls it (it holds
+// block barriers); act selects the threads that own an (f, il, q), and the lanes of
+// a warp that call it together span whole groups of Q (the shuffles run over a
+// group); warps without such a thread (run false) only take the barriers.  With
+// geometry, the record's mid and 1/half are written too.
+template <int IPB>
+__device__ __forceinline__ void series_fit(const Consts& c, const double (*sv)[IPB][kSeriesQ],
+                                           double (*sf)[IPB][kSeriesQ], double (*sc)[IPB][kSeriesQ],
+                                           const double (*dct)[kSeriesQ], const double (*tcoef)[kSeriesQ],
+                                           int (*skf)[IPB], SeriesRec* __restrict__ tab, const int i, const bool run,
+                                           const bool act, const int fa, const int il, const int q,
+                                           const bool geometry, const double mid, const double half) {
+    const int lane = threadIdx.x & 31;
+    const int f = act ? fa : 0;  // (inactive threads read the first function and write nothing)
+    if (run) {
+        const double lz = sv[0][il][q], lg = sv[1][il][q];
+        const double v = exp(f == 0 ? lz : f == 1 ? lg : fma(c.pG, lg, c.qZ * lz));
+        if (act) sf[f][il][q] = v;
+    }
+    __syncthreads();
+    if (run) {
+        double acc = 0.0;
+        for (int r = 0; r < kSeriesQ; ++r) acc = fma(sf[f][il][r], dct[q][r], acc);
+        if (act) sc[f][il][q] = (q == 0 ? 1.0 : 2.0) / kSeriesQ * acc;
+    }
+    __syncthreads();
+    SeriesRec& R = tab[i];
+    if (run) {  // (warp-uniform: the shuffles below run over whole warps)
+        double mono = 0.0;
+        for (int j = q; j < kSeriesQ; ++j) mono = fma(sc[f][il][j], tcoef[j][q], mono);
+        // the record's exponent of this function: the largest biased exponent of its
+        // coefficients (the Q lanes of the interval)
+        int E = (int)(((unsigned)__double2hiint(mono) >> 20) & 0x7ffu);
+        for (int off = kSeriesQ / 2; off > 0; off >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, off));
+        // double-float pair of mono 2^-(E - 1023): hi rounded to FP32, lo the rounded remainder
+        const double ms = ldexp(mono, 1023 - E);
+        const float hi = (float)ms;
+        const float lo = (float)(ms - (double)hi);
+        if (act) {
+            float* t = f < 2 ? &R.e[q].x + 2 * f : &R.w[q].x;
+            t[0] = hi;
+            t[1] = lo;
+            if (q == 0) R.ex[f] = E;
+        }
+        // the degree from which on the polynomial's tail is summed in FP32 alone: the
+        // smallest k >= 1 with sum_{k' >= k} |c_k'| <= 2^-30 |c_0| for all three
+        // functions (c_0, the value at the interval's middle, is positive), so that
+        // the FP32 rounding of the tail (16 roundings of 2^-24 at most) stays below
+        // 2^-50 of the value
+        double tail = fabs(ms);
+        for (int off = 1; off < kSeriesQ; off <<= 1) {
+            const double o = __shfl_down_sync(0xffffffffu, tail, off);
+            if (q + off < kSeriesQ) tail += o;
+        }
+        const double c0 = __shfl_sync(0xffffffffu, ms, lane & ~(kSeriesQ - 1));
+        int kq = (q >= 1 && tail <= 0x1p-30 * fabs(c0)) ? q : kSeriesQ;
+        for (int off = kSeriesQ / 2; off > 0; off >>= 1) kq = min(kq, __shfl_xor_sync(0xffffffffu, kq, off));
+        if (act && q == 0) skf[f][il] = kq;
+    }
+    __syncthreads();
+    if (run && act && f == 0 && q == 0) {
+        if (geometry) {
+            R.mid = mid;
+            R.invhalf = 1.0 / half;
+        }
+        R.ex[3] = max(skf[0][il], max(skf[1][il], skf[2][il]));
+    }
+}
+
+// Two intervals per block of three warps (the batched build).  Warp f < 2 (0: ln Z,
+// 1: ln G) evaluates its series by the compensated Clenshaw recurrence, lane
+// (il, q) = (lane / Q, lane % Q) at the node s_q of interval 2 blk + il; meanwhile
+// warp 2 builds the end-point record and the interpolation and monomial tables;
+// then series_fit with thread (warp, il, q).
 constexpr int kSeriesIntervalsPerBlock = 2;
 constexpr int kSeriesThreads = 96;
 static_assert(kSeriesIntervalsPerBlock * kSeriesQ == 32, "one warp holds one function of the block's intervals");
@@ -299,126 +424,40 @@ __device__ __forceinline__ void series_table_block(const Consts& c, const double
     __shared__ double tcoef[kSeriesQ][kSeriesQ];  // tcoef[j][k] = [u^k] T_j(u)
     __shared__ double dct[kSeriesQ][kSeriesQ];    // dct[k][r] = cos(pi k (r + 1/2)/Q)
     __shared__ double scf[2 * DSE_MAX_CHEB];      // a then b
+    __shared__ int skf[3][kSeriesIntervalsPerBlock];  // FP32-tail degree per function
     __shared__ double smh[kSeriesIntervalsPerBlock][4];  // cos th0, cos th1, sin((th0 + th1)/2), sin(h/2)
-    __shared__ double suq[kSeriesQ];                     // the Chebyshev points u_q
-    __shared__ int skf[3][kSeriesIntervalsPerBlock];     // FP32-tail degree per function
     if (blk * kSeriesIntervalsPerBlock >= c.sM) return;  // (batched grids span the largest table)
     const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int il = lane / kSeriesQ, q = lane % kSeriesQ;
     for (int j = threadIdx.x; j < c.n; j += blockDim.x) scf[j] = coef[j];
-    const double h = kPi / c.sM;
     if (f == 0 && lane < 4 * kSeriesIntervalsPerBlock) {
-        // the intervals' end points and half-widths: one sincos per lane
+        // the geometry of series_interval, one sincos per lane
+        const double h = kPi / c.sM;
         const int ii = blk * kSeriesIntervalsPerBlock + (lane >> 2), w = lane & 3;
         const double th0 = ii * h, th1 = (ii + 1) * h;
         const double x = w == 0 ? th0 : w == 1 ? th1 : w == 2 ? 0.5 * (th0 + th1) : 0.5 * h;
         double sn, cs;
         sincos(x, &sn, &cs);
         smh[lane >> 2][w] = w < 2 ? cs : sn;
-    } else if (f == 1 && lane < kSeriesQ) {
-        suq[lane] = cos(kPi * (lane + 0.5) / kSeriesQ);
     }
     const int i = blk * kSeriesIntervalsPerBlock + il;
-    __syncthreads();  // coefficients, end points and nodes staged
+    __syncthreads();  // coefficients and interval geometry staged
     const double mid = 0.5 * (smh[il][0] + smh[il][1]);
-    const double half = smh[il][2] * smh[il][3];  // (cos th0 - cos th1)/2 without cancellation
+    const double half = smh[il][2] * smh[il][3];
     if (f < 2) {
-        const double uq = suq[q];
-        // s = mid + half uq exactly as s_h + s_l
-        const DD p = dd_two_sum(half * uq, mid);
-        const DD sdd = dd_add(p, DD{fma(half, uq, -(half * uq)), 0.0});
+        const DD sdd = series_node(mid, half, q);
         sv[f][il][q] = f == 0 ? series_comp(scf, c.NZ, sdd.hi, sdd.lo) : series_comp(scf + c.NZ, c.NG, sdd.hi, sdd.lo);
     } else {
-        // the third warp, while the other two sum the series: the end-point record,
-        // the interpolation table and the monomial coefficients of the T_j
-        if (blk == 0 && lane < 4) {
-            // sum_j c_j T_j(+-1) with T_j(1) = 1, T_j(-1) = (-1)^j
-            const int e = lane;
-            const int nc = (e & 1) ? c.NG : c.NZ;
-            const double* cf = scf + ((e & 1) ? c.NZ : 0);
-            const double sgn = e < 2 ? 1.0 : -1.0;
-            double v = 0.5 * cf[0];
-            double t = 1.0;
-            for (int j = 1; j < nc; ++j) {
-                t *= sgn;
-                v = fma(cf[j], t, v);
-            }
-            reinterpret_cast<double*>(tab + kSeriesM)[e] = v;
-        }
+        if (blk == 0 && lane < 4) series_endpoint(c, scf, lane, tab);
         for (int e = lane; e < kSeriesQ * kSeriesQ; e += 32) {
             const int k = e / kSeriesQ, r = e % kSeriesQ;
             dct[k][r] = cos(kPi * k * (r + 0.5) / kSeriesQ);
         }
-        if (lane < kSeriesQ) {
-            // column k of every T_j, by the three-term recurrence (exact integers)
-            const int k = lane;
-            double tm = k == 0 ? 1.0 : 0.0;  // T_0
-            double tc = k == 1 ? 1.0 : 0.0;  // T_1
-            tcoef[0][k] = tm;
-            tcoef[1][k] = tc;
-            for (int j = 2; j < kSeriesQ; ++j) {
-                const double lower = __shfl_up_sync(0x0000ffffu, tc, 1);  // [u^{k-1}] T_{j-1}
-                const double tn = (k == 0 ? 0.0 : 2.0 * lower) - tm;
-                tcoef[j][k] = tn;
-                tm = tc;
-                tc = tn;
-            }
-        }
+        if (lane < kSeriesQ) series_tcoef_column(lane, tcoef);
     }
     __syncthreads();
-    {
-        const double lz = sv[0][il][q], lg = sv[1][il][q];
-        sf[f][il][q] = exp(f == 0 ? lz : f == 1 ? lg : fma(c.pG, lg, c.qZ * lz));
-    }
-    __syncthreads();
-    {
-        double acc = 0.0;
-        for (int r = 0; r < kSeriesQ; ++r) acc = fma(sf[f][il][r], dct[q][r], acc);
-        sc[f][il][q] = (q == 0 ? 1.0 : 2.0) / kSeriesQ * acc;
-    }
-    __syncthreads();
-    double mono = 0.0;
-    for (int j = q; j < kSeriesQ; ++j) mono = fma(sc[f][il][j], tcoef[j][q], mono);
-    // the record's exponent of this function: the largest biased exponent of its
-    // coefficients (the 16 lanes of the interval)
-    int E = (int)(((unsigned)__double2hiint(mono) >> 20) & 0x7ffu);
-    for (int off = kSeriesQ / 2; off > 0; off >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, off));
-    // double-float pair of mono 2^-(E - 1023): hi rounded to FP32, lo the rounded remainder
-    const double ms = ldexp(mono, 1023 - E);
-    const float hi = (float)ms;
-    const float lo = (float)(ms - (double)hi);
-    SeriesRec& R = tab[i];
-    float* t = f < 2 ? &R.e[q].x + 2 * f : &R.w[q].x;
-    t[0] = hi;
-    t[1] = lo;
-    if (q == 0) R.ex[f] = E;
-    // the degree from which on the polynomial's tail is summed in FP32 alone: the
-    // smallest k >= 1 with sum_{k' >= k} |c_k'| <= 2^-30 |c_0| for all three
-    // functions (c_0, the value at the interval's middle, is positive), so that
-    // the FP32 rounding of the tail (16 roundings of 2^-24 at most) stays below
-    // 2^-50 of the value
-    {
-        double tail = fabs(ms);
-        for (int off = 1; off < kSeriesQ; off <<= 1) {
-            const double o = __shfl_down_sync(0xffffffffu, tail, off);
-            if (q + off < kSeriesQ) tail += o;
-        }
-        const double c0 = __shfl_sync(0xffffffffu, ms, lane & ~(kSeriesQ - 1));
-        int kq = (q >= 1 && tail <= 0x1p-30 * fabs(c0)) ? q : kSeriesQ;
-        for (int off = kSeriesQ / 2; off > 0; off >>= 1) kq = min(kq, __shfl_xor_sync(0xffffffffu, kq, off));
-        if (q == 0) skf[f][il] = kq;
-    }
-    __syncthreads();
-    if (f == 0 && q == 0) {
-        R.mid = mid;
-        R.invhalf = 1.0 / half;
-        R.ex[3] = max(skf[0][il], max(skf[1][il], skf[2][il]));
-    }
-}
-
-__global__ void __launch_bounds__(kSeriesThreads) k_series_table(const Consts c, const double* __restrict__ coef,
-                                                      SeriesRec* __restrict__ tab) {
-    series_table_block(c, coef, tab, blockIdx.x);
+    series_fit<kSeriesIntervalsPerBlock>(c, sv, sf, sc, dct, tcoef, skf, tab, i, true, true, f, il, q, true, mid,
+                                         half);
 }
 
 __global__ void __launch_bounds__(kSeriesThreads) k_series_table_batched(const BatchProblem* __restrict__ P,
@@ -426,6 +465,120 @@ __global__ void __launch_bounds__(kSeriesThreads) k_series_table_batched(const B
     const BatchProblem& B = P[blockIdx.y];
     if (!B.active || !B.stab) return;
     series_table_block(B.t.c, coef_base + B.coef_off, B.stab, blockIdx.x);
+}
+
+// The single-problem build.  The nodes depend on the table's geometry alone, so
+// their Chebyshev values are formed once per plan (k_series_init): tq[(i Q + q) N + j]
+// = T_j(s_q) of interval i as a double-double (T_0 entered as 1/2), by the
+// recurrence T_{j+1} = 2 s T_j - T_{j-1} in double-double arithmetic (rounding
+// ~2^-104 per step), together with the records' geometry and, in cst, the
+// interpolation table dct[Q][Q] followed by the monomial table tcoef[Q][Q].  Per
+// Newton matrix (k_series_table) the node values ln Z(s_q) = sum_j a_j T_j(s_q),
+// ln G(s_q) = sum_j b_j T_j(s_q) are compensated dot products (Ogita, Rump and
+// Oishi's Dot2: the exact product error by FMA, the exact sum error by TwoSum,
+// both collected in FP64), each spread over four lanes whose partial results are
+// combined by TwoSum: the series as computed in about twice the working
+// precision, rounded once, like the compensated Clenshaw sums of the batched
+// build.  One block of four warps per interval (32 dot products: 16 nodes x 2
+// functions), so that the FP64 work of the build spreads over every SM.
+constexpr int kSeriesDotThreads = 128;
+constexpr int kSeriesDotLanes = 4;  // lanes per dot product
+static_assert(kSeriesDotThreads == 2 * kSeriesQ * kSeriesDotLanes, "one thread per (function, node, part)");
+
+__device__ __forceinline__ DD dd_mul(const DD a, const DD b) {
+    const double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);
+    e = fma(a.hi, b.lo, e);
+    e = fma(a.lo, b.hi, e);
+    return dd_fast_two_sum(p, e);
+}
+
+__global__ void __launch_bounds__(64) k_series_init(const Consts c, double2* __restrict__ tq,
+                                                    double* __restrict__ cst, SeriesRec* __restrict__ tab) {
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (tid < kSeriesQ) {
+        double mid, half;
+        series_interval(c.sM, i, mid, half);
+        if (tid == 0) {
+            tab[i].mid = mid;
+            tab[i].invhalf = 1.0 / half;
+        }
+        const DD s = series_node(mid, half, tid);
+        const DD s2 = {2.0 * s.hi, 2.0 * s.lo};
+        double2* T = tq + ((size_t)i * kSeriesQ + tid) * c.N;
+        DD tm = {1.0, 0.0}, tc = s;
+        T[0] = make_double2(0.5, 0.0);
+        if (c.N > 1) T[1] = make_double2(tc.hi, tc.lo);
+        for (int j = 2; j < c.N; ++j) {
+            const DD tn = dd_add(dd_mul(s2, tc), DD{-tm.hi, -tm.lo});
+            T[j] = make_double2(tn.hi, tn.lo);
+            tm = tc;
+            tc = tn;
+        }
+    } else if (i == 0 && tid >= 32) {
+        const int lane = tid - 32;
+        for (int e = lane; e < kSeriesQ * kSeriesQ; e += 32) {
+            const int k = e / kSeriesQ, r = e % kSeriesQ;
+            cst[e] = cos(kPi * k * (r + 0.5) / kSeriesQ);
+        }
+        if (lane < kSeriesQ) series_tcoef_column(lane, reinterpret_cast<double(*)[kSeriesQ]>(cst + kSeriesQ * kSeriesQ));
+    }
+}
+
+__global__ void __launch_bounds__(kSeriesDotThreads) k_series_table(const Consts c, const double* __restrict__ coef,
+                                                                    const double2* __restrict__ tq,
+                                                                    const double* __restrict__ cst,
+                                                                    SeriesRec* __restrict__ tab) {
+    __shared__ double sv[2][1][kSeriesQ];  // ln Z, ln G
+    __shared__ double sf[3][1][kSeriesQ];  // Z, G, W
+    __shared__ double sc[3][1][kSeriesQ];
+    __shared__ double tcoef[kSeriesQ][kSeriesQ];
+    __shared__ double dct[kSeriesQ][kSeriesQ];
+    __shared__ int skf[3][1];
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 2 * kSeriesQ * kSeriesQ; e += kSeriesDotThreads) {
+        const double v = __ldg(&cst[e]);
+        if (e < kSeriesQ * kSeriesQ) dct[e / kSeriesQ][e % kSeriesQ] = v;
+        else tcoef[(e - kSeriesQ * kSeriesQ) / kSeriesQ][e % kSeriesQ] = v;
+    }
+    {
+        const int chain = tid / kSeriesDotLanes, part = tid % kSeriesDotLanes;
+        const int f = chain / kSeriesQ, q = chain % kSeriesQ;
+        const int nf = f == 0 ? c.NZ : c.NG;
+        const double* __restrict__ cf = coef + (f == 0 ? 0 : c.NZ);
+        const double2* __restrict__ T = tq + ((size_t)i * kSeriesQ + q) * c.N;
+        double s = 0.0, e = 0.0;
+#pragma unroll 4
+        for (int j = part; j < nf; j += kSeriesDotLanes) {
+            const double2 t = __ldg(&T[j]);
+            const double a = __ldg(&cf[j]);
+            const double p = a * t.x;
+            const double pe = fma(a, t.x, -p);
+            const DD ts = dd_two_sum(s, p);
+            e += ts.lo + fma(a, t.y, pe);
+            s = ts.hi;
+        }
+        // the parts of a dot product (consecutive lanes): TwoSum of the leading sums,
+        // the errors added (the same on every lane of the group)
+#pragma unroll
+        for (int off = 1; off < kSeriesDotLanes; off <<= 1) {
+            const double so = __shfl_xor_sync(0xffffffffu, s, off);
+            const double eo = __shfl_xor_sync(0xffffffffu, e, off);
+            const DD ts = dd_two_sum(s, so);
+            e = (e + eo) + ts.lo;
+            s = ts.hi;
+        }
+        if (part == 0) sv[f][0][q] = s + e;
+    }
+    if (i == 0 && tid >= 64 && tid < 68) series_endpoint(c, coef, tid - 64, tab);
+    __syncthreads();
+    // threads 0 .. 3Q-1 (the first two warps) own (f, q) = (tid / Q, tid % Q); the
+    // rest of the second warp runs along for its shuffles, the last two warps take
+    // the barriers only
+    series_fit<1>(c, sv, sf, sc, dct, tcoef, skf, tab, i, tid < 64, tid < 3 * kSeriesQ, tid / kSeriesQ, 0,
+                  tid % kSeriesQ, false, 0.0, 0.0);
 }
 
 // ------------------------------------------------------------------------
@@ -437,14 +590,15 @@ __global__ void __launch_bounds__(kSeriesThreads) k_series_table_batched(const B
 //       dPi_G/da_j = -K V_G,  dPi_G/db_j = -K Y_G   (Sec. 2 equations, derivative
 // closure d ln G(u)/d b_j = d ln Z(u)/d a_j = phi_j(u)).
 // For x_G = 0, z = y: the ghost row is y-only and V_G = Y_G.
-constexpr int kRowBlock = 256;
+constexpr int kRowBlock = 512;
 constexpr int kRowJ = 32;                   // coefficients per block (one per lane)
 constexpr int kRowKG = kRowBlock / kRowJ;   // radial-node groups per block
-constexpr int kChunkK = 256;
+constexpr int kChunkK = 512;
 
 // Grid: (row r, block of 32 coefficients).  Thread (k-group kg, lane) owns
-// coefficient j = 32 jb + lane and the radial nodes kk = kg mod 8 of each chunk;
-// the 8 partial sums are combined in a fixed order at the end.
+// coefficient j = 32 jb + lane, the radial nodes kk = kg mod kRowKG of each chunk
+// and the radial splits kg mod kRowKG; the kRowKG partial sums are combined in a
+// fixed order at the end (sixteen groups: many L2 loads in flight per SM).
 template <bool FULL>
 __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS, int nch,
                                                 const Rad* __restrict__ rad, const Ang* __restrict__ ang,
@@ -2177,8 +2331,14 @@ cudaError_t launch_schwinger(const Consts& c, const double* coef, int n_nodes, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_series_table(const Consts& c, const double* coef, SeriesRec* tab, cudaStream_t s) {
-    k_series_table<<<c.sM / kSeriesIntervalsPerBlock, kSeriesThreads, 0, s>>>(c, coef, tab);
+cudaError_t launch_series_init(const Consts& c, double2* tq, double* cst, SeriesRec* tab, cudaStream_t s) {
+    k_series_init<<<c.sM, 64, 0, s>>>(c, tq, cst, tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_series_table(const Consts& c, const double* coef, const double2* tq, const double* cst,
+                                SeriesRec* tab, cudaStream_t s) {
+    k_series_table<<<c.sM, kSeriesDotThreads, 0, s>>>(c, coef, tq, cst, tab);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,8 @@ struct dse_plan {
     double* F;
     double* work;
     SeriesRec* stab;    // series table (read by the FP64 quadrature kernel when use_series_table(N))
+    double2* stq;       // the table's node values T_j(s_q) as double-doubles (set-up)
+    double* scst;       // the table's interpolation and monomial tables (set-up)
     float* As;          // row-scaled FP32 copy of J (Newton step)
     double2* rowinfo;   // row scales and row sums (Newton step)
     float* Xinv;        // FP32 inverse of the last eliminated Newton step, reused while it suffices
@@ -214,7 +216,7 @@ cudaError_t build_rows(dse_plan* pl, const double* coef, bool full, bool fp32) {
         // the series table (independent of the tables kernel) on the side stream
         e = cudaEventRecord(pl->fork, pl->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(pl->side, pl->fork, 0);
-        if (e == cudaSuccess) e = launch_series_table(pl->c, coef, pl->stab, pl->side);
+        if (e == cudaSuccess) e = launch_series_table(pl->c, coef, pl->stq, pl->scst, pl->stab, pl->side);
         if (e == cudaSuccess) e = cudaEventRecord(pl->join, pl->side);
         pl->launches += 1;
     }
@@ -332,6 +334,9 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     size_t o_F = off; off = align_up(off + sizeof(double) * n);
     size_t o_work = off; off = align_up(off + sizeof(double) * 2 * n);
     size_t o_stab = off; off = align_up(off + sizeof(SeriesRec) * kSeriesRecords);
+    const bool table = use_series_table(N);
+    size_t o_stq = off; off = align_up(off + (table ? sizeof(double2) * series_node_values(N) : 0));
+    size_t o_scst = off; off = align_up(off + (table ? sizeof(double) * kSeriesConsts : 0));
     size_t o_As = off; off = align_up(off + sizeof(float) * (size_t)n * n);
     size_t o_ri = off; off = align_up(off + sizeof(double2) * n);
     size_t o_X = off; off = align_up(off + (n <= 128 ? sizeof(float) * (size_t)n * n : 0));
@@ -365,6 +370,8 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     pl->F = (double*)(base + o_F);
     pl->work = (double*)(base + o_work);
     pl->stab = (SeriesRec*)(base + o_stab);
+    pl->stq = table ? (double2*)(base + o_stq) : nullptr;
+    pl->scst = table ? (double*)(base + o_scst) : nullptr;
     pl->As = (float*)(base + o_As);
     pl->rowinfo = (double2*)(base + o_ri);
     pl->Xinv = n <= 128 ? (float*)(base + o_X) : nullptr;
@@ -388,12 +395,13 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
     if (e == cudaSuccess)
         e = launch_setup_rules(pl->c, glr, gwr, gla, gwa, pl->rad, pl->ang, pl->theta, pl->xcol, pl->rows, pl->Rt,
                                pl->stream);
+    if (e == cudaSuccess && table) e = launch_series_init(pl->c, pl->stq, pl->scst, pl->stab, pl->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
     if (e != cudaSuccess) {
         free_plan(pl);
         return DSE_ERR_CUDA;
     }
-    pl->launches = 5;
+    pl->launches = table ? 6 : 5;
     *out = pl;
     return DSE_OK;
 }
