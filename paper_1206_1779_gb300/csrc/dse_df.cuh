@@ -41,6 +41,17 @@ __device__ __forceinline__ void df_fma(float2& c, const float2 a, const float2 b
     c.x = sm;
 }
 
+// 2 v exactly for finite |v| < 2^1023, by integer operations on its bits (the
+// exponent field plus one, or the significand shifted for zero and subnormals), so
+// that no FP64 instruction is spent on it.
+__device__ __forceinline__ double twice(double v) {
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    if (hi & 0x7ff00000) return __hiloint2double(hi + 0x00100000, (int)lo);
+    const unsigned mh = ((unsigned)hi << 1) | (lo >> 31);  // (the sign bit shifts out)
+    return __hiloint2double((int)((mh & 0x7fffffffu) | ((unsigned)hi & 0x80000000u)), (int)(lo << 1));
+}
+
 // f 2^(E - 1023) as a double, from the bits of f: the tile scale of phase B
 // folded into the exponent (zero and FP32 subnormals give 0, Inf/NaN or an
 // overflow give Inf/NaN).

@@ -31,6 +31,7 @@ struct Consts {
     int nrule, radmode, angmode, sM;  // sM: series-table intervals (0: no table)
     double eps2, lam2, ln_eps2, ln_lam2;
     double L0, L1, invL1;          // ln x = L0 + L1 s
+    double sL0;                    // -L0 / L1 (s = fma(ln x, invL1, sL0))
     double K;                      // g^2 Nc / (2 pi)^3
     double kappa, delta, gam;      // IR exponent, anomalous dimensions
     double pG, qZ;                 // vertex-model exponents on G and Z

@@ -1427,61 +1427,72 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale_rows_batched(const Batc
 constexpr int kReuseMax = 24;
 constexpr double kReuseRate = 0.5;
 
+// Row stride of the FP64 copy of J in shared memory: at least n and 4 mod 16
+// doubles, so that the loads of the residual (four threads per row, columns
+// j = part + 4 t, eight rows per warp) fall two by two into distinct bank pairs.
+__host__ __device__ inline int reg_ldj(int n) { return (n + 11) / 16 * 16 + 4; }
+
+// Upper bound of a non-negative double as a 32-bit key that orders like it (its
+// high word, plus one unit unless the low word is zero), and the double of a key
+// (which the key bounds from above when it came from key_up).
+__device__ __forceinline__ unsigned key_up(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v);
+    return hi + (__double2loint(v) != 0 && hi < 0x7ff00000u ? 1u : 0u);
+}
+__device__ __forceinline__ double key_value(unsigned k) { return __hiloint2double((int)k, 0); }
+
 __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, const float* Xs, const double* Sc,
                                            const double* Sn, const double* __restrict__ F, double* s_x, float* s_rf,
-                                           double (*s_red)[8], int* s_conv, double tolfac, int maxit,
+                                           unsigned (*s_red)[16], int* s_conv, double tolfac, int maxit,
                                            bool early_abort, int* sweeps) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double prev = INFINITY;  // lane 0 of warp 0 only
     int st = 0;
     for (int it = 0; it <= maxit; ++it) {
-        // residual: two threads per row (8 warps), each over half of the row
-        if (tid < 256) {
-            double rm = 0.0, xm = 0.0;
-            const int row = tid >> 1, hf = tid & 1;
+        // residual: four threads per row (16 warps), each over the columns
+        // j = part + 4 t in two chains; the maxima of |S r| and |x| as integer keys
+        // (one warp reduction each; the residual's key rounded up, x's down)
+        if (tid < 512) {
+            unsigned rk = 0u, xk = 0u;
+            const int row = tid >> 2, part = tid & 3;
             double acc = 0.0;
             if (row < n && it > 0) {  // x = 0 at the start: r = F
                 const double* Jr = Js + (size_t)row * ldj;
-                const int j0 = hf ? n / 2 : 0, j1 = hf ? n : n / 2;
                 double a0 = 0.0, a1 = 0.0;
-                int jj = j0;
+                int jj = part;
 #pragma unroll 4
-                for (; jj + 1 < j1; jj += 2) {
+                for (; jj + 4 < n; jj += 8) {
                     a0 = fma(Jr[jj], s_x[jj], a0);
-                    a1 = fma(Jr[jj + 1], s_x[jj + 1], a1);
+                    a1 = fma(Jr[jj + 4], s_x[jj + 4], a1);
                 }
-                if (jj < j1) a0 = fma(Jr[jj], s_x[jj], a0);
+                if (jj < n) a0 = fma(Jr[jj], s_x[jj], a0);
                 acc = a0 + a1;
             }
             acc += __shfl_xor_sync(kFullMask, acc, 1);
-            if (row < n && hf == 0) {
+            acc += __shfl_xor_sync(kFullMask, acc, 2);
+            if (row < n && part == 0) {
                 const double r = F[row] - acc;
                 s_rf[row] = (float)(Sc[row] * r);
                 const double rn = Sn[row] * r;
-                rm = isfinite(rn) ? fabs(rn) : INFINITY;
-                xm = fabs(s_x[row]);
+                rk = isfinite(rn) ? key_up(fabs(rn)) : 0x7ff00000u;
+                xk = (unsigned)__double2hiint(fabs(s_x[row]));
             }
-            for (int off = 16; off > 0; off >>= 1) {
-                rm = fmax(rm, __shfl_xor_sync(kFullMask, rm, off));
-                xm = fmax(xm, __shfl_xor_sync(kFullMask, xm, off));
-            }
+            rk = __reduce_max_sync(kFullMask, rk);
+            xk = __reduce_max_sync(kFullMask, xk);
             if (lane == 0) {
-                s_red[0][warp] = rm;
-                s_red[1][warp] = xm;
+                s_red[0][warp] = rk;
+                s_red[1][warp] = xk;
             }
         }
         __syncthreads();
         if (warp == 0) {
-            // the maxima over the eight warps by shuffles (a single thread's FP64
-            // chain is slow here), the decision by lane 0
-            double RM = s_red[0][lane & 7], XM = s_red[1][lane & 7];
-            for (int off = 4; off > 0; off >>= 1) {
-                RM = fmax(RM, __shfl_xor_sync(kFullMask, RM, off));
-                XM = fmax(XM, __shfl_xor_sync(kFullMask, XM, off));
-            }
+            // the maxima over the sixteen warps, the decision by lane 0
+            const unsigned RK = __reduce_max_sync(kFullMask, lane < 16 ? s_red[0][lane] : 0u);
+            const unsigned XK = __reduce_max_sync(kFullMask, lane < 16 ? s_red[1][lane] : 0u);
             if (lane == 0) {
+                const double RM = key_value(RK), XM = key_value(XK);
                 int v = 0;  // 0: continue, 1: converged, 2: give up
-                if (!isfinite(RM)) v = 2;
+                if (!(RK < 0x7ff00000u)) v = 2;
                 else if (RM <= tolfac * XM) v = 1;
                 else if (it == maxit) v = 2;
                 else if (early_abort && it > 0) {
@@ -1565,15 +1576,15 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     __shared__ double s_scale[128];
     __shared__ double s_sold[128];
     __shared__ float s_rf[128];
-    __shared__ double s_red[2][8];
+    __shared__ unsigned s_red[2][16];
     __shared__ int s_piv, s_fail, s_done, s_conv, s_reuse;
     __shared__ double s_anorm;
     __shared__ float s_panel[2][kGjBlock][128];                // panel rows of a round (by round parity)
     __shared__ __align__(16) float s_colb[kGjBlock][kColPad];  // the round's pivot columns
     __shared__ unsigned char s_used[128];                      // columns pivoted so far
     const int n = c.n;
-    const int ldj = n + 1;
-    double* Js = dsm;                                             // [n][n+1] FP64 copy of J
+    const int ldj = reg_ldj(n);
+    double* Js = dsm;                                             // [n][ldj] FP64 copy of J
     float* Xs = reinterpret_cast<float*>(dsm + (size_t)n * ldj);  // [n][n] inverse
     // G groups of R consecutive rows; G * R <= n + R - 1 < kColPad and
     // G * n <= 1024 because the launcher picks R >= n / min(1024 / n, 32)
@@ -2254,7 +2265,7 @@ cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const 
         k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const size_t smem = sizeof(double) * (size_t)n * (n + 1) + sizeof(float) * (size_t)n * n;
+        const size_t smem = sizeof(double) * (size_t)n * reg_ldj(n) + sizeof(float) * (size_t)n * n;
         const int G = kGjThreads / n < 32 ? kGjThreads / n : 32;  // same as in the kernel
         const int R = (n + G - 1) / G;
 #define DSE_LAUNCH_REG(RR)                                                                                   \
@@ -2379,7 +2390,7 @@ cudaError_t launch_assemble_batched(bool full, const BatchProblem* P, int nb, do
 
 cudaError_t prepare_newton_batched(int max_n) {
     if (max_n > 128) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * (size_t)max_n * (max_n + 1) + sizeof(float) * (size_t)max_n * max_n;
+    const size_t smem = sizeof(double) * (size_t)max_n * reg_ldj(max_n) + sizeof(float) * (size_t)max_n * max_n;
     return cudaFuncSetAttribute(k_newton_reg_batched<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -2393,7 +2404,7 @@ cudaError_t launch_newton_batched(const BatchProblem* P, int nb, int max_n, doub
     // R = 16 serves every n <= 128: G = ceil(n/16) <= 8 groups, G n <= 1024 threads;
     // the shared-memory limit was set by prepare_newton_batched (this launch may
     // be captured into a graph)
-    const size_t smem = sizeof(double) * (size_t)max_n * (max_n + 1) + sizeof(float) * (size_t)max_n * max_n;
+    const size_t smem = sizeof(double) * (size_t)max_n * reg_ldj(max_n) + sizeof(float) * (size_t)max_n * max_n;
     k_newton_reg_batched<16><<<nb, kGjThreads, smem, s>>>(const_cast<BatchProblem*>(P), coef_base, tol, rho_relax,
                                                            n_relax, n_active);
     return cudaGetLastError();

@@ -16,11 +16,11 @@ namespace {
 //          c = ln(1 + r) - r = -r^2 (1/2 - r/3 + r^2/4 - r^3/5 + r^4/6) (|c| < 2^-16.8);
 //   1/z = 2^-e inv_j ((1 - r) + [d]),  d = 1/(1 + r) - (1 - r) = r^2 (1 - r + r^2 - r^3 + r^4);
 // where the bracketed small terms are formed in double-float on the FP32 pipe (they
-// need about 40 significant bits) and only the leading sums, the product by inv_j and
-// the FMAs of r and of e ln2_hi take the FP64 pipe (10 FP64 operations).  ln2 = ln2_hi
+// need about 40 significant bits) and only the leading sums and the FMAs of r, of
+// e ln2_hi and of inv_j (1 - r) + inv_j d take the FP64 pipe (9 FP64 operations).  ln2 = ln2_hi
 // + ln2_lo with ln2_hi holding 42 significant bits, so e ln2_hi is exact.  Accuracy
 // (tests/test_ln_rcp.py, an emulation of these operations against 40-digit values over
-// z in [1e-14, 1e8]): ln z within 2 units of 2^-53 max(1, |ln z|), 1/z within 3 units in
+// z in [1e-14, 1e8]): ln z within 2 units of 2^-53 max(1, |ln z|), 1/z within 2 units in
 // the last place.  Zero, subnormal, negative, very large, infinite and NaN arguments
 // take the library routines.
 constexpr int kLnTab = 128;  // g_lntab: inv_j, L_j hi, L_j lo (kLnTab each), ln2_hi, ln2_lo
@@ -66,8 +66,9 @@ __device__ __forceinline__ LnRcp ln_rcp(double z) {
     const double ed = __hiloint2double(0x43380000, (int)((unsigned)e ^ 0x80000000u)) - 6755401588539392.0;
     const double hi = fma(ed, ln2h, Lh);
     o.ln = hi + ((r - df_widen(cm.x, 1023)) + df_widen(sl, 1023));
-    const double q = ((1.0 - r) + df_widen(dm.x, 1023)) + df_widen(dm.y, 1023);
-    const double t = q * inv;  // in (1/2, 1.004]: scaled by 2^-e in its exponent field
+    // inv (1 - r + d) = inv (1 - r) + inv d: two FMAs (d exact in FP64 as hi + lo)
+    const double t = fma(inv, df_widen(dm.x, 1023) + df_widen(dm.y, 1023), fma(-inv, r, inv));
+    // t in (1/2, 1.004]: scaled by 2^-e in its exponent field
     o.rcp = __hiloint2double(__double2hiint(t) - (e << 20), __double2loint(t));
     return o;
 }

@@ -110,6 +110,7 @@ Consts make_consts(const dse_problem* p) {
     c.L0 = 0.5 * (c.ln_eps2 + c.ln_lam2);
     c.L1 = 0.5 * (c.ln_lam2 - c.ln_eps2);
     c.invL1 = 1.0 / c.L1;
+    c.sL0 = -c.L0 * c.invL1;
     c.K = p->g2nc / (8.0 * kPi * kPi * kPi);
     c.kappa = p->kappa;
     c.delta = p->delta;

@@ -119,12 +119,14 @@ __device__ __forceinline__ void series_eval(const SeriesRec* __restrict__ R, con
 // (T_4i hi, lo, T_4i+1 hi, lo).  sd is s as a double-float pair.
 __device__ __forceinline__ void store_anchors(const double s, const float2 sd, const int nq,
                                               float4* __restrict__ dst) {
-    const double T2 = fma(2.0 * s, s, -1.0);
-    const double T3 = fma(2.0 * s, T2, -s);
-    const double T4 = fma(2.0 * T2, T2, -1.0);
-    const float2 c4 = df_split(2.0 * T4, 0);
+    // (the doublings by integer operations: four FMAs on the FP64 pipe)
+    const double s2 = twice(s);
+    const double T2 = fma(s2, s, -1.0);
+    const double T3 = fma(s2, T2, -s);
+    const double T4 = fma(twice(T2), T2, -1.0);
+    const float2 c4 = df_split(T4, -1);  // 2 T4
     float2 a0 = make_float2(1.0f, 0.0f), a1 = df_split(T4, 0);
-    float2 b0 = sd, b1 = df_split(fma(2.0 * s, T4, -T3), 0);
+    float2 b0 = sd, b1 = df_split(fma(s2, T4, -T3), 0);
     for (int i = 1; i < nq; ++i) {
         dst[i - 1] = make_float4(a1.x, a1.y, b1.x, b1.y);
         const float2 an = df_mulsub(c4, a1, a0);
@@ -192,9 +194,10 @@ __device__ __forceinline__ TripleW triple_weights(const TripleArgs& A, const boo
     const double z = fma(f[1], an.sig, f[0]);
     const LnRcp lr = ln_rcp(z);
     const double lz = lr.ln;
-    // s(z), clamped to [-1, 1] for z outside [eps2, lambda2] (inside, it can leave
-    // the interval only by a rounding)
-    double s = (lz - c.L0) * c.invL1;
+    // s(z) = ln z / L1 - L0 / L1 (one FMA; the same value as (ln z - L0) / L1 rounded
+    // twice when L0 = 0, i.e. eps2 lambda2 = 1), clamped to [-1, 1] for z outside
+    // [eps2, lambda2] (inside, it can leave the interval only by a rounding)
+    double s = fma(lz, c.invL1, c.sL0);
     const double iz = lr.rcp;
     const double iz2 = iz * iz;
     double Zz = 0.0, Gz = 0.0, Wz = 0.0;  // Z(z), G(z), W(z) = G(z)^p Z(z)^q

@@ -9,7 +9,7 @@ FP64 FMA), forms the small terms c = ln(1 + r) - r and d = 1/(1 + r) - (1 - r) i
 double-float (FP32 pairs) and adds them to the FP64 leading parts.  Each FP32
 operation below rounds once (numpy float32), FMA is exact rational arithmetic
 rounded once, FP64 operations are Python floats.  Pinned: ln z within 2 units of
-2^-53 max(1, |ln z|) and 1/z within 3 units in the last place.  A dropped term of
+2^-53 max(1, |ln z|) and 1/z within 2 units in the last place.  A dropped term of
 either series, a wrong sign, or the small terms computed in plain FP32 break it.
 """
 import math
@@ -63,8 +63,8 @@ def ln_rcp(z, t, third, ln2lo_f):
     dm = _dmul((p2, e2), (qh, ql))
     hi = _fma64(float(e), ln2h, Lh)
     ln = hi + ((r - cm[0]) + sl)
-    q = ((1.0 - r) + dm[0]) + dm[1]
-    rcp = math.ldexp(q * inv, -e)
+    t1 = _fma64(-inv, r, inv)
+    rcp = math.ldexp(_fma64(inv, dm[0] + dm[1], t1), -e)
     return ln, rcp
 
 
@@ -97,4 +97,4 @@ def test_ln_rcp_bounds():
         worst_rcp = max(worst_rcp, err_rcp)
     print("ln z: worst %.2f units of 2^-53 max(1, |ln z|); 1/z: worst %.2f ulp" % (worst_ln, worst_rcp))
     assert worst_ln <= 2.0
-    assert worst_rcp <= 3.0
+    assert worst_rcp <= 2.0
