@@ -63,20 +63,25 @@ __device__ __forceinline__ void series_eval_df(const SeriesRec* __restrict__ R, 
                                                const bool w, float2& Zm, float2& Gm, float2& Wm, int& Zs, int& Gs,
                                                int& Ws) {
     const int kf = __reduce_max_sync(__activemask(), __ldg(&R->ex[3]));
+    // (kf is the same on every lane: two loops, the FP32 tail from degree
+    // kSeriesP - 1 down to kf, then the double-float steps, instead of a branch
+    // per degree)
     if (zg) {
         const float4 top = __ldg(&R->e[kSeriesP]);
         float2 tz = make_float2(top.x, kf > kSeriesP ? top.y : 0.0f);
         float2 tg = make_float2(top.z, kf > kSeriesP ? top.w : 0.0f);
-#pragma unroll
-        for (int k = kSeriesP - 1; k >= 0; --k) {
+        int k = kSeriesP - 1;
+#pragma unroll 4
+        for (; k >= kf; --k) {
             const float4 ck = __ldg(&R->e[k]);
-            if (k >= kf) {
-                tz.x = fmaf(tz.x, uf.x, ck.x);
-                tg.x = fmaf(tg.x, uf.x, ck.z);
-            } else {
-                tz = df_muladd(tz, uf, make_float2(ck.x, ck.y));
-                tg = df_muladd(tg, uf, make_float2(ck.z, ck.w));
-            }
+            tz.x = fmaf(tz.x, uf.x, ck.x);
+            tg.x = fmaf(tg.x, uf.x, ck.z);
+        }
+#pragma unroll 4
+        for (; k >= 0; --k) {
+            const float4 ck = __ldg(&R->e[k]);
+            tz = df_muladd(tz, uf, make_float2(ck.x, ck.y));
+            tg = df_muladd(tg, uf, make_float2(ck.z, ck.w));
         }
         const int2 ex = __ldg(reinterpret_cast<const int2*>(R->ex));
         Zm = tz;
@@ -87,12 +92,11 @@ __device__ __forceinline__ void series_eval_df(const SeriesRec* __restrict__ R, 
     if (w) {
         const float2 top = __ldg(&R->w[kSeriesP]);
         float2 tw = make_float2(top.x, kf > kSeriesP ? top.y : 0.0f);
-#pragma unroll
-        for (int k = kSeriesP - 1; k >= 0; --k) {
-            const float2 ck = __ldg(&R->w[k]);
-            if (k >= kf) tw.x = fmaf(tw.x, uf.x, ck.x);
-            else tw = df_muladd(tw, uf, ck);
-        }
+        int k = kSeriesP - 1;
+#pragma unroll 4
+        for (; k >= kf; --k) tw.x = fmaf(tw.x, uf.x, __ldg(&R->w[k]).x);
+#pragma unroll 4
+        for (; k >= 0; --k) tw = df_muladd(tw, uf, __ldg(&R->w[k]));
         Wm = tw;
         Ws = __ldg(&R->ex[2]) - 1023;
     }
@@ -205,7 +209,9 @@ __device__ __forceinline__ TripleW triple_weights(const TripleArgs& A, const boo
     const long long zb = __double_as_longlong(z);
     const bool beyond = zb < __double_as_longlong(c.eps2) || zb > __double_as_longlong(c.lam2);
     const bool outside = c.extrap == 0 && beyond;
-    if (beyond) s = fmin(1.0, fmax(-1.0, s));
+    // beyond the range s is +-1 exactly (s of the clamped z), chosen on the integer
+    // comparison (no FP64 operation)
+    if (beyond) s = zb > __double_as_longlong(c.lam2) ? 1.0 : -1.0;
     if (A.stab && !outside) {
         // from the table: the interval by arccos in FP32 (FP32 s from the bits of s,
         // truncated: the interval only; a neighbouring interval is as good), the
