@@ -102,7 +102,8 @@ def measure_alu_peaks(dse, local: int):
     clocks.start()
     out = {}
     for name, kind in (("fp64_fma", dse.DSE_PEAK_FP64_FMA), ("fp32_fma", dse.DSE_PEAK_FP32_FMA),
-                       ("mufu_ex2", dse.DSE_PEAK_MUFU_EX2), ("mufu_lg2", dse.DSE_PEAK_MUFU_LG2)):
+                       ("mufu_ex2", dse.DSE_PEAK_MUFU_EX2), ("mufu_lg2", dse.DSE_PEAK_MUFU_LG2),
+                       ("fp64_dmma", dse.DSE_PEAK_FP64_DMMA)):
         best = 0.0
         for _ in range(2):
             rate, _ms = dse.alu_peak(kind, 150.0)
@@ -111,6 +112,9 @@ def measure_alu_peaks(dse, local: int):
     clk = clocks.stop()
     out["fp64_tflops"] = 2.0 * out["fp64_fma_per_s"] / 1e12
     out["fp32_tflops"] = 2.0 * out["fp32_fma_per_s"] / 1e12
+    # the FP64 tensor cores (mma.sync m8n8k4) against the FP64 FMA pipe: the y-only
+    # contraction would move to them only if they were faster
+    out["fp64_dmma_tflops"] = 2.0 * out["fp64_dmma_per_s"] / 1e12
     out["clocks"] = clk
     out["how"] = ("dse_alu_peak: eight independent FMA (or exp2/log2) chains per thread, SM count x resident "
                   "blocks of 256 threads, ~150 ms per launch, CUDA events, best of 2")
@@ -171,16 +175,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_record(kernel_src: str):
+# the sources the hot kernel is compiled from (its translation unit and the headers it includes)
+HOT_KERNEL_SOURCES = [os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", f) for f in
+                      ("dse_triple.cu", "dse_df.cuh", "dse_lnrcp.cuh", "dse_lntab.cuh", "dse_internal.cuh")] + \
+                     [os.path.join(ROOT, "include", "dse.h")]
+
+
+def hot_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in HOT_KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def traffic_record():
     """ncu record of the hot kernel (DRAM bytes and warp instructions per launch at
-    the benchmark's size), if it was taken on the current kernel source (else None)."""
+    the benchmark's size), if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "triple_kernel_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    if rec.get("kernel_sha256") != h:
+    if rec.get("kernel_sources_sha256") != hot_kernel_hash():
         return None
     return rec
 
@@ -288,7 +304,7 @@ def run_gb300(args):
     achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = flops_launch / t_min / 1e12
     f64ops_pt, f64_pt, f32_pt, dfops_pt = work_per_triple(N)
-    rec = traffic_record(os.path.join(ROOT, "paper_1206_1779_gb300", "csrc", "dse_triple.cu"))
+    rec = traffic_record()
     traffic = rec.get("dram_bytes_per_launch_full_size") if rec else None
     issue = None
     if rec and rec.get("warp_instructions_per_launch"):
@@ -305,6 +321,9 @@ def run_gb300(args):
     diff = None
     if rank == 0 and not args.no_grad:
         diff = measure_differentiation(dse, args)
+    n16 = None
+    if rank == 0 and not args.no_n16:
+        n16 = measure_newton_matrix_n16(dse, args)
     n128 = None
     if rank == 0 and not args.no_n128:
         n128 = measure_mixed_n128(dse, args)
@@ -379,6 +398,8 @@ def run_gb300(args):
             line["mixed_precision"] = mixed
         if n128 is not None:
             line["mixed_precision_n128"] = n128
+        if n16 is not None:
+            line["newton_matrix_n16"] = n16
         if diff is not None:
             line["differentiation"] = diff
         if sweep is not None:
@@ -562,6 +583,56 @@ def measure_batch(dse, args):
             "graph_launches_per_sweep": int(max(its))}
 
 
+def measure_newton_matrix_n16(dse, args):
+    """The small configuration (newton_step_n16: N = 16 per function, 64 x 32 nodes):
+    time per dse_newton_matrix call, launched one by one and replayed from a CUDA
+    graph that captured one call (the launch overhead of the six kernels is what
+    the graph removes), over 200 calls each."""
+    import torch
+    p = inputs.workload_problem("newton_step_n16")
+    N, nr, na = p["n_cheb"], p["n_radial"], p["n_angular"]
+    reps = 200
+    with dse.Plan(p) as plan:
+        coef = torch.from_numpy(inputs.starting_guess(p, seed=0)).cuda()
+        J = torch.empty(2 * N, 2 * N, dtype=torch.float64, device="cuda")
+        F = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+        for _ in range(5):
+            plan.newton_matrix(coef, J, F)
+        stream = torch.cuda.current_stream()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(reps):
+            plan.newton_matrix(coef, J, F)
+        e[1].record(stream)
+        e[1].synchronize()
+        J1 = J.clone()
+        per_call_us = e[0].elapsed_time(e[1]) * 1e3 / reps
+        units = 4.0 * N * N * nr * na
+        out = {"workload": "newton_step_n16", "n_cheb": N, "n_radial": nr, "n_angular": na,
+               "per_call_us": per_call_us, "per_call_value": units / (per_call_us * 1e-6), "unit": UNIT}
+        try:
+            g = torch.cuda.CUDAGraph()
+            # (relaxed: the launchers set kernel attributes, a host call, while capturing)
+            with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                plan.newton_matrix(coef, J, F)
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            e[2].record(stream)
+            for _ in range(reps):
+                g.replay()
+            e[3].record(stream)
+            e[3].synchronize()
+            graph_us = e[2].elapsed_time(e[3]) * 1e3 / reps
+            out.update({"graph_replay_us": graph_us, "graph_replay_value": units / (graph_us * 1e-6),
+                        "graph_matches_calls": bool(torch.equal(J, J1))})
+        except Exception as exc:  # noqa: BLE001 (reported, not fatal)
+            out["graph_replay_us"] = None
+            out["graph_error"] = str(exc)[:200]
+    return out
+
+
 def measure_paper_algorithm(dse, args):
     """The paper's own discretisation and Jacobian at the benchmark's size: N = 64,
     the radial split [0, eps2] + [eps2, x] + [x, lambda2] with 85 nodes per piece
@@ -670,6 +741,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-n128", action="store_true")
+    ap.add_argument("--no-n16", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     args = ap.parse_args()

@@ -17,11 +17,15 @@ enum {
     DSE_PEAK_FP64_FMA = 0, /* FP64 fused multiply-add (2 flops each) */
     DSE_PEAK_FP32_FMA = 1, /* FP32 fused multiply-add (2 flops each) */
     DSE_PEAK_MUFU_EX2 = 2, /* FP32 base-2 exponential on the special-function unit */
-    DSE_PEAK_MUFU_LG2 = 3  /* FP32 base-2 logarithm on the special-function unit */
+    DSE_PEAK_MUFU_LG2 = 3, /* FP32 base-2 logarithm on the special-function unit */
+    DSE_PEAK_FP64_DMMA = 4 /* FP64 tensor-core multiply-add (mma.sync m8n8k4): one 8x8x4
+                              warp product counts as 256 FMAs, 8 per thread */
 };
 
 /* Rate of one arithmetic pipe on the current device, in operations per second
- * (thread-level: one FMA or one exp2 of one thread is one operation).
+ * (thread-level: one FMA or one exp2 of one thread is one operation; for
+ * DSE_PEAK_FP64_DMMA the FMAs of the warp's matrix products divided among its
+ * threads, so that the rate compares with DSE_PEAK_FP64_FMA's).
  *
  * kind:      one of the DSE_PEAK_* values.
  * target_ms: approximate duration of the timed launch in milliseconds (1 .. 5000);

@@ -32,6 +32,7 @@ DSE_PEAK_FP64_FMA = 0
 DSE_PEAK_FP32_FMA = 1
 DSE_PEAK_MUFU_EX2 = 2
 DSE_PEAK_MUFU_LG2 = 3
+DSE_PEAK_FP64_DMMA = 4
 
 
 class DseError(RuntimeError):

@@ -28,7 +28,16 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
-// iters x kUnroll x kChains operations per thread.
+// D = A B + D for one 8x8x4 FP64 tile of the warp (a and b: this thread's
+// elements of A and B, d: its two of D).
+__device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(d0), "+d"(d1)
+                 : "d"(a), "d"(b));
+}
+
+// iters x kUnroll x kChains operations per thread (for DMMA, matrix products:
+// 8 FMAs per thread each).
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) k_alu_peak(int iters, double seed) {
     const double t = seed + 1e-9 * threadIdx.x;
@@ -46,6 +55,21 @@ __global__ void __launch_bounds__(kThreads) k_alu_peak(int iters, double seed) {
         double s = 0.0;
 #pragma unroll
         for (int i = 0; i < kChains; ++i) s += a[i];
+        if (s == -1.0) g_peak_sink = s;
+    } else if (KIND == DSE_PEAK_FP64_DMMA) {
+        double d[kChains][2];
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) d[i][0] = d[i][1] = t + i;
+        const double a = 1e-4 * (1.0 + 1e-3 * (threadIdx.x & 31)), b = 1e-4;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int i = 0; i < kChains; ++i) dmma_8x8x4(d[i][0], d[i][1], a, b);
+        }
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) s += d[i][0] + d[i][1];
         if (s == -1.0) g_peak_sink = s;
     } else if (KIND == DSE_PEAK_FP32_FMA) {
         float a[kChains];
@@ -92,6 +116,7 @@ cudaError_t launch(int kind, int grid, int iters, cudaStream_t s) {
         case DSE_PEAK_FP64_FMA: return run<DSE_PEAK_FP64_FMA>(grid, iters, s);
         case DSE_PEAK_FP32_FMA: return run<DSE_PEAK_FP32_FMA>(grid, iters, s);
         case DSE_PEAK_MUFU_EX2: return run<DSE_PEAK_MUFU_EX2>(grid, iters, s);
+        case DSE_PEAK_FP64_DMMA: return run<DSE_PEAK_FP64_DMMA>(grid, iters, s);
         default: return run<DSE_PEAK_MUFU_LG2>(grid, iters, s);
     }
 }
@@ -108,6 +133,9 @@ int occupancy(int kind) {
             break;
         case DSE_PEAK_MUFU_EX2:
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alu_peak<DSE_PEAK_MUFU_EX2>, kThreads, 0);
+            break;
+        case DSE_PEAK_FP64_DMMA:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alu_peak<DSE_PEAK_FP64_DMMA>, kThreads, 0);
             break;
         default:
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alu_peak<DSE_PEAK_MUFU_LG2>, kThreads, 0);
@@ -129,7 +157,7 @@ cudaError_t timed(int kind, int grid, int iters, cudaStream_t s, cudaEvent_t e0,
 }  // namespace
 
 extern "C" int dse_alu_peak(int kind, double target_ms, void* stream, double* ops_per_s, double* ms) {
-    if (kind < DSE_PEAK_FP64_FMA || kind > DSE_PEAK_MUFU_LG2 || !ops_per_s || !(target_ms >= 1.0) ||
+    if (kind < DSE_PEAK_FP64_FMA || kind > DSE_PEAK_FP64_DMMA || !ops_per_s || !(target_ms >= 1.0) ||
         !(target_ms <= 5000.0))
         return DSE_ERR_ARG;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -167,7 +195,7 @@ extern "C" int dse_alu_peak(int kind, double target_ms, void* stream, double* op
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return DSE_ERR_CUDA;
-    const double ops = (double)grid * kThreads * (double)iters * kUnroll * kChains;
+    const double ops = (double)grid * kThreads * (double)iters * kUnroll * kChains * (kind == DSE_PEAK_FP64_DMMA ? 8 : 1);
     *ops_per_s = ops / (t * 1e-3);
     if (ms) *ms = t;
     return DSE_OK;

@@ -182,3 +182,34 @@ def test_batch_sweep_256(dse, oracle, inputs):
             gG, gZ = plan.dressing(to_dev(batch.split(cg)[b]), to_dev(x))
             gG, gZ = to_host(gG), to_host(gZ)
         assert np.max(np.abs(gG - lG)) < 1e-8 and np.max(np.abs(gZ - lZ)) < 1e-8
+
+
+def test_batch_sweep_matrices_per_order_pair(dse, oracle, inputs):
+    """The Newton matrices and residuals of the 256-problem sweep from one batched
+    call at the starting guesses: for every (N_Z, N_G) pair of the sweep, its first
+    problem with 256 x 128 nodes against the oracle at the full and the strict bar
+    (each problem of a batch is the Sec. 3 system with its own orders, quadrature
+    and G(x_G)^{-1})."""
+    probs = inputs.batch_problems(256)
+    c0 = np.concatenate([inputs.starting_guess(p, seed=b) for b, p in enumerate(probs)])
+    with dse.Batch(probs) as batch:
+        J, F = batch.newton_matrix(to_dev(c0))
+        Js = [to_host(m) for m in batch.matrices(J)]
+        Fs = batch.split(to_host(F))
+        cs = batch.split(c0)
+    first = {}
+    for b, p in enumerate(probs):
+        key = (p["n_cheb"], p["n_cheb_G"])
+        if p["n_radial"] == 256 and key not in first:
+            first[key] = b
+    assert len(first) == 16, sorted(first)  # every pair of {24, 32, 48, 64}^2 occurs
+    for key, b in sorted(first.items()):
+        p = probs[b]
+        Jo, Fo = oracle.newton_matrix(p, cs[b])
+        A, AF = oracle.newton_matrix_magnitudes(p, cs[b])
+        r = entries_ok(Js[b], Jo, A, column_index(p))
+        rF = entries_ok(Fs[b], Fo, AF)
+        print("orders %s (problem %d): J max err/A %.2e, strict %.2f of the bar, %.4f within 1e-11; "
+              "F max err/A %.2e" % (key, b, r.worst, r.strict_ratio, r.frac_rel, rF.worst))
+        assert r.ok and r.strict_ok, (key, b, r)
+        assert rF.ok and rF.strict_ok, (key, b, rF)
