@@ -95,6 +95,16 @@ __device__ __forceinline__ float2 df_mulsub(const float2 a, const float2 b, cons
     return make_float2(hi, lo - (hi - sm));
 }
 
+// a + b in double-float (renormalised; exact sum of the leading parts)
+__device__ __forceinline__ float2 df_add(const float2 a, const float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
 __device__ __forceinline__ void df_renorm(float2& c) {
     const float sm = c.x + c.y;
     c.y = c.y - (sm - c.x);

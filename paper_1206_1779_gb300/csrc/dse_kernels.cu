@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kSeriesDotThreads) k_series_table(const Consts
 constexpr int kRowBlock = 512;
 constexpr int kRowJ = 32;                   // coefficients per block (one per lane)
 constexpr int kRowKG = kRowBlock / kRowJ;   // radial-node groups per block
-constexpr int kChunkK = 512;
+constexpr int kChunkK = 256;
 
 // Grid: (row r, block of 32 coefficients).  Thread (k-group kg, lane) owns
 // coefficient j = 32 jb + lane, the radial nodes kk = kg mod kRowKG of each chunk
@@ -607,8 +607,11 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
                                                 const double* __restrict__ Vpart, double* __restrict__ D, const int r,
                                                 const int jb) {
     __shared__ double sU[kChunkK][3];
+    __shared__ float2 sUd[kChunkK][3];           // U at the chunk's scale, double-float
+    __shared__ unsigned sEm[3][kRowBlock / 32];  // per-warp maxima of U's exponents
     __shared__ double sY[kRowKG][3][kRowJ];
     __shared__ double sV[kRowKG][3][kRowJ];
+    __shared__ double sR[6][kRowJ];              // the six combined sums (Y_Q, Y_M, Y_G, V_Q, V_M, V_G)
     __shared__ double sS4;
     const int N = c.N;
     const int NZ = c.NZ, NG = c.NG, n = c.n, Rc = c.Rc;
@@ -643,6 +646,7 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
     __syncthreads();
     for (int kb = 0; kb < c.nr; kb += kChunkK) {
         const int kn = min(kChunkK, c.nr - kb);
+        unsigned e0 = 0u, e1 = 0u, e2 = 0u;
         for (int kk = tid; kk < kn; kk += kRowBlock) {
             const int k = kb + kk;
             double u0 = 0.0, u1 = 0.0, u2 = 0.0;
@@ -661,6 +665,35 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
             sU[kk][0] = u0;
             sU[kk][1] = u1;
             sU[kk][2] = u2;
+            e0 = max(e0, ((unsigned)__double2hiint(u0) >> 20) & 0x7ffu);
+            e1 = max(e1, ((unsigned)__double2hiint(u1) >> 20) & 0x7ffu);
+            e2 = max(e2, ((unsigned)__double2hiint(u2) >> 20) & 0x7ffu);
+        }
+        // the chunk's scale per kind: the largest biased exponent of its U values
+        if (FULL) {
+            e0 = __reduce_max_sync(kFullMask, e0);
+            e1 = __reduce_max_sync(kFullMask, e1);
+            e2 = __reduce_max_sync(kFullMask, e2);
+            if (lane == 0) {
+                sEm[0][kg] = e0;
+                sEm[1][kg] = e1;
+                sEm[2][kg] = e2;
+            }
+        }
+        __syncthreads();
+        int E0 = 0, E1 = 0, E2 = 0;
+        if (FULL) {
+#pragma unroll
+            for (int w = 0; w < kRowBlock / 32; ++w) {
+                E0 = max(E0, (int)sEm[0][w]);
+                E1 = max(E1, (int)sEm[1][w]);
+                E2 = max(E2, (int)sEm[2][w]);
+            }
+            for (int kk = tid; kk < kn; kk += kRowBlock) {
+                sUd[kk][0] = df_split(sU[kk][0], E0 - 1023);
+                sUd[kk][1] = df_split(sU[kk][1], E1 - 1023);
+                sUd[kk][2] = df_split(sU[kk][2], E2 - 1023);
+            }
         }
         __syncthreads();
         if (do_pi && kg == 0) {
@@ -671,13 +704,29 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
             }
         }
         if (FULL && j < N) {
-#pragma unroll 8
+            // the y-only contraction on the FP32 pipe: double-float products of the
+            // scaled U and phi_j(y_k), renormalised every four nodes, widened once
+            // per chunk (within ~2^-47 of the magnitudes it sums, like the z part)
+            float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, a2 = a0;
+            int q = 0;
+#pragma unroll 4
             for (int kk = kg; kk < kn; kk += kRowKG) {  // (unrolled: loads in flight, same order)
-                const double ph = phiy[(size_t)(kb + kk) * N + j];
-                Y0 = fma(sU[kk][0], ph, Y0);
-                Y1 = fma(sU[kk][1], ph, Y1);
-                Y2 = fma(sU[kk][2], ph, Y2);
+                const float2 ph = df_split(phiy[(size_t)(kb + kk) * N + j], 0);
+                df_fma(a0, sUd[kk][0], ph);
+                df_fma(a1, sUd[kk][1], ph);
+                df_fma(a2, sUd[kk][2], ph);
+                if ((++q & 3) == 0) {
+                    df_renorm(a0);
+                    df_renorm(a1);
+                    df_renorm(a2);
+                }
             }
+            df_renorm(a0);
+            df_renorm(a1);
+            df_renorm(a2);
+            Y0 += df_widen(a0.x, E0) + df_widen(a0.y, E0);
+            Y1 += df_widen(a1.x, E1) + df_widen(a1.y, E1);
+            Y2 += df_widen(a2.x, E2) + df_widen(a2.y, E2);
         }
         __syncthreads();
     }
@@ -686,43 +735,48 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
         sY[kg][1][lane] = Y1;
         sY[kg][2][lane] = Y2;
     }
-    // the z-derivative sums of the radial splits: warp kg adds the splits
-    // kg, kg + kRowKG, ... (independent loads in flight), warp 0 the warps' sums
-    // in a fixed order
+    // the z-derivative sums of the radial splits kg, kg + kRowKG, ...: in
+    // double-float at the thread's own scale (the largest exponent among its
+    // values, a first pass over them), widened once
     if (FULL && !special && j < N) {
         const double* vp = Vpart + (size_t)rt * KS * 3 * N;
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+        unsigned m0 = 0u, m1 = 0u, m2 = 0u;
 #pragma unroll 4
         for (int sp = kg; sp < KS; sp += kRowKG) {
-            v0 += vp[(size_t)sp * 3 * N + j];
-            v1 += vp[(size_t)sp * 3 * N + N + j];
-            v2 += vp[(size_t)sp * 3 * N + 2 * N + j];
+            m0 = max(m0, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + j]) >> 20) & 0x7ffu);
+            m1 = max(m1, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + N + j]) >> 20) & 0x7ffu);
+            m2 = max(m2, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + 2 * N + j]) >> 20) & 0x7ffu);
         }
-        sV[kg][0][lane] = v0;
-        sV[kg][1][lane] = v1;
-        sV[kg][2][lane] = v2;
+        float2 v0 = make_float2(0.0f, 0.0f), v1 = v0, v2 = v0;
+#pragma unroll 4
+        for (int sp = kg; sp < KS; sp += kRowKG) {
+            v0 = df_add(v0, df_split(vp[(size_t)sp * 3 * N + j], (int)m0 - 1023));
+            v1 = df_add(v1, df_split(vp[(size_t)sp * 3 * N + N + j], (int)m1 - 1023));
+            v2 = df_add(v2, df_split(vp[(size_t)sp * 3 * N + 2 * N + j], (int)m2 - 1023));
+        }
+        sV[kg][0][lane] = df_widen(v0.x, (int)m0) + df_widen(v0.y, (int)m0);
+        sV[kg][1][lane] = df_widen(v1.x, (int)m1) + df_widen(v1.y, (int)m1);
+        sV[kg][2][lane] = df_widen(v2.x, (int)m2) + df_widen(v2.y, (int)m2);
+    }
+    __syncthreads();
+    // the six sums over the groups in a fixed order, one per warp
+    if (FULL && kg < 6 && j < N) {
+        double v = 0.0;
+        if (kg < 3) {
+            for (int q = 0; q < kRowKG; ++q) v += sY[q][kg][lane];
+        } else if (!special) {
+            for (int q = 0; q < kRowKG; ++q) v += sV[q][kg - 3][lane];
+        }
+        sR[kg][lane] = v;
     }
     __syncthreads();
     const Row rw = rows[rt >= 0 ? rt : 0];
     const double pre = gluon ? rw.pre : 0.0;
     double* out = D + (size_t)r * ldD(c);
     if (FULL && kg == 0 && j < N) {
-        double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-        for (int q = 0; q < kRowKG; ++q) {
-            y0 += sY[q][0][lane];
-            y1 += sY[q][1][lane];
-            y2 += sY[q][2][lane];
-        }
-        double VQ = 0.0, VM = 0.0, VG = 0.0;
-        if (!special) {
-            for (int q = 0; q < kRowKG; ++q) {
-                VQ += sV[q][0][lane];
-                VM += sV[q][1][lane];
-                VG += sV[q][2][lane];
-            }
-        } else {
-            VG = y2;
-        }
+        const double y0 = sR[0][lane], y1 = sR[1][lane], y2 = sR[2][lane];
+        const double VQ = sR[3][lane], VM = sR[4][lane];
+        const double VG = special ? y2 : sR[5][lane];
         const double tq = y0 + VQ;
         if (j < NZ) {
             out[j] = gluon ? pre * c.qZ * tq : 0.0;

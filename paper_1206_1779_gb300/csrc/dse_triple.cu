@@ -43,16 +43,6 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 
 __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 : 64; }
 
-// a + b in double-float (renormalised; exact sum of the leading parts)
-__device__ __forceinline__ float2 df_add(const float2 a, const float2 b) {
-    const float s = a.x + b.x;
-    const float bb = s - a.x;
-    float e = (a.x - (s - bb)) + (b.x - bb);
-    e += a.y + b.y;
-    const float hi = s + e;
-    return make_float2(hi, e - (hi - s));
-}
-
 // Z(z), G(z) (zg) and W(z) (w) from the series-table record R at u = uf
 // (double-float): Horner over the kSeriesQ coefficients of each, the terms of
 // degree >= kf in FP32 on the leading parts (the record's tail is small enough
