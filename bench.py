@@ -353,6 +353,20 @@ def run_gb300(args):
         torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, time.perf_counter() - w0)
     e2e_value = world * e2e_steps * matrices_per_step * entries_nodes / e2e_s
+    # one Newton matrix (dse_newton_matrix: tables, series table, quadrature kernel,
+    # row contraction, assembly) at the seeded guess, 20 calls, CUDA events
+    Jm = torch.empty(2 * N, 2 * N, dtype=torch.float64, device="cuda")
+    Fm = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+    cm = torch.from_numpy(c0).cuda()
+    plan.newton_matrix(cm, Jm, Fm)
+    em = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    em[0].record(stream)
+    for _ in range(20):
+        plan.newton_matrix(cm, Jm, Fm)
+    em[1].record(stream)
+    em[1].synchronize()
+    newton_matrix_ms = em[0].elapsed_time(em[1]) / 20
     plan.close()
 
     cpu = None
@@ -369,6 +383,7 @@ def run_gb300(args):
                        "newton_matrices_per_step": matrices_per_step, "parallelism": "replicas%d" % world,
                        "l2": "flushed between steps (256 MiB write); working set < 2 MiB"},
             "solves_per_s": solves_per_s,
+            "newton_matrix_ms": newton_matrix_ms,
             "plan_create_s": t_plan,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
