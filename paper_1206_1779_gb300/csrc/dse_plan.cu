@@ -19,6 +19,7 @@ struct dse_plan {
     cudaStream_t side;
     cudaEvent_t fork, join;
     int Rt, KB, KS, nch;
+    int KB32, KS32;  // the radial split of the FP32-integrand kernel (mixed precision)
     // fixed workspace (one allocation)
     void* ws;
     Rad* rad;
@@ -148,6 +149,13 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 #define DSE_SPLIT_WAVES 8
 #endif
 constexpr int kSplitWaves = DSE_SPLIT_WAVES;
+// The FP32-integrand kernel's blocks hold at least this many radial nodes: its
+// per-block set-up and final group sums weigh more against its cheaper tiles
+// (measured at N = 64 with 256 x 128 nodes).
+#ifndef DSE_MIXED_SPLIT_NODES
+#define DSE_MIXED_SPLIT_NODES 4
+#endif
+constexpr int kMixedSplitNodes = DSE_MIXED_SPLIT_NODES;
 
 void choose_split(dse_plan* pl) {
     int dev = 0, nsm = 152;
@@ -162,6 +170,9 @@ void choose_split(dse_plan* pl) {
     while ((nr + kb - 1) / kb > 128) ++kb;
     pl->KB = (int)kb;
     pl->KS = (int)((nr + kb - 1) / kb);
+    const long long kb32 = kb > kMixedSplitNodes ? kb : (kMixedSplitNodes < nr ? kMixedSplitNodes : nr);
+    pl->KB32 = (int)kb32;
+    pl->KS32 = (int)((nr + kb32 - 1) / kb32);  // <= KS: the split sums fit the same buffer
 }
 
 void release_events(dse_plan* pl) {
@@ -233,16 +244,19 @@ cudaError_t build_rows(dse_plan* pl, const double* coef, bool full, bool fp32) {
         }
         if (e == cudaSuccess) e = cudaEventRecord(pl->ev[2 * pl->n_ev], pl->stream);
     }
-    if (e == cudaSuccess)
-        e = fp32 ? launch_triple32(full, triple_args(pl, coef), pl->stream)
-                 : launch_triple(full, triple_args(pl, coef), pl->stream);
+    TripleArgs a = triple_args(pl, coef);
+    if (fp32) {
+        a.KB = pl->KB32;
+        a.KS = pl->KS32;
+    }
+    if (e == cudaSuccess) e = fp32 ? launch_triple32(full, a, pl->stream) : launch_triple(full, a, pl->stream);
     if (timed && e == cudaSuccess) {
         e = cudaEventRecord(pl->ev[2 * pl->n_ev + 1], pl->stream);
         ++pl->n_ev;
     }
     pl->launches += 4;
     if (e == cudaSuccess)
-        e = launch_rowreduce(full, pl->c, pl->Rt, pl->KS, pl->nch, pl->rad, pl->ang, pl->rows, pl->ytab, pl->phiy,
+        e = launch_rowreduce(full, pl->c, pl->Rt, a.KS, pl->nch, pl->rad, pl->ang, pl->rows, pl->ytab, pl->phiy,
                              pl->Upart, pl->Vpart, pl->D, pl->stream);
     return e;
 }
