@@ -100,8 +100,8 @@ extern "C" int dse_residual_static(const dse_problem* problem, const double* d_c
     int* status = (int*)(b + L.status);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    // radial splits: about eight waves of blocks over the resident slots (the rule
-    // of the plans); the queries allocate nothing
+    // radial splits: about eight waves of blocks over the resident slots, at least
+    // two radial nodes per block, at most 128 splits; the queries allocate nothing
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)

@@ -136,19 +136,20 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? DSE_OK : DSE_ERR_CUDA
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Radial nodes per block: about eight waves of Rt * KS blocks over the resident
-// slots, so that the block scheduler evens out rows of unequal cost (rows near
-// Lambda^2 evaluate the UV forms with exponentials for many triples); at least
-// two radial nodes per block and at most 128 splits.  Measured at N = 64 with
-// 256 x 128 nodes on an earlier version of the kernel: one wave (KS = 11) 0.84 ms
-// per launch, KS = 23 / 35 / 47 / 64: 0.81 / 0.78 / 0.76 / 0.74 ms; on the current
-// one KS = 64 / 128: 0.617 / 0.608 ms.
-// Radial splits of the quadrature kernel: about kSplitWaves waves of blocks over the
-// resident slots, at least two radial nodes per block, at most 128 splits.
+// Radial nodes per block: several waves of Rt * KS blocks over the resident slots,
+// so that the block scheduler evens out rows of unequal cost (rows near Lambda^2
+// evaluate the UV forms with exponentials for many triples); at least two radial
+// nodes per block and at most 128 splits.  Measured at N = 64 with 256 x 128 nodes
+// on an earlier version of the kernel: one wave (KS = 11) 0.84 ms per launch,
+// KS = 23 / 35 / 47 / 64: 0.81 / 0.78 / 0.76 / 0.74 ms.
 #ifndef DSE_SPLIT_WAVES
 #define DSE_SPLIT_WAVES 8
 #endif
 constexpr int kSplitWaves = DSE_SPLIT_WAVES;
+// With 128-thread blocks (N <= 96) fewer, longer blocks pay: at N = 64 with 256 x 128
+// nodes one Newton matrix took 0.480 / 0.472 / 0.470 / 0.513 ms for 8 / 6 / 4 / 2 waves,
+// while at N = 128 (64-thread blocks, 512 x 256 nodes) 5.50 / 5.61 / 5.84 / 6.81 ms.
+constexpr int kSplitWavesWide = 6;
 // The FP32-integrand kernel's blocks hold at least this many radial nodes: its
 // per-block set-up and final group sums weigh more against its cheaper tiles
 // (measured at N = 64 with 256 x 128 nodes).
@@ -164,7 +165,8 @@ void choose_split(dse_plan* pl) {
     if (occ < 1) occ = 1;
     const long long slots = (long long)nsm * occ;
     const int nr = pl->c.nr;
-    long long kb = ((long long)nr * pl->Rt) / (kSplitWaves * slots);
+    const int waves = triple_block_threads(pl->c.N) == 128 ? kSplitWavesWide : kSplitWaves;
+    long long kb = ((long long)nr * pl->Rt) / (waves * slots);
     if (kb < 2) kb = 2;
     if (kb > nr) kb = nr;
     while ((nr + kb - 1) / kb > 128) ++kb;
