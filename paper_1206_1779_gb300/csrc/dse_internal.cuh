@@ -191,6 +191,24 @@ cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const 
                              double* coef, double rho, double* work, float* As, double2* rowinfo,
                              double* stats, int* status, cudaStream_t s, float* Xinv = nullptr,
                              double* Sinv = nullptr, int* xstate = nullptr, int* done = nullptr);
+// Control block of a Newton iteration run as one CUDA graph (a while node whose
+// body is one Newton step followed by the decision kernel).
+struct SolveCtl {
+    double tol;       // stop when the dimensionless residual of a step is below it
+    int max_steps;    // at most this many steps
+    int steps;        // steps taken
+    int status;       // the status word when the iteration stopped
+    int converged;    // 1 when it stopped on tol
+    double stats[4];  // the last step's stats (max|F|, dimensionless residual, max|Delta|, sweeps)
+};
+// begin: ctl <- (tol, max_steps), dst[0..n) <- src; decide: after a step, counts it
+// and sets the while node's condition (0: stop on a status, on tol or at max_steps);
+// end: dst[0..n) <- src.
+cudaError_t launch_solve_begin(SolveCtl* ctl, double tol, int max_steps, const double* src, double* dst, int n,
+                               cudaStream_t s);
+cudaError_t launch_solve_decide(SolveCtl* ctl, const double* stats, const int* status,
+                                cudaGraphConditionalHandle cond, cudaStream_t s);
+cudaError_t launch_solve_end(const double* src, double* dst, int n, cudaStream_t s);
 size_t newton_lu32_smem_bytes(int n);
 cudaError_t launch_newton_lu32(const Consts& c, const double* J, float* As, const double2* rowinfo, const double* F,
                                const XTab* xtab, double* coef, double rho, double* stats, int* status, int* done,

@@ -2300,6 +2300,54 @@ cudaError_t launch_rowreduce(bool full, const Consts& c, int Rt, int KS, int nch
     return cudaGetLastError();
 }
 
+// ---- Newton iteration as a device-driven loop (the body of a CUDA-graph while node)
+__global__ void k_solve_begin(SolveCtl* __restrict__ ctl, double tol, int max_steps, const double* __restrict__ src,
+                              double* __restrict__ dst, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+        ctl->tol = tol;
+        ctl->max_steps = max_steps;
+        ctl->steps = 0;
+        ctl->status = 0;
+        ctl->converged = 0;
+    }
+}
+
+// The stopping rule of the host loop: a status word set by any kernel of the
+// step, the dimensionless residual below tol (a NaN never is), or the step limit.
+__global__ void k_solve_decide(SolveCtl* __restrict__ ctl, const double* __restrict__ stats,
+                               const int* __restrict__ status, cudaGraphConditionalHandle cond) {
+    const int steps = ctl->steps + 1;
+    const int st = *status;
+    const bool conv = st == 0 && stats[1] < ctl->tol;
+    ctl->steps = steps;
+    ctl->status = st;
+    ctl->converged = conv ? 1 : 0;
+    for (int k = 0; k < 4; ++k) ctl->stats[k] = stats[k];
+    cudaGraphSetConditional(cond, (st != 0 || conv || steps >= ctl->max_steps) ? 0u : 1u);
+}
+
+__global__ void k_copy_vector(const double* __restrict__ src, double* __restrict__ dst, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_solve_begin(SolveCtl* ctl, double tol, int max_steps, const double* src, double* dst, int n,
+                               cudaStream_t s) {
+    k_solve_begin<<<1, 256, 0, s>>>(ctl, tol, max_steps, src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_decide(SolveCtl* ctl, const double* stats, const int* status,
+                                cudaGraphConditionalHandle cond, cudaStream_t s) {
+    k_solve_decide<<<1, 1, 0, s>>>(ctl, stats, status, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_end(const double* src, double* dst, int n, cudaStream_t s) {
+    k_copy_vector<<<1, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const double* phix, const double* D,
                             double* J, double* F, int* status, cudaStream_t s) {
     const long long total = (full ? (long long)c.n * c.n : 0) + c.n;

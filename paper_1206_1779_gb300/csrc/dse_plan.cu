@@ -59,6 +59,16 @@ struct dse_plan {
     size_t sch_partial_cap;
     // pinned host mirror of stats + status
     double* h_misc;
+    // the Newton iteration as one CUDA graph: a while node whose body is one
+    // Newton step with rho = 1 and FP64 residual, then the decision kernel
+    // (captured on cap at the first dse_solve that can use it)
+    cudaStream_t cap;
+    cudaGraphExec_t sgx;
+    int sg_state;            // 0 not built, 1 built, -1 unavailable (host-driven loop)
+    long long sg_launches;   // kernels per iteration of the body
+    double* coef_g;          // the coefficient vector the body's kernels update
+    SolveCtl* ctl;           // device control block
+    SolveCtl* h_ctl;         // pinned host copy
     // instrumentation
     long long launches;
     int profiling;
@@ -152,7 +162,8 @@ constexpr int kSplitWaves = DSE_SPLIT_WAVES;
 constexpr int kSplitWavesWide = 6;
 // The FP32-integrand kernel's blocks hold at least this many radial nodes: its
 // per-block set-up and final group sums weigh more against its cheaper tiles
-// (measured at N = 64 with 256 x 128 nodes).
+// (one Newton matrix at N = 64 with 256 x 128 nodes: 0.529 ms at two nodes per
+// block, 0.486 ms at four; eight and sixteen were slower).
 #ifndef DSE_MIXED_SPLIT_NODES
 #define DSE_MIXED_SPLIT_NODES 4
 #endif
@@ -189,9 +200,19 @@ void free_fd(dse_plan* pl) {
     pl->fd_buf = nullptr;
 }
 
+void free_solve_graph(dse_plan* pl) {
+    if (pl->sg_state == 1) cudaGraphExecDestroy(pl->sgx);
+    pl->sg_state = 0;
+}
+
 void free_plan(dse_plan* pl) {
     if (!pl) return;
     free_fd(pl);
+    free_solve_graph(pl);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    if (pl->coef_g) cudaFree(pl->coef_g);
+    if (pl->ctl) cudaFree(pl->ctl);
+    if (pl->h_ctl) cudaFreeHost(pl->h_ctl);
     release_events(pl);
     if (pl->fork) cudaEventDestroy(pl->fork);
     if (pl->join) cudaEventDestroy(pl->join);
@@ -494,6 +515,98 @@ int newton_step_impl(dse_plan* plan, double* d_coeffs, double rho, double* h_sta
     if (e != cudaSuccess) return DSE_ERR_CUDA;
     return read_status(plan, h_stats);
 }
+
+// Captures the Newton step (rho = 1, FP64 residual) and the decision kernel into
+// the body of a while node.  The capture runs on the plan's private stream, so
+// that the graph can be launched on any stream, the legacy default one included.
+// On any failure the plan keeps the host-driven loop (sg_state = -1).
+void build_solve_graph(dse_plan* pl) {
+    pl->sg_state = -1;
+    const int n = pl->c.n;
+    if (!pl->cap && cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        pl->cap = nullptr;
+        return;
+    }
+    if (!pl->coef_g && cudaMalloc(&pl->coef_g, sizeof(double) * n) != cudaSuccess) {
+        pl->coef_g = nullptr;
+        return;
+    }
+    if (!pl->ctl && cudaMalloc(&pl->ctl, sizeof(SolveCtl)) != cudaSuccess) {
+        pl->ctl = nullptr;
+        return;
+    }
+    if (!pl->h_ctl && cudaMallocHost(&pl->h_ctl, sizeof(SolveCtl)) != cudaSuccess) {
+        pl->h_ctl = nullptr;
+        return;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return;
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    cudaGraphNode_t node;
+    bool ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const cudaStream_t user = pl->stream;
+        const long long l0 = pl->launches;
+        pl->stream = pl->cap;
+        ok = cudaStreamBeginCaptureToGraph(pl->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            int st = build_newton(pl, pl->coef_g, pl->J, pl->F, true);
+            cudaError_t e = st ? cudaErrorUnknown
+                               : launch_lu_newton(pl->c, pl->J, pl->F, pl->xtab, pl->coef_g, 1.0, pl->work, pl->As,
+                                                  pl->rowinfo, pl->stats, pl->status, pl->cap, pl->Xinv, pl->Sinv,
+                                                  pl->xstate, pl->lu_done);
+            pl->launches += pl->c.n <= 128 ? 2 : pl->c.n <= 160 ? 1 : 3;
+            if (e == cudaSuccess) e = launch_solve_decide(pl->ctl, pl->stats, pl->status, cond, pl->cap);
+            cudaGraph_t out = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(pl->cap, &out);
+            ok = e == cudaSuccess && ec == cudaSuccess;
+        }
+        pl->sg_launches = pl->launches - l0 + 1;
+        pl->launches = l0;
+        pl->stream = user;
+    }
+    if (ok) ok = cudaGraphInstantiate(&pl->sgx, g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    cudaGetLastError();  // a failed capture leaves no sticky error; clear the last one
+    if (ok) pl->sg_state = 1;
+}
+
+// Runs at most max_steps Newton steps through the graph: copies the coefficients
+// in, launches the while node, copies them back and reads the control block.
+// Returns DSE_OK (converged), DSE_ERR_NOT_CONVERGED (step limit) or the status
+// of the step that stopped it; *taken = the steps run, st4 = their last stats.
+int run_solve_graph(dse_plan* pl, double* d_coeffs, double tol, int max_steps, int* taken, double* st4) {
+    const cudaStream_t s = pl->stream;
+    const int n = pl->c.n;
+    *taken = 0;
+    cudaError_t e = launch_solve_begin(pl->ctl, tol, max_steps, d_coeffs, pl->coef_g, n, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(pl->sgx, s);
+    if (e == cudaSuccess) e = launch_solve_end(pl->coef_g, d_coeffs, n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl->h_ctl, pl->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return DSE_ERR_CUDA;
+    const SolveCtl& h = *pl->h_ctl;
+    *taken = h.steps;
+    memcpy(st4, h.stats, 4 * sizeof(double));
+    pl->launches += 2 + (long long)h.steps * pl->sg_launches;
+    if (h.status) {
+        e = cudaMemsetAsync(pl->status, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return DSE_ERR_CUDA;
+        if (h.status & kStatusSingular) return DSE_ERR_SINGULAR;
+        if (h.status & kStatusNonfinite) return DSE_ERR_NONFINITE;
+    }
+    return h.converged ? DSE_OK : DSE_ERR_NOT_CONVERGED;
+}
 }  // namespace
 
 int dse_newton_step(dse_plan* plan, double* d_coeffs, double rho, double* h_stats) {
@@ -516,6 +629,19 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
     // every solve starts without a kept inverse, so its steps depend on its input alone
     if (cudaMemsetAsync(plan->xstate, 0, sizeof(int), plan->stream) != cudaSuccess) return DSE_ERR_CUDA;
     for (; it < max_iter; ++it) {
+        // past the relaxed steps and the FP32 residuals, the remaining steps run as
+        // one CUDA graph with the stopping test on the device (no host round trip per
+        // step); the host loop serves instrumented plans, whose events a graph body
+        // cannot hold
+        if (f64_res && it >= n_relax && !plan->profiling) {
+            if (plan->sg_state == 0) build_solve_graph(plan);
+            if (plan->sg_state == 1) {
+                int taken = 0;
+                st = run_solve_graph(plan, d_coeffs, tol, max_iter - it, &taken, st3);
+                it += taken;
+                break;
+            }
+        }
         const double rho = it < n_relax ? rho_relax : 1.0;
         const int s = newton_step_impl(plan, d_coeffs, rho, st3, f64_res);
         if (!s && !f64_res && (st3[1] < kSwitch || (it >= n_relax && st3[1] > 0.5 * prev))) {
@@ -602,6 +728,7 @@ int dse_plan_set_couplings(dse_plan* plan, double g2nc, double ginv_G, double zi
     if (st) return st;
     plan->prob = p;
     plan->c = make_consts(&p);
+    free_solve_graph(plan);  // its kernels hold the old constants
     plan->launches += 1;
     if (plan->fd_batch) {
         cudaError_t e = cudaStreamSynchronize(plan->stream);
