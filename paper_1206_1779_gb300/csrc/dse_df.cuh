@@ -121,4 +121,61 @@ __device__ __forceinline__ float2 df_mul(const float2 a, const float2 b) {
     return make_float2(hi, e - (hi - p));
 }
 
+// ---- two double-float values at once, on the paired FP32 instructions of this GPU
+// (f32x2: one instruction serves both lanes of a float2, each lane rounded exactly
+// as the scalar instruction).  A pair of double-float values is (h, l): h holds the
+// two leading parts, l the two trailing parts.  Each routine below gives, lane by
+// lane, the bits of the scalar routine of the same name, with half the issued
+// instructions.  Subtraction is a - b = fma(b, -1, a) (one rounding, the same
+// result as the subtraction, signed zeros included).
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, make_float2(-1.0f, -1.0f)); }
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+
+// (ch, cl) += (ah, al) (bh, bl) lane by lane (df_fma), given nbh = -bh: the
+// product's leading part enters as -p = ah nbh, so that its rounding error is
+// fma(ah, bh, -p) without a negation per product
+__device__ __forceinline__ void df_fma2(float2& ch, float2& cl, const float2 ah, const float2 al, const float2 bh,
+                                        const float2 bl, const float2 nbh) {
+    const float2 np = mul2(ah, nbh);
+    float2 e = fma2(ah, bh, np);
+    e = fma2(ah, bl, e);
+    e = fma2(al, bh, e);
+    const float2 sm = sub2(ch, np);   // c + p
+    const float2 bb = sub2(sm, ch);
+    const float2 err = sub2(sub2(ch, sub2(sm, bb)), add2(np, bb));  // (c - (sm - bb)) + (p - bb)
+    cl = add2(cl, add2(err, e));
+    ch = sm;
+}
+
+// (ah, al) (bh, bl) - (dh, dl) lane by lane (df_mulsub), given nah = -ah and
+// nal = -al: the rounding error of the leading product is collected negated,
+// ne = -e, which fma(-a, b, p) gives exactly
+__device__ __forceinline__ void df_mulsub2(const float2 ah, const float2 nah, const float2 nal, const float2 bh,
+                                           const float2 bl, const float2 dh, const float2 dl, float2& rh,
+                                           float2& rl) {
+    const float2 p = mul2(ah, bh);
+    float2 ne = fma2(nah, bh, p);
+    ne = fma2(nah, bl, ne);
+    ne = fma2(nal, bh, ne);
+    const float2 sm = sub2(p, dh);
+    const float2 bb = sub2(sm, p);
+    const float2 err = sub2(sub2(p, sub2(sm, bb)), add2(dh, bb));  // (p - (sm - bb)) + (-d - bb)
+    const float2 lo = sub2(sub2(err, ne), dl);                     // (e + err) - d.lo
+    const float2 hi = add2(sm, lo);
+    rh = hi;
+    rl = sub2(lo, sub2(hi, sm));
+}
+
+// df_renorm on both lanes
+__device__ __forceinline__ void df_renorm2(float2& ch, float2& cl) {
+    const float2 sm = add2(ch, cl);
+    cl = sub2(cl, sub2(sm, ch));
+    ch = sm;
+}
+
 }  // namespace dse

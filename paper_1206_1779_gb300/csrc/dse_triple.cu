@@ -109,8 +109,10 @@ __device__ __forceinline__ void series_eval(const SeriesRec* __restrict__ R, con
 // X_(i+1) = 2 T_4 X_i - X_(i-1) (from T_(m+4) + T_(m-4) = 2 T_4 T_m), in
 // double-float from T_4 and T_5 formed in FP64 from s (their rounding to 48 bits,
 // 2^-49 relative, is the start error, which grows at most like i over i steps; the
-// steps' own rounding errors, 2^-48 each, at most like i^2); dst[i - 1] =
-// (T_4i hi, lo, T_4i+1 hi, lo).  sd is s as a double-float pair.
+// steps' own rounding errors, 2^-48 each, at most like i^2); the two sequences
+// run as the two lanes of paired FP32 instructions; dst[i - 1] = (T_4i hi,
+// T_4i+1 hi, T_4i lo, T_4i+1 lo), so that phase B loads both as one pair.  sd is s
+// as a double-float pair.
 __device__ __forceinline__ void store_anchors(const double s, const float2 sd, const int nq,
                                               float4* __restrict__ dst) {
     // (the doublings by integer operations: four FMAs on the FP64 pipe)
@@ -119,16 +121,18 @@ __device__ __forceinline__ void store_anchors(const double s, const float2 sd, c
     const double T3 = fma(s2, T2, -s);
     const double T4 = fma(twice(T2), T2, -1.0);
     const float2 c4 = df_split(T4, -1);  // 2 T4
-    float2 a0 = make_float2(1.0f, 0.0f), a1 = df_split(T4, 0);
-    float2 b0 = sd, b1 = df_split(fma(s2, T4, -T3), 0);
+    const float2 t4 = df_split(T4, 0), t5 = df_split(fma(s2, T4, -T3), 0);
+    const float2 ch = bcast2(c4.x), nch = bcast2(-c4.x), ncl = bcast2(-c4.y);
+    float2 x0h = make_float2(1.0f, sd.x), x0l = make_float2(0.0f, sd.y);  // (T_0, T_1)
+    float2 x1h = make_float2(t4.x, t5.x), x1l = make_float2(t4.y, t5.y);  // (T_4, T_5)
     for (int i = 1; i < nq; ++i) {
-        dst[i - 1] = make_float4(a1.x, a1.y, b1.x, b1.y);
-        const float2 an = df_mulsub(c4, a1, a0);
-        a0 = a1;
-        a1 = an;
-        const float2 bn = df_mulsub(c4, b1, b0);
-        b0 = b1;
-        b1 = bn;
+        dst[i - 1] = make_float4(x1h.x, x1h.y, x1l.x, x1l.y);
+        float2 xnh, xnl;
+        df_mulsub2(ch, nch, ncl, x1h, x1l, x0h, x0l, xnh, xnl);
+        x0h = x1h;
+        x0l = x1l;
+        x1h = xnh;
+        x1l = xnl;
     }
 }
 
@@ -411,11 +415,14 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
     const bool bact = g < G;
     const int mlo = min(BT, g * R);
     const int mhi = min(BT, mlo + R);
-    float2 acc[3][4];
+    // accumulators: kind kd, columns (4 qi, 4 qi + 1) in accH/accL[kd][0] and
+    // (4 qi + 2, 4 qi + 3) in [kd][1], leading parts in H, trailing in L (the lanes of
+    // the paired instructions)
+    float2 accH[3][2], accL[3][2];
 #pragma unroll
     for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[kd][q] = make_float2(0.0f, 0.0f);
+        for (int q = 0; q < 2; ++q) accH[kd][q] = accL[kd][q] = make_float2(0.0f, 0.0f);
     int Erun[3] = {0, 0, 0};  // running biased exponents of the accumulators' scale (0: nothing yet)
 
     // a group of kgrp nodes spans whole tiles when kgrp = kRadGroup (kRadGroup nch is
@@ -474,9 +481,12 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
 #pragma unroll
             for (int ww = 1; ww < WARPS; ++ww) Et = max(Et, sE[ww * 4 + kd]);
             if (Et > Erun[kd]) {
-                const float f = pow2f(Erun[kd] - Et);
+                const float2 f = bcast2(pow2f(Erun[kd] - Et));
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[kd][q] = make_float2(acc[kd][q].x * f, acc[kd][q].y * f);
+                for (int q = 0; q < 2; ++q) {
+                    accH[kd][q] = mul2(accH[kd][q], f);
+                    accL[kd][q] = mul2(accL[kd][q], f);
+                }
                 Erun[kd] = Et;
             }
         }
@@ -489,7 +499,9 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
         }
         __syncthreads();
         if (bact) {
-            // rows in groups of four, the accumulators renormalised after each
+            // rows in groups of four, the accumulators renormalised after each; the
+            // twelve multiply-adds of a row as six pairs (columns 4 qi, 4 qi + 1 and
+            // 4 qi + 2, 4 qi + 3 in the two lanes)
             for (int m0 = mlo; m0 < mhi; m0 += 4) {
                 const int m1 = min(mhi, m0 + 4);
                 for (int m = m0; m < m1; ++m) {
@@ -498,30 +510,26 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
                     const float4 h23 = Tm[1];
                     const float4 an = Tm[1 + (qi > 0 ? qi : 1)];
                     const float2 s2 = make_float2(h01.x, h01.y);
-                    const float2 t0 = qi > 0 ? make_float2(an.x, an.y) : make_float2(1.0f, 0.0f);
-                    const float2 t1 = qi > 0 ? make_float2(an.z, an.w) : make_float2(0.5f * h01.x, 0.5f * h01.y);
+                    // (T_4qi, T_4qi+1): the anchors, or (T_0, T_1) = (1, s)
+                    const float2 aH = qi > 0 ? make_float2(an.x, an.y) : make_float2(1.0f, 0.5f * h01.x);
+                    const float2 aL = qi > 0 ? make_float2(an.z, an.w) : make_float2(0.0f, 0.5f * h01.y);
+                    const float2 t0 = make_float2(aH.x, aL.x), t1 = make_float2(aH.y, aL.y);
                     const float2 t2 = df_mulsub(s2, t1, t0);
                     const float2 t3 = df_mulsub(s2, t2, t1);
-                    const float2 w0 = make_float2(h01.z, h01.w);
-                    const float2 w1 = make_float2(h23.x, h23.y);
-                    const float2 w2 = make_float2(h23.z, h23.w);
-                    df_fma(acc[0][0], w0, t0);
-                    df_fma(acc[0][1], w0, t1);
-                    df_fma(acc[0][2], w0, t2);
-                    df_fma(acc[0][3], w0, t3);
-                    df_fma(acc[1][0], w1, t0);
-                    df_fma(acc[1][1], w1, t1);
-                    df_fma(acc[1][2], w1, t2);
-                    df_fma(acc[1][3], w1, t3);
-                    df_fma(acc[2][0], w2, t0);
-                    df_fma(acc[2][1], w2, t1);
-                    df_fma(acc[2][2], w2, t2);
-                    df_fma(acc[2][3], w2, t3);
+                    const float2 bH = make_float2(t2.x, t3.x), bL = make_float2(t2.y, t3.y);
+                    const float2 naH = neg2(aH), nbH = neg2(bH);
+                    const float2 wH[3] = {bcast2(h01.z), bcast2(h23.x), bcast2(h23.z)};
+                    const float2 wL[3] = {bcast2(h01.w), bcast2(h23.y), bcast2(h23.w)};
+#pragma unroll
+                    for (int kd = 0; kd < 3; ++kd) {
+                        df_fma2(accH[kd][0], accL[kd][0], wH[kd], wL[kd], aH, aL, naH);
+                        df_fma2(accH[kd][1], accL[kd][1], wH[kd], wL[kd], bH, bL, nbH);
+                    }
                 }
 #pragma unroll
                 for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) df_renorm(acc[kd][q]);
+                    for (int q = 0; q < 2; ++q) df_renorm2(accH[kd][q], accL[kd][q]);
             }
         }
         __syncthreads();
@@ -537,7 +545,8 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
             for (int q = 0; q < 4; ++q) {
                 const int j = 4 * qi + q;
                 if (j < N) {
-                    float2 v = acc[kd][q];
+                    const float2 hh = accH[kd][q >> 1], ll = accL[kd][q >> 1];
+                    float2 v = (q & 1) ? make_float2(hh.y, ll.y) : make_float2(hh.x, ll.x);
                     if (j == 0) v = make_float2(0.5f * v.x, 0.5f * v.y);
                     red[((size_t)g * 3 + kd) * N + j] = v;
                 }
