@@ -171,6 +171,23 @@ __device__ __forceinline__ void df_mulsub2(const float2 ah, const float2 nah, co
     rl = sub2(lo, sub2(hi, sm));
 }
 
+// (ah, al) (bh, bl) + (dh, dl) lane by lane (df_muladd), given nbh = -bh
+__device__ __forceinline__ void df_muladd2(const float2 ah, const float2 al, const float2 bh, const float2 bl,
+                                           const float2 nbh, const float2 dh, const float2 dl, float2& rh,
+                                           float2& rl) {
+    const float2 np = mul2(ah, nbh);  // -p
+    float2 e = fma2(ah, bh, np);
+    e = fma2(ah, bl, e);
+    e = fma2(al, bh, e);
+    const float2 sm = sub2(dh, np);  // p + d
+    const float2 bb = add2(sm, np);  // sm - p
+    const float2 err = sub2(sub2(dh, bb), add2(np, sub2(sm, bb)));  // (p - (sm - bb)) + (d - bb)
+    const float2 lo = add2(add2(e, err), dl);
+    const float2 hi = add2(sm, lo);
+    rh = hi;
+    rl = sub2(lo, sub2(hi, sm));
+}
+
 // df_renorm on both lanes
 __device__ __forceinline__ void df_renorm2(float2& ch, float2& cl) {
     const float2 sm = add2(ch, cl);

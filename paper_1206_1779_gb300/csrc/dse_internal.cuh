@@ -87,7 +87,7 @@ struct SeriesRec {
     double mid, invhalf;
     int ex[4];                  // biased FP64 exponents E of Z, G, W; ex[3]: the degree kf from
                                 // which on the coefficients (hi parts) are summed in FP32 alone
-    float4 e[kSeriesQ];         // (Z hi, Z lo, G hi, G lo) 2^-E, coefficients 0 .. kSeriesP
+    float4 e[kSeriesQ];         // (Z hi, G hi, Z lo, G lo) 2^-E, coefficients 0 .. kSeriesP
     float2 w[kSeriesQ];         // (W hi, W lo) 2^-E
 };
 // A table is kSeriesRecords records: the kSeriesM intervals, then one record whose

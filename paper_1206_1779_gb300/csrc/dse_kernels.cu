@@ -377,9 +377,10 @@ __device__ __forceinline__ void series_fit(const Consts& c, const double (*sv)[I
         const float hi = (float)ms;
         const float lo = (float)(ms - (double)hi);
         if (act) {
-            float* t = f < 2 ? &R.e[q].x + 2 * f : &R.w[q].x;
+            // (Z and G interleaved: leading parts, then trailing parts)
+            float* t = f < 2 ? &R.e[q].x + f : &R.w[q].x;
             t[0] = hi;
-            t[1] = lo;
+            t[f < 2 ? 2 : 1] = lo;
             if (q == 0) R.ex[f] = E;
         }
         // the degree from which on the polynomial's tail is summed in FP32 alone: the

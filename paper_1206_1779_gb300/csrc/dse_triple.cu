@@ -47,8 +47,9 @@ __host__ __device__ inline int block_threads_for(int N) { return N <= 96 ? 128 :
 // (double-float): Horner over the kSeriesQ coefficients of each, the terms of
 // degree >= kf in FP32 on the leading parts (the record's tail is small enough
 // for that: kf = R->ex[3], here the largest over the lanes that evaluate together,
-// so that they take the same steps), the rest in double-float.  Results as
-// double-float mantissas Zm, Gm, Wm and exponent shifts (Z = Zm 2^Zs).
+// so that they take the same steps), the rest in double-float; Z and G as the two
+// lanes of paired FP32 instructions.  Results as double-float mantissas Zm, Gm, Wm
+// and exponent shifts (Z = Zm 2^Zs).
 __device__ __forceinline__ void series_eval_df(const SeriesRec* __restrict__ R, const float2 uf, const bool zg,
                                                const bool w, float2& Zm, float2& Gm, float2& Wm, int& Zs, int& Gs,
                                                int& Ws) {
@@ -57,25 +58,24 @@ __device__ __forceinline__ void series_eval_df(const SeriesRec* __restrict__ R, 
     // kSeriesP - 1 down to kf, then the double-float steps, instead of a branch
     // per degree)
     if (zg) {
-        const float4 top = __ldg(&R->e[kSeriesP]);
-        float2 tz = make_float2(top.x, kf > kSeriesP ? top.y : 0.0f);
-        float2 tg = make_float2(top.z, kf > kSeriesP ? top.w : 0.0f);
+        const float4 top = __ldg(&R->e[kSeriesP]);  // (Z hi, G hi, Z lo, G lo)
+        float2 th = make_float2(top.x, top.y);
+        float2 tl = kf > kSeriesP ? make_float2(top.z, top.w) : make_float2(0.0f, 0.0f);
+        const float2 uh = bcast2(uf.x), ul = bcast2(uf.y), nuh = bcast2(-uf.x);
         int k = kSeriesP - 1;
 #pragma unroll 4
         for (; k >= kf; --k) {
             const float4 ck = __ldg(&R->e[k]);
-            tz.x = fmaf(tz.x, uf.x, ck.x);
-            tg.x = fmaf(tg.x, uf.x, ck.z);
+            th = fma2(th, uh, make_float2(ck.x, ck.y));
         }
 #pragma unroll 4
         for (; k >= 0; --k) {
             const float4 ck = __ldg(&R->e[k]);
-            tz = df_muladd(tz, uf, make_float2(ck.x, ck.y));
-            tg = df_muladd(tg, uf, make_float2(ck.z, ck.w));
+            df_muladd2(th, tl, uh, ul, nuh, make_float2(ck.x, ck.y), make_float2(ck.z, ck.w), th, tl);
         }
         const int2 ex = __ldg(reinterpret_cast<const int2*>(R->ex));
-        Zm = tz;
-        Gm = tg;
+        Zm = make_float2(th.x, tl.x);
+        Gm = make_float2(th.y, tl.y);
         Zs = ex.x - 1023;
         Gs = ex.y - 1023;
     }
@@ -428,30 +428,39 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
     // a group of kgrp nodes spans whole tiles when kgrp = kRadGroup (kRadGroup nch is
     // a multiple of WARPS); with fewer nodes per block one group covers the block
     const int group_units = kgrp * nch;
+    // this warp's unit u = base + warp as (radial node kk, angular chunk ch), and the
+    // first node of the current group, kept by increments (no integer divisions)
+    int kk = warp / nch, ch = warp - (warp / nch) * nch;
+    int gnode = -kgrp, next_group = 0;
     for (int base = 0; base < nunits; base += WARPS) {
-        if (base % group_units == 0) {
+        if (base == next_group) {
+            next_group += group_units;
+            gnode += kgrp;
             __syncthreads();  // the previous group's factors are no longer read (and the coefficients staged)
-            if (warp == 0 && lane < kgrp && k0 + base / nch + lane < k1)
-                radial_factors(A, row, rt, k0 + base / nch + lane, srad + lane * kRadFactors);
+            if (warp == 0 && lane < kgrp && k0 + gnode + lane < k1)
+                radial_factors(A, row, rt, k0 + gnode + lane, srad + lane * kRadFactors);
             __syncthreads();
         }
         const int u = base + warp;
         TripleW w;
         w.hQ = w.hM = w.hG = w.s = 0.0;
         bool live = false;
-        int k = 0, ch = 0;
+        const int k = k0 + kk;
         if (u < nunits) {
-            const int kk = u / nch;
-            ch = u - kk * nch;
-            k = k0 + kk;
             const int l = ch * 32 + lane;
             if (l < c.na) {
                 live = true;
-                w = triple_weights(A, gluon, ghost, srad + (kk % kgrp) * kRadFactors, l, sa, sb, sbnd, ith_scale);
+                w = triple_weights(A, gluon, ghost, srad + (kk - gnode) * kRadFactors, l, sa, sb, sbnd, ith_scale);
             }
         }
         angular_sums(w, lane, u < nunits, A.Upart + (((size_t)rt * c.nr + k) * nch + ch) * 3);
-        float4* Trow = sT + (size_t)tid * rs4;
+        // the next unit of this warp
+        ch += WARPS;
+        while (ch >= nch) {
+            ch -= nch;
+            ++kk;
+        }
+        float4* Trow = sT + tid * rs4;
         const float2 sd = df_split(w.s, 0);  // s as a double-float pair (48 bits)
         if (live) {
             store_anchors(w.s, sd, nq, Trow + 2);
@@ -502,13 +511,14 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
             // rows in groups of four, the accumulators renormalised after each; the
             // twelve multiply-adds of a row as six pairs (columns 4 qi, 4 qi + 1 and
             // 4 qi + 2, 4 qi + 3 in the two lanes)
+            const int aslot = 1 + (qi > 0 ? qi : 1);
             for (int m0 = mlo; m0 < mhi; m0 += 4) {
                 const int m1 = min(mhi, m0 + 4);
-                for (int m = m0; m < m1; ++m) {
-                    const float4* Tm = sT + (size_t)m * rs4;
+                const float4* Tm = sT + m0 * rs4;
+                for (int m = m0; m < m1; ++m, Tm += rs4) {
                     const float4 h01 = Tm[0];
                     const float4 h23 = Tm[1];
-                    const float4 an = Tm[1 + (qi > 0 ? qi : 1)];
+                    const float4 an = Tm[aslot];
                     const float2 s2 = make_float2(h01.x, h01.y);
                     // (T_4qi, T_4qi+1): the anchors, or (T_0, T_1) = (1, s)
                     const float2 aH = qi > 0 ? make_float2(an.x, an.y) : make_float2(1.0f, 0.5f * h01.x);

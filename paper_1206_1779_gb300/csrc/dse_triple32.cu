@@ -219,12 +219,12 @@ __global__ void __launch_bounds__(BT) k_triple32(const __grid_constant__ TripleA
                     const int4 ex = __ldg(reinterpret_cast<const int4*>(Rr->ex));
                     if (ghost || gluon) {
                         const float4 top = __ldg(&Rr->e[kSeriesP]);
-                        float tz = top.x, tg = top.z;
+                        float tz = top.x, tg = top.y;
 #pragma unroll
                         for (int q = kSeriesP - 1; q >= 0; --q) {
                             const float4 ck = __ldg(&Rr->e[q]);
                             tz = fmaf(tz, uu, ck.x);
-                            tg = fmaf(tg, uu, ck.z);
+                            tg = fmaf(tg, uu, ck.y);
                         }
                         Zz = tz * pow2f32(ex.x - 1023);
                         Gz = tg * pow2f32(ex.y - 1023);
