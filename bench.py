@@ -55,7 +55,7 @@ SERIES_TABLE_DF_STEPS = 7   # Horner steps in double-float per polynomial (the r
 
 def work_per_triple(N: int):
     """Algorithmic work of the hot kernel per (x, y, theta) triple in the Newton-matrix
-    mode: (FP64 operations, FP64 flops, FP32 instructions, double-float multiply-adds).
+    mode: (FP64 operations, FP64 flops, FP32 operations, double-float multiply-adds).
 
     FP64 operations are the instructions of the FP64 pipe, each of which takes one
     slot of it whether it is an FMA, an add or a multiply; flops count an FMA as 2.
@@ -64,11 +64,12 @@ def work_per_triple(N: int):
     widened table values (3); T_2 .. T_5 for the anchors (7); the integrands (13);
     the angular sums (6).  Without the table (N < 24) the two series and the
     recurrence add 3N FMAs and the exponentials replace the table lookup.
-    FP32 (double-float, on the FP32 pipe): the derivative sums weight * T_j (3N
-    double-float multiply-adds, 12 instructions each), the T_j recurrences (N
-    multiply-subtracts, 15 each: the stride-4 anchors and the steps to T_4i+2, T_4i+3),
-    the three table polynomials (3 x SERIES_TABLE_DF_STEPS double-float steps of 15,
-    the others one FFMA each) and the small terms of ln z and 1/z (40)."""
+    FP32 (double-float, on the FP32 pipe), in operations (a paired f32x2 instruction
+    performs two): the derivative sums weight * T_j (3N double-float multiply-adds,
+    12 operations each), the T_j recurrences (N multiply-subtracts, 15 each: the
+    stride-4 anchors and the steps to T_4i+2, T_4i+3), the three table polynomials
+    (3 x SERIES_TABLE_DF_STEPS double-float steps of 15, the others one FMA each) and
+    the small terms of ln z and 1/z (40)."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
         f64_ops, f64 = 44.0, 54.0
         horner = 3.0 * (SERIES_TABLE_DF_STEPS * 15.0 + (SERIES_TABLE_DEGREE - SERIES_TABLE_DF_STEPS))
@@ -81,16 +82,16 @@ def work_per_triple(N: int):
     return f64_ops, f64, f32, df_ops
 
 
-def roofline_model(N: int, triples: int, fp64_ops_per_s: float, fp32_inst_per_s: float):
+def roofline_model(N: int, triples: int, fp64_ops_per_s: float, fp32_ops_per_s: float):
     """Lower bound on one launch's duration (s): the FP64 and FP32 pipes issue
     independently, so the bound is the larger of the two pipes' times at their
     measured rates (FP64 operations at the measured FP64 FMA instruction rate, FP32
-    instructions at the measured FP32 FMA rate, which is also the schedulers' issue
-    rate); and the FP64-equivalent flops of the launch (a double-float multiply-add
-    or -subtract counted as one FP64 FMA, 2 flops)."""
+    operations at the faster of the measured scalar and paired FP32 FMA rates); and
+    the FP64-equivalent flops of the launch (a double-float multiply-add or
+    -subtract counted as one FP64 FMA, 2 flops)."""
     f64_ops, f64, f32, df_ops = work_per_triple(N)
     t_fp64 = triples * f64_ops / fp64_ops_per_s
-    t_fp32 = triples * f32 / fp32_inst_per_s
+    t_fp32 = triples * f32 / fp32_ops_per_s
     flops = triples * (f64 + 2.0 * df_ops)
     return max(t_fp64, t_fp32), flops, t_fp64, t_fp32
 
@@ -103,7 +104,7 @@ def measure_alu_peaks(dse, local: int):
     out = {}
     for name, kind in (("fp64_fma", dse.DSE_PEAK_FP64_FMA), ("fp32_fma", dse.DSE_PEAK_FP32_FMA),
                        ("mufu_ex2", dse.DSE_PEAK_MUFU_EX2), ("mufu_lg2", dse.DSE_PEAK_MUFU_LG2),
-                       ("fp64_dmma", dse.DSE_PEAK_FP64_DMMA)):
+                       ("fp64_dmma", dse.DSE_PEAK_FP64_DMMA), ("fp32x2_fma", dse.DSE_PEAK_FP32X2_FMA)):
         best = 0.0
         for _ in range(2):
             rate, _ms = dse.alu_peak(kind, 150.0)
@@ -112,6 +113,8 @@ def measure_alu_peaks(dse, local: int):
     clk = clocks.stop()
     out["fp64_tflops"] = 2.0 * out["fp64_fma_per_s"] / 1e12
     out["fp32_tflops"] = 2.0 * out["fp32_fma_per_s"] / 1e12
+    # the paired f32x2 FMA, both lanes counted: the FP32 bound takes the faster form
+    out["fp32x2_tflops"] = 2.0 * out["fp32x2_fma_per_s"] / 1e12
     # the FP64 tensor cores (mma.sync m8n8k4) against the FP64 FMA pipe: the y-only
     # contraction would move to them only if they were faster
     out["fp64_dmma_tflops"] = 2.0 * out["fp64_dmma_per_s"] / 1e12
@@ -311,7 +314,7 @@ def run_gb300(args):
     avg_launch_ms = timed_ms / max(n_timed, 1)
     sm_mhz = clk.get("sm_mhz") or 2070.0
     t_min, flops_launch, t_fp64, t_fp32 = roofline_model(N, triples, peaks["fp64_fma_per_s"],
-                                                         peaks["fp32_fma_per_s"])
+                                                         max(peaks["fp32_fma_per_s"], peaks["fp32x2_fma_per_s"]))
     achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = flops_launch / t_min / 1e12
     f64ops_pt, f64_pt, f32_pt, dfops_pt = work_per_triple(N)
@@ -402,16 +405,19 @@ def run_gb300(args):
                          "kernel": "k_triple (radial x angular quadrature: FP64 integrands, double-float derivative sums)",
                          "peak_source": ("measured (dse_alu_peak on this GPU): FP64-equivalent flops of a launch over "
                                          "max(t_fp64, t_fp32), the FP64 operations at the measured FP64 FMA "
-                                         "instruction rate and the FP32 instructions at the measured FP32 FMA rate, "
-                                         "the two pipes overlapped"),
+                                         "instruction rate and the FP32 operations at the faster of the measured "
+                                         "scalar and paired (f32x2) FP32 FMA rates, the two pipes overlapped; "
+                                         "the hot kernel is timed in a second pass of the same steps with CUDA "
+                                         "events around each of its launches"),
                          "timed_launches": n_timed, "avg_launch_ms": avg_launch_ms, "triples_per_launch": triples,
                          "fp64_operations_per_triple": f64ops_pt,
-                         "fp64_flops_per_triple": f64_pt, "fp32_instructions_per_triple": f32_pt,
+                         "fp64_flops_per_triple": f64_pt, "fp32_operations_per_triple": f32_pt,
                          "double_float_ops_per_triple": dfops_pt,
                          "t_fp64_bound_ms": t_fp64 * 1e3, "t_fp32_bound_ms": t_fp32 * 1e3,
                          "fp64_achieved_tflops": triples * f64_pt / (avg_launch_ms * 1e-3) / 1e12,
                          "fp64_measured_peak_tflops": peaks["fp64_tflops"],
                          "fp32_measured_peak_tflops": peaks["fp32_tflops"],
+                         "fp32x2_measured_peak_tflops": peaks["fp32x2_tflops"],
                          "issue": issue},
             "alu_peaks": peaks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(c0.nbytes + tt.nbytes),

@@ -18,14 +18,18 @@ enum {
     DSE_PEAK_FP32_FMA = 1, /* FP32 fused multiply-add (2 flops each) */
     DSE_PEAK_MUFU_EX2 = 2, /* FP32 base-2 exponential on the special-function unit */
     DSE_PEAK_MUFU_LG2 = 3, /* FP32 base-2 logarithm on the special-function unit */
-    DSE_PEAK_FP64_DMMA = 4 /* FP64 tensor-core multiply-add (mma.sync m8n8k4): one 8x8x4
-                              warp product counts as 256 FMAs, 8 per thread */
+    DSE_PEAK_FP64_DMMA = 4, /* FP64 tensor-core multiply-add (mma.sync m8n8k4): one 8x8x4
+                               warp product counts as 256 FMAs, 8 per thread */
+    DSE_PEAK_FP32X2_FMA = 5 /* FP32 fused multiply-add on float pairs (the paired f32x2
+                               instruction): each instruction counts as 2 FMAs */
 };
 
 /* Rate of one arithmetic pipe on the current device, in operations per second
  * (thread-level: one FMA or one exp2 of one thread is one operation; for
  * DSE_PEAK_FP64_DMMA the FMAs of the warp's matrix products divided among its
- * threads, so that the rate compares with DSE_PEAK_FP64_FMA's).
+ * threads, so that the rate compares with DSE_PEAK_FP64_FMA's; for
+ * DSE_PEAK_FP32X2_FMA both lanes of a paired instruction, so that the rate
+ * compares with DSE_PEAK_FP32_FMA's).
  *
  * kind:      one of the DSE_PEAK_* values.
  * target_ms: approximate duration of the timed launch in milliseconds (1 .. 5000);

@@ -33,6 +33,7 @@ DSE_PEAK_FP32_FMA = 1
 DSE_PEAK_MUFU_EX2 = 2
 DSE_PEAK_MUFU_LG2 = 3
 DSE_PEAK_FP64_DMMA = 4
+DSE_PEAK_FP32X2_FMA = 5
 
 
 class DseError(RuntimeError):

@@ -71,6 +71,21 @@ __global__ void __launch_bounds__(kThreads) k_alu_peak(int iters, double seed) {
 #pragma unroll
         for (int i = 0; i < kChains; ++i) s += d[i][0] + d[i][1];
         if (s == -1.0) g_peak_sink = s;
+    } else if (KIND == DSE_PEAK_FP32X2_FMA) {
+        float2 a[kChains];
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) a[i] = make_float2((float)t + i, (float)t - i);
+        const float2 b = make_float2(0.9999999f, 0.9999998f), c = make_float2(1e-7f, 2e-7f);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int i = 0; i < kChains; ++i) a[i] = __ffma2_rn(a[i], b, c);
+        }
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) s += a[i].x + a[i].y;
+        if (s == -1.0f) g_peak_sink = s;
     } else if (KIND == DSE_PEAK_FP32_FMA) {
         float a[kChains];
 #pragma unroll
@@ -117,6 +132,7 @@ cudaError_t launch(int kind, int grid, int iters, cudaStream_t s) {
         case DSE_PEAK_FP32_FMA: return run<DSE_PEAK_FP32_FMA>(grid, iters, s);
         case DSE_PEAK_MUFU_EX2: return run<DSE_PEAK_MUFU_EX2>(grid, iters, s);
         case DSE_PEAK_FP64_DMMA: return run<DSE_PEAK_FP64_DMMA>(grid, iters, s);
+        case DSE_PEAK_FP32X2_FMA: return run<DSE_PEAK_FP32X2_FMA>(grid, iters, s);
         default: return run<DSE_PEAK_MUFU_LG2>(grid, iters, s);
     }
 }
@@ -136,6 +152,9 @@ int occupancy(int kind) {
             break;
         case DSE_PEAK_FP64_DMMA:
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alu_peak<DSE_PEAK_FP64_DMMA>, kThreads, 0);
+            break;
+        case DSE_PEAK_FP32X2_FMA:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alu_peak<DSE_PEAK_FP32X2_FMA>, kThreads, 0);
             break;
         default:
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_alu_peak<DSE_PEAK_MUFU_LG2>, kThreads, 0);
@@ -157,7 +176,7 @@ cudaError_t timed(int kind, int grid, int iters, cudaStream_t s, cudaEvent_t e0,
 }  // namespace
 
 extern "C" int dse_alu_peak(int kind, double target_ms, void* stream, double* ops_per_s, double* ms) {
-    if (kind < DSE_PEAK_FP64_FMA || kind > DSE_PEAK_FP64_DMMA || !ops_per_s || !(target_ms >= 1.0) ||
+    if (kind < DSE_PEAK_FP64_FMA || kind > DSE_PEAK_FP32X2_FMA || !ops_per_s || !(target_ms >= 1.0) ||
         !(target_ms <= 5000.0))
         return DSE_ERR_ARG;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -195,7 +214,8 @@ extern "C" int dse_alu_peak(int kind, double target_ms, void* stream, double* op
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return DSE_ERR_CUDA;
-    const double ops = (double)grid * kThreads * (double)iters * kUnroll * kChains * (kind == DSE_PEAK_FP64_DMMA ? 8 : 1);
+    const double ops = (double)grid * kThreads * (double)iters * kUnroll * kChains *
+                       (kind == DSE_PEAK_FP64_DMMA ? 8 : kind == DSE_PEAK_FP32X2_FMA ? 2 : 1);
     *ops_per_s = ops / (t * 1e-3);
     if (ms) *ms = t;
     return DSE_OK;

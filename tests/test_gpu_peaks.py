@@ -22,14 +22,16 @@ def test_alu_peaks(dse):
     r = {}
     for name, kind in (("fp64", dse.DSE_PEAK_FP64_FMA), ("fp32", dse.DSE_PEAK_FP32_FMA),
                        ("ex2", dse.DSE_PEAK_MUFU_EX2), ("lg2", dse.DSE_PEAK_MUFU_LG2),
-                       ("dmma", dse.DSE_PEAK_FP64_DMMA)):
+                       ("dmma", dse.DSE_PEAK_FP64_DMMA), ("fp32x2", dse.DSE_PEAK_FP32X2_FMA)):
         a, ms_a = dse.alu_peak(kind, 20.0)
         b, ms_b = dse.alu_peak(kind, 20.0)
         assert a > 0 and b > 0 and 5.0 < ms_a < 200.0, (name, a, ms_a)
         assert abs(a / b - 1.0) < 0.2, (name, a, b)
         r[name] = max(a, b)
-    print("FMA/s: FP64 %.3e, FP32 %.3e, FP64 tensor (DMMA) %.3e; exp2/s %.3e, log2/s %.3e"
-          % (r["fp64"], r["fp32"], r["dmma"], r["ex2"], r["lg2"]))
+    print("FMA/s: FP64 %.3e, FP32 %.3e, FP32 paired %.3e, FP64 tensor (DMMA) %.3e; exp2/s %.3e, log2/s %.3e"
+          % (r["fp64"], r["fp32"], r["fp32x2"], r["dmma"], r["ex2"], r["lg2"]))
+    # the paired instruction does two FMAs: at least the scalar rate, at most twice it
+    assert 0.8 * r["fp32"] < r["fp32x2"] < 2.5 * r["fp32"]
     assert 16.0 < r["fp32"] / r["fp64"] < 256.0
     assert r["ex2"] < r["fp32"] and r["lg2"] < r["fp32"]
     # the FP64 tensor path is an FP64 unit too: within a small factor of the FP64 FMA pipe
