@@ -1608,7 +1608,8 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
 //     change J little, so refinement sweeps with the old X reach the same
 //     backward error and the elimination is skipped; if the observed contraction
 //     per sweep is above kReuseRate, or predicts more than kReuseMax sweeps in
-//     all, the step eliminates afresh;
+//     all, the step eliminates afresh; after a failed attempt the next one waits
+//     for an update ten times smaller than the one that preceded the failure;
 //   - FP64 LU fallback if the sweeps stall.
 template <int R>
 __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __restrict__ J,
@@ -1680,22 +1681,46 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     }
     for (int i = tid; i < n; i += kGjThreads) s_scale[i] = rowinfo[i].x;
     for (int i = n + tid; i < kColPad; i += kGjThreads) s_colq[0][i] = s_colq[1][i] = 0.0f;  // rows past n
-    for (int base = 0; base < n * n; base += 4 * kGjThreads) {
-        double t[4];
+    // J to shared memory: warp w copies rows w, w + 32, ..., its loads all in flight
+    // before the stores (no integer division per element)
+    for (int i0r = 0; i0r < n; i0r += 4 * (kGjThreads / 32)) {
+        double t[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * kGjThreads + tid;
-            t[u] = idx < n * n ? J[idx] : 0.0;
+            const int i = i0r + u * (kGjThreads / 32) + warp;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int jj = lane + 32 * v;
+                t[u][v] = (i < n && jj < n) ? J[(size_t)i * n + jj] : 0.0;
+            }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * kGjThreads + tid;
-            if (idx < n * n) Js[(idx / n) * ldj + (idx % n)] = t[u];
+            const int i = i0r + u * (kGjThreads / 32) + warp;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int jj = lane + 32 * v;
+                if (i < n && jj < n) Js[i * ldj + jj] = t[u][v];
+            }
         }
     }
+    // (columns 128 .. n - 1 when n > 128 do not occur: this kernel serves n <= 128)
     for (int i = n + tid; i < kColPad; i += kGjThreads)
         for (int p = 0; p < kGjBlock; ++p) s_colb[p][i] = 0.0f;  // rows past n
-    if (tid == 0) s_reuse = (Xg != nullptr && *xstate == 1) ? 1 : 0;
+    if (tid == 0) {
+        // try the kept inverse unless the last attempt failed and the update since
+        // then is not ten times smaller than the one that preceded that failure
+        // (a plan's state, xcount: xstate[4], xstate[5] hold the max |Delta| of the
+        // previous step and of the step before the last failed attempt, as FP32
+        // bits; 0: none); an attempt that would fail leaves the result unchanged,
+        // as the elimination starts afresh
+        bool reuse = Xg != nullptr && *xstate == 1;
+        if (reuse && xcount) {
+            const float dprev = __int_as_float(xstate[4]), dfail = __int_as_float(xstate[5]);
+            if (dfail > 0.0f && !(dprev <= 0.1f * dfail)) reuse = false;
+        }
+        s_reuse = reuse ? 1 : 0;
+    }
     if (tid < n) s_x[tid] = 0.0;
     __syncthreads();
     if (s_fail) {
@@ -1708,12 +1733,26 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     if (s_reuse) {
         // the previous Newton step's inverse (of its row-scaled matrix) as the
         // approximate inverse; J changes little between late Newton steps
-        for (int idx = tid; idx < n * n; idx += kGjThreads) Xs[idx] = Xg[idx];
+        {
+            // 16 values per thread in flight (n <= 128: n^2 <= 16 x 1024)
+            float t[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int idx = u * kGjThreads + tid;
+                t[u] = idx < n * n ? Xg[idx] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int idx = u * kGjThreads + tid;
+                if (idx < n * n) Xs[idx] = t[u];
+            }
+        }
         for (int i = tid; i < n; i += kGjThreads) s_sold[i] = Sg[i];
         __syncthreads();
         converged = refine_fp64(n, ldj, Js, Xs, s_sold, s_scale, F, s_x, s_rf, s_red, &s_conv, tolfac, kReuseMax,
                                 true, &sweeps) == 1;
         if (xcount && converged && tid == 0) xstate[2] += 1;  // counter of steps that reused the inverse
+        if (xcount && !converged && tid == 0) xstate[5] = xstate[4];
     }
     if (!converged) {
         sweeps = 0;  // the reported sweeps are those of the solve that is kept
@@ -2016,6 +2055,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
             stats[2] = mD;
             stats[3] = converged ? (double)sweeps : -1.0;
             if (bad) s_fail = kStatusNonfinite;
+            if (Xg != nullptr && xcount) xstate[4] = __float_as_int((float)mD);
         }
     }
     __syncthreads();
@@ -2036,7 +2076,8 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, doubl
                                                            double* __restrict__ stats, int* __restrict__ status,
                                                            float* __restrict__ Xinv, double* __restrict__ Sinv,
                                                            int* __restrict__ xstate) {
-    // a plan's xstate word is followed by its two solver counters
+    // a plan's xstate word is followed by its two solver counters and the two words
+    // of the reuse gate
     newton_reg_block<R>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status, Xinv, Sinv, xstate, true);
 }
 

@@ -44,7 +44,8 @@ struct dse_plan {
     double2* rowinfo;   // row scales and row sums (Newton step)
     float* Xinv;        // FP32 inverse of the last eliminated Newton step, reused while it suffices
     double* Sinv;       // its row scales
-    int* xstate;        // 1 while Xinv is usable, then 2 counters: eliminations, reuses (after the status word)
+    int* xstate;        // 1 while Xinv is usable, then 2 counters: eliminations, reuses (after the status word);
+                        // [4], [5]: the reuse gate's max |Delta| of the last step and before the last failed try
     int* lu_done;       // 1 when the FP32 LU path took the Newton step (n > 160)
     double* aux;        // derivative scratch: dPi rows, dressing-VJP partial sums
     // finite-difference Newton matrix: a batch of 2n copies of the problem
@@ -626,8 +627,11 @@ int dse_solve(dse_plan* plan, double* d_coeffs, double tol, int max_iter, double
     const double kSwitch = 1e-5;
     bool f64_res = plan->prob.precision == 0;
     double prev = INFINITY;
-    // every solve starts without a kept inverse, so its steps depend on its input alone
-    if (cudaMemsetAsync(plan->xstate, 0, sizeof(int), plan->stream) != cudaSuccess) return DSE_ERR_CUDA;
+    // every solve starts without a kept inverse (and without the record of the last
+    // failed attempt to reuse one), so its steps depend on its input alone
+    if (cudaMemsetAsync(plan->xstate, 0, sizeof(int), plan->stream) != cudaSuccess ||
+        cudaMemsetAsync(plan->xstate + 4, 0, 2 * sizeof(int), plan->stream) != cudaSuccess)
+        return DSE_ERR_CUDA;
     for (; it < max_iter; ++it) {
         // past the relaxed steps and the FP32 residuals, the remaining steps run as
         // one CUDA graph with the stopping test on the device (no host round trip per
