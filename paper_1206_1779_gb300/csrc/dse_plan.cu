@@ -160,7 +160,10 @@ constexpr int kSplitWaves = DSE_SPLIT_WAVES;
 // With 128-thread blocks (N <= 96) fewer, longer blocks pay: at N = 64 with 256 x 128
 // nodes one Newton matrix took 0.480 / 0.472 / 0.470 / 0.513 ms for 8 / 6 / 4 / 2 waves,
 // while at N = 128 (64-thread blocks, 512 x 256 nodes) 5.50 / 5.61 / 5.84 / 6.81 ms.
-constexpr int kSplitWavesWide = 6;
+#ifndef DSE_SPLIT_WAVES_WIDE
+#define DSE_SPLIT_WAVES_WIDE 6
+#endif
+constexpr int kSplitWavesWide = DSE_SPLIT_WAVES_WIDE;
 // The FP32-integrand kernel's blocks hold at least this many radial nodes: its
 // per-block set-up and final group sums weigh more against its cheaper tiles
 // (one Newton matrix at N = 64 with 256 x 128 nodes: 0.529 ms at two nodes per
