@@ -95,6 +95,20 @@ __device__ __forceinline__ float2 df_mulsub(const float2 a, const float2 b, cons
     return make_float2(hi, lo - (hi - sm));
 }
 
+// a b - d in double-float, not renormalised: (sum of the leading parts, collected
+// low parts), |lo| within a few units of the leading part's last place; for a value
+// that only enters products as an operand
+__device__ __forceinline__ float2 df_mulsub_nr(const float2 a, const float2 b, const float2 d) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float sm = p - d.x;
+    const float bb = sm - p;
+    const float err = (p - (sm - bb)) + (-d.x - bb);
+    return make_float2(sm, (e + err) - d.y);
+}
+
 // a + b in double-float (renormalised; exact sum of the leading parts)
 __device__ __forceinline__ float2 df_add(const float2 a, const float2 b) {
     const float s = a.x + b.x;

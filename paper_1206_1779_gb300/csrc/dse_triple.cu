@@ -508,12 +508,12 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
         }
         __syncthreads();
         if (bact) {
-            // rows in groups of four, the accumulators renormalised after each; the
+            // rows in groups of eight, the accumulators renormalised after each; the
             // twelve multiply-adds of a row as six pairs (columns 4 qi, 4 qi + 1 and
             // 4 qi + 2, 4 qi + 3 in the two lanes)
             const int aslot = 1 + (qi > 0 ? qi : 1);
-            for (int m0 = mlo; m0 < mhi; m0 += 4) {
-                const int m1 = min(mhi, m0 + 4);
+            for (int m0 = mlo; m0 < mhi; m0 += 8) {
+                const int m1 = min(mhi, m0 + 8);
                 const float4* Tm = sT + m0 * rs4;
                 for (int m = m0; m < m1; ++m, Tm += rs4) {
                     const float4 h01 = Tm[0];
@@ -525,7 +525,7 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
                     const float2 aL = qi > 0 ? make_float2(an.z, an.w) : make_float2(0.0f, 0.5f * h01.y);
                     const float2 t0 = make_float2(aH.x, aL.x), t1 = make_float2(aH.y, aL.y);
                     const float2 t2 = df_mulsub(s2, t1, t0);
-                    const float2 t3 = df_mulsub(s2, t2, t1);
+                    const float2 t3 = df_mulsub_nr(s2, t2, t1);  // (a product operand only)
                     const float2 bH = make_float2(t2.x, t3.x), bL = make_float2(t2.y, t3.y);
                     const float2 naH = neg2(aH), nbH = neg2(bH);
                     const float2 wH[3] = {bcast2(h01.z), bcast2(h23.x), bcast2(h23.z)};
