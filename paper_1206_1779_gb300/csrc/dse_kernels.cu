@@ -2155,15 +2155,16 @@ __global__ void k_schwinger_weights(const Consts c, const double* __restrict__ c
 
 // cos x for |x| < 2^49 (the caller takes the library cos beyond), FP64-accurate (a
 // few units in the last place) with most of the arithmetic on the FP32 pipe.  Cody-Waite reduction (Cody & Waite 1980):
-// k = nearest integer to 2x/pi (the 1.5 2^52 shifter), r = x - k pi/2 with pi/2 in
-// two FP64 parts (FMA; P1 = pi/2 rounded to FP64, P2 = pi/2 - P1 rounded; the
-// remainder |pi/2 - P1 - P2| < 1.5e-33 leaves k below 2^50 an error under 2e-18,
-// below an ulp of r), |r| <= pi/4.  Then by the quadrant k mod 4
+// k = nearest integer to 2x/pi (the 1.5 2^52 shifter; below |x| = 2^18 an integer
+// within 0.52 of 2x/pi from FP32 arithmetic), r = x - k pi/2 with pi/2 in two FP64
+// parts (FMA; P1 = pi/2 rounded to FP64, P2 = pi/2 - P1 rounded; the remainder
+// |pi/2 - P1 - P2| < 1.5e-33 leaves k below 2^50 an error under 2e-18, below an ulp
+// of r), |r| <= pi/4 (+ 0.031 below 2^18).  Then by the quadrant k mod 4
 // cos x = +-cos r or -+sin r, with the Taylor series split as
 //   cos r = (1 - r^2/2) + r^4 (1/4! - r^2/6! + ... + r^14/18!)
 //   sin r = (r - r^3/6) + r^5 (1/5! - r^2/7! + ... + r^14/19!)
-// (truncation below 4e-21 for |r| <= pi/4): the leading terms in FP64, the tails
-// (at most 0.016) in double-float, both tails for every lane so that the quadrant
+// (truncation below 1e-20 for |r| <= pi/4 + 0.031): the leading terms in FP64, the
+// tails (at most 0.019) in double-float, both tails for every lane so that the quadrant
 // selects without divergence.  The caller keeps the two parts apart (an FP64 sum of
 // w lead, a double-float sum of w tail) and adds them once at the end.
 constexpr double kPio2_1 = 1.5707963267948966;
@@ -2171,6 +2172,28 @@ constexpr double kPio2_2 = 6.123233995736766e-17;
 constexpr double kTwoOverPi = 0.6366197723675814;
 constexpr double kRoundShifter = 6755399441055744.0;  // 1.5 2^52
 constexpr unsigned kCosReduceMaxHi = 0x43000000u;  // high word of 2^49: from there the library cos
+constexpr unsigned kCosFastHi = 0x41100000u;       // high word of 2^18: below it, k from FP32
+constexpr float kTwoOverPiF = 0.636619772f;        // 2/pi rounded to FP32
+
+// The leading 24 significant bits of x as an FP32 number (truncated toward zero;
+// 0 below the FP32 normal range), by integer operations on its bits (|x| < 2^18).
+__device__ __forceinline__ float lead24(double x) {
+    const unsigned hb = (unsigned)__double2hiint(x), lb = (unsigned)__double2loint(x);
+    const int e = (int)((hb >> 20) & 0x7ffu) - 896;  // biased FP32 exponent
+    if (e < 1) return 0.0f;
+    return __int_as_float((int)((hb & 0x80000000u) | ((unsigned)e << 23) | ((hb & 0xfffffu) << 3) | (lb >> 29)));
+}
+
+// An integer k (|k| < 2^31) as a double, by integer operations: the exponent from
+// the position of the leading one, the bits below it as the significand.
+__device__ __forceinline__ double int_as_double(int k) {
+    if (k == 0) return 0.0;
+    const unsigned sign = k < 0 ? 0x80000000u : 0u;
+    const unsigned a = k < 0 ? 0u - (unsigned)k : (unsigned)k;
+    const int lz = __clz((int)a);
+    const unsigned m = (a << lz) << 1;  // the bits below the leading one, left-aligned
+    return __hiloint2double((int)(sign | ((unsigned)(1054 - lz) << 20) | (m >> 12)), (int)(m << 20));
+}
 
 struct CosTail { float2 c[8], s[8]; };
 
@@ -2192,9 +2215,21 @@ __device__ __forceinline__ CosTail cos_tail_coefficients() {
 struct CosParts { double lead; float2 tail; };
 
 __device__ __forceinline__ CosParts cos_df(double x, const CosTail& T) {
-    double kd = fma(x, kTwoOverPi, kRoundShifter);
-    const int q = __double2loint(kd) & 3;
-    kd -= kRoundShifter;
+    int k;
+    double kd;
+    if (((unsigned)__double2hiint(x) & 0x7fffffffu) < kCosFastHi) {
+        // |x| < 2^18: k from the FP32 product of the leading 24 bits of x and 2/pi,
+        // rounded by the 1.5 2^23 shifter (within 0.02 of x 2/pi, so |r| <= pi/4 +
+        // 0.031, where the truncated series keep their accuracy), and its double by
+        // integer operations: no FP64 instruction
+        k = __float_as_int(fmaf(lead24(x), kTwoOverPiF, 12582912.0f)) - 0x4b400000;
+        kd = int_as_double(k);
+    } else {
+        kd = fma(x, kTwoOverPi, kRoundShifter);
+        k = __double2loint(kd);
+        kd -= kRoundShifter;
+    }
+    const int q = k & 3;
     double r = fma(-kd, kPio2_1, x);
     r = fma(-kd, kPio2_2, r);
     const double r2 = r * r;
