@@ -59,7 +59,7 @@ def work_per_triple(N: int):
 
     FP64 operations are the instructions of the FP64 pipe, each of which takes one
     slot of it whether it is an FMA, an add or a multiply; flops count an FMA as 2.
-    On the table path (44 operations, 54 flops): z (1); ln z and 1/z (10: the FMAs
+    On the table path (43 operations, 53 flops): z (1); ln z and 1/z (9: the FMAs
     of r and of e ln2_hi, the leading sums, the product by inv_j); s and u (4); the
     widened table values (3); T_2 .. T_5 for the anchors (7); the integrands (13);
     the angular sums (6).  Without the table (N < 24) the two series and the
@@ -71,11 +71,11 @@ def work_per_triple(N: int):
     (3 x SERIES_TABLE_DF_STEPS double-float steps of 15, the others one FMA each) and
     the small terms of ln z and 1/z (40)."""
     if SERIES_TABLE_N[0] <= N <= SERIES_TABLE_N[1]:
-        f64_ops, f64 = 44.0, 54.0
+        f64_ops, f64 = 43.0, 53.0
         horner = 3.0 * (SERIES_TABLE_DF_STEPS * 15.0 + (SERIES_TABLE_DEGREE - SERIES_TABLE_DF_STEPS))
         df_ops = 3.0 * N + N + 3.0 * SERIES_TABLE_DF_STEPS
     else:
-        f64_ops, f64 = 44.0 + 3.0 * N, 54.0 + 6.0 * N
+        f64_ops, f64 = 43.0 + 3.0 * N, 53.0 + 6.0 * N
         horner = 0.0
         df_ops = 3.0 * N + N
     f32 = 12.0 * 3 * N + 15.0 * N + horner + 40.0

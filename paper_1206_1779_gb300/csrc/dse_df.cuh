@@ -52,6 +52,17 @@ __device__ __forceinline__ double twice(double v) {
     return __hiloint2double((int)((mh & 0x7fffffffu) | ((unsigned)hi & 0x80000000u)), (int)(lo << 1));
 }
 
+// An integer k (|k| < 2^31) as a double, by integer operations: the exponent from
+// the position of the leading one, the bits below it as the significand.
+__device__ __forceinline__ double int_as_double(int k) {
+    if (k == 0) return 0.0;
+    const unsigned sign = k < 0 ? 0x80000000u : 0u;
+    const unsigned a = k < 0 ? 0u - (unsigned)k : (unsigned)k;
+    const int lz = __clz((int)a);
+    const unsigned m = (a << lz) << 1;  // the bits below the leading one, left-aligned
+    return __hiloint2double((int)(sign | ((unsigned)(1054 - lz) << 20) | (m >> 12)), (int)(m << 20));
+}
+
 // f 2^(E - 1023) as a double, from the bits of f: the tile scale of phase B
 // folded into the exponent (zero and FP32 subnormals give 0, Inf/NaN or an
 // overflow give Inf/NaN).

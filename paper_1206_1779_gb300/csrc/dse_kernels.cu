@@ -2184,16 +2184,6 @@ __device__ __forceinline__ float lead24(double x) {
     return __int_as_float((int)((hb & 0x80000000u) | ((unsigned)e << 23) | ((hb & 0xfffffu) << 3) | (lb >> 29)));
 }
 
-// An integer k (|k| < 2^31) as a double, by integer operations: the exponent from
-// the position of the leading one, the bits below it as the significand.
-__device__ __forceinline__ double int_as_double(int k) {
-    if (k == 0) return 0.0;
-    const unsigned sign = k < 0 ? 0x80000000u : 0u;
-    const unsigned a = k < 0 ? 0u - (unsigned)k : (unsigned)k;
-    const int lz = __clz((int)a);
-    const unsigned m = (a << lz) << 1;  // the bits below the leading one, left-aligned
-    return __hiloint2double((int)(sign | ((unsigned)(1054 - lz) << 20) | (m >> 12)), (int)(m << 20));
-}
 
 struct CosTail { float2 c[8], s[8]; };
 

@@ -17,7 +17,8 @@ namespace {
 //   1/z = 2^-e inv_j ((1 - r) + [d]),  d = 1/(1 + r) - (1 - r) = r^2 (1 - r + r^2 - r^3 + r^4);
 // where the bracketed small terms are formed in double-float on the FP32 pipe (they
 // need about 40 significant bits) and only the leading sums and the FMAs of r, of
-// e ln2_hi and of inv_j (1 - r) + inv_j d take the FP64 pipe (9 FP64 operations).  ln2 = ln2_hi
+// e ln2_hi and of inv_j (1 - r) + inv_j d take the FP64 pipe (8 FP64 operations; e as
+// a double comes from integer operations).  ln2 = ln2_hi
 // + ln2_lo with ln2_hi holding 42 significant bits, so e ln2_hi is exact.  Accuracy
 // (tests/test_ln_rcp.py, an emulation of these operations against 40-digit values over
 // z in [1e-14, 1e8]): ln z within 2 units of 2^-53 max(1, |ln z|), 1/z within 2 units in
@@ -63,7 +64,7 @@ __device__ __forceinline__ LnRcp ln_rcp(double z) {
     const float ql = (((1.0f - qh) - rf) - rd.y) + p2 * (1.0f - rf + p2);
     const float2 dm = df_mul(make_float2(p2, e2), make_float2(qh, ql));
     // e as a double without a conversion instruction: 1.5 2^52 + (e + 2^31) - (1.5 2^52 + 2^31)
-    const double ed = __hiloint2double(0x43380000, (int)((unsigned)e ^ 0x80000000u)) - 6755401588539392.0;
+    const double ed = int_as_double(e);  // (integer operations, no FP64 instruction)
     const double hi = fma(ed, ln2h, Lh);
     o.ln = hi + ((r - df_widen(cm.x, 1023)) + df_widen(sl, 1023));
     // inv (1 - r + d) = inv (1 - r) + inv d: two FMAs (d exact in FP64 as hi + lo)
