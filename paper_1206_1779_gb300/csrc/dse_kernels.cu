@@ -1611,6 +1611,85 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
 //     all, the step eliminates afresh; after a failed attempt the next one waits
 //     for an update ten times smaller than the one that preceded the failure;
 //   - FP64 LU fallback if the sweeps stall.
+// One warp pivots the panel of a round in registers (lane L holds columns L + 32 c):
+// rows k0 .. k0 + nb - 1 of the partly eliminated matrix, with column pivoting.
+// Writes the final panel rows back, the pivot columns to s_q[k0 ..], the columns
+// used so far to s_used, and *s_done = -1 on a pivot below 1e-30.  Not inlined: the
+// pivot chain gets the registers that the caller's rows hold meanwhile.
+__device__ __noinline__ void gj_pivot_panel(float (*panel)[128], const int k0, const int nb, const int n,
+                                            const int lane, unsigned char* s_used, int* s_q, int* s_done) {
+        float P[kGjBlock][kGjCols];
+        bool ucol[kGjCols];
+#pragma unroll
+        for (int cc = 0; cc < kGjCols; ++cc) {
+            const int col = lane + 32 * cc;
+            ucol[cc] = col >= n || s_used[col] != 0;
+#pragma unroll
+            for (int p = 0; p < kGjBlock; ++p) P[p][cc] = (col < n && p < nb) ? panel[p][col] : 0.0f;
+        }
+        bool sing = false;
+#pragma unroll
+        for (int p = 0; p < kGjBlock; ++p) {
+            if (p < nb && !sing) {  // uniform over the warp
+                // pivot column: the largest unused entry of panel row p,
+                // by one warp reduction over keys that hold |a| as bits
+                // (monotonic for non-negative floats) cut to 16 fraction
+                // bits, and 127 - column in the 7 bits below: of entries
+                // equal to 2^-16 the lowest column wins (pivoted columns: 0)
+                unsigned key = 0u;
+#pragma unroll
+                for (int cc = 0; cc < kGjCols; ++cc) {
+                    const unsigned ab = (unsigned)__float_as_int(fabsf(P[p][cc])) & 0xffffff80u;
+                    const unsigned bv = ucol[cc] ? 0u : (ab | (unsigned)(127 - (lane + 32 * cc)));
+                    key = max(key, bv);
+                }
+                const unsigned mk = __reduce_max_sync(kFullMask, key);
+                const int idx = 127 - (int)(mk & 0x7fu);
+                const float a = __int_as_float((int)(mk & 0xffffff80u));
+                if (!(a > 1e-30f)) {
+                    if (lane == 0) *s_done = -1;
+                    sing = true;
+                } else {
+                    const int q = idx;
+                    const int ql = q & 31, qc = q >> 5;
+                    // the pivot column's panel entries, from the lane that holds it
+                    float pc[kGjBlock];
+#pragma unroll
+                    for (int pp = 0; pp < kGjBlock; ++pp) {
+                        float mine = P[pp][0];
+#pragma unroll
+                        for (int cc = 1; cc < kGjCols; ++cc)
+                            if (cc == qc) mine = P[pp][cc];
+                        pc[pp] = __shfl_sync(kFullMask, mine, ql);
+                    }
+                    const float inv = __frcp_rn(pc[p]);
+#pragma unroll
+                    for (int cc = 0; cc < kGjCols; ++cc) {
+                        const bool isq = (lane + 32 * cc) == q;
+                        if (isq) ucol[cc] = true;
+                        const float nk = isq ? inv : P[p][cc] * inv;
+#pragma unroll
+                        for (int pp = 0; pp < kGjBlock; ++pp)
+                            if (pp != p) P[pp][cc] = fmaf(-pc[pp], nk, isq ? 0.0f : P[pp][cc]);
+                        P[p][cc] = nk;
+                    }
+                    if (lane == 0) s_q[k0 + p] = q;
+                }
+            }
+        }
+#pragma unroll
+        for (int cc = 0; cc < kGjCols; ++cc) {
+            const int col = lane + 32 * cc;
+            if (col < n) {
+                s_used[col] = ucol[cc] ? 1 : 0;
+#pragma unroll
+                for (int p = 0; p < kGjBlock; ++p)
+                    if (p < nb) panel[p][col] = P[p][cc];
+            }
+        }
+    
+}
+
 template <int R>
 __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __restrict__ J,
                                                  const float* __restrict__ As, const double2* __restrict__ rowinfo,
@@ -1796,77 +1875,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
                     }
                     __syncthreads();
                     // (2) warp 0 pivots the panel: lane L holds columns L + 32 c
-                    if (warp == 0) {
-                        float P[kGjBlock][kGjCols];
-                        bool ucol[kGjCols];
-#pragma unroll
-                        for (int cc = 0; cc < kGjCols; ++cc) {
-                            const int col = lane + 32 * cc;
-                            ucol[cc] = col >= n || s_used[col] != 0;
-#pragma unroll
-                            for (int p = 0; p < kGjBlock; ++p) P[p][cc] = (col < n && p < nb) ? panel[p][col] : 0.0f;
-                        }
-                        bool sing = false;
-#pragma unroll
-                        for (int p = 0; p < kGjBlock; ++p) {
-                            if (p < nb && !sing) {  // uniform over the warp
-                                // pivot column: the largest unused entry of panel row p,
-                                // by one warp reduction over keys that hold |a| as bits
-                                // (monotonic for non-negative floats) cut to 16 fraction
-                                // bits, and 127 - column in the 7 bits below: of entries
-                                // equal to 2^-16 the lowest column wins (pivoted columns: 0)
-                                unsigned key = 0u;
-#pragma unroll
-                                for (int cc = 0; cc < kGjCols; ++cc) {
-                                    const unsigned ab = (unsigned)__float_as_int(fabsf(P[p][cc])) & 0xffffff80u;
-                                    const unsigned bv = ucol[cc] ? 0u : (ab | (unsigned)(127 - (lane + 32 * cc)));
-                                    key = max(key, bv);
-                                }
-                                const unsigned mk = __reduce_max_sync(kFullMask, key);
-                                const int idx = 127 - (int)(mk & 0x7fu);
-                                const float a = __int_as_float((int)(mk & 0xffffff80u));
-                                if (!(a > 1e-30f)) {
-                                    if (lane == 0) s_done = -1;
-                                    sing = true;
-                                } else {
-                                    const int q = idx;
-                                    const int ql = q & 31, qc = q >> 5;
-                                    // the pivot column's panel entries, from the lane that holds it
-                                    float pc[kGjBlock];
-#pragma unroll
-                                    for (int pp = 0; pp < kGjBlock; ++pp) {
-                                        float mine = P[pp][0];
-#pragma unroll
-                                        for (int cc = 1; cc < kGjCols; ++cc)
-                                            if (cc == qc) mine = P[pp][cc];
-                                        pc[pp] = __shfl_sync(kFullMask, mine, ql);
-                                    }
-                                    const float inv = __frcp_rn(pc[p]);
-#pragma unroll
-                                    for (int cc = 0; cc < kGjCols; ++cc) {
-                                        const bool isq = (lane + 32 * cc) == q;
-                                        if (isq) ucol[cc] = true;
-                                        const float nk = isq ? inv : P[p][cc] * inv;
-#pragma unroll
-                                        for (int pp = 0; pp < kGjBlock; ++pp)
-                                            if (pp != p) P[pp][cc] = fmaf(-pc[pp], nk, isq ? 0.0f : P[pp][cc]);
-                                        P[p][cc] = nk;
-                                    }
-                                    if (lane == 0) s_q[k0 + p] = q;
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int cc = 0; cc < kGjCols; ++cc) {
-                            const int col = lane + 32 * cc;
-                            if (col < n) {
-                                s_used[col] = ucol[cc] ? 1 : 0;
-#pragma unroll
-                                for (int p = 0; p < kGjBlock; ++p)
-                                    if (p < nb) panel[p][col] = P[p][cc];
-                            }
-                        }
-                    }
+                    if (warp == 0) gj_pivot_panel(panel, k0, nb, n, lane, s_used, s_q, &s_done);
                     __syncthreads();
                     if (s_done != 0) goto elimination_done;  // uniform
                     // (3)
