@@ -594,6 +594,7 @@ __global__ void __launch_bounds__(kSeriesDotThreads) k_series_table(const Consts
 constexpr int kRowBlock = 512;
 constexpr int kRowJ = 32;                   // coefficients per block (one per lane)
 constexpr int kRowKG = kRowBlock / kRowJ;   // radial-node groups per block
+constexpr int kRowSplitsPer = (128 + kRowKG - 1) / kRowKG;  // splits per group held in registers (KS <= 128)
 constexpr int kChunkK = 256;
 
 // Grid: (row r, block of 32 coefficients).  Thread (k-group kg, lane) owns
@@ -738,22 +739,51 @@ __device__ __forceinline__ void rowreduce_block(const Consts& c, int Rt, int KS,
     }
     // the z-derivative sums of the radial splits kg, kg + kRowKG, ...: in
     // double-float at the thread's own scale (the largest exponent among its
-    // values, a first pass over them), widened once
+    // values), widened once.  With KS <= 128 (every plan) the thread's values, at
+    // most kRowSplitsPer per kind, are loaded once, all in flight, and scanned twice
+    // in registers; more splits (large radial rules of a batch) take two passes over
+    // memory.  Both add the same terms in the same order.
     if (FULL && !special && j < N) {
         const double* vp = Vpart + (size_t)rt * KS * 3 * N;
         unsigned m0 = 0u, m1 = 0u, m2 = 0u;
-#pragma unroll 4
-        for (int sp = kg; sp < KS; sp += kRowKG) {
-            m0 = max(m0, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + j]) >> 20) & 0x7ffu);
-            m1 = max(m1, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + N + j]) >> 20) & 0x7ffu);
-            m2 = max(m2, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + 2 * N + j]) >> 20) & 0x7ffu);
-        }
         float2 v0 = make_float2(0.0f, 0.0f), v1 = v0, v2 = v0;
+        if (KS <= kRowSplitsPer * kRowKG) {
+            double w0[kRowSplitsPer], w1[kRowSplitsPer], w2[kRowSplitsPer];
+#pragma unroll
+            for (int t = 0; t < kRowSplitsPer; ++t) {
+                const int sp = kg + t * kRowKG;
+                const bool in = sp < KS;
+                w0[t] = in ? vp[(size_t)sp * 3 * N + j] : 0.0;
+                w1[t] = in ? vp[(size_t)sp * 3 * N + N + j] : 0.0;
+                w2[t] = in ? vp[(size_t)sp * 3 * N + 2 * N + j] : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < kRowSplitsPer; ++t) {
+                m0 = max(m0, ((unsigned)__double2hiint(w0[t]) >> 20) & 0x7ffu);
+                m1 = max(m1, ((unsigned)__double2hiint(w1[t]) >> 20) & 0x7ffu);
+                m2 = max(m2, ((unsigned)__double2hiint(w2[t]) >> 20) & 0x7ffu);
+            }
+#pragma unroll
+            for (int t = 0; t < kRowSplitsPer; ++t) {
+                if (kg + t * kRowKG < KS) {
+                    v0 = df_add(v0, df_split(w0[t], (int)m0 - 1023));
+                    v1 = df_add(v1, df_split(w1[t], (int)m1 - 1023));
+                    v2 = df_add(v2, df_split(w2[t], (int)m2 - 1023));
+                }
+            }
+        } else {
 #pragma unroll 4
-        for (int sp = kg; sp < KS; sp += kRowKG) {
-            v0 = df_add(v0, df_split(vp[(size_t)sp * 3 * N + j], (int)m0 - 1023));
-            v1 = df_add(v1, df_split(vp[(size_t)sp * 3 * N + N + j], (int)m1 - 1023));
-            v2 = df_add(v2, df_split(vp[(size_t)sp * 3 * N + 2 * N + j], (int)m2 - 1023));
+            for (int sp = kg; sp < KS; sp += kRowKG) {
+                m0 = max(m0, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + j]) >> 20) & 0x7ffu);
+                m1 = max(m1, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + N + j]) >> 20) & 0x7ffu);
+                m2 = max(m2, ((unsigned)__double2hiint(vp[(size_t)sp * 3 * N + 2 * N + j]) >> 20) & 0x7ffu);
+            }
+#pragma unroll 4
+            for (int sp = kg; sp < KS; sp += kRowKG) {
+                v0 = df_add(v0, df_split(vp[(size_t)sp * 3 * N + j], (int)m0 - 1023));
+                v1 = df_add(v1, df_split(vp[(size_t)sp * 3 * N + N + j], (int)m1 - 1023));
+                v2 = df_add(v2, df_split(vp[(size_t)sp * 3 * N + 2 * N + j], (int)m2 - 1023));
+            }
         }
         sV[kg][0][lane] = df_widen(v0.x, (int)m0) + df_widen(v0.y, (int)m0);
         sV[kg][1][lane] = df_widen(v1.x, (int)m1) + df_widen(v1.y, (int)m1);
