@@ -120,8 +120,8 @@ __device__ __forceinline__ void store_anchors(const double s, const float2 sd, c
     const double T2 = fma(s2, s, -1.0);
     const double T3 = fma(s2, T2, -s);
     const double T4 = fma(twice(T2), T2, -1.0);
-    const float2 c4 = df_split(T4, -1);  // 2 T4
     const float2 t4 = df_split(T4, 0), t5 = df_split(fma(s2, T4, -T3), 0);
+    const float2 c4 = make_float2(2.0f * t4.x, 2.0f * t4.y);  // 2 T4 (exact scaling)
     const float2 ch = bcast2(c4.x), nch = bcast2(-c4.x), ncl = bcast2(-c4.y);
     float2 x0h = make_float2(1.0f, sd.x), x0l = make_float2(0.0f, sd.y);  // (T_0, T_1)
     float2 x1h = make_float2(t4.x, t5.x), x1l = make_float2(t4.y, t5.y);  // (T_4, T_5)
@@ -178,6 +178,7 @@ __device__ __forceinline__ void radial_factors(const TripleArgs& A, const Row& r
 // the per-triple series and the IR/UV forms, and the kernels M and Q.
 struct TripleW {
     double hQ, hM, hG, s;
+    float2 sd;  // s as a double-float pair (48 bits)
 };
 
 __device__ __forceinline__ TripleW triple_weights(const TripleArgs& A, const bool gluon, const bool ghost,
@@ -188,6 +189,7 @@ __device__ __forceinline__ TripleW triple_weights(const TripleArgs& A, const boo
     const int N = c.N;
     TripleW o;
     o.hQ = o.hM = o.hG = 0.0;
+    o.sd = make_float2(0.0f, 0.0f);
     const Ang an = A.ang[l];
     const double z = fma(f[1], an.sig, f[0]);
     const LnRcp lr = ln_rcp(z);
@@ -206,11 +208,13 @@ __device__ __forceinline__ TripleW triple_weights(const TripleArgs& A, const boo
     // beyond the range s is +-1 exactly (s of the clamped z), chosen on the integer
     // comparison (no FP64 operation)
     if (beyond) s = zb > __double_as_longlong(c.lam2) ? 1.0 : -1.0;
+    const float2 sd = df_split(s, 0);  // (also the anchors' s)
+    o.sd = sd;
     if (A.stab && !outside) {
         // from the table: the interval by arccos in FP32 (FP32 s from the bits of s,
         // truncated: the interval only; a neighbouring interval is as good), the
         // polynomials in double-float
-        const float sf = fminf(1.0f, fmaxf(-1.0f, df_split(s, 0).x));
+        const float sf = fminf(1.0f, fmaxf(-1.0f, sd.x));
         int it = (int)(acosf(sf) * ith_scale);
         it = min(max(it, 0), c.sM - 1);
         const SeriesRec* Rr = A.stab + it;
@@ -444,6 +448,7 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
         const int u = base + warp;
         TripleW w;
         w.hQ = w.hM = w.hG = w.s = 0.0;
+        w.sd = make_float2(0.0f, 0.0f);
         bool live = false;
         const int k = k0 + kk;
         if (u < nunits) {
@@ -461,7 +466,7 @@ __device__ __forceinline__ void triple_tile_full(const TripleArgs& A, const int 
             ++kk;
         }
         float4* Trow = sT + tid * rs4;
-        const float2 sd = df_split(w.s, 0);  // s as a double-float pair (48 bits)
+        const float2 sd = w.sd;  // s as a double-float pair (48 bits)
         if (live) {
             store_anchors(w.s, sd, nq, Trow + 2);
         } else {
