@@ -190,7 +190,15 @@ cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const 
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab,
                              double* coef, double rho, double* work, float* As, double2* rowinfo,
                              double* stats, int* status, cudaStream_t s, float* Xinv = nullptr,
-                             double* Sinv = nullptr, int* xstate = nullptr, int* done = nullptr);
+                             double* Sinv = nullptr, int* xstate = nullptr, int* done = nullptr,
+                             bool prescaled = false);
+// Whether launch_lu_newton scales the rows of J (n <= 128, or the FP32 LU path
+// when lu32 is set); prescaled = the rows were scaled by launch_assemble_scale.
+bool lu_scales_rows(int n, bool lu32);
+// The assembly of J and F fused with the row scaling that launch_lu_newton
+// would otherwise launch (one block per row; J, F, As, rowinfo as there).
+cudaError_t launch_assemble_scale(const Consts& c, const XTab* xtab, const double* phix, const double* D, double* J,
+                                  double* F, float* As, double2* rowinfo, int* status, cudaStream_t s);
 // Control block of a Newton iteration run as one CUDA graph (a while node whose
 // body is one Newton step followed by the decision kernel).
 struct SolveCtl {

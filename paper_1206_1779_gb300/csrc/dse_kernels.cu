@@ -860,48 +860,53 @@ __global__ void __launch_bounds__(kRowBlock) k_rowreduce_batched(const BatchProb
 //   J[NZ+i][j]   = -G(x_i)^{-1} phi_{j-NZ}(x_i) [j >= NZ] - dPi_G(x_i)/dc_j + dPi_G(x_G)/dc_j
 //   F[i]    = Z(x_i)^{-1} - Z(x_Z)^{-1} - Pi_Z(x_i) + Pi_Z(x_Z)
 //   F[NZ+i] = G(x_i)^{-1} - G(x_G)^{-1} - Pi_G(x_i) + Pi_G(x_G)
+// Entry (i, j) of J and entry i of F from the D vectors (the rows above).
+__device__ __forceinline__ double assemble_J(const Consts& c, const XTab* __restrict__ xtab,
+                                             const double* __restrict__ phix, const double* __restrict__ D,
+                                             const int i, const int j) {
+    const int N = c.N;
+    const int NZ = c.NZ;
+    const int n = c.n;
+    const size_t ld = ldD(c);
+    if (i < NZ) {
+        const double* Di = D + (size_t)i * ld;
+        const double* DZ = D + (size_t)c.Rc * ld;  // x_Z row
+        if (j < NZ) return -xtab[i].Zinv * phix[(size_t)i * N + j] - Di[j] + DZ[j];
+        return -Di[j] + DZ[j];
+    }
+    const int r = c.gofs + (i - NZ);
+    const double* Di = D + (size_t)r * ld;
+    const double* DG = D + (size_t)(c.Rc + 1) * ld;  // x_G row
+    if (j < NZ) return -Di[n + j] + DG[n + j];
+    return -xtab[r].Ginv * phix[(size_t)r * N + (j - NZ)] - Di[n + j] + DG[n + j];
+}
+
+__device__ __forceinline__ double assemble_F(const Consts& c, const XTab* __restrict__ xtab,
+                                             const double* __restrict__ D, const int i) {
+    const int n = c.n;
+    const size_t ld = ldD(c);
+    if (i < c.NZ) return xtab[i].Zinv - c.zinv_Z - D[(size_t)i * ld + 2 * n] + D[(size_t)c.Rc * ld + 2 * n];
+    const int r = c.gofs + (i - c.NZ);
+    return xtab[r].Ginv - c.ginv_G - D[(size_t)r * ld + 2 * n + 1] + D[(size_t)(c.Rc + 1) * ld + 2 * n + 1];
+}
+
 template <bool FULL>
 __device__ __forceinline__ void assemble_range(const Consts& c, const XTab* __restrict__ xtab,
                                                const double* __restrict__ phix, const double* __restrict__ D,
                                                double* __restrict__ J, double* __restrict__ F,
                                                int* __restrict__ status, const size_t first, const size_t stride) {
-    const int N = c.N;
-    const int NZ = c.NZ;
     const int n = c.n;
-    const size_t ld = ldD(c);
-    const double* DZ = D + (size_t)c.Rc * ld;        // x_Z row
-    const double* DG = D + (size_t)(c.Rc + 1) * ld;  // x_G row
     const size_t total = FULL ? (size_t)n * n : 0;
     bool bad = false;
     for (size_t e = first; e < total + n; e += stride) {
         if (e < total) {
-            const int i = (int)(e / n);
-            const int j = (int)(e % n);
-            double v;
-            if (i < NZ) {
-                const double* Di = D + (size_t)i * ld;
-                if (j < NZ) v = -xtab[i].Zinv * phix[(size_t)i * N + j] - Di[j] + DZ[j];
-                else v = -Di[j] + DZ[j];
-            } else {
-                const int r = c.gofs + (i - NZ);
-                const double* Di = D + (size_t)r * ld;
-                if (j < NZ) v = -Di[n + j] + DG[n + j];
-                else v = -xtab[r].Ginv * phix[(size_t)r * N + (j - NZ)] - Di[n + j] + DG[n + j];
-            }
+            const double v = assemble_J(c, xtab, phix, D, (int)(e / n), (int)(e % n));
             J[e] = v;
             bad |= !isfinite(v);
-        } else {
-            const int i = (int)(e - total);
-            if (F) {
-                double v;
-                if (i < NZ) v = xtab[i].Zinv - c.zinv_Z - D[(size_t)i * ld + 2 * n] + DZ[2 * n];
-                else {
-                    const int r = c.gofs + (i - NZ);
-                    v = xtab[r].Ginv - c.ginv_G - D[(size_t)r * ld + 2 * n + 1] + DG[2 * n + 1];
-                }
-                F[i] = v;
-                bad |= !isfinite(v);
-            }
+        } else if (F) {
+            const double v = assemble_F(c, xtab, D, (int)(e - total));
+            F[e - total] = v;
+            bad |= !isfinite(v);
         }
     }
     if (bad) atomicOr(status, kStatusNonfinite);
@@ -1490,6 +1495,32 @@ __global__ void __launch_bounds__(kScaleThreads) k_scale_rows(int n, const doubl
                                                               float* __restrict__ As, double2* __restrict__ rowinfo,
                                                               int* __restrict__ status) {
     scale_row(n, J, As, rowinfo, status, blockIdx.x);
+}
+
+// The assembly of row i of J (and of F[i]) followed by its scaling, one block
+// per row: the same entries as k_assemble and the same scaled row as
+// k_scale_rows (which re-reads the row this block has just written), in one
+// launch instead of two dependent ones.
+__global__ void __launch_bounds__(kScaleThreads)
+    k_assemble_scale(const Consts c, const XTab* __restrict__ xtab, const double* __restrict__ phix,
+                     const double* __restrict__ D, double* __restrict__ J, double* __restrict__ F,
+                     float* __restrict__ As, double2* __restrict__ rowinfo, int* __restrict__ status) {
+    const int n = c.n;
+    const int i = blockIdx.x;
+    bool bad = false;
+    for (int j = threadIdx.x; j < n; j += kScaleThreads) {
+        const double v = assemble_J(c, xtab, phix, D, i, j);
+        J[(size_t)i * n + j] = v;
+        bad |= !isfinite(v);
+    }
+    if (F && threadIdx.x == 0) {
+        const double v = assemble_F(c, xtab, D, i);
+        F[i] = v;
+        bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(status, kStatusNonfinite);
+    __syncthreads();  // the row's stores are visible to the whole block
+    scale_row(n, J, As, rowinfo, status, i);
 }
 
 __global__ void __launch_bounds__(kScaleThreads) k_scale_rows_batched(const BatchProblem* __restrict__ P) {
@@ -2463,14 +2494,22 @@ cudaError_t launch_assemble(bool full, const Consts& c, const XTab* xtab, const 
     return cudaGetLastError();
 }
 
+bool lu_scales_rows(int n, bool lu32) { return n <= 128 || (n > kGjMaxN && lu32 && n <= 2 * DSE_MAX_CHEB); }
+
+cudaError_t launch_assemble_scale(const Consts& c, const XTab* xtab, const double* phix, const double* D, double* J,
+                                  double* F, float* As, double2* rowinfo, int* status, cudaStream_t s) {
+    k_assemble_scale<<<c.n, kScaleThreads, 0, s>>>(c, xtab, phix, D, J, F, As, rowinfo, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
                              double* work, float* As, double2* rowinfo, double* stats, int* status, cudaStream_t s,
-                             float* Xinv, double* Sinv, int* xstate, int* done) {
+                             float* Xinv, double* Sinv, int* xstate, int* done, bool prescaled) {
     if (!Xinv || !Sinv || !xstate) Xinv = nullptr, Sinv = nullptr, xstate = nullptr;
     const int n = c.n;
     cudaError_t e = cudaSuccess;
     if (n <= 128) {
-        k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
+        if (!prescaled) k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const size_t smem = sizeof(double) * (size_t)n * reg_ldj(n) + sizeof(float) * (size_t)n * n;
@@ -2494,7 +2533,7 @@ cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const 
         k_newton_mixed<<<1, kGjThreads, smem, s>>>(c, J, F, xtab, coef, rho, work, stats, status);
     } else {
         if (done && n <= 2 * DSE_MAX_CHEB) {
-            k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
+            if (!prescaled) k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = launch_newton_lu32(c, J, As, rowinfo, F, xtab, coef, rho, stats, status, done, s);
             if (e != cudaSuccess) return e;

@@ -288,18 +288,23 @@ cudaError_t build_rows(dse_plan* pl, const double* coef, bool full, bool fp32) {
     return e;
 }
 
-// ... followed by the assembly of J (full) and F.
-int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool full, bool fp32 = false) {
+// ... followed by the assembly of J (full) and F; scale: fused with the row
+// scaling of the Newton step (plan->As, plan->rowinfo).
+int build_system(dse_plan* pl, const double* coef, double* J, double* F, bool full, bool fp32 = false,
+                 bool scale = false) {
     cudaError_t e = build_rows(pl, coef, full, fp32);
-    if (e == cudaSuccess) e = launch_assemble(full, pl->c, pl->xtab, pl->phix, pl->D, J, F, pl->status, pl->stream);
+    if (e == cudaSuccess)
+        e = full && scale ? launch_assemble_scale(pl->c, pl->xtab, pl->phix, pl->D, J, F, pl->As, pl->rowinfo,
+                                                  pl->status, pl->stream)
+                          : launch_assemble(full, pl->c, pl->xtab, pl->phix, pl->D, J, F, pl->status, pl->stream);
     return cuda_status(e);
 }
 
 // Newton matrix of the plan's precision: FP64 throughout, or (mixed) J from FP32
 // integrands followed by an FP64 residual pass that overwrites F (f64_residual).
-int build_newton(dse_plan* pl, const double* coef, double* J, double* F, bool f64_residual) {
-    if (pl->prob.precision == 0) return build_system(pl, coef, J, F, true, false);
-    int st = build_system(pl, coef, J, F, true, true);
+int build_newton(dse_plan* pl, const double* coef, double* J, double* F, bool f64_residual, bool scale = false) {
+    if (pl->prob.precision == 0) return build_system(pl, coef, J, F, true, false, scale);
+    int st = build_system(pl, coef, J, F, true, true, scale);
     if (st || !f64_residual || !F) return st;
     // the FP64 residual pass reuses the tables, writes Upart and the Pi entries of D only
     cudaError_t e = launch_triple(false, triple_args(pl, coef), pl->stream);
@@ -510,12 +515,13 @@ namespace {
 // One Newton step; in mixed precision f64_residual selects the FP64 residual
 // (otherwise F comes from the FP32 integrands as well).
 int newton_step_impl(dse_plan* plan, double* d_coeffs, double rho, double* h_stats, bool f64_residual) {
-    int st = build_newton(plan, d_coeffs, plan->J, plan->F, f64_residual);
+    const bool pre = lu_scales_rows(plan->c.n, plan->lu_done != nullptr);
+    int st = build_newton(plan, d_coeffs, plan->J, plan->F, f64_residual, pre);
     if (st) return st;
     cudaError_t e = launch_lu_newton(plan->c, plan->J, plan->F, plan->xtab, d_coeffs, rho, plan->work, plan->As,
                                      plan->rowinfo, plan->stats, plan->status, plan->stream, plan->Xinv, plan->Sinv,
-                                     plan->xstate, plan->lu_done);
-    plan->launches += plan->c.n <= 128 ? 2 : plan->c.n <= 160 ? 1 : 3;
+                                     plan->xstate, plan->lu_done, pre);
+    plan->launches += (plan->c.n <= 128 ? 2 : plan->c.n <= 160 ? 1 : 3) - (pre ? 1 : 0);
     if (e != cudaSuccess) return DSE_ERR_CUDA;
     return read_status(plan, h_stats);
 }
@@ -563,12 +569,13 @@ void build_solve_graph(dse_plan* pl) {
         ok = cudaStreamBeginCaptureToGraph(pl->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
              cudaSuccess;
         if (ok) {
-            int st = build_newton(pl, pl->coef_g, pl->J, pl->F, true);
+            const bool pre = lu_scales_rows(n, pl->lu_done != nullptr);
+            int st = build_newton(pl, pl->coef_g, pl->J, pl->F, true, pre);
             cudaError_t e = st ? cudaErrorUnknown
                                : launch_lu_newton(pl->c, pl->J, pl->F, pl->xtab, pl->coef_g, 1.0, pl->work, pl->As,
                                                   pl->rowinfo, pl->stats, pl->status, pl->cap, pl->Xinv, pl->Sinv,
-                                                  pl->xstate, pl->lu_done);
-            pl->launches += pl->c.n <= 128 ? 2 : pl->c.n <= 160 ? 1 : 3;
+                                                  pl->xstate, pl->lu_done, pre);
+            pl->launches += (n <= 128 ? 2 : n <= 160 ? 1 : 3) - (pre ? 1 : 0);
             if (e == cudaSuccess) e = launch_solve_decide(pl->ctl, pl->stats, pl->status, cond, pl->cap);
             cudaGraph_t out = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(pl->cap, &out);
