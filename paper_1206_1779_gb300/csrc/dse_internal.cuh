@@ -192,6 +192,10 @@ cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const 
                              double* stats, int* status, cudaStream_t s, float* Xinv = nullptr,
                              double* Sinv = nullptr, int* xstate = nullptr, int* done = nullptr,
                              bool prescaled = false);
+// The Newton-step kernel's set-up for n unknowns ahead of its first launch (its
+// shared-memory limit, and whether its thread-block cluster can be placed), so
+// that a graph capture of the step makes no such query.
+cudaError_t prepare_newton_step(int n);
 // Whether launch_lu_newton scales the rows of J (n <= 128, or the FP32 LU path
 // when lu32 is set); prescaled = the rows were scaled by launch_assemble_scale.
 bool lu_scales_rows(int n, bool lu32);

@@ -1557,18 +1557,172 @@ __device__ __forceinline__ unsigned key_up(double v) {
 }
 __device__ __forceinline__ double key_value(unsigned k) { return __hiloint2double((int)k, 0); }
 
+// ---- the residual over a thread-block cluster ----
+// With n > 64 the Newton-step kernel runs as a cluster of ceil(n / 16) CTAs: CTA 0
+// does the elimination and the refinement; every CTA (CTA 0 included) holds 16
+// rows of J and forms their part of each refinement sweep's FP64 residual, so that
+// the n^2 FP64 FMAs of a sweep, which on one SM take ~4.7 us at n = 128 (the FP64
+// rate of one SM), spread over up to eight SMs.  The other CTAs read x and the row
+// scales from CTA 0's shared memory and write their rows of S r and their maxima
+// keys into it (distributed shared memory).  A sweep is one round of two cluster
+// barriers: (1) CTA 0 has written x and the round's command, (2) every CTA has
+// written its rows.  CTA 0 ends with a stop command and one more round, so every
+// CTA passes the same number of cluster barriers.
+__shared__ int s_ncmd[2];  // CTA 0: 0 stop, 1 residual, 2 residual at x = 0; Sc is the kept scale
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_ctas() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every CTA of the cluster: the writes before it are visible after it
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// the address of this CTA's shared variable p in CTA rank of the cluster
+__device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double cluster_ld_f64(unsigned a) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ int cluster_ld_s32(unsigned a) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cluster_st_f32(unsigned a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_st_u32(unsigned a, unsigned v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// (J x)[row] for one of a CTA's 16 rows: eight threads per row (threads 0 .. 127,
+// part = tid mod 8) over the columns j = part + 8 t in two chains, combined over
+// the eight by shuffles (every lane of warps 0 .. 3 takes part; dot = false: 0)
+__device__ __forceinline__ double cl_row_dot(const double* __restrict__ Jr, const double* __restrict__ x, int n,
+                                             int part, bool dot) {
+    double a0 = 0.0, a1 = 0.0;
+    if (dot) {
+        int jj = part;
+#pragma unroll 2
+        for (; jj + 8 < n; jj += 16) {
+            a0 = fma(Jr[jj], x[jj], a0);
+            a1 = fma(Jr[jj + 8], x[jj + 8], a1);
+        }
+        if (jj < n) a0 = fma(Jr[jj], x[jj], a0);
+    }
+    double acc = a0 + a1;
+    acc += __shfl_xor_sync(kFullMask, acc, 1);
+    acc += __shfl_xor_sync(kFullMask, acc, 2);
+    acc += __shfl_xor_sync(kFullMask, acc, 4);
+    return acc;
+}
+
+// CTAs 1 .. of the cluster: rows 16 rank .. 16 rank + 15 of every sweep's residual
+// until CTA 0 sends the stop command.  Jl: this CTA's dynamic shared memory; the
+// other pointers are this CTA's copies of CTA 0's shared variables (the same
+// offsets in every CTA of the kernel).
+__device__ __noinline__ void newton_residual_rows(int n, int ldj, const double* __restrict__ J,
+                                                  const double* __restrict__ F, double* Jl, double* s_x,
+                                                  const double* s_scale, const double* s_sold, const float* s_rf,
+                                                  const unsigned* s_red, unsigned rank) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = 16 * (int)rank;
+    for (int rr = warp; rr < 16; rr += kGjThreads / 32) {
+        const int i = r0 + rr;
+        for (int jj = lane; jj < n; jj += 32) Jl[rr * ldj + jj] = i < n ? J[(size_t)i * n + jj] : 0.0;
+    }
+    const int row = r0 + (tid >> 3), part = tid & 7;
+    const bool head = tid < 128 && part == 0 && row < n;  // the thread that finishes its row
+    const double Fr = head ? F[row] : 0.0;
+    const unsigned a_cmd = cluster_addr(s_ncmd, 0), a_x = cluster_addr(s_x, 0);
+    const unsigned a_sc = cluster_addr(s_scale, 0), a_so = cluster_addr(s_sold, 0);
+    const unsigned a_rf = cluster_addr(s_rf, 0), a_red = cluster_addr(s_red, 0);
+    __syncthreads();
+    for (;;) {
+        cluster_barrier();  // (1)
+        const int cmd = cluster_ld_s32(a_cmd);
+        if (cmd == 0) break;
+        const int sel = cluster_ld_s32(a_cmd + 4u);
+        if (tid < n) s_x[tid] = cmd == 2 ? 0.0 : cluster_ld_f64(a_x + 8u * (unsigned)tid);
+        double sn = 0.0, sc = 0.0;
+        if (head) {
+            sn = cluster_ld_f64(a_sc + 8u * (unsigned)row);
+            sc = sel ? cluster_ld_f64(a_so + 8u * (unsigned)row) : sn;
+        }
+        __syncthreads();
+        if (tid < 128) {
+            const double acc = cl_row_dot(Jl + (tid >> 3) * ldj, s_x, n, part, cmd == 1 && row < n);
+            unsigned rk = 0u, xk = 0u;
+            if (head) {
+                const double r = Fr - acc;
+                cluster_st_f32(a_rf + 4u * (unsigned)row, (float)(sc * r));
+                const double rn = sn * r;
+                rk = isfinite(rn) ? key_up(fabs(rn)) : 0x7ff00000u;
+                xk = (unsigned)__double2hiint(fabs(s_x[row]));
+            }
+            rk = __reduce_max_sync(kFullMask, rk);
+            xk = __reduce_max_sync(kFullMask, xk);
+            if (lane == 0) {
+                const unsigned slot = 4u * rank + (unsigned)warp;
+                cluster_st_u32(a_red + 4u * slot, rk);
+                cluster_st_u32(a_red + 4u * (32u + slot), xk);
+            }
+        }
+        cluster_barrier();  // (2)
+    }
+    cluster_barrier();  // (2) of the stop round
+}
+
 __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, const float* Xs, const double* Sc,
                                            const double* Sn, const double* __restrict__ F, double* s_x, float* s_rf,
-                                           unsigned (*s_red)[16], int* s_conv, double tolfac, int maxit,
-                                           bool early_abort, int* sweeps) {
+                                           unsigned (*s_red)[32], int* s_conv, double tolfac, int maxit,
+                                           bool early_abort, int* sweeps, const bool cl) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double prev = INFINITY;  // lane 0 of warp 0 only
     int st = 0;
     for (int it = 0; it <= maxit; ++it) {
+        if (cl) {
+            // in a cluster: this CTA's rows 0 .. 15 (the other CTAs' rows meanwhile)
+            if (tid == 0) {
+                s_ncmd[0] = it > 0 ? 1 : 2;
+                s_ncmd[1] = Sc != Sn ? 1 : 0;
+            }
+            cluster_barrier();  // (1) x and the command
+            if (tid < 128) {
+                const int row = tid >> 3, part = tid & 7;
+                const double acc = cl_row_dot(Js + row * ldj, s_x, n, part, it > 0 && row < n);
+                unsigned rk = 0u, xk = 0u;
+                if (part == 0 && row < n) {
+                    const double r = F[row] - acc;
+                    s_rf[row] = (float)(Sc[row] * r);
+                    const double rn = Sn[row] * r;
+                    rk = isfinite(rn) ? key_up(fabs(rn)) : 0x7ff00000u;
+                    xk = (unsigned)__double2hiint(fabs(s_x[row]));
+                }
+                rk = __reduce_max_sync(kFullMask, rk);
+                xk = __reduce_max_sync(kFullMask, xk);
+                if (lane == 0) {
+                    s_red[0][warp] = rk;
+                    s_red[1][warp] = xk;
+                }
+            }
+            cluster_barrier();  // (2) every CTA's rows of S r and its keys
+        } else if (tid < 512) {
         // residual: four threads per row (16 warps), each over the columns
         // j = part + 4 t in two chains; the maxima of |S r| and |x| as integer keys
         // (one warp reduction each; the residual's key rounded up, x's down)
-        if (tid < 512) {
             unsigned rk = 0u, xk = 0u;
             const int row = tid >> 2, part = tid & 3;
             double acc = 0.0;
@@ -1602,9 +1756,10 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
         }
         __syncthreads();
         if (warp == 0) {
-            // the maxima over the sixteen warps, the decision by lane 0
-            const unsigned RK = __reduce_max_sync(kFullMask, lane < 16 ? s_red[0][lane] : 0u);
-            const unsigned XK = __reduce_max_sync(kFullMask, lane < 16 ? s_red[1][lane] : 0u);
+            // the maxima over the 32 slots (16 warps here, or 4 per CTA of a
+            // cluster; unused slots hold 0), the decision by lane 0
+            const unsigned RK = __reduce_max_sync(kFullMask, s_red[0][lane]);
+            const unsigned XK = __reduce_max_sync(kFullMask, s_red[1][lane]);
             if (lane == 0) {
                 const double RM = key_value(RK), XM = key_value(XK);
                 int v = 0;  // 0: continue, 1: converged, 2: give up
@@ -1758,7 +1913,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
                                                  double* __restrict__ coef, const double rho, double* __restrict__ work,
                                                  double* __restrict__ stats, int* __restrict__ status,
                                                  float* __restrict__ Xg, double* __restrict__ Sg,
-                                                 int* __restrict__ xstate, const bool xcount) {
+                                                 int* __restrict__ xstate, const bool xcount, const bool cl) {
     extern __shared__ __align__(16) double dsm[];
     __shared__ __align__(16) float s_colq[2][kColPad];
     __shared__ float s_rowk[2][128];
@@ -1772,7 +1927,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     __shared__ double s_scale[128];
     __shared__ double s_sold[128];
     __shared__ float s_rf[128];
-    __shared__ unsigned s_red[2][16];
+    __shared__ unsigned s_red[2][32];
     __shared__ int s_piv, s_fail, s_done, s_conv, s_reuse;
     __shared__ double s_anorm;
     __shared__ float s_panel[2][kGjBlock][128];                // panel rows of a round (by round parity)
@@ -1780,6 +1935,13 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
     __shared__ unsigned char s_used[128];                      // columns pivoted so far
     const int n = c.n;
     const int ldj = reg_ldj(n);
+    if (cl) {
+        const unsigned rank = cluster_rank();
+        if (rank != 0) {
+            newton_residual_rows(n, ldj, J, F, dsm, s_x, s_scale, s_sold, s_rf, &s_red[0][0], rank);
+            return;
+        }
+    }
     double* Js = dsm;                                             // [n][ldj] FP64 copy of J
     float* Xs = reinterpret_cast<float*>(dsm + (size_t)n * ldj);  // [n][n] inverse
     // G groups of R consecutive rows; G * R <= n + R - 1 < kColPad and
@@ -1820,6 +1982,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
         }
     }
     for (int i = tid; i < n; i += kGjThreads) s_scale[i] = rowinfo[i].x;
+    if (tid < 64) s_red[tid >> 5][tid & 31] = 0u;  // slots without a warp stay 0
     for (int i = n + tid; i < kColPad; i += kGjThreads) s_colq[0][i] = s_colq[1][i] = 0.0f;  // rows past n
     // J to shared memory: warp w copies rows w, w + 32, ..., its loads all in flight
     // before the stores (no integer division per element)
@@ -1890,7 +2053,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
         for (int i = tid; i < n; i += kGjThreads) s_sold[i] = Sg[i];
         __syncthreads();
         converged = refine_fp64(n, ldj, Js, Xs, s_sold, s_scale, F, s_x, s_rf, s_red, &s_conv, tolfac, kReuseMax,
-                                true, &sweeps) == 1;
+                                true, &sweeps, cl) == 1;
         if (xcount && converged && tid == 0) xstate[2] += 1;  // counter of steps that reused the inverse
         if (xcount && !converged && tid == 0) xstate[5] = xstate[4];
     }
@@ -2082,7 +2245,7 @@ __device__ __forceinline__ void newton_reg_block(const Consts& c, double* __rest
         __syncthreads();
         if (s_done == 0) {
             converged = refine_fp64(n, ldj, Js, Xs, s_scale, s_scale, F, s_x, s_rf, s_red, &s_conv, tolfac,
-                                    kRefineMax, false, &sweeps) == 1;
+                                    kRefineMax, false, &sweeps, cl) == 1;
             // keep an inverse that worked for the next Newton step
             if (Xg != nullptr) {
                 if (converged) {
@@ -2147,8 +2310,18 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, doubl
                                                            float* __restrict__ Xinv, double* __restrict__ Sinv,
                                                            int* __restrict__ xstate) {
     // a plan's xstate word is followed by its two solver counters and the two words
-    // of the reuse gate
-    newton_reg_block<R>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status, Xinv, Sinv, xstate, true);
+    // of the reuse gate; launched as a cluster (n > 64), CTA 0 solves and every CTA
+    // forms 16 rows of each residual
+    const bool cl = cluster_ctas() > 1;
+    newton_reg_block<R>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status, Xinv, Sinv, xstate, true, cl);
+    if (cl && cluster_rank() == 0) {
+        // the stop round: the other CTAs read the command, and none leaves while
+        // another may still read its shared memory
+        __syncthreads();
+        if (threadIdx.x == 0) s_ncmd[0] = 0;
+        cluster_barrier();  // (1)
+        cluster_barrier();  // (2)
+    }
 }
 
 // One block per problem of a batch; afterwards thread 0 advances the problem's
@@ -2164,7 +2337,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg_batched(BatchProblem*
     if (!B.active) return;
     const double rho = B.iter < n_relax ? rho_relax : 1.0;
     newton_reg_block<R>(B.t.c, B.J, B.As, B.rowinfo, B.F, B.xtab, coef_base + B.coef_off, rho, B.work, B.stats,
-                        B.status, B.Xinv, B.Sinv, &B.xstate, false);
+                        B.status, B.Xinv, B.Sinv, &B.xstate, false, false);
     __syncthreads();
     if (threadIdx.x == 0) {
         B.iter += 1;
@@ -2502,6 +2675,84 @@ cudaError_t launch_assemble_scale(const Consts& c, const XTab* xtab, const doubl
     return cudaGetLastError();
 }
 
+// The Newton-step kernel for n <= 128: as a cluster of ceil(n / 16) CTAs (one per
+// SM; the residual of each refinement sweep shared out by rows) when n exceeds
+// DSE_NEWTON_CLUSTER_MIN_N and this GPU can place such a cluster, else one CTA.
+#ifndef DSE_NEWTON_CLUSTER_MIN_N
+#define DSE_NEWTON_CLUSTER_MIN_N 65
+#endif
+size_t newton_reg_smem(int n) { return sizeof(double) * (size_t)n * reg_ldj(n) + sizeof(float) * (size_t)n * n; }
+int newton_reg_rows(int n) {
+    const int G = kGjThreads / n < 32 ? kGjThreads / n : 32;  // same as in the kernel
+    const int R = (n + G - 1) / G;
+    return R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : R <= 8 ? 8 : 16;
+}
+
+// The launch configuration of k_newton_reg<R> for n unknowns; whether a cluster of
+// that size can be placed is asked once per kernel and size (prepare_newton_step
+// asks it outside any graph capture) and kept.
+template <int R>
+cudaError_t newton_reg_config(int n, cudaStream_t s, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
+    static int placeable[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+    const size_t smem = newton_reg_smem(n);
+    cudaError_t e = cudaFuncSetAttribute(k_newton_reg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cfg = cudaLaunchConfig_t{};
+    cfg.blockDim = dim3(kGjThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.gridDim = dim3(1);
+    const int ncta = (n + 15) / 16;
+    if (n >= DSE_NEWTON_CLUSTER_MIN_N && ncta > 1 && ncta <= 8) {
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)ncta;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(ncta);
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (placeable[ncta] < 0) {
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_newton_reg<R>, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                nclusters = 0;
+            }
+            placeable[ncta] = nclusters > 0 ? 1 : 0;
+        }
+        if (placeable[ncta] != 1) {
+            cfg.gridDim = dim3(1);
+            cfg.attrs = nullptr;
+            cfg.numAttrs = 0;
+        }
+    }
+    return cudaSuccess;
+}
+
+template <int R>
+cudaError_t launch_newton_reg(int n, cudaStream_t s, const Consts& c, double* J, const float* As,
+                              const double2* rowinfo, const double* F, const XTab* xtab, double* coef, double rho,
+                              double* work, double* stats, int* status, float* Xinv, double* Sinv, int* xstate) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    cudaError_t e = newton_reg_config<R>(n, s, cfg, at);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k_newton_reg<R>, c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status,
+                              Xinv, Sinv, xstate);
+}
+
+cudaError_t prepare_newton_step(int n) {
+    if (n > 128) return cudaSuccess;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    switch (newton_reg_rows(n)) {
+        case 1: return newton_reg_config<1>(n, 0, cfg, at);
+        case 2: return newton_reg_config<2>(n, 0, cfg, at);
+        case 4: return newton_reg_config<4>(n, 0, cfg, at);
+        case 8: return newton_reg_config<8>(n, 0, cfg, at);
+        default: return newton_reg_config<16>(n, 0, cfg, at);
+    }
+}
+
 cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const XTab* xtab, double* coef, double rho,
                              double* work, float* As, double2* rowinfo, double* stats, int* status, cudaStream_t s,
                              float* Xinv, double* Sinv, int* xstate, int* done, bool prescaled) {
@@ -2512,20 +2763,17 @@ cudaError_t launch_lu_newton(const Consts& c, double* J, const double* F, const 
         if (!prescaled) k_scale_rows<<<n, kScaleThreads, 0, s>>>(n, J, As, rowinfo, status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const size_t smem = sizeof(double) * (size_t)n * reg_ldj(n) + sizeof(float) * (size_t)n * n;
-        const int G = kGjThreads / n < 32 ? kGjThreads / n : 32;  // same as in the kernel
-        const int R = (n + G - 1) / G;
-#define DSE_LAUNCH_REG(RR)                                                                                   \
-    e = cudaFuncSetAttribute(k_newton_reg<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
-    if (e != cudaSuccess) return e;                                                                          \
-    k_newton_reg<RR><<<1, kGjThreads, smem, s>>>(c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status, Xinv, \
-                                                 Sinv, xstate);
-        if (R <= 1) { DSE_LAUNCH_REG(1) }
-        else if (R <= 2) { DSE_LAUNCH_REG(2) }
-        else if (R <= 4) { DSE_LAUNCH_REG(4) }
-        else if (R <= 8) { DSE_LAUNCH_REG(8) }
-        else { DSE_LAUNCH_REG(16) }
+#define DSE_LAUNCH_REG(RR) \
+    e = launch_newton_reg<RR>(n, s, c, J, As, rowinfo, F, xtab, coef, rho, work, stats, status, Xinv, Sinv, xstate);
+        switch (newton_reg_rows(n)) {
+            case 1: DSE_LAUNCH_REG(1) break;
+            case 2: DSE_LAUNCH_REG(2) break;
+            case 4: DSE_LAUNCH_REG(4) break;
+            case 8: DSE_LAUNCH_REG(8) break;
+            default: DSE_LAUNCH_REG(16) break;
+        }
 #undef DSE_LAUNCH_REG
+        if (e != cudaSuccess) return e;
     } else if (n <= kGjMaxN) {
         const size_t smem = sizeof(float) * (size_t)n * 2 * n;
         e = cudaFuncSetAttribute(k_newton_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

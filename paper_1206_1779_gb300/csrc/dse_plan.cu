@@ -443,6 +443,7 @@ int dse_plan_create(const dse_problem* problem, void* cuda_stream, dse_plan** ou
         e = launch_setup_rules(pl->c, glr, gwr, gla, gwa, pl->rad, pl->ang, pl->theta, pl->xcol, pl->rows, pl->Rt,
                                pl->stream);
     if (e == cudaSuccess && table) e = launch_series_init(pl->c, pl->stq, pl->scst, pl->stab, pl->stream);
+    if (e == cudaSuccess) e = prepare_newton_step(n);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
     if (e != cudaSuccess) {
         free_plan(pl);
