@@ -1562,13 +1562,13 @@ __device__ __forceinline__ double key_value(unsigned k) { return __hiloint2doubl
 // does the elimination and the refinement; every CTA (CTA 0 included) holds 16
 // rows of J and forms their part of each refinement sweep's FP64 residual, so that
 // the n^2 FP64 FMAs of a sweep, which on one SM take ~4.7 us at n = 128 (the FP64
-// rate of one SM), spread over up to eight SMs.  The other CTAs read x and the row
-// scales from CTA 0's shared memory and write their rows of S r and their maxima
-// keys into it (distributed shared memory).  A sweep is one round of two cluster
-// barriers: (1) CTA 0 has written x and the round's command, (2) every CTA has
-// written its rows.  CTA 0 ends with a stop command and one more round, so every
-// CTA passes the same number of cluster barriers.
-__shared__ int s_ncmd[2];  // CTA 0: 0 stop, 1 residual, 2 residual at x = 0; Sc is the kept scale
+// rate of one SM), spread over up to eight SMs.  CTA 0 writes x, the round's
+// command and the row scales into the other CTAs' shared memory, and they write
+// their rows of S r and their maxima keys into CTA 0's (distributed shared memory).
+// A sweep is one round of two cluster barriers: (1) CTA 0 has written x and the
+// command, (2) every CTA has written its rows.  CTA 0 ends with a stop command and
+// one more round, so every CTA passes the same number of cluster barriers.
+__shared__ int s_ncmd[2];  // 0 stop, 1 residual, 2 residual at x = 0; Sc is the kept scale
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -1581,8 +1581,11 @@ __device__ __forceinline__ unsigned cluster_ctas() {
     return r;
 }
 // every thread of every CTA of the cluster: the writes before it are visible after it
+// (called where every thread of the block arrives; the warp is reconverged first,
+// as the aligned forms require)
 __device__ __forceinline__ void cluster_barrier() {
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 // the address of this CTA's shared variable p in CTA rank of the cluster
 __device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
@@ -1590,21 +1593,17 @@ __device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
     return r;
 }
-__device__ __forceinline__ double cluster_ld_f64(unsigned a) {
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ int cluster_ld_s32(unsigned a) {
-    int v;
-    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
 __device__ __forceinline__ void cluster_st_f32(unsigned a, float v) {
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
 __device__ __forceinline__ void cluster_st_u32(unsigned a, unsigned v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_st_f64(unsigned a, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_st_s32(unsigned a, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
 // (J x)[row] for one of a CTA's 16 rows: eight threads per row (threads 0 .. 127,
@@ -1630,11 +1629,12 @@ __device__ __forceinline__ double cl_row_dot(const double* __restrict__ Jr, cons
 }
 
 // CTAs 1 .. of the cluster: rows 16 rank .. 16 rank + 15 of every sweep's residual
-// until CTA 0 sends the stop command.  Jl: this CTA's dynamic shared memory; the
-// other pointers are this CTA's copies of CTA 0's shared variables (the same
-// offsets in every CTA of the kernel).
+// until CTA 0 sends the stop command.  Jl: this CTA's dynamic shared memory; s_x,
+// s_scale, s_sold hold what CTA 0 wrote (x, the row scales Sn and the kept ones);
+// s_rf, s_red are this CTA's copies of CTA 0's variables (the same offsets in every
+// CTA of the kernel), mapped to CTA 0's.
 __device__ __noinline__ void newton_residual_rows(int n, int ldj, const double* __restrict__ J,
-                                                  const double* __restrict__ F, double* Jl, double* s_x,
+                                                  const double* __restrict__ F, double* Jl, const double* s_x,
                                                   const double* s_scale, const double* s_sold, const float* s_rf,
                                                   const unsigned* s_red, unsigned rank) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1646,22 +1646,15 @@ __device__ __noinline__ void newton_residual_rows(int n, int ldj, const double* 
     const int row = r0 + (tid >> 3), part = tid & 7;
     const bool head = tid < 128 && part == 0 && row < n;  // the thread that finishes its row
     const double Fr = head ? F[row] : 0.0;
-    const unsigned a_cmd = cluster_addr(s_ncmd, 0), a_x = cluster_addr(s_x, 0);
-    const unsigned a_sc = cluster_addr(s_scale, 0), a_so = cluster_addr(s_sold, 0);
     const unsigned a_rf = cluster_addr(s_rf, 0), a_red = cluster_addr(s_red, 0);
     __syncthreads();
     for (;;) {
         cluster_barrier();  // (1)
-        const int cmd = cluster_ld_s32(a_cmd);
+        const int cmd = s_ncmd[0];
         if (cmd == 0) break;
-        const int sel = cluster_ld_s32(a_cmd + 4u);
-        if (tid < n) s_x[tid] = cmd == 2 ? 0.0 : cluster_ld_f64(a_x + 8u * (unsigned)tid);
-        double sn = 0.0, sc = 0.0;
-        if (head) {
-            sn = cluster_ld_f64(a_sc + 8u * (unsigned)row);
-            sc = sel ? cluster_ld_f64(a_so + 8u * (unsigned)row) : sn;
-        }
-        __syncthreads();
+        const int sel = s_ncmd[1];
+        const double sn = head ? s_scale[row] : 0.0;
+        const double sc = head ? (sel ? s_sold[row] : sn) : 0.0;
         if (tid < 128) {
             const double acc = cl_row_dot(Jl + (tid >> 3) * ldj, s_x, n, part, cmd == 1 && row < n);
             unsigned rk = 0u, xk = 0u;
@@ -1670,7 +1663,7 @@ __device__ __noinline__ void newton_residual_rows(int n, int ldj, const double* 
                 cluster_st_f32(a_rf + 4u * (unsigned)row, (float)(sc * r));
                 const double rn = sn * r;
                 rk = isfinite(rn) ? key_up(fabs(rn)) : 0x7ff00000u;
-                xk = (unsigned)__double2hiint(fabs(s_x[row]));
+                xk = cmd == 1 ? (unsigned)__double2hiint(fabs(s_x[row])) : 0u;
             }
             rk = __reduce_max_sync(kFullMask, rk);
             xk = __reduce_max_sync(kFullMask, xk);
@@ -1692,12 +1685,20 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double prev = INFINITY;  // lane 0 of warp 0 only
     int st = 0;
+    const int ncta = cl ? (int)cluster_ctas() : 1;
     for (int it = 0; it <= maxit; ++it) {
         if (cl) {
-            // in a cluster: this CTA's rows 0 .. 15 (the other CTAs' rows meanwhile)
-            if (tid == 0) {
-                s_ncmd[0] = it > 0 ? 1 : 2;
-                s_ncmd[1] = Sc != Sn ? 1 : 0;
+            // in a cluster: the command into every other CTA, at the first round the
+            // row scales of its rows (x reached them with the last update; x = 0 at
+            // the first round), then this CTA's rows 0 .. 15 (the others' meanwhile)
+            if (tid >= 1 && tid < ncta) {
+                cluster_st_s32(cluster_addr(&s_ncmd[0], (unsigned)tid), it > 0 ? 1 : 2);
+                cluster_st_s32(cluster_addr(&s_ncmd[1], (unsigned)tid), Sc != Sn ? 1 : 0);
+            }
+            if (it == 0 && tid >= 16 && tid < n && (tid >> 4) < ncta) {
+                const unsigned h = (unsigned)tid >> 4;  // the CTA that holds row tid
+                cluster_st_f64(cluster_addr(Sn + tid, h), Sn[tid]);
+                if (Sc != Sn) cluster_st_f64(cluster_addr(Sc + tid, h), Sc[tid]);
             }
             cluster_barrier();  // (1) x and the command
             if (tid < 128) {
@@ -1799,7 +1800,12 @@ __device__ __forceinline__ int refine_fp64(int n, int ldj, const double* Js, con
             acc += __shfl_xor_sync(kFullMask, acc, 4);
             acc += __shfl_xor_sync(kFullMask, acc, 2);
             acc += __shfl_xor_sync(kFullMask, acc, 1);
-            if (part == 0 && i < n) s_x[i] += (double)acc;
+            if (part == 0 && i < n) {
+                const double xn = s_x[i] + (double)acc;
+                s_x[i] = xn;
+                // (in a cluster, x of the next sweep into every other CTA)
+                for (int h = 1; h < ncta; ++h) cluster_st_f64(cluster_addr(s_x + i, (unsigned)h), xn);
+            }
         }
         __syncthreads();
     }
@@ -2318,7 +2324,7 @@ __global__ void __launch_bounds__(kGjThreads) k_newton_reg(const Consts c, doubl
         // the stop round: the other CTAs read the command, and none leaves while
         // another may still read its shared memory
         __syncthreads();
-        if (threadIdx.x == 0) s_ncmd[0] = 0;
+        if (threadIdx.x >= 1 && threadIdx.x < cluster_ctas()) cluster_st_s32(cluster_addr(&s_ncmd[0], threadIdx.x), 0);
         cluster_barrier();  // (1)
         cluster_barrier();  // (2)
     }
