@@ -54,7 +54,10 @@ CASES = {
     "n256_max": dict(n_cheb=256, n_radial=12, n_angular=10),
 }
 # a Newton step of the largest order (512 unknowns)
-CASES_NEWTON = {"n256_newton": dict(n_cheb=256, n_radial=96, n_angular=48)}
+CASES_NEWTON = {"n256_newton": dict(n_cheb=256, n_radial=96, n_angular=48),
+                # n = 73: the Newton-step kernel as a cluster of five CTAs, the last
+                # holding 9 of its 16 rows
+                "orders_40_33_cluster": dict(n_cheb=40, n_cheb_G=33, n_radial=48, n_angular=32)}
 
 
 def check_matrix(name, J, F, Jo, Fo, A, AF, p):
@@ -199,7 +202,7 @@ def test_production_size_matrix_parity(dse, oracle, inputs, name):
 
 
 @pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64", "n100", "orders_11_7", "orders_64_24",
-                                  "matrix_n128", "n256_newton"])
+                                  "matrix_n128", "n256_newton", "orders_40_33_cluster"])
 def test_newton_step_parity(dse, oracle, inputs, name):
     # n = N_Z + N_G <= 160: FP32 Gauss-Jordan inverse + FP64 refinement; larger
     # (up to 512): FP32 blocked LU + FP64 refinement (FP64 LU only as a fallback)
@@ -251,13 +254,18 @@ def step_residual_ok(J, F, d, c0, c1, tol=1e-13):
     return ratio <= 1.0, ratio
 
 
-@pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64"])
+@pytest.mark.parametrize("name", ["newton_step_n16", "full_solve_n64", "orders_40_33_cluster"])
 def test_newton_steps_with_kept_inverse(dse, inputs, name):
     # every step of a Newton iteration solves the step's own J, F to a backward-stable
     # residual: the steps that reuse the inverse kept from an earlier elimination as
-    # well as the eliminating ones, and late steps do reuse it
-    p = inputs.workload_problem(name)
+    # well as the eliminating ones, and late steps do reuse it (n = 32: one CTA;
+    # n = 128 and n = 73: the refinement residual over a cluster, whose last CTA
+    # holds fewer rows at n = 73)
+    p = inputs.workload_problem(name) if name in inputs.WORKLOADS else inputs.problem(**CASES_NEWTON[name])
     c = inputs.starting_guess(p, seed=0)
+    # (at 48 x 32 nodes the dimensionless residual's rounding floor is near 1e-11:
+    # the oracle's own iteration of that case passes 1e-11 only at its 12th step)
+    tol = 1e-10 if name == "orders_40_33_cluster" else 1e-11
     steps = 0
     with dse.Plan(p) as plan:
         ct = to_dev(c)
@@ -271,10 +279,10 @@ def test_newton_steps_with_kept_inverse(dse, inputs, name):
             ok, ratio = step_residual_ok(J, F, c0 - c1, c0, c1)
             assert ok, (steps, ratio)
             assert 1 <= sg[3] <= 24, sg  # up to 12 sweeps after an elimination, 24 with a kept inverse
-            if sg[1] < 1e-11:
+            if sg[1] < tol:
                 break
         elim, reused = plan.solver_counters()
-    assert sg[1] < 1e-11
+    assert sg[1] < tol
     assert elim + reused == steps and elim >= 1 and reused >= 1, (elim, reused, steps)
 
 
